@@ -1,0 +1,184 @@
+"""Seeded synthetic workloads: species tables, geometry and initial densities.
+
+This module only builds inputs (grids, species parameters, external
+potentials, starting densities).  It holds none of the method's arithmetic and
+is the one module that both the CUDA path's tests/benchmarks and the CPU
+oracle's tests draw inputs from.  numpy only; no torch, no CUDA.
+
+Geometry is expressed as the external potential beta*mu_ext (the paper defines
+the problem geometry through mu_ext, Sec. "Theory"): V_i(x) = +inf where the
+voxel centre x lies strictly inside the contact distance of a hard obstacle
+(distance < R_obstacle + R_i, minimum image on the periodic box), else the
+smooth potential of the workload (0 for pure hard geometry).
+
+Grid points sit at x_j = j h_d, j = 0..N_d-1; the box is [0, N_d h_d) periodic.
+Arrays are float64, shaped (S, Nz, Ny, Nx) with x fastest.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Species of the workloads: (name, radius nm, valence)
+NA = ("Na+", 0.095, 1.0)
+CL = ("Cl-", 0.181, -1.0)
+CA = ("Ca2+", 0.099, 2.0)
+O_HALF = ("O-1/2", 0.14, -0.5)
+
+
+@dataclass
+class Workload:
+    name: str
+    shape: tuple                 # (Nz, Ny, Nx)
+    h: tuple                     # (hx, hy, hz), nm
+    species: list                # names
+    radius: np.ndarray           # nm
+    z: np.ndarray                # valences
+    bulk_molar: np.ndarray       # mol/L
+    V: np.ndarray                # (S, Nz, Ny, Nx) beta*mu_ext, +inf = excluded
+    temperature_K: float = 298.15
+    eps_r: float = 78.5
+    mixing: float = None         # fixed Picard mixing, or None for line search
+    max_it: int = 50
+    tol: float = 0.0
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def nspecies(self):
+        return len(self.radius)
+
+    def initial_rho_nm3(self, per_nm3_bulk):
+        """Bulk density on accessible voxels, 0 on excluded ones (per_nm3_bulk: (S,) nm^-3)."""
+        acc = ~np.isinf(self.V)
+        return np.where(acc, np.asarray(per_nm3_bulk)[:, None, None, None], 0.0)
+
+
+def grid_coordinates(shape, h):
+    nz, ny, nx = shape
+    hx, hy, hz = h
+    x = (np.arange(nx) * hx)[None, None, :]
+    y = (np.arange(ny) * hy)[None, :, None]
+    z = (np.arange(nz) * hz)[:, None, None]
+    return z, y, x
+
+
+def _min_image(d, length):
+    return d - length * np.round(d / length)
+
+
+def sphere_exclusion(shape, h, radius_species, centres, radii):
+    """V (S, Nz, Ny, Nx): +inf where min-image distance to any centre < R_obs + R_i."""
+    zc, yc, xc = grid_coordinates(shape, h)
+    L = (shape[2] * h[0], shape[1] * h[1], shape[0] * h[2])
+    S = len(radius_species)
+    V = np.zeros((S,) + tuple(shape), dtype=np.float64)
+    for (cx, cy, cz), ro in zip(centres, radii):
+        dx = _min_image(xc - cx, L[0])
+        dy = _min_image(yc - cy, L[1])
+        dz = _min_image(zc - cz, L[2])
+        r2 = dx * dx + dy * dy + dz * dz
+        for i in range(S):
+            V[i][r2 < (ro + radius_species[i]) ** 2] = np.inf
+    return V
+
+
+def _species(table):
+    names = [t[0] for t in table]
+    radius = np.array([t[1] for t in table])
+    z = np.array([t[2] for t in table])
+    return names, radius, z
+
+
+def centred_sphere(n=32, h=0.1, molar=0.1, sphere_radius=0.5, mixing=0.1, max_it=50):
+    """Two species Na+/Cl- at `molar` each, one neutral hard sphere at the box centre."""
+    names, radius, z = _species([NA, CL])
+    shape = (n, n, n)
+    hh = (h, h, h)
+    c = n * h / 2.0
+    V = sphere_exclusion(shape, hh, radius, [(c, c, c)], [sphere_radius])
+    return Workload(name=f"nacl_sphere_{n}^3", shape=shape, h=hh, species=names, radius=radius, z=z,
+                    bulk_molar=np.array([molar, molar]), V=V, mixing=mixing, max_it=max_it,
+                    notes={"sphere_radius": sphere_radius})
+
+
+def obstacles_3species(n=128, h=0.05, n_obstacles=16, r_lo=0.3, r_hi=0.6, seed=1, tol=1e-8, max_it=2000):
+    """Na+ 0.1 M, Ca2+ 0.01 M, Cl- 0.12 M around seeded non-overlapping hard neutral spheres."""
+    names, radius, z = _species([NA, CA, CL])
+    shape = (n, n, n)
+    hh = (h, h, h)
+    L = n * h
+    rng = np.random.default_rng(seed)
+    centres, radii = [], []
+    while len(centres) < n_obstacles:
+        r = rng.uniform(r_lo, r_hi)
+        c = rng.uniform(0.0, L, size=3)
+        ok = True
+        for c2, r2 in zip(centres, radii):
+            d = _min_image(c - np.asarray(c2), L)
+            if np.sqrt(np.sum(d * d)) < r + r2:
+                ok = False
+                break
+        if ok:
+            centres.append(tuple(c))
+            radii.append(r)
+    V = sphere_exclusion(shape, hh, radius, centres, radii)
+    return Workload(name=f"3species_16obstacles_{n}^3", shape=shape, h=hh, species=names, radius=radius,
+                    z=z, bulk_molar=np.array([0.1, 0.01, 0.12]), V=V, mixing=None, max_it=max_it, tol=tol,
+                    notes={"centres": centres, "radii": radii, "seed": seed})
+
+
+def gaussian_random_field(shape, h, corr_len, std, seed):
+    """Zero-mean periodic Gaussian field with covariance ~ exp(-r^2 / (2 l^2)), scaled to `std`."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(shape)
+    kz = 2 * np.pi * np.fft.fftfreq(shape[0], d=h[2])[:, None, None]
+    ky = 2 * np.pi * np.fft.fftfreq(shape[1], d=h[1])[None, :, None]
+    kx = 2 * np.pi * np.fft.fftfreq(shape[2], d=h[0])[None, None, :]
+    filt = np.exp(-0.25 * (kx * kx + ky * ky + kz * kz) * corr_len * corr_len)
+    g = np.real(np.fft.ifftn(np.fft.fftn(white) * filt))
+    g -= g.mean()
+    return g * (std / g.std())
+
+
+def smooth_field_nacl(n=64, h=0.1, molar=0.5, corr_len=0.5, std=1.0, seed=2):
+    """NaCl with V_i = z_i g(x), g a seeded Gaussian random field (no hard exclusion)."""
+    names, radius, z = _species([NA, CL])
+    shape = (n, n, n)
+    hh = (h, h, h)
+    g = gaussian_random_field(shape, hh, corr_len, std, seed)
+    V = np.stack([zi * g for zi in z])
+    return Workload(name=f"nacl_grf_{n}^3", shape=shape, h=hh, species=names, radius=radius, z=z,
+                    bulk_molar=np.array([molar, molar]), V=V, mixing=None, max_it=200,
+                    notes={"corr_len": corr_len, "std": std, "seed": seed})
+
+
+def batch_state_points(count=64, sizes=(32, 48, 64, 96), h=0.1, c_lo=0.01, c_hi=1.0,
+                       r_lo=0.3, r_hi=1.0, seed=4, max_it=100):
+    """Seeded ragged batch of NaCl state points, each with a centred neutral hard sphere."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = int(rng.choice(sizes))
+        c = float(np.exp(rng.uniform(np.log(c_lo), np.log(c_hi))))
+        r = float(rng.uniform(r_lo, r_hi))
+        w = centred_sphere(n=n, h=h, molar=c, sphere_radius=r, mixing=None, max_it=max_it)
+        w.name = f"batch{b}_{n}^3"
+        out.append(w)
+    return out
+
+
+def fd_voxels(shape, count=64, seed=3):
+    """Seeded voxel indices (z, y, x) for finite-difference gradient checks."""
+    rng = np.random.default_rng(seed)
+    return [tuple(int(rng.integers(0, s)) for s in shape) for _ in range(count)]
+
+
+def random_density(shape, nspecies, mean, amplitude, seed):
+    """Smooth positive random densities (S, Nz, Ny, Nx) for parity tests of the convolutions."""
+    rng = np.random.default_rng(seed)
+    mean = np.asarray(mean, dtype=np.float64)
+    out = np.empty((nspecies,) + tuple(shape))
+    for i in range(nspecies):
+        g = gaussian_random_field(shape, (1.0, 1.0, 1.0), 2.0, 1.0, int(rng.integers(1 << 31)))
+        out[i] = mean[i] * (1.0 + amplitude * np.tanh(g))
+    return out

@@ -1,0 +1,83 @@
+"""Pins of the Picard/line-search solver (Sec. "Nonlinear solver") and of its fixed point
+(Sec. "Verification": homogeneity over planes parallel to a wall)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import functional as F, picard
+from paper_0910_1531_gb300 import workloads
+
+
+def test_quadratic_alpha_recovers_parabola_minimum():
+    f = lambda a: 3.0 * (a - 0.37) ** 2 + 0.1
+    assert picard.quadratic_alpha(f(0), f(0.5), f(1.0), 1.0) == pytest.approx(0.37, rel=1e-14)
+    g = lambda a: 2.0 * (a - 0.11) ** 2 + 0.5
+    assert picard.quadratic_alpha(g(0), g(0.2), g(0.4), 0.4) == pytest.approx(0.11, rel=1e-14)
+    # vertex beyond alpha_max -> alpha_max; vertex below the floor -> floor
+    h = lambda a: (a - 3.0) ** 2
+    assert picard.quadratic_alpha(h(0), h(0.5), h(1.0), 1.0) == 1.0
+    k = lambda a: (a + 1.0) ** 2
+    assert picard.quadratic_alpha(k(0), k(0.5), k(1.0), 1.0) == pytest.approx(1e-3)
+    # concave: the better non-zero sample
+    c = lambda a: -(a - 0.2) ** 2
+    assert picard.quadratic_alpha(c(0), c(0.5), c(1.0), 1.0) == 1.0
+
+
+def test_alpha_bound_is_the_printed_n3_bound():
+    assert picard.alpha_bound(0.3, 0.2) == 1.0
+    assert picard.alpha_bound(0.3, 0.6) == 1.0
+    assert picard.alpha_bound(0.5, 1.3) == pytest.approx(0.5)
+    # a step with alpha_max keeps (1 - a) M0 + a M1 at the bound
+    a = picard.alpha_bound(0.45, 0.95)
+    assert (1 - a) * 0.45 + a * 0.95 == pytest.approx(0.9)
+
+
+def test_fixed_mixing_step():
+    w = workloads.centred_sphere(n=8, h=0.1, molar=0.1, sphere_radius=0.2)
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    rho0 = w.initial_rho_nm3(prob.bath.rho)
+    g = F.picard_map(prob, rho0, w.V)
+    rho1, info = picard.picard_step(prob, rho0, w.V, mixing=0.1)
+    assert info["alpha"] == 0.1
+    assert np.allclose(rho1, 0.9 * rho0 + 0.1 * g, rtol=1e-15)
+
+
+def _wall_problem(molar=1.0):
+    # Hard uncharged wall at z = 0 (zero thickness): a centre is excluded within R_i of the wall plane.
+    shape, h = (32, 4, 4), (0.1, 0.1, 0.025)
+    radius, z = np.array([0.1, 0.2125]), np.array([1.0, -1.0])
+    prob = F.Problem(shape, h, radius, z, [molar, molar])
+    zc = np.arange(shape[0]) * h[2]
+    L = shape[0] * h[2]
+    dist = np.minimum(zc, L - zc)
+    V = np.zeros((2,) + shape)
+    for i in range(2):
+        V[i][dist < radius[i]] = np.inf
+    return prob, V
+
+
+def test_planar_wall_solution_is_homogeneous_over_planes():
+    prob, V = _wall_problem()
+    rho = np.where(np.isinf(V), 0.0, prob.bath.rho[:, None, None, None])
+    rho, it, r = picard.solve(prob, rho, V, tol=0.0, max_it=15)
+    plane_spread = np.max(np.ptp(rho, axis=(2, 3)))
+    assert plane_spread < 1e-12 * np.max(rho)
+    assert r < 1e-2   # the iteration makes progress from the bulk start
+
+
+def test_line_search_converges_to_fixed_point():
+    w = workloads.centred_sphere(n=12, h=0.1, molar=0.5, sphere_radius=0.25)
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    rho, it, r = picard.solve(prob, rho, w.V, tol=1e-10, max_it=200)
+    assert r < 1e-10
+    g = F.picard_map(prob, rho, w.V)
+    acc = ~np.isinf(w.V)
+    assert np.max(np.abs(rho - g)[acc] / prob.bath.rho[np.nonzero(acc)[0]]) < 1e-8
+    # a sphere centred on a grid point of a cubic grid: the solution is symmetric under axis swaps
+    assert np.allclose(rho, np.swapaxes(rho, 1, 3), rtol=1e-9, atol=1e-14)
+    assert np.allclose(rho, np.swapaxes(rho, 2, 3), rtol=1e-9, atol=1e-14)
+    # and the gradient of Omega vanishes there
+    grad = F.grad_omega_rho(prob, rho, w.V)
+    assert np.max(np.abs(grad)) < 1e-8 * prob.dv
