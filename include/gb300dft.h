@@ -1,0 +1,186 @@
+/*
+ * gb300dft.h -- C ABI of the GB300 (sm_103a) FFT/Picard classical-DFT library.
+ *
+ * The library evaluates, on one GPU, the hot path of the 3D density functional
+ * solver for charged hard spheres of Knepley, Karpeev, Davidovits, Eisenberg
+ * and Gillespie (arXiv:0910.1531): the FFT convolutions of one Picard
+ * residual evaluation (Sec. "Hard Sphere Interaction", Sec. "Electrostatics",
+ * App. B) and the Picard iteration with line search around them
+ * (Sec. "Discretization and Solution in Equilibrium").
+ *
+ * Conventions for every entry point below:
+ *  - Units: lengths nm, energies kT, number densities nm^-3, concentrations
+ *    mol/L.  V (the external potential beta*mu_ext, which defines the
+ *    geometry, Sec. "Theory") is in kT; +inf marks hard exclusion.
+ *  - Fields are caller-owned DEVICE memory, contiguous, x fastest:
+ *    a species field set is [S][nz][ny][nx]; the ten weighted densities are
+ *    [10][nz][ny][nx] in the order n0, n1, n2, n3, nV1x, nV1y, nV1z, nV2x,
+ *    nV2y, nV2z.  The element type is float for DFT_FP32_STAB plans and
+ *    double for DFT_FP64 plans.  Pointers must be 16-byte aligned.
+ *  - All work is issued on the plan's CUDA stream, in stream order.  Calls
+ *    that return host scalars (resid_out, alpha_out, iters_out, omega_out,
+ *    ...) synchronise that stream before returning; the others return as soon
+ *    as the work is queued.
+ *  - The plan owns its scratch memory (allocated at create, freed at
+ *    destroy) and never frees caller memory.  A plan is not thread-safe; use
+ *    one plan per host thread.
+ *  - Every call returns a dft_status and never aborts or throws.  On error
+ *    dft_last_error() gives a one-line description.
+ */
+#ifndef GB300DFT_H
+#define GB300DFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dft_plan dft_plan;
+
+typedef enum {
+    DFT_OK = 0,
+    DFT_EINVAL = -1,       /* bad argument (sizes, radii, NULL pointer, ...) */
+    DFT_ENONNEUTRAL = -2,  /* bath is not electroneutral */
+    DFT_ENOMEM = -3,       /* device allocation failed */
+    DFT_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    DFT_EN3BOUND = -5,     /* local packing fraction n3 >= 1 somewhere (log(1-n3) undefined) */
+    DFT_ENONFINITE = -6,   /* NaN or Inf appeared in a density */
+    DFT_ENOCONV = -7,      /* dft_solve reached max_it without reaching tol */
+    DFT_ETIMEOUT = -8      /* reserved: a bounded device-side wait gave up */
+} dft_status;
+
+enum { DFT_FP32_STAB = 0, DFT_FP64 = 1 };
+enum { DFT_MAX_SPECIES = 5 };
+
+typedef struct {
+    int nx, ny, nz;                 /* grid points per axis; each 2^a 3^b, 4 <= n <= 512 */
+    double hx, hy, hz;              /* spacing (nm); periodic box L_d = n_d h_d */
+    int nspecies;                   /* 1 .. DFT_MAX_SPECIES */
+    const double* radius_nm;        /* [nspecies] hard-sphere radii R_i > 0 */
+    const double* valence;          /* [nspecies] z_i */
+    const double* bulk_molar;       /* [nspecies] bath concentrations (mol/L) >= 0 */
+    double temperature_K;           /* T > 0 */
+    double eps_r;                   /* relative permittivity > 0 */
+    int precision;                  /* DFT_FP32_STAB or DFT_FP64 */
+} dft_params;
+
+/*
+ * Create a plan: checks the parameters, computes the bath thermodynamics of
+ * App. A (Percus-Yevick mu^HS and P, MSA Gamma, eta, Omega and mu^ES; Gamma
+ * by Newton's method as in App. A), builds the FFT plans of each axis and
+ * allocates scratch on the current CUDA device.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Rejects (DFT_EINVAL) sizes outside the supported set, R <= 0, negative
+ * concentrations, a bath packing fraction >= 0.9; rejects a bath with
+ * |sum z_i c_i| > 1e-12 sum |z_i| c_i (DFT_ENONNEUTRAL).
+ * On success *out owns device memory until dft_plan_destroy.
+ */
+dft_status dft_plan_create(const dft_params* params, void* cuda_stream, dft_plan** out);
+
+/* Free the plan and its scratch (synchronises the plan's stream). NULL is a no-op. */
+dft_status dft_plan_destroy(dft_plan* plan);
+
+/* One-line description of the last error on this plan (or of the last failed create if plan is NULL). */
+const char* dft_last_error(const dft_plan* plan);
+
+/*
+ * Bath values computed at create (App. A), all host arrays of length nspecies
+ * except the scalars; any pointer may be NULL.  rho_bulk in nm^-3, mu_* in kT,
+ * gamma in nm^-1, beta_p in nm^-3, lambda_b the Bjerrum length in nm.
+ */
+dft_status dft_plan_bulk(const dft_plan* plan, double* rho_bulk, double* mu_hs, double* mu_es,
+                         double* gamma, double* beta_p, double* lambda_b);
+
+/*
+ * Weighted densities n_alpha(x) = sum_i int rho_i(x') w_i^alpha(x' - x) d^3x'
+ * (eq. nDef) by the convolution theorem (eq. conv) with the analytic weight
+ * transforms of App. B.  rho: [S][N] device, n_out: [10][N] device.
+ */
+dft_status dft_weighted_densities(dft_plan* plan, const void* rho, void* n_out);
+
+/*
+ * Hard-sphere one-body direct correlation c1_hs_i(x) = -beta mu^HS_i(x):
+ * the back-convolution of the ten dPhi/dn_alpha of eq. Phi with the weights
+ * (eq. muHS), with the |nV2| <= n2 bound of Sec. "Numerical Stability".
+ * rho: [S][N], c1_out: [S][N] device.
+ */
+dft_status dft_c1_hs(dft_plan* plan, const void* rho, void* c1_out);
+
+/*
+ * Electrostatic part c1_es_i(x) = -(beta mu^SC_i(x) + z_i psi(x)) with the
+ * bulk-fluid screening term of eq. muESexpansion (kernel eq. CplusPsiFunc,
+ * transform eq. CplusPsiHat with the prefactor read as 2 pi lambda_B z_i z_j / k)
+ * and the mean-field potential psi = e phi / kT of eq. potentialSolution
+ * (psi_hat(0) = 0, eq. potentialConstraint).
+ * rho: [S][N]; c1_out: [S][N]; psi_out: [N] or NULL.
+ */
+dft_status dft_c1_es(dft_plan* plan, const void* rho, void* c1_out, void* psi_out);
+
+/*
+ * The Picard map G of eq. rhoEquation:
+ * G_i(x) = rho_bath_i exp(beta mu^ex,bath_i - V_i(x) - beta mu^ex_i(x)), 0 where V_i = +inf.
+ * rho, V: [S][N]; g_out: [S][N] device.  resid_out (may be NULL) receives
+ * r = sqrt(sum_i sum_x ((rho_i - G_i)/rho_bath_i)^2 / (S N)).
+ */
+dft_status dft_picard_map(dft_plan* plan, const void* rho, const void* V, void* g_out, double* resid_out);
+
+/*
+ * One Picard iteration (eq. picard) with the line search of Sec. "Nonlinear
+ * solver": rho <- (1 - alpha) rho + alpha G(rho).  alpha_or_neg >= 0 gives
+ * fixed mixing alpha = min(alpha_or_neg, alpha_max); a negative value selects
+ * the quadratic line search on r^2 sampled at alpha_max/2 and alpha_max.
+ * alpha_max = min(1, (0.9 - max n3(rho)) / (max n3(G) - max n3(rho))) when
+ * max n3(G) > max n3(rho), else 1.  rho_inout: [S][N] device, updated in place.
+ * resid_out receives r(rho) before the update, alpha_out the alpha used (either may be NULL).
+ */
+dft_status dft_picard_step(dft_plan* plan, void* rho_inout, const void* V, double alpha_or_neg,
+                           double* resid_out, double* alpha_out);
+
+/*
+ * Iterate dft_picard_step until r(rho) < tol or max_it iterations.  Returns
+ * DFT_ENOCONV (with rho holding the last iterate) if tol was not reached.
+ * iters_out: iterations taken; resid_out: r of the returned rho.
+ */
+dft_status dft_solve(dft_plan* plan, void* rho_inout, const void* V, double alpha_or_neg, double tol,
+                     int max_it, int* iters_out, double* resid_out);
+
+/*
+ * Stateful iteration for callers that drive the loop themselves (and for
+ * timing): dft_iter_begin evaluates G(rho) and keeps it, with the weighted
+ * densities of rho, inside the plan; each dft_iter_step then performs one
+ * Picard iteration on rho_inout exactly as dft_picard_step does, reusing the
+ * kept state (no re-evaluation of G(rho)).  rho_inout and V must be the same
+ * buffers, unmodified by the caller, between begin and the steps.
+ * resid_out/alpha_out: as dft_picard_step; NULL skips the synchronisation.
+ */
+dft_status dft_iter_begin(dft_plan* plan, void* rho_inout, const void* V);
+dft_status dft_iter_step(dft_plan* plan, void* rho_inout, const void* V, double alpha_or_neg,
+                         double* resid_out, double* alpha_out);
+
+/*
+ * End-to-end convenience for host buffers: copies rho (and V) from HOST
+ * memory to the plan's device scratch, performs one dft_picard_step, and
+ * copies the updated rho back to HOST memory.  rho_host: [S][N], V_host:
+ * [S][N], element type as the plan's precision.  Synchronous.
+ */
+dft_status dft_picard_step_host(dft_plan* plan, void* rho_host, const void* V_host, double alpha_or_neg,
+                                double* resid_out, double* alpha_out);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the plan's stream around
+ * each launch.  enable != 0 starts collection (and clears totals).
+ * dft_profile_read returns, for the kernel kind named by `name`, the number
+ * of launches and their total duration (ms) since the last enable; it
+ * synchronises the stream.  Names: "xfwd", "yfft", "zconv_fwd", "xphi",
+ * "zconv_bwd", "xupdate", "xinv", "finalize".
+ */
+dft_status dft_profile_enable(dft_plan* plan, int enable);
+dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, double* total_ms);
+
+/* Library version string. */
+const char* dft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300DFT_H */

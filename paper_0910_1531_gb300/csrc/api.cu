@@ -1,0 +1,704 @@
+// C ABI of the GB300 classical-DFT library: plan creation, the FFT/Picard entry points
+// and per-kernel profiling.  All device work is queued on the plan's stream; the
+// Picard iteration keeps its scalars (mixing weights, residuals, alpha) in a device
+// control block so an iteration needs no host round trip.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bulk.h"
+#include "gb300dft.h"
+#include "passes.h"
+
+namespace {
+
+enum Kind { K_XFWD, K_YFFT, K_ZFWD, K_XPHI, K_ZBWD, K_XUPD, K_XINV, K_FIN, K_COUNT };
+const char* kKindNames[K_COUNT] = {"xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize"};
+
+constexpr double kN3Bound = 0.9;       // Sec. "Nonlinear solver"
+constexpr double kAlphaFloor = 1e-3;   // lower clamp of the parabola minimiser, in units of alpha_max
+
+std::string g_create_error;
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct dft_plan {
+    int S = 0;
+    int precision = DFT_FP32_STAB;
+    std::vector<double> R, z, molar;
+    double T = 0, eps_r = 0;
+    BathState bath;
+    GridDesc g{};
+    AxisPlan ax{}, ay{}, az{};
+    double kf[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t csize = 0, rsize = 0;
+    void* tw[3] = {nullptr, nullptr, nullptr};
+    void* T1 = nullptr;
+    void* slotA = nullptr;
+    void* slotB = nullptr;
+    void* gbuf = nullptr;
+    void* stage_rho = nullptr;
+    void* stage_V = nullptr;
+    double* red_sum = nullptr;
+    float* red_max = nullptr;
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;
+    int Ty = 1, Tz = 1, LX = 1, LRphi = 1, LRupd = 1, LRn3 = 1, LR10 = 1;
+    SpeciesDesc<float> spf{};
+    SpeciesDesc<double> spd{};
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> evpool;
+    size_t ev_used = 0;
+    int prof_launches[K_COUNT] = {0};
+    double prof_ms[K_COUNT] = {0};
+    std::string err;
+    bool iter_ready = false;
+    const void* iter_rho = nullptr;
+    const void* iter_V = nullptr;
+
+    long long blocks_x(int LR) const { return ceil_div((long long)g.ny * g.nz, LR); }
+};
+
+namespace {
+
+dft_status fail(dft_plan* p, dft_status code, const std::string& msg) {
+    if (p) p->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+bool radix_plan(int n, AxisPlan* out) {
+    out->n = n;
+    out->nstages = 0;
+    int m = n;
+    while (m % 3 == 0) { out->radix[out->nstages++] = 3; m /= 3; }
+    while (m >= 16 && m % 16 == 0) { out->radix[out->nstages++] = 16; m /= 16; }
+    if (m == 2 || m == 4 || m == 8) { out->radix[out->nstages++] = m; m = 1; }
+    return m == 1 && out->nstages <= DFT_MAXSTAGES && out->nstages > 0;
+}
+
+bool valid_n(int n) {
+    if (n < 4 || n > 512) return false;
+    int m = n;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+int pick_tile(int n, size_t csize, int nbuf, size_t budget) {
+    for (int T = 16; T >= 1; T /= 2)
+        if ((size_t(n) + size_t(nbuf) * T * n) * csize + 16 <= budget) return T;
+    return 1;
+}
+
+int pick_lines(int nx, size_t csize, int lines_per_unit, size_t budget, int cap) {
+    const long long avail = (long long)(budget / csize) - nx;
+    long long L = avail / (2LL * (nx + 1) * lines_per_unit);
+    if (L < 1) L = 1;
+    if (L > cap) L = cap;
+    return (int)L;
+}
+
+template <typename Real> SpeciesDesc<Real>& species(dft_plan* p);
+template <> SpeciesDesc<float>& species<float>(dft_plan* p) { return p->spf; }
+template <> SpeciesDesc<double>& species<double>(dft_plan* p) { return p->spd; }
+
+template <typename Real> void fill_species(dft_plan* p) {
+    SpeciesDesc<Real>& sp = species<Real>(p);
+    memset(&sp, 0, sizeof(sp));
+    const BathState& b = p->bath;
+    const double pi = 3.14159265358979323846;
+    sp.S = p->S;
+    for (int i = 0; i < p->S; ++i) {
+        sp.R[i] = Real(p->R[i]);
+        sp.z[i] = Real(p->z[i]);
+        sp.rho_b[i] = Real(b.rho[i]);
+        sp.inv_rho_b[i] = b.rho[i] > 0 ? Real(1.0 / b.rho[i]) : Real(0);
+        sp.mu_hs_b[i] = Real(b.mu_hs[i]);
+        sp.n_rho_b[i] = Real(double(p->g.n) * b.rho[i]);
+    }
+    for (int i = 0; i < p->S; ++i)
+        for (int j = 0; j < p->S; ++j) {
+            const double li = b.lam[i], lj = b.lam[j];
+            sp.es_pref[i][j] = Real(0.5 * b.lb * p->z[i] * p->z[j]);
+            if (b.gamma > 0.0) {
+                sp.es_a[i][j] = Real(1.0 / (2.0 * li * lj));
+                sp.es_b[i][j] = Real((li + lj) / (li * lj));
+                sp.es_c[i][j] = Real((li - lj) * (li - lj) / (2.0 * li * lj) + 2.0);
+            } else {   // Gamma = 0: l -> infinity leaves the Coulomb term 2/r
+                sp.es_a[i][j] = Real(0);
+                sp.es_b[i][j] = Real(0);
+                sp.es_c[i][j] = Real(2);
+            }
+            sp.es_R[i][j] = Real(p->R[i] + p->R[j]);
+            sp.pois[i][j] = Real(4.0 * pi * b.lb * p->z[i] * p->z[j]);
+        }
+    sp.inv_n = Real(1.0 / double(p->g.n));
+    sp.coulomb_limit = b.gamma > 0.0 ? 0 : 1;
+}
+
+template <typename C> void fill_twiddles(int n, std::vector<C>* out) {
+    out->resize(n);
+    const double two_pi = 6.28318530717958647692;
+    for (int m = 0; m < n; ++m) {
+        const double a = -two_pi * double(m) / double(n);
+        (*out)[m].x = decltype(C().x)(std::cos(a));
+        (*out)[m].y = decltype(C().x)(std::sin(a));
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// profiling helpers
+// --------------------------------------------------------------------------------------
+cudaEvent_t take_event(dft_plan* p) {
+    if (p->ev_used == p->evpool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        p->evpool.push_back(e);
+    }
+    return p->evpool[p->ev_used++];
+}
+
+struct Prof {
+    dft_plan* p;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Prof(dft_plan* pp, int k) : p(pp), kind(k) {
+        if (p->prof) {
+            a = take_event(p);
+            cudaEventRecord(a, p->stream);
+        }
+    }
+    ~Prof() {
+        if (p->prof) {
+            cudaEvent_t b = take_event(p);
+            cudaEventRecord(b, p->stream);
+            p->recs.push_back({kind, a, b});
+        }
+    }
+};
+
+void collect_profile(dft_plan* p) {
+    if (p->recs.empty()) return;
+    cudaStreamSynchronize(p->stream);
+    for (const ProfRec& r : p->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            p->prof_launches[r.kind] += 1;
+            p->prof_ms[r.kind] += ms;
+        }
+    }
+    p->recs.clear();
+    p->ev_used = 0;
+}
+
+#define LAUNCH(p, kind, call)                                                                 \
+    do {                                                                                      \
+        {                                                                                     \
+            Prof _pr((p), (kind));                                                            \
+            call;                                                                             \
+        }                                                                                     \
+        cudaError_t _e = cudaGetLastError();                                                  \
+        if (_e != cudaSuccess)                                                                \
+            return fail((p), DFT_ECUDA, std::string(kKindNames[kind]) + ": " + cudaGetErrorString(_e)); \
+        if ((p)->prof && (p)->recs.size() > 4096) collect_profile(p);                         \
+    } while (0)
+
+// --------------------------------------------------------------------------------------
+// sequences
+// --------------------------------------------------------------------------------------
+template <typename Real> struct Ops {
+    using C = typename Cplx<Real>::type;
+    using P = Passes<Real>;
+
+    static const C* tw(dft_plan* p, int a) { return static_cast<const C*>(p->tw[a]); }
+    static C* T1(dft_plan* p) { return static_cast<C*>(p->T1); }
+    static C* slot_n(void* s) { return static_cast<C*>(s); }
+    static C* slot_es(dft_plan* p, void* s) { return static_cast<C*>(s) + DFT_NCOMP * p->g.nc; }
+    static Real kf(dft_plan* p, int a) { return Real(p->kf[a]); }
+
+    // rho (S real fields) -> slot: ten weighted densities (kx, ky, z) and the S (+psi)
+    // bulk-fluid / Poisson spectra (kx, ky, kz)
+    static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi) {
+        const SpeciesDesc<Real>& sp = species<Real>(p);
+        LAUNCH(p, K_XFWD, P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
+        LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_ZFWD, P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
+                                       T1(p), slot_n(slot), slot_es(p, slot), tw(p, 2)));
+        LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), tw(p, 1)));
+        return DFT_OK;
+    }
+
+    // weighted densities mixed from slot A (and slot B) -> G at rho = w0 rho0 + w1 rho1
+    static dft_status second_half(dft_plan* p, bool use_B, bool materialise, const Real* rho0, const Real* rho1,
+                                  const Real* V, Real* rho_out, Real* g_out) {
+        const SpeciesDesc<Real>& sp = species<Real>(p);
+        C* A = slot_n(p->slotA);
+        C* B = use_B ? slot_n(p->slotB) : nullptr;
+        C* esA = slot_es(p, p->slotA);
+        C* esB = use_B ? slot_es(p, p->slotB) : nullptr;
+        LAUNCH(p, K_XPHI, P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
+                                  p->red_max, &p->ctl->status, tw(p, 0)));
+        LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), tw(p, 1)));
+        LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
+                                       p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
+        LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_XUPD, P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
+                                     g_out, p->red_sum, &p->ctl->status, tw(p, 0)));
+        return DFT_OK;
+    }
+
+    static dft_status xinv(dft_plan* p, int ncomp, const C* spec, Real* out, Real* out_last, const double* offs,
+                           int cmax, float* red_max, int* blocks_out) {
+        const int lpr = (ncomp + 1) / 2;
+        const int LR = pick_lines(p->g.nx, sizeof(C), lpr, 48 * 1024, 16);
+        Offsets<Real> off;
+        for (int c = 0; c < DFT_NCOMP + 2; ++c) off.v[c] = Real(0);
+        if (offs)
+            for (int c = 0; c < ncomp; ++c) off.v[c] = Real(offs[c]);
+        LAUNCH(p, K_XINV, P::xinv(p->stream, p->g, p->ax, LR, ncomp, spec, out, out_last, off, cmax, red_max,
+                                  tw(p, 0)));
+        if (blocks_out) *blocks_out = (int)p->blocks_x(LR);
+        return DFT_OK;
+    }
+};
+
+dft_status finalize(dft_plan* p, int op, int nsum, int nmax, double alpha_fixed) {
+    const double inv_count = 1.0 / (double(p->S) * double(p->g.n));
+    LAUNCH(p, K_FIN, launch_finalize(p->stream, p->ctl, p->red_sum, nsum, p->red_max, nmax, op, inv_count,
+                                     alpha_fixed, kN3Bound, kAlphaFloor));
+    return DFT_OK;
+}
+
+dft_status read_ctl(dft_plan* p) {
+    cudaError_t e = cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("reading control block: ") + cudaGetErrorString(e));
+    if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
+    if (p->ctl_host->status & DEV_NONFINITE) return fail(p, DFT_ENONFINITE, "non-finite density or residual met");
+    return DFT_OK;
+}
+
+dft_status reset_status(dft_plan* p) {
+    cudaError_t e = cudaMemsetAsync(&p->ctl->status, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
+    return DFT_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        dft_status _s = (x);          \
+        if (_s != DFT_OK) return _s;  \
+    } while (0)
+
+template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const Real* V) {
+    using O = Ops<Real>;
+    TRY(reset_status(p));
+    TRY(O::first_half(p, rho, p->slotA, 0));
+    TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, static_cast<Real*>(p->gbuf)));
+    TRY(finalize(p, FIN_F0 | FIN_N3CUR, (int)p->blocks_x(p->LRupd), (int)p->blocks_x(p->LRphi), -1.0));
+    p->iter_ready = true;
+    p->iter_rho = rho;
+    p->iter_V = V;
+    return DFT_OK;
+}
+
+template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Real* V, double alpha) {
+    using O = Ops<Real>;
+    using C = typename Cplx<Real>::type;
+    Real* g = static_cast<Real*>(p->gbuf);
+    TRY(O::first_half(p, g, p->slotB, 0));
+    int nb = 0;
+    TRY(O::xinv(p, 1, O::slot_n(p->slotB) + 3 * p->g.nc, nullptr, nullptr, nullptr, 0, p->red_max, &nb));
+    TRY(finalize(p, FIN_AMAX, 0, nb, alpha));
+    const int nsum = (int)p->blocks_x(p->LRupd);
+    if (alpha < 0.0) {
+        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr));
+        TRY(finalize(p, FIN_F1, nsum, 0, alpha));
+        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr));
+        TRY(finalize(p, FIN_F2_CHOOSE, nsum, 0, alpha));
+    }
+    TRY(O::second_half(p, true, true, rho, g, V, rho, g));
+    TRY(finalize(p, FIN_ACCEPT, nsum, (int)p->blocks_x(p->LRphi), alpha));
+    (void)sizeof(C);
+    return DFT_OK;
+}
+
+dft_status check_plan(dft_plan* p) {
+    if (!p) return fail(nullptr, DFT_EINVAL, "NULL plan");
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return DFT_OK;
+}
+
+bool is_fp64(const dft_plan* p) { return p->precision == DFT_FP64; }
+
+template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* c1) {
+    using O = Ops<Real>;
+    using P = Passes<Real>;
+    const SpeciesDesc<Real>& sp = species<Real>(p);
+    TRY(O::first_half(p, rho, p->slotA, 0));
+    TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    LAUNCH(p, K_XPHI, P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
+                              O::T1(p), p->red_max, &p->ctl->status, O::tw(p, 0)));
+    LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
+                                   p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
+    LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), O::tw(p, 1)));
+    TRY(O::xinv(p, p->S, O::T1(p), c1, nullptr, nullptr, -1, nullptr, nullptr));
+    return DFT_OK;
+}
+
+template <typename Real> dft_status c1_es_t(dft_plan* p, const Real* rho, Real* c1, Real* psi) {
+    using O = Ops<Real>;
+    using P = Passes<Real>;
+    const SpeciesDesc<Real>& sp = species<Real>(p);
+    const int want_psi = psi ? 1 : 0;
+    const int nout = p->S + want_psi;
+    TRY(O::first_half(p, rho, p->slotA, want_psi));
+    TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 2, nout,
+                                   p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
+    LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), O::tw(p, 1)));
+    double offs[DFT_NCOMP + 2] = {0};
+    for (int s = 0; s < p->S; ++s) offs[s] = -p->bath.mu_es[s];
+    TRY(O::xinv(p, nout, O::T1(p), c1, psi, offs, -1, nullptr, nullptr));
+    return DFT_OK;
+}
+
+template <typename Real> dft_status picard_map_t(dft_plan* p, const Real* rho, const Real* V, Real* g) {
+    using O = Ops<Real>;
+    TRY(reset_status(p));
+    TRY(O::first_half(p, rho, p->slotA, 0));
+    TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, g));
+    TRY(finalize(p, FIN_F0 | FIN_N3CUR, (int)p->blocks_x(p->LRupd), (int)p->blocks_x(p->LRphi), -1.0));
+    return DFT_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+const char* dft_version(void) { return "gb300dft 0.1 (sm_103a)"; }
+
+const char* dft_last_error(const dft_plan* plan) {
+    return plan ? plan->err.c_str() : g_create_error.c_str();
+}
+
+dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** out) {
+    if (!prm || !out) return fail(nullptr, DFT_EINVAL, "NULL params or out");
+    *out = nullptr;
+    if (!valid_n(prm->nx) || !valid_n(prm->ny) || !valid_n(prm->nz))
+        return fail(nullptr, DFT_EINVAL, "grid sizes must be 2^a 3^b with 4 <= n <= 512");
+    if (!(prm->hx > 0 && prm->hy > 0 && prm->hz > 0)) return fail(nullptr, DFT_EINVAL, "grid spacing must be > 0");
+    if (prm->nspecies < 1 || prm->nspecies > DFT_MAX_SPECIES) return fail(nullptr, DFT_EINVAL, "nspecies out of range");
+    if (!prm->radius_nm || !prm->valence || !prm->bulk_molar) return fail(nullptr, DFT_EINVAL, "NULL species array");
+    if (!(prm->temperature_K > 0 && prm->eps_r > 0)) return fail(nullptr, DFT_EINVAL, "T and eps_r must be > 0");
+    if (prm->precision != DFT_FP32_STAB && prm->precision != DFT_FP64)
+        return fail(nullptr, DFT_EINVAL, "unknown precision");
+    const int S = prm->nspecies;
+    double charge = 0.0, scale = 0.0, eta = 0.0;
+    for (int i = 0; i < S; ++i) {
+        if (!(prm->radius_nm[i] > 0)) return fail(nullptr, DFT_EINVAL, "radius must be > 0");
+        if (!(prm->bulk_molar[i] >= 0)) return fail(nullptr, DFT_EINVAL, "bulk concentration must be >= 0");
+        charge += prm->valence[i] * prm->bulk_molar[i];
+        scale += std::fabs(prm->valence[i]) * prm->bulk_molar[i];
+        eta += prm->bulk_molar[i] * 0.602214076 * 4.18879020478639098 * std::pow(prm->radius_nm[i], 3);
+    }
+    if (std::fabs(charge) > 1e-12 * scale) return fail(nullptr, DFT_ENONNEUTRAL, "bath is not electroneutral");
+    if (eta >= kN3Bound) return fail(nullptr, DFT_EINVAL, "bath packing fraction >= 0.9");
+
+    dft_plan* p = new dft_plan();
+    p->S = S;
+    p->precision = prm->precision;
+    p->R.assign(prm->radius_nm, prm->radius_nm + S);
+    p->z.assign(prm->valence, prm->valence + S);
+    p->molar.assign(prm->bulk_molar, prm->bulk_molar + S);
+    p->T = prm->temperature_K;
+    p->eps_r = prm->eps_r;
+    std::string err;
+    if (!compute_bath(S, p->R.data(), p->z.data(), p->molar.data(), p->T, p->eps_r, &p->bath, &err)) {
+        delete p;
+        return fail(nullptr, DFT_EINVAL, err);
+    }
+    GridDesc& g = p->g;
+    g.nx = prm->nx; g.ny = prm->ny; g.nz = prm->nz;
+    g.nxh = g.nx / 2 + 1;
+    g.n = (long long)g.nx * g.ny * g.nz;
+    g.nc = (long long)g.nz * g.ny * g.nxh;
+    g.hx = prm->hx; g.hy = prm->hy; g.hz = prm->hz;
+    const double two_pi = 6.28318530717958647692;
+    p->kf[0] = two_pi / (g.nx * g.hx);
+    p->kf[1] = two_pi / (g.ny * g.hy);
+    p->kf[2] = two_pi / (g.nz * g.hz);
+    if (!radix_plan(g.nx, &p->ax) || !radix_plan(g.ny, &p->ay) || !radix_plan(g.nz, &p->az)) {
+        delete p;
+        return fail(nullptr, DFT_EINVAL, "no radix plan for the grid sizes");
+    }
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&p->device);
+    const bool f64 = prm->precision == DFT_FP64;
+    p->csize = f64 ? sizeof(double2) : sizeof(float2);
+    p->rsize = f64 ? sizeof(double) : sizeof(float);
+    p->Ty = pick_tile(g.ny, p->csize, 2, 100 * 1024);
+    p->Tz = pick_tile(g.nz, p->csize, 7, 112 * 1024);
+    p->LX = pick_lines(g.nx, p->csize, 1, 48 * 1024, 32);
+    p->LRphi = pick_lines(g.nx, p->csize, 5, 64 * 1024, 16);
+    p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, 48 * 1024, 16);
+    if (f64) fill_species<double>(p);
+    else fill_species<float>(p);
+
+    cudaError_t e = f64 ? Passes<double>::init_attributes() : Passes<float>::init_attributes();
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(nullptr, DFT_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+    // twiddles
+    const int ns[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        size_t bytes = size_t(ns[a]) * p->csize;
+        if (cudaMalloc(&p->tw[a], bytes) != cudaSuccess) { dft_plan_destroy(p); return fail(nullptr, DFT_ENOMEM, "twiddles"); }
+        if (f64) {
+            std::vector<double2> t;
+            fill_twiddles(ns[a], &t);
+            cudaMemcpy(p->tw[a], t.data(), bytes, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float2> t;
+            fill_twiddles(ns[a], &t);
+            cudaMemcpy(p->tw[a], t.data(), bytes, cudaMemcpyHostToDevice);
+        }
+    }
+    const size_t slot_comps = DFT_NCOMP + S + 1;
+    const size_t nred = size_t(g.ny) * g.nz + 1;
+    struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
+        {&p->T1, size_t(DFT_NCOMP) * g.nc * p->csize, "work spectra"},
+        {&p->slotA, slot_comps * g.nc * p->csize, "slot A"},
+        {&p->slotB, slot_comps * g.nc * p->csize, "slot B"},
+        {&p->gbuf, size_t(S) * g.n * p->rsize, "G buffer"},
+        {(void**)&p->red_sum, nred * sizeof(double), "reduction sums"},
+        {(void**)&p->red_max, nred * sizeof(float), "reduction maxima"},
+        {(void**)&p->ctl, sizeof(Ctl), "control block"},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            dft_plan_destroy(p);
+            return fail(nullptr, DFT_ENOMEM, std::string("cudaMalloc failed: ") + a.what);
+        }
+    }
+    cudaMemset(p->ctl, 0, sizeof(Ctl));
+    if (cudaMallocHost(&p->ctl_host, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        dft_plan_destroy(p);
+        return fail(nullptr, DFT_ENOMEM, "pinned control block");
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dft_plan_destroy(p);
+        return fail(nullptr, DFT_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return DFT_OK;
+}
+
+dft_status dft_plan_destroy(dft_plan* p) {
+    if (!p) return DFT_OK;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    for (int a = 0; a < 3; ++a) cudaFree(p->tw[a]);
+    cudaFree(p->T1);
+    cudaFree(p->slotA);
+    cudaFree(p->slotB);
+    cudaFree(p->gbuf);
+    cudaFree(p->stage_rho);
+    cudaFree(p->stage_V);
+    cudaFree(p->red_sum);
+    cudaFree(p->red_max);
+    cudaFree(p->ctl);
+    if (p->ctl_host) cudaFreeHost(p->ctl_host);
+    for (cudaEvent_t ev : p->evpool) cudaEventDestroy(ev);
+    delete p;
+    return DFT_OK;
+}
+
+dft_status dft_plan_bulk(const dft_plan* p, double* rho_bulk, double* mu_hs, double* mu_es, double* gamma,
+                         double* beta_p, double* lambda_b) {
+    if (!p) return fail(nullptr, DFT_EINVAL, "NULL plan");
+    for (int i = 0; i < p->S; ++i) {
+        if (rho_bulk) rho_bulk[i] = p->bath.rho[i];
+        if (mu_hs) mu_hs[i] = p->bath.mu_hs[i];
+        if (mu_es) mu_es[i] = p->bath.mu_es[i];
+    }
+    if (gamma) *gamma = p->bath.gamma;
+    if (beta_p) *beta_p = p->bath.beta_p;
+    if (lambda_b) *lambda_b = p->bath.lb;
+    return DFT_OK;
+}
+
+dft_status dft_weighted_densities(dft_plan* p, const void* rho, void* n_out) {
+    TRY(check_plan(p));
+    if (!rho || !n_out) return fail(p, DFT_EINVAL, "NULL field pointer");
+    p->iter_ready = false;
+    if (is_fp64(p)) {
+        using O = Ops<double>;
+        TRY(O::first_half(p, static_cast<const double*>(rho), p->slotA, 0));
+        TRY(O::xinv(p, DFT_NCOMP, O::slot_n(p->slotA), static_cast<double*>(n_out), nullptr, nullptr, -1, nullptr, nullptr));
+    } else {
+        using O = Ops<float>;
+        TRY(O::first_half(p, static_cast<const float*>(rho), p->slotA, 0));
+        TRY(O::xinv(p, DFT_NCOMP, O::slot_n(p->slotA), static_cast<float*>(n_out), nullptr, nullptr, -1, nullptr, nullptr));
+    }
+    return DFT_OK;
+}
+
+
+dft_status dft_c1_hs(dft_plan* p, const void* rho, void* c1_out) {
+    TRY(check_plan(p));
+    if (!rho || !c1_out) return fail(p, DFT_EINVAL, "NULL field pointer");
+    p->iter_ready = false;
+    TRY(reset_status(p));
+    if (is_fp64(p)) return c1_hs_t<double>(p, static_cast<const double*>(rho), static_cast<double*>(c1_out));
+    return c1_hs_t<float>(p, static_cast<const float*>(rho), static_cast<float*>(c1_out));
+}
+
+
+dft_status dft_c1_es(dft_plan* p, const void* rho, void* c1_out, void* psi_out) {
+    TRY(check_plan(p));
+    if (!rho || !c1_out) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (psi_out && p->S > DFT_MAX_SPECIES - 1) return fail(p, DFT_EINVAL, "psi_out needs nspecies <= 4");
+    p->iter_ready = false;
+    if (is_fp64(p))
+        return c1_es_t<double>(p, static_cast<const double*>(rho), static_cast<double*>(c1_out),
+                               static_cast<double*>(psi_out));
+    return c1_es_t<float>(p, static_cast<const float*>(rho), static_cast<float*>(c1_out), static_cast<float*>(psi_out));
+}
+
+
+dft_status dft_picard_map(dft_plan* p, const void* rho, const void* V, void* g_out, double* resid_out) {
+    TRY(check_plan(p));
+    if (!rho || !V || !g_out) return fail(p, DFT_EINVAL, "NULL field pointer");
+    p->iter_ready = false;
+    if (is_fp64(p))
+        TRY(picard_map_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V),
+                                 static_cast<double*>(g_out)));
+    else
+        TRY(picard_map_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V),
+                                static_cast<float*>(g_out)));
+    if (resid_out) {
+        TRY(read_ctl(p));
+        *resid_out = p->ctl_host->resid;
+    }
+    return DFT_OK;
+}
+
+dft_status dft_iter_begin(dft_plan* p, void* rho, const void* V) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (is_fp64(p)) return iter_begin_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V));
+    return iter_begin_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V));
+}
+
+dft_status dft_iter_step(dft_plan* p, void* rho, const void* V, double alpha, double* resid_out, double* alpha_out) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (!p->iter_ready || p->iter_rho != rho || p->iter_V != V)
+        return fail(p, DFT_EINVAL, "dft_iter_step needs a preceding dft_iter_begin on the same rho and V");
+    if (is_fp64(p)) TRY(iter_step_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V), alpha));
+    else TRY(iter_step_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V), alpha));
+    if (resid_out || alpha_out) {
+        TRY(read_ctl(p));
+        if (resid_out) *resid_out = p->ctl_host->resid_prev;
+        if (alpha_out) *alpha_out = p->ctl_host->alpha;
+    }
+    return DFT_OK;
+}
+
+dft_status dft_picard_step(dft_plan* p, void* rho, const void* V, double alpha, double* resid_out, double* alpha_out) {
+    TRY(dft_iter_begin(p, rho, V));
+    return dft_iter_step(p, rho, V, alpha, resid_out, alpha_out);
+}
+
+dft_status dft_solve(dft_plan* p, void* rho, const void* V, double alpha, double tol, int max_it, int* iters_out,
+                     double* resid_out) {
+    TRY(dft_iter_begin(p, rho, V));
+    TRY(read_ctl(p));
+    double r = p->ctl_host->resid;
+    int it = 0;
+    while (it < max_it && !(r < tol)) {
+        TRY(dft_iter_step(p, rho, V, alpha, nullptr, nullptr));
+        TRY(read_ctl(p));
+        r = p->ctl_host->resid;
+        ++it;
+    }
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = r;
+    if (!(r < tol)) return fail(p, DFT_ENOCONV, "max_it reached before tol");
+    return DFT_OK;
+}
+
+dft_status dft_picard_step_host(dft_plan* p, void* rho_host, const void* V_host, double alpha, double* resid_out,
+                                double* alpha_out) {
+    TRY(check_plan(p));
+    if (!rho_host || !V_host) return fail(p, DFT_EINVAL, "NULL host pointer");
+    const size_t bytes = size_t(p->S) * p->g.n * p->rsize;
+    if (!p->stage_rho) {
+        if (cudaMalloc(&p->stage_rho, bytes) != cudaSuccess || cudaMalloc(&p->stage_V, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(p, DFT_ENOMEM, "staging buffers");
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(p->stage_rho, rho_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->stage_V, V_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+    double r = 0, a = 0;
+    TRY(dft_picard_step(p, p->stage_rho, p->stage_V, alpha, &r, &a));
+    e = cudaMemcpyAsync(rho_host, p->stage_rho, bytes, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+    if (resid_out) *resid_out = r;
+    if (alpha_out) *alpha_out = a;
+    return DFT_OK;
+}
+
+dft_status dft_profile_enable(dft_plan* p, int enable) {
+    TRY(check_plan(p));
+    collect_profile(p);
+    for (int k = 0; k < K_COUNT; ++k) {
+        p->prof_launches[k] = 0;
+        p->prof_ms[k] = 0.0;
+    }
+    p->prof = enable != 0;
+    return DFT_OK;
+}
+
+dft_status dft_profile_read(dft_plan* p, const char* name, int* launches, double* total_ms) {
+    TRY(check_plan(p));
+    if (!name) return fail(p, DFT_EINVAL, "NULL name");
+    collect_profile(p);
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (std::strcmp(name, kKindNames[k]) == 0) {
+            if (launches) *launches = p->prof_launches[k];
+            if (total_ms) *total_ms = p->prof_ms[k];
+            return DFT_OK;
+        }
+    }
+    return fail(p, DFT_EINVAL, std::string("unknown kernel name ") + name);
+}
+
+}  // extern "C"

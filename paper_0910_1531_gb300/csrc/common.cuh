@@ -1,0 +1,103 @@
+// Shared definitions of the GB300 classical-DFT kernels: complex arithmetic,
+// per-axis FFT plans, grid / species descriptors and the device control block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DFT_MAXS 5          // species (the back-convolution keeps 5 k-space accumulators)
+#define DFT_MAXSTAGES 8     // radix stages per axis
+#define DFT_NCOMP 10        // n0 n1 n2 n3 nV1(xyz) nV2(xyz)
+
+template <typename Real> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C().x) re, decltype(C().x) im) {
+    C c; c.x = re; c.y = im; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C().x) s) { return cmake<C>(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+// multiply by +i or -i
+template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmake<C>(-a.y, a.x); }
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
+
+// Radix decomposition of one axis length: n = prod radix[s]; radices in {2,3,4,8,16}.
+struct AxisPlan {
+    int n;
+    int nstages;
+    int radix[DFT_MAXSTAGES];
+};
+
+// Grid of one state point.  Real fields: [c][nz][ny][nx]; half spectra after the
+// x transform: [c][nz][ny][nxh], nxh = nx/2 + 1.
+struct GridDesc {
+    int nx, ny, nz, nxh;
+    long long n;     // nx * ny * nz
+    long long nc;    // nz * ny * nxh
+    double hx, hy, hz;
+};
+
+// Species constants in the kernels' precision (host fills them in double, then converts).
+template <typename Real>
+struct SpeciesDesc {
+    int S;
+    Real R[DFT_MAXS];
+    Real z[DFT_MAXS];
+    Real rho_b[DFT_MAXS];
+    Real inv_rho_b[DFT_MAXS];   // residual weights 1 / rho_bath
+    Real mu_hs_b[DFT_MAXS];     // beta mu^{HS,bath}
+    Real n_rho_b[DFT_MAXS];     // N * rho_bath: DFT of the bath density at k = 0
+    // bulk-fluid kernel per pair (i, j), in kT units
+    Real es_pref[DFT_MAXS][DFT_MAXS];   // lambda_B z_i z_j / 2
+    Real es_a[DFT_MAXS][DFT_MAXS];      // 1 / (2 l_i l_j)
+    Real es_b[DFT_MAXS][DFT_MAXS];      // (l_i + l_j) / (l_i l_j)
+    Real es_c[DFT_MAXS][DFT_MAXS];      // (l_i - l_j)^2 / (2 l_i l_j) + 2
+    Real es_R[DFT_MAXS][DFT_MAXS];      // R_ij = R_i + R_j
+    Real pois[DFT_MAXS][DFT_MAXS];      // 4 pi lambda_B z_i z_j
+    Real inv_n;                         // 1 / N
+    int coulomb_limit;                  // Gamma == 0: kernel is lambda_B z_i z_j / r inside R_ij
+};
+
+// Per-component additive constants of the plain x inverse.
+template <typename Real> struct Offsets { Real v[DFT_NCOMP + 2]; };
+
+// Device-resident control block of the Picard iteration.  Kernels read the mixing
+// weights from here, so a whole iteration can be queued (or captured) without a
+// host round trip.
+struct Ctl {
+    double wA, wB;          // weights of slot A / slot B weighted densities (XPHI, ZK2)
+    double w0, w1;          // weights of rho^(0) / rho^(1) (XU)
+    double f[4];            // squared residuals: f0 = r^2(rho0), f1, f2 samples, f3 = accepted point
+    double alpha_max;
+    double alpha;           // accepted alpha of the last step
+    double alpha_fixed;     // < 0: line search
+    double n3max_cur;       // max n3 of the current iterate
+    double n3max_next;      // max n3 of G(current)
+    double resid;           // sqrt(f0)
+    double resid_prev;      // r of the iterate a step started from
+    double sample_alpha[2];
+    int status;             // dft_status bits raised on the device (see DEV_* below)
+    int iter;
+};
+
+enum {
+    DEV_N3BOUND = 1,        // n3 >= 1 met
+    DEV_NONFINITE = 2       // non-finite density or residual met
+};
+
+// finalize() operations
+enum {
+    FIN_F0 = 1,             // f0 = sum, resid = sqrt(f0)
+    FIN_N3CUR = 2,          // n3max_cur = max
+    FIN_AMAX = 4,           // n3max_next = max; alpha_max; weights for the first sample (or the fixed alpha)
+    FIN_F1 = 8,             // f1 = sum; weights for the second sample
+    FIN_F2_CHOOSE = 16,     // f2 = sum; alpha from the parabola; weights for the accepted point
+    FIN_ACCEPT = 32,        // f0 = f3 = sum; n3max_cur = max; resid; iter++
+    FIN_IDENTITY = 64       // weights (1, 0) for a plain G evaluation
+};

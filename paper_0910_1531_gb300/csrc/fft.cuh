@@ -1,0 +1,156 @@
+// Shared-memory Stockham FFT of many independent lines.
+//
+// A CTA holds `lines` transforms of length n in shared memory; element e of
+// line l sits at buf[e * es + l * ls].  Tiles of columns of the y / z axes use
+// es = T (tile width), ls = 1 so that consecutive threads touch consecutive
+// addresses; rows of the x axis use es = 1, ls = n + 1 (odd line pitch, free
+// of bank conflicts for 8-byte elements).
+//
+// Stage with radix R and Ns = product of the earlier radices (self-sorting,
+// out of place):  for butterfly j of n/R,
+//     v[r] = src[j + r n/R] * w^( (j mod Ns) r n/(Ns R) ),  w = exp(-+2 pi i / n)
+//     v    = DFT_R(v)
+//     dst[(j / Ns) Ns R + (j mod Ns) + r Ns] = v[r]
+// After all stages the result is in natural order.  The twiddle table holds
+// exp(-2 pi i m / n), m < n, computed in double on the host.
+#pragma once
+
+#include "common.cuh"
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+// rotate by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot(C a) { return INV ? cmul_i(a) : cmul_mi(a); }
+
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C* v) {
+    using R = decltype(C().x);
+    const R h = R(0.86602540378443864676);   // sqrt(3)/2
+    C s = cadd(v[1], v[2]);
+    C d = csub(v[1], v[2]);
+    C m = csub(v[0], cscale(s, R(0.5)));
+    C t = rot<INV>(cscale(d, h));              // -i h d (forward)
+    v[0] = cadd(v[0], s);
+    v[1] = cadd(m, t);
+    v[2] = csub(m, t);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+    C a0 = cadd(x0, x2), a1 = csub(x0, x2);
+    C a2 = cadd(x1, x3), a3 = rot<INV>(csub(x1, x3));
+    x0 = cadd(a0, a2);
+    x2 = csub(a0, a2);
+    x1 = cadd(a1, a3);
+    x3 = csub(a1, a3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C* v) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
+    using R = decltype(C().x);
+    const R s = R(0.70710678118654752440);
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    // o_k *= W8^k, W8 = exp(-+ 2 pi i / 8)
+    o1 = INV ? cmake<C>((o1.x - o1.y) * s, (o1.x + o1.y) * s) : cmake<C>((o1.x + o1.y) * s, (o1.y - o1.x) * s);
+    o2 = rot<INV>(o2);
+    o3 = INV ? cmake<C>((-o3.x - o3.y) * s, (o3.x - o3.y) * s) : cmake<C>((o3.y - o3.x) * s, (-o3.x - o3.y) * s);
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C* v) {
+    using R = decltype(C().x);
+    // Y_r = DFT4(v[r], v[r+4], v[r+8], v[r+12]);  X[k1 + 4 k2] = DFT4_r(W16^(r k1) Y_r[k1])
+    C y[16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        C a = v[r], b = v[r + 4], c = v[r + 8], d = v[r + 12];
+        dft4<INV>(a, b, c, d);
+        y[r * 4 + 0] = a; y[r * 4 + 1] = b; y[r * 4 + 2] = c; y[r * 4 + 3] = d;
+    }
+    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), c2 = R(0.70710678118654752440);
+    const R sg = INV ? R(1) : R(-1);
+    // W16^m for m = r k1 in {0..9}: (cos(2 pi m/16), sg sin(2 pi m/16))
+    const R wc[10] = {R(1), c1, c2, s1, R(0), -s1, -c2, -c1, R(-1), -c1};
+    const R ws[10] = {R(0), s1, c2, c1, R(1), c1, c2, s1, R(0), -s1};
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) {
+            const int m = r * k1;
+            y[r * 4 + k1] = cmul(y[r * 4 + k1], cmake<C>(wc[m], sg * ws[m]));
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C a = y[0 * 4 + k1], b = y[1 * 4 + k1], c = y[2 * 4 + k1], d = y[3 * 4 + k1];
+        dft4<INV>(a, b, c, d);
+        v[k1] = a; v[k1 + 4] = b; v[k1 + 8] = c; v[k1 + 12] = d;
+    }
+}
+
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft_small(C* v) {
+    if constexpr (R == 2) dft2<INV>(v);
+    else if constexpr (R == 3) dft3<INV>(v);
+    else if constexpr (R == 4) dft4<INV>(v);
+    else if constexpr (R == 8) dft8<INV>(v);
+    else dft16<INV>(v);
+}
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int n, int ns,
+                                               int lines, int es, int ls, const C* __restrict__ tw) {
+    const int m = n / R;
+    const int twstep = n / (ns * R);
+    const int total = m * lines;
+    for (int task = threadIdx.x; task < total; task += blockDim.x) {
+        const int line = task % lines;
+        const int j = task / lines;
+        const int k = j % ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es + line * ls];
+        if (ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[k * r * twstep];
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_small<R, INV>(v);
+        const int base = (j / ns) * ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(base + r * ns) * es + line * ls] = v[r];
+    }
+}
+
+// Transform all lines held in `a` (b is scratch of the same size).  The caller must
+// __syncthreads() before the call (data in a visible).  Returns the buffer holding
+// the result; all threads see it on return.
+template <bool INV, typename C>
+__device__ C* smem_fft(C* a, C* b, const AxisPlan& p, int lines, int es, int ls, const C* tw) {
+    int ns = 1;
+    for (int s = 0; s < p.nstages; ++s) {
+        const int R = p.radix[s];
+        switch (R) {
+            case 2: stockham_stage<2, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            case 3: stockham_stage<3, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            case 4: stockham_stage<4, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            case 8: stockham_stage<8, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            default: stockham_stage<16, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+        }
+        __syncthreads();
+        C* t = a; a = b; b = t;
+        ns *= R;
+    }
+    return a;
+}

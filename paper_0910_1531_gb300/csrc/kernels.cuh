@@ -1,0 +1,834 @@
+// Pass kernels of one residual evaluation G(rho) (Sec. "Discretization and Solution
+// in Equilibrium"): every 3D transform is split into an x pass (rows, real <-> half
+// spectrum), a y pass and a z pass (column tiles), and the pointwise work rides
+// inside those passes:
+//
+//   first half  (rho -> weighted densities of eq. nDef, bulk-fluid + Poisson spectra)
+//     k_xfwd     x R2C of the S densities
+//     k_yfft     y forward
+//     k_zconv_fwd  z forward, the analytic weights of App. B (n_hat_alpha), the
+//                bulk-fluid kernel (eq. CplusPsiHat) and the Poisson symbol
+//                (eq. potentialSolution) applied in k space, z inverse of the ten n
+//     k_yfft     y inverse of the ten n
+//   second half (weighted densities -> c1 -> G)
+//     k_xphi     x C2R of the ten n, dPhi/dn_alpha of eq. Phi (|nV2| <= n2 bound,
+//                FP64 log(1-n3) and 1/(1-n3)^m), x R2C of the ten derivatives
+//     k_yfft     y forward
+//     k_zconv_bwd  z forward, adjoint weights (eq. muHS), + bulk-fluid/Poisson spectra,
+//                z inverse of the S one-body correlations
+//     k_yfft     y inverse
+//     k_xupdate  x C2R and the update G_i = rho_bath_i exp(mu_HS_bath_i - V_i + c1_i)
+//                (eq. rhoEquation), mixing of rho for the line search, residual sums
+//
+// Linear stages carry mixing weights (read from the device control block) so that
+// n_alpha at a line-search point is the mix of two stored weighted-density sets:
+// n3, and every n_alpha, is linear in rho (Sec. "Nonlinear solver").
+#pragma once
+
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace dftk {
+
+constexpr int kThreads = 256;
+
+template <typename Real> __device__ __forceinline__ void sc(Real x, Real* s, Real* c);
+template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+// Wave number of index j on an axis of n points (eq. Kvalues); kf = 2 pi / (n h).
+template <typename Real> __device__ __forceinline__ Real kval(int j, int n, Real kf) {
+    return (2 * j <= n) ? Real(j) * kf : -Real(n - j) * kf;
+}
+
+// Power series sum_m (-1)^m y^(2m) / ((2m+1)! (2m+q)) in t = y^2, q = n + 3 of the ball
+// integral (4 pi / k) I_n = 4 pi R^(n+3) * series (expansion of sin(k r) under the integral).
+__host__ __device__ constexpr double series_coef(int m, int q) {
+    double f = 1.0;
+    for (int i = 2; i <= 2 * m + 1; ++i) f *= double(i);
+    return ((m & 1) ? -1.0 : 1.0) / (f * double(2 * m + q));
+}
+
+template <typename Real, int Q> __device__ __forceinline__ Real ball_series(Real t) {
+    constexpr int M = sizeof(Real) == 4 ? 9 : 11;
+    Real acc = Real(0);
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) acc = acc * t + Real(series_coef(m, Q));
+    return acc;
+}
+
+template <typename Real> __device__ __forceinline__ Real series_cut() { return sizeof(Real) == 4 ? Real(1.5) : Real(1.0); }
+
+// (sin x - x cos x) / x^3 (1/3 at x = 0), s = sin x, c = cos x
+template <typename Real> __device__ __forceinline__ Real sinc3(Real x, Real s, Real c) {
+    if (x < series_cut<Real>()) return ball_series<Real, 3>(x * x);
+    return (s - x * c) / (x * x * x);
+}
+
+// FMT scalar weights of App. B for one species at |k| (x = |k| R).  Returns w0 (w1 = R w0,
+// w2 = 4 pi R^2 w0) and j3 = (sin x - x cos x)/x^3 (w3 = 4 pi R^3 j3).
+template <typename Real> __device__ __forceinline__ void fmt_weights(Real kmag, Real R, Real* w0, Real* j3) {
+    const Real x = kmag * R;
+    Real s, c;
+    sc<Real>(x, &s, &c);
+    if (x < series_cut<Real>()) {
+        // sin x / x series for accuracy next to the series of j3
+        const Real t = x * x;
+        *w0 = Real(1) + t * (Real(-1.0 / 6) + t * (Real(1.0 / 120) + t * (Real(-1.0 / 5040) + t * (Real(1.0 / 362880)
+              + t * (Real(-1.0 / 39916800) + t * Real(1.0 / 6227020800.0))))));
+    } else {
+        *w0 = s / x;
+    }
+    *j3 = sinc3<Real>(x, s, c);
+}
+
+// Bulk-fluid kernel DC_ij_hat(|k|) of eq. CplusPsiHat (prefactor 2 pi lambda_B z_i z_j / k, i.e.
+// (lambda_B z_i z_j / 2)(4 pi / k) I_n) in kT units.
+template <typename Real>
+__device__ __forceinline__ Real delta_c_hat(Real kmag, Real R, Real pref, Real a, Real b, Real c) {
+    const Real y = kmag * R;
+    Real bm1, b0, b1;   // (4 pi / k) I_n / (4 pi R^(n+3))
+    if (y < series_cut<Real>()) {
+        const Real t = y * y;
+        bm1 = ball_series<Real, 2>(t);
+        b0 = ball_series<Real, 3>(t);
+        b1 = ball_series<Real, 4>(t);
+    } else {
+        Real s, co;
+        sc<Real>(y, &s, &co);
+        Real sh, chh;
+        sc<Real>(Real(0.5) * y, &sh, &chh);
+        const Real omc = Real(2) * sh * sh;           // 1 - cos y, without cancellation
+        const Real iy = Real(1) / y;
+        const Real iy2 = iy * iy;
+        bm1 = omc * iy2;
+        b0 = (s - y * co) * iy2 * iy;
+        b1 = -co * iy2 + Real(2) * s * iy2 * iy - Real(2) * omc * iy2 * iy2;
+    }
+    const Real R2 = R * R;
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    return pref * fourpi * R2 * (a * R2 * b1 - b * R * b0 + c * bm1);
+}
+
+// ------------------------------------------------------------------------------------
+// Reductions
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (l < (int)(blockDim.x >> 5)) ? scratch[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    return r;   // valid in thread 0
+}
+
+__device__ __forceinline__ float block_max(float v, float* scratch) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    float r = -CUDART_INF_F;
+    if (threadIdx.x < 32) {
+        r = (l < (int)(blockDim.x >> 5)) ? scratch[l] : -CUDART_INF_F;
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    }
+    return r;
+}
+
+template <typename C> __device__ __forceinline__ C* align_ptr(unsigned char* p) {
+    uintptr_t u = reinterpret_cast<uintptr_t>(p);
+    u = (u + 15) & ~uintptr_t(15);
+    return reinterpret_cast<C*>(u);
+}
+
+// ------------------------------------------------------------------------------------
+// x pass, forward: S real fields -> half spectra.  Two real rows a, b are packed as a + i b
+// into one complex transform of length nx and separated afterwards:
+//   X_a[k] = (Z[k] + conj Z[-k]) / 2,  X_b[k] = (Z[k] - conj Z[-k]) / (2 i).
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int ncomp, int lx,
+                                                   const Real* __restrict__ in,
+                                                   typename Cplx<Real>::type* __restrict__ out,
+                                                   const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lx * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long rows = (long long)ncomp * g.ny * g.nz;
+    const long long pair0 = (long long)blockIdx.x * lx;
+    for (int idx = threadIdx.x; idx < lx * nx; idx += blockDim.x) {
+        const int l = idx / nx, x = idx - (idx / nx) * nx;
+        const long long ra = 2 * (pair0 + l), rb = ra + 1;
+        const Real a = (ra < rows) ? in[ra * nx + x] : Real(0);
+        const Real b = (rb < rows) ? in[rb * nx + x] : Real(0);
+        A[l * pitch + x] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    C* R = smem_fft<false>(A, B, px, lx, 1, pitch, tw);
+    for (int idx = threadIdx.x; idx < lx * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const long long ra = 2 * (pair0 + l), rb = ra + 1;
+        const C zk = R[l * pitch + k];
+        const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
+        const C s = cadd(zk, cconj(znk));
+        const C d = csub(zk, cconj(znk));
+        if (ra < rows) out[ra * nxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+        if (rb < rows) out[rb * nxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// y pass: in-place transform of ncomp half spectra along y, tiles of T kx columns.
+// grid (ceil(nxh/T), nz, ncomp)
+// ------------------------------------------------------------------------------------
+template <typename Real, bool INV>
+__global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int T,
+                                                   typename Cplx<Real>::type* __restrict__ data,
+                                                   const typename Cplx<Real>::type* __restrict__ twy) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int ny = g.ny, nxh = g.nxh;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + ny;
+    C* B = A + T * ny;
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = twy[i];
+    const int kx0 = blockIdx.x * T;
+    C* base = data + (long long)blockIdx.z * g.nc + (long long)blockIdx.y * ny * nxh + kx0;
+    for (int idx = threadIdx.x; idx < T * ny; idx += blockDim.x) {
+        const int y = idx / T, t = idx - (idx / T) * T;
+        A[idx] = (kx0 + t < nxh) ? base[(long long)y * nxh + t] : cmake<C>(Real(0), Real(0));
+    }
+    __syncthreads();
+    C* R = smem_fft<INV>(A, B, py, T, T, 1, tw);
+    for (int idx = threadIdx.x; idx < T * ny; idx += blockDim.x) {
+        const int y = idx / T, t = idx - (idx / T) * T;
+        if (kx0 + t < nxh) base[(long long)y * nxh + t] = R[idx];
+    }
+}
+
+// Wave vector components of tile point (kz index, t) in a z-pass tile at (kx0, ky index)
+template <typename Real> struct KPoint {
+    Real kx, ky, kz, kmag;
+    bool nyq_x, nyq_y, nyq_z, zero;
+};
+
+template <typename Real>
+__device__ __forceinline__ KPoint<Real> kpoint(const GridDesc& g, int kxi, int kyi, int kzi, Real kfx, Real kfy,
+                                               Real kfz) {
+    KPoint<Real> p;
+    p.kx = kval<Real>(kxi, g.nx, kfx);
+    p.ky = kval<Real>(kyi, g.ny, kfy);
+    p.kz = kval<Real>(kzi, g.nz, kfz);
+    p.kmag = sqrt(p.kx * p.kx + p.ky * p.ky + p.kz * p.kz);
+    p.nyq_x = (g.nx % 2 == 0) && (2 * kxi == g.nx);
+    p.nyq_y = (g.ny % 2 == 0) && (2 * kyi == g.ny);
+    p.nyq_z = (g.nz % 2 == 0) && (2 * kzi == g.nz);
+    p.zero = (kxi == 0) && (kyi == 0) && (kzi == 0);
+    return p;
+}
+
+// Bulk-fluid + mean-field kernel K_ij(k) = DC_ij_hat(k) - 4 pi lambda_B z_i z_j / lap(k) (k != 0),
+// lap(k) = sum_d 4 sin^2(k_d h_d / 2) / h_d^2 (eq. potentialSolution), psi_hat(0) = 0.
+template <typename Real>
+__device__ __forceinline__ Real es_kernel(const SpeciesDesc<Real>& sp, int i, int j, const KPoint<Real>& p, Real inv_lap) {
+    Real K = delta_c_hat<Real>(p.kmag, sp.es_R[i][j], sp.es_pref[i][j], sp.es_a[i][j], sp.es_b[i][j], sp.es_c[i][j]);
+    if (!p.zero) K -= sp.pois[i][j] * inv_lap;
+    return K;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real inverse_laplacian(const KPoint<Real>& p, Real hx, Real hy, Real hz) {
+    if (p.zero) return Real(0);
+    const Real sx = sin(Real(0.5) * p.kx * hx), sy = sin(Real(0.5) * p.ky * hy), sz = sin(Real(0.5) * p.kz * hz);
+    const Real lap = Real(4) * (sx * sx / (hx * hx) + sy * sy / (hy * hy) + sz * sz / (hz * hz));
+    return Real(1) / lap;
+}
+
+// ------------------------------------------------------------------------------------
+// z pass of the first half.  grid (ceil(nxh/T), ny)
+//   in:      S half spectra after x, y forward  (kx, ky, z)
+//   slot_n:  10 weighted densities, 1/N applied, after z inverse (kx, ky, z)
+//   slot_es: S (+1 with psi) unnormalised bulk-fluid/Poisson spectra sum_j K_ij drho_hat_j (kx, ky, kz)
+// Shared pool of 7 tiles of T x nz.
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int T,
+                                                        Real kfx, Real kfy, Real kfz, int want_psi,
+                                                        const typename Cplx<Real>::type* __restrict__ in,
+                                                        typename Cplx<Real>::type* __restrict__ slot_n,
+                                                        typename Cplx<Real>::type* __restrict__ slot_es,
+                                                        const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int nz = g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int tile = T * nz;
+    C* tw = align_ptr<C>(smem_raw);
+    C* pool[7];
+    for (int i = 0; i < 7; ++i) pool[i] = tw + nz + i * tile;
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twz[i];
+    const int kx0 = blockIdx.x * T;
+    const int kyi = blockIdx.y;
+    const long long zstride = (long long)ny * nxh;
+    const long long col0 = (long long)kyi * nxh + kx0;
+
+    // phase 1: forward z transform of each species tile; results end in pool[0..S-1]
+    for (int s = 0; s < S; ++s) {
+        const C* src = in + (long long)s * g.nc + col0;
+        C* b = pool[s];
+        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+            const int z = idx / T, t = idx - (idx / T) * T;
+            b[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
+        }
+        __syncthreads();
+        C* r = smem_fft<false>(b, pool[6], pz, T, T, 1, tw);
+        if (r != b) { pool[6] = b; pool[s] = r; }
+    }
+
+    // phase 2: k-space products at each tile point
+    const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        const int kzi = idx / T, t = idx - (idx / T) * T;
+        const int kxi = kx0 + t;
+        const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+        C v[DFT_MAXS];
+        for (int s = 0; s < S; ++s) v[s] = pool[s][idx];
+        C acc[5];
+        for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
+        for (int s = 0; s < S; ++s) {
+            Real w0, j3;
+            fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
+            const Real R = sp.R[s];
+            acc[0] = cadd(acc[0], cscale(v[s], w0));
+            acc[1] = cadd(acc[1], cscale(v[s], R * w0));
+            acc[2] = cadd(acc[2], cscale(v[s], fourpi * R * R * w0));
+            acc[3] = cadd(acc[3], cscale(v[s], fourpi * R * R * R * j3));
+            acc[4] = cadd(acc[4], cscale(v[s], R * R * j3));       // w3 / (4 pi R)
+        }
+        if (kxi < nxh) {
+            const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+            C dv[DFT_MAXS];
+            for (int s = 0; s < S; ++s) {
+                dv[s] = v[s];
+                if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+            }
+            C es[DFT_MAXS];
+            for (int s = 0; s < S; ++s) es[s] = cmake<C>(Real(0), Real(0));
+            for (int i = 0; i < S; ++i) {
+                for (int j = i; j < S; ++j) {
+                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap);
+                    es[i] = cadd(es[i], cscale(dv[j], K));
+                    if (j != i) es[j] = cadd(es[j], cscale(dv[i], K));
+                }
+            }
+            const long long o = (long long)kzi * zstride + col0 + t;
+            for (int s = 0; s < S; ++s) slot_es[(long long)s * g.nc + o] = es[s];
+            if (want_psi) {
+                C q = cmake<C>(Real(0), Real(0));
+                for (int s = 0; s < S; ++s) q = cadd(q, cscale(v[s], sp.z[s]));
+                // psi_hat = 4 pi lambda_B q_hat / lap; pois[s][s] / z_s^2 = 4 pi lambda_B
+                Real flb = Real(0);
+                for (int s = 0; s < S; ++s)
+                    if (sp.z[s] != Real(0)) { flb = sp.pois[s][s] / (sp.z[s] * sp.z[s]); break; }
+                slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
+            }
+        }
+        for (int a = 0; a < 5; ++a) pool[a][idx] = cscale(acc[a], sp.inv_n);
+    }
+    __syncthreads();
+
+    // phase 3: inverse z of the ten weighted densities.  Vector spectra are i k_d n3_hat and
+    // i k_d m_hat (n_V2 = grad n3, n_V1 = grad m), zero on the Nyquist index of axis d.
+    const int order[10] = {4, 5, 6, 7, 8, 9, 3, 0, 1, 2};
+    for (int oi = 0; oi < 10; ++oi) {
+        const int a = order[oi];
+        C* r;
+        if (a >= 4) {
+            const C* src = (a < 7) ? pool[4] : pool[3];
+            const int d = (a - 4) % 3;
+            C* W = pool[5];
+            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+                const int kzi = idx / T, t = idx - (idx / T) * T;
+                const int kxi = kx0 + t;
+                Real kd;
+                bool nyq;
+                if (d == 0) { kd = kval<Real>(kxi, g.nx, kfx); nyq = (g.nx % 2 == 0) && (2 * kxi == g.nx); }
+                else if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
+                else { kd = kval<Real>(kzi, g.nz, kfz); nyq = (g.nz % 2 == 0) && (2 * kzi == g.nz); }
+                const C u = src[idx];
+                W[idx] = nyq ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd * u.y, kd * u.x);
+            }
+            __syncthreads();
+            r = smem_fft<true>(W, pool[6], pz, T, T, 1, tw);
+        } else {
+            r = smem_fft<true>(pool[a], pool[5], pz, T, T, 1, tw);
+        }
+        C* dst = slot_n + (long long)a * g.nc + col0;
+        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+            const int z = idx / T, t = idx - (idx / T) * T;
+            if (kx0 + t < nxh) dst[z * zstride + t] = r[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Pointwise derivatives of eq. Phi.  The log(1 - n3) and 1/(1 - n3)^m factors are formed
+// in FP64; xi = |nV2|^2/n2^2 is clamped to [0, 1] (Sec. "Numerical Stability"), and the
+// xi terms vanish where n2 <= 1e-30.  Returns false if n3 >= 1.
+// ------------------------------------------------------------------------------------
+template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n) {
+    const Real n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
+    const Real v1x = n[4], v1y = n[5], v1z = n[6], v2x = n[7], v2y = n[8], v2z = n[9];
+    const double D = 1.0 - double(n3);
+    const bool ok = D > 0.0;
+    const double lnD = log(D);
+    const double iD = 1.0 / D;
+    const double iD2 = iD * iD;
+    const double iD3 = iD2 * iD;
+    const Real fiD = Real(iD), fiD2 = Real(iD2), fiD3 = Real(iD3);
+    const Real q = v2x * v2x + v2y * v2y + v2z * v2z;
+    Real xi = (n2 > Real(1e-30)) ? q / (n2 * n2) : Real(1);
+    xi = xi < Real(0) ? Real(0) : (xi > Real(1) ? Real(1) : xi);
+    const Real om = Real(1) - xi;
+    const Real dot = v1x * v2x + v1y * v2y + v1z * v2z;
+    const Real pi = Real(CUDART_PI);
+    n[0] = Real(-lnD);
+    n[1] = n2 * fiD;
+    n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 / (Real(8) * pi);
+    n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 / (Real(12) * pi);
+    const Real cv = n2 * om * om * fiD2 / (Real(4) * pi);
+    n[4] = -v2x * fiD;
+    n[5] = -v2y * fiD;
+    n[6] = -v2z * fiD;
+    n[7] = -v1x * fiD - cv * v2x;
+    n[8] = -v1y * fiD - cv * v2y;
+    n[9] = -v1z * fiD - cv * v2z;
+    return ok;
+}
+
+// Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
+// full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
+template <typename Real>
+__device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
+                                               long long nrows, int ncomp,
+                                               const typename Cplx<Real>::type* A,
+                                               const typename Cplx<Real>::type* Bm, Real wA, Real wB,
+                                               typename Cplx<Real>::type* mat_out,
+                                               typename Cplx<Real>::type* dst) {
+    using C = typename Cplx<Real>::type;
+    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    const bool even = (nx % 2) == 0;
+    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const long long row = row0 + l / lines_per_row;
+        const int ca = 2 * (l % lines_per_row), cb = ca + 1;
+        C a = cmake<C>(Real(0), Real(0)), b = a;
+        if (row < nrows) {
+            const long long oa = (long long)ca * g.nc + row * nxh + k;
+            const long long ob = (long long)cb * g.nc + row * nxh + k;
+            a = cscale(A[oa], wA);
+            if (Bm) a = cadd(a, cscale(Bm[oa], wB));
+            if (cb < ncomp) {
+                b = cscale(A[ob], wA);
+                if (Bm) b = cadd(b, cscale(Bm[ob], wB));
+            }
+            if (k == 0 || (even && 2 * k == nx)) { a.y = Real(0); b.y = Real(0); }
+            if (mat_out) {
+                mat_out[oa] = a;
+                if (cb < ncomp) mat_out[ob] = b;
+            }
+        }
+        dst[l * pitch + k] = cmake<C>(a.x - b.y, a.y + b.x);
+        if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + (nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+    }
+}
+
+// Separate Z = FFT(a + i b) of two real rows into their half spectra and store them.
+template <typename Real>
+__device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
+                                                long long nrows, int ncomp, const typename Cplx<Real>::type* R,
+                                                typename Cplx<Real>::type* out) {
+    using C = typename Cplx<Real>::type;
+    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const long long row = row0 + l / lines_per_row;
+        if (row >= nrows) continue;
+        const int ca = 2 * (l % lines_per_row), cb = ca + 1;
+        const C zk = R[l * pitch + k];
+        const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
+        const C s = cadd(zk, cconj(znk));
+        const C d = csub(zk, cconj(znk));
+        out[(long long)ca * g.nc + row * nxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+        if (cb < ncomp) out[(long long)cb * g.nc + row * nxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// x pass of the second half's start: n_alpha (mixed from slots A and B) -> real space ->
+// dPhi/dn_alpha -> half spectra.  grid: ceil(ny nz / LR); 5 lines (component pairs) per row.
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int LR, const Ctl* __restrict__ ctl,
+                                                   const typename Cplx<Real>::type* slotA,
+                                                   const typename Cplx<Real>::type* slotB,
+                                                   typename Cplx<Real>::type* mat_out,
+                                                   typename Cplx<Real>::type* __restrict__ phi_out,
+                                                   float* __restrict__ red_max, int* __restrict__ status,
+                                                   const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float scratch_f[32];
+    const int nx = g.nx, pitch = nx + 1;
+    const int lines = 5 * LR;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lines * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long nrows = (long long)g.ny * g.nz;
+    const long long row0 = (long long)blockIdx.x * LR;
+    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+    load_pair_rows<Real>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A);
+    __syncthreads();
+    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    float mx = -CUDART_INF_F;
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        C* base = R + (r * 5) * pitch + x;
+        Real n[DFT_NCOMP];
+#pragma unroll
+        for (int p = 0; p < 5; ++p) {
+            const C v = base[p * pitch];
+            n[2 * p] = v.x;
+            n[2 * p + 1] = v.y;
+        }
+        if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
+        const bool ok = phi_derivatives<Real>(n);
+        if (!ok && row0 + r < nrows) bad = true;
+#pragma unroll
+        for (int p = 0; p < 5; ++p) base[p * pitch] = cmake<C>(n[2 * p], n[2 * p + 1]);
+    }
+    if (bad) atomicOr(status, DEV_N3BOUND);
+    __syncthreads();
+    C* other = (R == A) ? B : A;
+    C* F = smem_fft<false>(R, other, px, lines, 1, pitch, tw);
+    store_pair_rows<Real>(g, lines, 5, row0, nrows, DFT_NCOMP, F, phi_out);
+    const float bm = block_max(mx, scratch_f);
+    if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
+}
+
+// ------------------------------------------------------------------------------------
+// z pass of the second half.  grid (ceil(nxh/T), ny)
+//   phi:  in  10 dPhi/dn_alpha spectra after x, y forward (kx, ky, z)
+//         out S one-body correlation spectra after z inverse, 1/N applied (kx, ky, z)
+//   mu_hat_i = sum_alpha Phi_hat_alpha w_hat_i^alpha(+k) (eq. muHS): with the vector weights
+//   w_hat^V2 = -i k w_hat^3 and w_hat^V1 = w_hat^V2/(4 pi R) the k-space sum needs only the five
+//   species-independent spectra Phi0, Phi1, Phi2, Phi3 + div(PhiV2), div(PhiV1).
+//   c_hat_i = (-mu_hat_i + wA es_A_i + wB es_B_i) / N.
+// flags: 1 = hard-sphere part, 2 = electrostatic part; ncomp_out = S (or S + 1 for psi).
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int T,
+                                                        Real kfx, Real kfy, Real kfz, int flags, int ncomp_out,
+                                                        const Ctl* __restrict__ ctl,
+                                                        typename Cplx<Real>::type* phi,
+                                                        const typename Cplx<Real>::type* esA,
+                                                        const typename Cplx<Real>::type* esB,
+                                                        typename Cplx<Real>::type* es_mat,
+                                                        const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int nz = g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int tile = T * nz;
+    C* tw = align_ptr<C>(smem_raw);
+    C* pool[7];
+    for (int i = 0; i < 7; ++i) pool[i] = tw + nz + i * tile;
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twz[i];
+    const int kx0 = blockIdx.x * T;
+    const int kyi = blockIdx.y;
+    const long long zstride = (long long)ny * nxh;
+    const long long col0 = (long long)kyi * nxh + kx0;
+    const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
+    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+
+    if (hs) {
+        for (int a = 0; a < 4; ++a) {
+            const C* src = phi + (long long)a * g.nc + col0;
+            C* b = pool[a];
+            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+                const int z = idx / T, t = idx - (idx / T) * T;
+                b[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
+            }
+            __syncthreads();
+            C* r = smem_fft<false>(b, pool[6], pz, T, T, 1, tw);
+            if (r != b) { pool[6] = b; pool[a] = r; }
+        }
+        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) pool[4][idx] = cmake<C>(Real(0), Real(0));
+        for (int a = 4; a < 10; ++a) {
+            const C* src = phi + (long long)a * g.nc + col0;
+            C* W = pool[5];
+            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+                const int z = idx / T, t = idx - (idx / T) * T;
+                W[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
+            }
+            __syncthreads();
+            C* r = smem_fft<false>(W, pool[6], pz, T, T, 1, tw);
+            C* acc = (a < 7) ? pool[4] : pool[3];
+            const int d = (a - 4) % 3;
+            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+                const int kzi = idx / T, t = idx - (idx / T) * T;
+                const int kxi = kx0 + t;
+                Real kd;
+                bool nyq;
+                if (d == 0) { kd = kval<Real>(kxi, g.nx, kfx); nyq = (g.nx % 2 == 0) && (2 * kxi == g.nx); }
+                else if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
+                else { kd = kval<Real>(kzi, g.nz, kfz); nyq = (g.nz % 2 == 0) && (2 * kzi == g.nz); }
+                if (!nyq) {
+                    const C u = r[idx];
+                    acc[idx] = cadd(acc[idx], cmake<C>(kd * u.y, -kd * u.x));    // -i k_d u
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        const int kzi = idx / T, t = idx - (idx / T) * T;
+        const int kxi = kx0 + t;
+        C out[DFT_MAXS + 1];
+        for (int s = 0; s < DFT_MAXS + 1; ++s) out[s] = cmake<C>(Real(0), Real(0));
+        if (hs) {
+            const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+            const C a0 = pool[0][idx], a1 = pool[1][idx], a2 = pool[2][idx], a3 = pool[3][idx], a4 = pool[4][idx];
+            for (int s = 0; s < S; ++s) {
+                Real w0, j3;
+                const Real R = sp.R[s];
+                fmt_weights<Real>(p.kmag, R, &w0, &j3);
+                C mu = cscale(a0, w0);
+                mu = cadd(mu, cscale(a1, R * w0));
+                mu = cadd(mu, cscale(a2, fourpi * R * R * w0));
+                mu = cadd(mu, cscale(a3, fourpi * R * R * R * j3));
+                mu = cadd(mu, cscale(a4, R * R * j3));
+                out[s] = cmake<C>(-mu.x, -mu.y);
+            }
+        }
+        if (es_on && kxi < nxh) {
+            const long long o = (long long)kzi * zstride + col0 + t;
+            for (int s = 0; s < ncomp_out; ++s) {
+                C e = cscale(esA[(long long)s * g.nc + o], wA);
+                if (esB) e = cadd(e, cscale(esB[(long long)s * g.nc + o], wB));
+                if (es_mat) es_mat[(long long)s * g.nc + o] = e;
+                out[s] = cadd(out[s], e);
+            }
+        }
+        for (int s = 0; s < ncomp_out; ++s) pool[s][idx] = cscale(out[s], sp.inv_n);
+    }
+    __syncthreads();
+
+    for (int s = 0; s < ncomp_out; ++s) {
+        C* r = smem_fft<true>(pool[s], pool[5 + (s & 1)], pz, T, T, 1, tw);
+        C* dst = phi + (long long)s * g.nc + col0;
+        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+            const int z = idx / T, t = idx - (idx / T) * T;
+            if (kx0 + t < nxh) dst[z * zstride + t] = r[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Final x pass: one-body correlations c_i (half spectra) -> real space -> Picard map
+//   G_i = rho_bath_i exp(beta mu_HS_bath_i - V_i + c_i)   (0 where V_i = +inf)
+// at rho = w0 rho0 + w1 rho1, with the residual sum_i sum_x ((rho_i - G_i)/rho_bath_i)^2
+// accumulated in FP64.  grid: ceil(ny nz / LR); ceil(S/2) lines per row.
+// rho_out may alias rho0 and g_out may alias rho1 (each point is read before it is written).
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR,
+                                                      const Ctl* __restrict__ ctl,
+                                                      const typename Cplx<Real>::type* __restrict__ cspec,
+                                                      const Real* rho0, const Real* rho1,
+                                                      const Real* __restrict__ V, Real* rho_out, Real* g_out,
+                                                      double* __restrict__ red_sum, int* __restrict__ status,
+                                                      const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double scratch_d[32];
+    const int nx = g.nx, pitch = nx + 1, S = sp.S;
+    const int lpr = (S + 1) / 2;
+    const int lines = lpr * LR;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lines * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long nrows = (long long)g.ny * g.nz;
+    const long long row0 = (long long)blockIdx.x * LR;
+    load_pair_rows<Real>(g, lines, lpr, row0, nrows, S, cspec, nullptr, Real(1), Real(0), nullptr, A);
+    __syncthreads();
+    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
+    double acc = 0.0;
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        const long long row = row0 + r;
+        if (row >= nrows) continue;
+        for (int s = 0; s < S; ++s) {
+            const C pr = R[(r * lpr + s / 2) * pitch + x];
+            const Real c = (s & 1) ? pr.y : pr.x;
+            const long long o = (long long)s * g.n + row * nx + x;
+            Real rho = w0 * rho0[o];
+            if (rho1) rho += w1 * rho1[o];
+            const Real v = V[o];
+            Real gval;
+            if (isinf(v) && v > Real(0)) gval = Real(0);
+            else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
+            if (!isfinite(gval) || !isfinite(rho)) bad = true;
+            const Real e = (rho - gval) * sp.inv_rho_b[s];
+            acc += double(e) * double(e);
+            if (rho_out) rho_out[o] = rho;
+            if (g_out) g_out[o] = gval;
+        }
+    }
+    if (bad) atomicOr(status, DEV_NONFINITE);
+    const double bs = block_sum(acc, scratch_d);
+    if (threadIdx.x == 0) red_sum[blockIdx.x] = bs;
+}
+
+// ------------------------------------------------------------------------------------
+// Plain x inverse of ncomp half spectra to real fields, out[c] = value + offset[c].
+// Optional max of component cmax into red_max.  grid: ceil(ny nz / LR).
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int LR, int ncomp,
+                                                   const typename Cplx<Real>::type* __restrict__ spec,
+                                                   Real* __restrict__ out, Real* __restrict__ out_last,
+                                                   Offsets<Real> off, int cmax,
+                                                   float* __restrict__ red_max,
+                                                   const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float scratch_f[32];
+    const int nx = g.nx, pitch = nx + 1;
+    const int lpr = (ncomp + 1) / 2;
+    const int lines = lpr * LR;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lines * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long nrows = (long long)g.ny * g.nz;
+    const long long row0 = (long long)blockIdx.x * LR;
+    load_pair_rows<Real>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
+    __syncthreads();
+    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    float mx = -CUDART_INF_F;
+    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        const long long row = row0 + r;
+        if (row >= nrows) continue;
+        for (int c = 0; c < ncomp; ++c) {
+            const C pr = R[(r * lpr + c / 2) * pitch + x];
+            const Real v = ((c & 1) ? pr.y : pr.x) + off.v[c];
+            if (out_last && c == ncomp - 1) out_last[row * nx + x] = v;
+            else if (out) out[(long long)c * g.n + row * nx + x] = v;
+            if (c == cmax) mx = fmaxf(mx, float(v));
+        }
+    }
+    if (red_max) {
+        const float bm = block_max(mx, scratch_f);
+        if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
+    }
+}
+
+#ifdef DFT_DEFINE_FINALIZE
+// ------------------------------------------------------------------------------------
+// Line-search bookkeeping on the device (Sec. "Nonlinear solver"), one block.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void set_weights(Ctl* c, double a) {
+    c->wA = 1.0 - a; c->wB = a; c->w0 = 1.0 - a; c->w1 = a;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
+                                                       const float* __restrict__ red_max, int nmax, int op,
+                                                       double inv_count, double alpha_fixed, double n3_bound,
+                                                       double alpha_floor) {
+    __shared__ double scratch_d[32];
+    __shared__ float scratch_f[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nsum; i += blockDim.x) s += red_sum[i];
+    float m = -CUDART_INF_F;
+    for (int i = threadIdx.x; i < nmax; i += blockDim.x) m = fmaxf(m, red_max[i]);
+    const double tot = block_sum(s, scratch_d);
+    const float mx = block_max(m, scratch_f);
+    if (threadIdx.x != 0) return;
+    Ctl* c = ctl;
+    const double f = tot * inv_count;
+    if (op & FIN_IDENTITY) set_weights(c, 0.0);
+    if (op & FIN_F0) {
+        c->f[0] = f;
+        c->resid = sqrt(f);
+        if (!isfinite(f)) c->status |= DEV_NONFINITE;
+    }
+    if (op & FIN_N3CUR) c->n3max_cur = mx;
+    if (op & FIN_AMAX) {
+        c->n3max_next = mx;
+        c->resid_prev = c->resid;
+        const double m0 = c->n3max_cur, m1 = mx;
+        double am = 1.0;
+        if (m1 > m0) am = fmin(1.0, (n3_bound - m0) / (m1 - m0));
+        c->alpha_max = am;
+        c->alpha_fixed = alpha_fixed;
+        if (alpha_fixed >= 0.0) {
+            const double a = fmin(alpha_fixed, am);
+            c->alpha = a;
+            set_weights(c, a);
+        } else {
+            c->sample_alpha[0] = 0.5 * am;
+            set_weights(c, 0.5 * am);
+        }
+    }
+    if (op & FIN_F1) {
+        c->f[1] = f;
+        c->sample_alpha[1] = c->alpha_max;
+        set_weights(c, c->alpha_max);
+    }
+    if (op & FIN_F2_CHOOSE) {
+        c->f[2] = f;
+        const double am = c->alpha_max, a = 0.5 * am;
+        const double f0 = c->f[0], f1 = c->f[1], f2 = f;
+        const double c2 = (f0 - 2.0 * f1 + f2) / (2.0 * a * a);
+        const double c1 = (-3.0 * f0 + 4.0 * f1 - f2) / (2.0 * a);
+        double al;
+        if (c2 > 0.0) al = fmin(fmax(-c1 / (2.0 * c2), alpha_floor * am), am);
+        else al = (f1 <= f2) ? a : am;
+        c->alpha = al;
+        set_weights(c, al);
+    }
+    if (op & FIN_ACCEPT) {
+        c->f[3] = f;
+        c->f[0] = f;
+        c->resid = sqrt(f);
+        c->n3max_cur = mx;
+        c->iter += 1;
+        if (!isfinite(f)) c->status |= DEV_NONFINITE;
+    }
+}
+
+#endif  // DFT_DEFINE_FINALIZE
+
+}  // namespace dftk

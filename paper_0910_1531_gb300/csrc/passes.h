@@ -1,0 +1,42 @@
+// Host-side launchers of the pass kernels, instantiated for float (kernels_f32.cu) and
+// double (kernels_f64.cu).  Each launcher sizes its grid from the grid descriptor and
+// the tile parameters and queues one kernel on `st`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+template <typename Real>
+struct Passes {
+    using C = typename Cplx<Real>::type;
+    static cudaError_t init_attributes();
+    // dynamic shared memory of an x pass with `lines` lines and of a column pass with nbuf tiles
+    static size_t smem_x(int nx, int lines) { return (size_t(nx) + 2 * size_t(lines) * (nx + 1)) * sizeof(C) + 16; }
+    static size_t smem_col(int n, int T, int nbuf) { return (size_t(n) + size_t(nbuf) * T * n) * sizeof(C) + 16; }
+
+    static void xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+                     C* out, const C* tw);
+    static void yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
+                     const C* tw);
+    static void zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+                          Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
+                          const C* tw);
+    static void xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+                     const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
+    static void zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+                          Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
+                          const C* esA, const C* esB, C* es_mat, const C* tw);
+    static void xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+                        const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
+                        Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
+    static void xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+};
+
+cudaError_t finalize_init_attributes();
+void launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
+                     int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor);
+
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
