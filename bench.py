@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT/Picard classical-DFT hot path on GB300.
+
+A step is one Picard iteration with the quadratic line search (three residual
+evaluations sharing one weighted-density pass) on the 128^3,
+three-species workload with 16 seeded hard obstacles, inputs resident in HBM.
+Prints one JSON line.  Usage:
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path does not shard; no collective on the data path); the value is the
+sum of iterations over ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Picard iterations/s and FFT-conv HBM GB/s at 128³–256³ (FP32 vs FP64 GPU)"
+UNIT = "Picard iterations/s"
+L2_BYTES = 129e6
+FALLBACK_HBM_GBS = 6800.0
+KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
+
+# DRAM traffic per launch (bytes) of the kernels measured by ncu on this workload, keyed by
+# kernel name, with the source digest of csrc/ at capture time; None until captured.
+NCU_TRAFFIC = None
+
+
+def workload(n=128):
+    from paper_0910_1531_gb300 import workloads
+    return workloads.obstacles_3species(n=n, h=0.05 * 128 / n, seed=1)
+
+
+def csrc_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0910_1531_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def blas_threads():
+    """Threads numpy's BLAS uses (best effort), else the CPU count."""
+    try:
+        import ctypes
+        with open("/proc/self/maps") as fh:
+            libs = sorted({ln.split()[-1] for ln in fh if "openblas" in ln.lower() and ln.strip().endswith(".so")})
+        for lib in libs:
+            dl = ctypes.CDLL(lib)
+            for sym in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_", "openblas_get_num_threads"):
+                if hasattr(dl, sym):
+                    return int(getattr(dl, sym)())
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while kernels run."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "50"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(w, prob=None):
+    """Time one G evaluation and one weighted-density evaluation of the oracle on the full
+    workload; a line-search iteration of the oracle costs 3 G + 2 weighted densities."""
+    import numpy as np
+    from oracle import functional as F
+    if prob is None:
+        prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    t0 = time.perf_counter()
+    F.picard_map(prob, rho, w.V)
+    t1 = time.perf_counter()
+    F.weighted_densities(prob, rho)
+    t2 = time.perf_counter()
+    t_it = 3 * (t1 - t0) + 2 * (t2 - t1)
+    return prob, t1 - t0, t2 - t1, t_it
+
+
+def run_reference(args):
+    world, rank, _ = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if rank != 0:
+        return 0
+    w = workload(args.n)
+    prob = None
+    for _ in range(args.warmup):
+        prob, *_ = oracle_sample(w, prob)
+    t_its, t_g, t_wd = [], [], []
+    for _ in range(args.steps):
+        prob, tg, twd, tit = oracle_sample(w, prob)
+        t_its.append(tit)
+        t_g.append(tg)
+        t_wd.append(twd)
+    mean_it = sum(t_its) / len(t_its)
+    value = 1.0 / mean_it
+    cores = blas_threads()
+    sample = (f"per step one oracle G(rho) ({sum(t_g)/len(t_g):.2f} s) and one weighted-density evaluation "
+              f"({sum(t_wd)/len(t_wd):.2f} s) on the full {w.shape[0]}^3 workload; iteration time = 3 G + 2 WD")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_it * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
+                       "oracle": "plain FP64 numpy, explicit per-axis DFT matrices (no FFT library)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_0910_1531_gb300 import binding, build
+
+    world, rank, local = dist_setup()
+    build.build()
+    torch.cuda.set_device(local)
+    w = workload(args.n)
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=args.precision)
+    dt = plan.dtype
+    rho_b = plan.bulk()["rho"]
+    rho0 = w.initial_rho_nm3(rho_b)
+    rho = torch.tensor(rho0, dtype=dt, device="cuda")
+    V = torch.tensor(w.V, dtype=dt, device="cuda")
+    S, N = w.nspecies, int(np.prod(w.shape))
+    elem = 8 if args.precision == "fp64" else 4
+    nc = w.shape[0] * w.shape[1] * (w.shape[2] // 2 + 1)
+    working_set = (2 * (10 + S + 1) + 10) * nc * 2 * elem + 3 * S * N * elem
+
+    plan.iter_begin(rho, V)
+    for _ in range(args.warmup):
+        plan.iter_step(rho, V, -1.0, sync=False)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    # warm the sampler window with a few untimed iterations
+    for _ in range(max(1, args.warmup)):
+        plan.iter_step(rho, V, -1.0, sync=False)
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    plan.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.iter_step(rho, V, -1.0, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    prof = {k: plan.profile_read(k) for k in KERNELS}
+    plan.profile_enable(False)
+    resid_after, alpha_after = plan.iter_step(rho, V, -1.0, sync=True)
+    value = args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    peak, peak_kind = measured_peaks()
+    dom = max((k for k in KERNELS if k != "finalize"), key=lambda k: prof[k][1])
+    n_l, t_ms, by = prof[dom]
+    achieved = by / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+    traffic = None
+    if NCU_TRAFFIC and NCU_TRAFFIC.get("digest") == csrc_digest():
+        traffic = NCU_TRAFFIC["per_launch"].get(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": by / max(n_l, 1), "ms_per_launch": t_ms / max(n_l, 1)}
+    total_kernel_ms = sum(prof[k][1] for k in KERNELS)
+    kernels = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 4),
+                   "share": round(prof[k][1] / total_kernel_ms, 4) if total_kernel_ms else None,
+                   "GBps": round(prof[k][2] / (prof[k][1] * 1e-3) / 1e9, 1) if prof[k][1] > 0 else None}
+               for k in KERNELS}
+    launches = sum(prof[k][0] for k in KERNELS)
+
+    # end to end: public host-buffer entry point, pinned buffers, copies inside the timed region
+    rho_h = torch.tensor(rho0, dtype=dt).pin_memory()
+    V_h = torch.tensor(w.V, dtype=dt).pin_memory()
+    plan.picard_step_host(rho_h, V_h, -1.0)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.picard_step_host(rho_h, V_h, -1.0)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, world)
+    e2e = {"value": args.e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * S * N * elem,
+           "d2h_bytes_per_step": S * N * elem,
+           "note": "dft_picard_step_host: H2D rho+V, G(rho) and one line-search iteration, D2H rho"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, tg, twd, tit = oracle_sample(w)
+        cpu = {"value": 1.0 / tit, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"one oracle G(rho) ({tg:.2f} s) + one weighted-density evaluation ({twd:.2f} s) on the "
+                         f"same {w.shape[0]}^3 workload on the host cores; iteration = 3 G + 2 WD"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
+                           "bulk_molar": list(map(float, w.bulk_molar)), "obstacles": 16, "seed": 1,
+                           "precision": "FP32 fields, FP64 log(1-n3)/(1-n3)^-m, residual and line-search sums"
+                           if args.precision == "fp32" else "all FP64",
+                           "step": "one Picard iteration with quadratic line search (dft_iter_step)",
+                           "parallelism": f"replicas x{world}",
+                           "l2": f"no flush: working set {working_set/1e6:.0f} MB > L2 129 MB",
+                           "resid_after": resid_after},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu, "kernels": kernels}
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -169,12 +169,15 @@ dft_status dft_picard_step_host(dft_plan* plan, void* rho_host, const void* V_ho
  * Per-kernel timing with CUDA events recorded on the plan's stream around
  * each launch.  enable != 0 starts collection (and clears totals).
  * dft_profile_read returns, for the kernel kind named by `name`, the number
- * of launches and their total duration (ms) since the last enable; it
+ * of launches, their total duration (ms) and their total algorithmic global
+ * memory traffic (bytes: every input element read once and every output
+ * element written once by each launch) since the last enable; it
  * synchronises the stream.  Names: "xfwd", "yfft", "zconv_fwd", "xphi",
- * "zconv_bwd", "xupdate", "xinv", "finalize".
+ * "zconv_bwd", "xupdate", "xinv", "finalize".  Any out pointer may be NULL.
  */
 dft_status dft_profile_enable(dft_plan* plan, int enable);
-dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, double* total_ms);
+dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, double* total_ms,
+                            double* total_bytes);
 
 /* Library version string. */
 const char* dft_version(void);

@@ -65,7 +65,7 @@ SIGNATURES = {
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_profile_enable": (_I, [_P, _I]),
-    "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD]),
+    "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
 }
 
@@ -232,9 +232,11 @@ class Plan:
         self._check(self.lib.dft_profile_enable(self.handle, 1 if enable else 0))
 
     def profile_read(self, name):
-        n, ms = _I(), _D()
-        self._check(self.lib.dft_profile_read(self.handle, name.encode(), ctypes.byref(n), ctypes.byref(ms)))
-        return n.value, ms.value
+        """(launches, total ms, total algorithmic bytes) of one kernel kind since profile_enable."""
+        n, ms, by = _I(), _D(), _D()
+        self._check(self.lib.dft_profile_read(self.handle, name.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                              ctypes.byref(by)))
+        return n.value, ms.value, by.value
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

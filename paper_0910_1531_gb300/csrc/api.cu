@@ -24,6 +24,7 @@ std::string g_create_error;
 
 struct ProfRec {
     int kind;
+    double bytes;
     cudaEvent_t a, b;
 };
 
@@ -61,6 +62,7 @@ struct dft_plan {
     size_t ev_used = 0;
     int prof_launches[K_COUNT] = {0};
     double prof_ms[K_COUNT] = {0};
+    double prof_bytes[K_COUNT] = {0};
     std::string err;
     bool iter_ready = false;
     const void* iter_rho = nullptr;
@@ -172,8 +174,9 @@ cudaEvent_t take_event(dft_plan* p) {
 struct Prof {
     dft_plan* p;
     int kind;
+    double bytes;
     cudaEvent_t a = nullptr;
-    Prof(dft_plan* pp, int k) : p(pp), kind(k) {
+    Prof(dft_plan* pp, int k, double by) : p(pp), kind(k), bytes(by) {
         if (p->prof) {
             a = take_event(p);
             cudaEventRecord(a, p->stream);
@@ -183,10 +186,14 @@ struct Prof {
         if (p->prof) {
             cudaEvent_t b = take_event(p);
             cudaEventRecord(b, p->stream);
-            p->recs.push_back({kind, a, b});
+            p->recs.push_back({kind, bytes, a, b});
         }
     }
 };
+
+// bytes of one complex half-spectrum component and of one real field component
+double CB(const dft_plan* p) { return double(p->g.nc) * double(p->csize); }
+double RB(const dft_plan* p) { return double(p->g.n) * double(p->rsize); }
 
 void collect_profile(dft_plan* p) {
     if (p->recs.empty()) return;
@@ -196,16 +203,19 @@ void collect_profile(dft_plan* p) {
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             p->prof_launches[r.kind] += 1;
             p->prof_ms[r.kind] += ms;
+            p->prof_bytes[r.kind] += r.bytes;
         }
     }
     p->recs.clear();
     p->ev_used = 0;
 }
 
-#define LAUNCH(p, kind, call)                                                                 \
+// Queue one kernel; `bytes` is its algorithmic global traffic (each input element read once,
+// each output element written once), accumulated by the profiler.
+#define LAUNCH(p, kind, bytes, call)                                                          \
     do {                                                                                      \
         {                                                                                     \
-            Prof _pr((p), (kind));                                                            \
+            Prof _pr((p), (kind), double(bytes));                                             \
             call;                                                                             \
         }                                                                                     \
         cudaError_t _e = cudaGetLastError();                                                  \
@@ -231,11 +241,11 @@ template <typename Real> struct Ops {
     // bulk-fluid / Poisson spectra (kx, ky, kz)
     static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
-        LAUNCH(p, K_XFWD, P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
-        LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
-        LAUNCH(p, K_ZFWD, P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
+        LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_ZFWD, (p->S + DFT_NCOMP + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
                                        T1(p), slot_n(slot), slot_es(p, slot), tw(p, 2)));
-        LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), tw(p, 1)));
         return DFT_OK;
     }
 
@@ -247,13 +257,16 @@ template <typename Real> struct Ops {
         C* B = use_B ? slot_n(p->slotB) : nullptr;
         C* esA = slot_es(p, p->slotA);
         C* esB = use_B ? slot_es(p, p->slotB) : nullptr;
-        LAUNCH(p, K_XPHI, P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
+        LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NCOMP * CB(p),
+               P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
                                   p->red_max, &p->ctl->status, tw(p, 0)));
-        LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), tw(p, 1)));
-        LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), tw(p, 1)));
+        LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
+               P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
                                        p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
-        LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
-        LAUNCH(p, K_XUPD, P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0))),
+               P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
                                      g_out, p->red_sum, &p->ctl->status, tw(p, 0)));
         return DFT_OK;
     }
@@ -266,7 +279,7 @@ template <typename Real> struct Ops {
         for (int c = 0; c < DFT_NCOMP + 2; ++c) off.v[c] = Real(0);
         if (offs)
             for (int c = 0; c < ncomp; ++c) off.v[c] = Real(offs[c]);
-        LAUNCH(p, K_XINV, P::xinv(p->stream, p->g, p->ax, LR, ncomp, spec, out, out_last, off, cmax, red_max,
+        LAUNCH(p, K_XINV, ncomp * (CB(p) + (out || out_last ? RB(p) : 0.0)), P::xinv(p->stream, p->g, p->ax, LR, ncomp, spec, out, out_last, off, cmax, red_max,
                                   tw(p, 0)));
         if (blocks_out) *blocks_out = (int)p->blocks_x(LR);
         return DFT_OK;
@@ -275,7 +288,7 @@ template <typename Real> struct Ops {
 
 dft_status finalize(dft_plan* p, int op, int nsum, int nmax, double alpha_fixed) {
     const double inv_count = 1.0 / (double(p->S) * double(p->g.n));
-    LAUNCH(p, K_FIN, launch_finalize(p->stream, p->ctl, p->red_sum, nsum, p->red_max, nmax, op, inv_count,
+    LAUNCH(p, K_FIN, nsum * 8.0 + nmax * 4.0, launch_finalize(p->stream, p->ctl, p->red_sum, nsum, p->red_max, nmax, op, inv_count,
                                      alpha_fixed, kN3Bound, kAlphaFloor));
     return DFT_OK;
 }
@@ -350,12 +363,12 @@ template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* 
     const SpeciesDesc<Real>& sp = species<Real>(p);
     TRY(O::first_half(p, rho, p->slotA, 0));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
-    LAUNCH(p, K_XPHI, P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
+    LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
                               O::T1(p), p->red_max, &p->ctl->status, O::tw(p, 0)));
-    LAUNCH(p, K_YFFT, P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), O::tw(p, 1)));
-    LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
+    LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), O::tw(p, 1)));
     TRY(O::xinv(p, p->S, O::T1(p), c1, nullptr, nullptr, -1, nullptr, nullptr));
     return DFT_OK;
 }
@@ -368,9 +381,9 @@ template <typename Real> dft_status c1_es_t(dft_plan* p, const Real* rho, Real* 
     const int nout = p->S + want_psi;
     TRY(O::first_half(p, rho, p->slotA, want_psi));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
-    LAUNCH(p, K_ZBWD, P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 2, nout,
+    LAUNCH(p, K_ZBWD, 2.0 * nout * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 2, nout,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (nout) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), O::tw(p, 1)));
     double offs[DFT_NCOMP + 2] = {0};
     for (int s = 0; s < p->S; ++s) offs[s] = -p->bath.mu_es[s];
     TRY(O::xinv(p, nout, O::T1(p), c1, psi, offs, -1, nullptr, nullptr));
@@ -682,12 +695,13 @@ dft_status dft_profile_enable(dft_plan* p, int enable) {
     for (int k = 0; k < K_COUNT; ++k) {
         p->prof_launches[k] = 0;
         p->prof_ms[k] = 0.0;
+        p->prof_bytes[k] = 0.0;
     }
     p->prof = enable != 0;
     return DFT_OK;
 }
 
-dft_status dft_profile_read(dft_plan* p, const char* name, int* launches, double* total_ms) {
+dft_status dft_profile_read(dft_plan* p, const char* name, int* launches, double* total_ms, double* total_bytes) {
     TRY(check_plan(p));
     if (!name) return fail(p, DFT_EINVAL, "NULL name");
     collect_profile(p);
@@ -695,6 +709,7 @@ dft_status dft_profile_read(dft_plan* p, const char* name, int* launches, double
         if (std::strcmp(name, kKindNames[k]) == 0) {
             if (launches) *launches = p->prof_launches[k];
             if (total_ms) *total_ms = p->prof_ms[k];
+            if (total_bytes) *total_bytes = p->prof_bytes[k];
             return DFT_OK;
         }
     }

@@ -197,7 +197,9 @@ def test_profile_counts_launches():
     plan = plan_for(prob, "fp32")
     plan.profile_enable(True)
     plan.picard_map(to_dev(rho, plan), to_dev(V, plan))
-    n, ms = plan.profile_read("xphi")
+    n, ms, by = plan.profile_read("xphi")
     assert n == 1 and ms > 0
-    n, ms = plan.profile_read("yfft")
+    nc = 16 * 16 * 9
+    assert by == 2 * 10 * nc * 8
+    n, ms, by = plan.profile_read("yfft")
     assert n == 4
