@@ -30,6 +30,8 @@
 #ifndef GB300DFT_H
 #define GB300DFT_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -178,6 +180,40 @@ dft_status dft_picard_step_host(dft_plan* plan, void* rho_host, const void* V_ho
 dft_status dft_profile_enable(dft_plan* plan, int enable);
 dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, double* total_ms,
                             double* total_bytes);
+
+/*
+ * Allocation-free weighted densities.  The paper has no counterpart: this is a
+ * deployment variant of dft_weighted_densities for callers that cannot allocate
+ * device memory -- code running inside a memory pool whose owner has reserved the
+ * GPU's memory and forbids cudaMalloc, code that must not trigger the implicit
+ * device synchronisation an allocation can cause, and users who must know their
+ * whole device footprint when the library loads.  It computes exactly what
+ * dft_weighted_densities computes, with the same kernels, but needs no plan: all
+ * of its scratch (twiddles, spectra, weighted densities) lives in one file-scope
+ * device array of DFT_NOALLOC_SCRATCH_BYTES that every GPU loading this part of
+ * the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * params: as for dft_plan_create; precision must be DFT_FP32_STAB; only the
+ *   grid and the radii are used (the weighted densities need no bath).
+ * cuda_stream: cudaStream_t for all work (NULL = legacy default stream).
+ * rho: [S][N] float device input; n_out: [10][N] float device output.
+ * errbuf/errbuf_len: optional buffer for a one-line error text (may be NULL).
+ * Limits: a grid and species count whose scratch exceeds
+ *   DFT_NOALLOC_SCRATCH_BYTES is rejected with DFT_EINVAL and a message naming the
+ *   bytes needed (64^3 fits with up to 5 species; 96^3 does not).
+ * Set-up: the first call on each device looks up the device address of the
+ *   scratch array (and sets the kernels' shared-memory limits) with that device
+ *   current; make that first call before any CUDA stream capture.
+ * Sharing: every call on a device uses the same array and leaves its contents
+ *   behind; each call writes every scratch element before reading it, so nothing
+ *   needs clearing, but calls whose work overlaps on the GPU (different streams,
+ *   or host threads without ordering) race on the array and corrupt each other.
+ *   Order the calls (one stream, or events) to keep them apart.
+ */
+#define DFT_NOALLOC_SCRATCH_BYTES (24u << 20)
+dft_status dft_weighted_densities_noalloc(const dft_params* params, void* cuda_stream, const void* rho,
+                                          void* n_out, char* errbuf, size_t errbuf_len);
 
 /* Library version string. */
 const char* dft_version(void);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dft_profile_enable": (_I, [_P, _I]),
     "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
+    "dft_weighted_densities_noalloc": (_I, [ctypes.POINTER(DftParams), _P, _P, _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 

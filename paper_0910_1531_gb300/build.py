@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libgb300dft.so"
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "api.cu", "bulk.cpp"]
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "api.cu", "bulk.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
