@@ -16,7 +16,12 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libgb300dft.so"
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "api.cu", "bulk.cpp", "noalloc.cu"]
+# (source, object name, extra defines); kinst.cu is compiled once per (precision, axis length)
+CT_SIZES = (0, 32, 48, 64, 96, 128, 256)
+SOURCES = ([("api.cu", "api", []), ("bulk.cpp", "bulk", []), ("noalloc.cu", "noalloc", []),
+            ("dispatch.cu", "dispatch", [])]
+           + [("kinst.cu", f"kinst_{r}_{n}", [f"-DDFT_INST_REAL={r}", f"-DDFT_INST_N={n}"])
+              for r in ("float", "double") for n in CT_SIZES])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,10 +51,11 @@ def up_to_date():
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(entry, extra):
+    src, name, defines = entry
+    obj = os.path.join(BUILD, name + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
-           "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH + extra
+           "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH + defines + extra
     if src.endswith(".cpp"):
         cmd += ["-x", "c++"]
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,7 +69,8 @@ def build(force=False, verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     if not force and up_to_date():
         return lib_path()
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(2, min(len(SOURCES), os.cpu_count() or 4))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
     objs = [r[0] for r in results]
     if verbose:

@@ -97,12 +97,6 @@ bool valid_n(int n) {
     return m == 1;
 }
 
-int pick_tile(int n, size_t csize, int nbuf, size_t budget) {
-    for (int T = 16; T >= 1; T /= 2)
-        if ((size_t(n) + size_t(nbuf) * T * n) * csize + 16 <= budget) return T;
-    return 1;
-}
-
 int pick_lines(int nx, size_t csize, int lines_per_unit, size_t budget, int cap) {
     const long long avail = (long long)(budget / csize) - nx;
     long long L = avail / (2LL * (nx + 1) * lines_per_unit);
@@ -468,8 +462,8 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     const bool f64 = prm->precision == DFT_FP64;
     p->csize = f64 ? sizeof(double2) : sizeof(float2);
     p->rsize = f64 ? sizeof(double) : sizeof(float);
-    p->Ty = pick_tile(g.ny, p->csize, 2, 100 * 1024);
-    p->Tz = pick_tile(g.nz, p->csize, 7, 112 * 1024);
+    p->Ty = f64 ? Passes<double>::tile_y(g.ny, 100 * 1024) : Passes<float>::tile_y(g.ny, 100 * 1024);
+    p->Tz = f64 ? Passes<double>::tile_z(g.nz, 112 * 1024) : Passes<float>::tile_z(g.nz, 112 * 1024);
     p->LX = pick_lines(g.nx, p->csize, 1, 48 * 1024, 32);
     p->LRphi = pick_lines(g.nx, p->csize, 5, 64 * 1024, 16);
     p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, 48 * 1024, 16);

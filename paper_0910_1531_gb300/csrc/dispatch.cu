@@ -1,0 +1,115 @@
+// Passes<Real>: dispatch on the axis length to the compile-time or run-time kernels, and the
+// line-search bookkeeping kernel.
+#define DFT_DEFINE_FINALIZE
+#include "kernels.cuh"
+#include "passes.h"
+
+#define DFT_DECLARE_EXTERN(N)                      \
+    extern template struct LaunchX<float, N>;      \
+    extern template struct LaunchY<float, N>;      \
+    extern template struct LaunchZ<float, N>;      \
+    extern template struct LaunchX<double, N>;     \
+    extern template struct LaunchY<double, N>;     \
+    extern template struct LaunchZ<double, N>;
+DFT_CT_SIZES(DFT_DECLARE_EXTERN)
+DFT_DECLARE_EXTERN(0)
+
+#define DFT_CASE(N, L, call) case N: L<Real, N>::call; break;
+#define DFT_SWITCH_X(n, call) switch (n) { \
+    case 32: LaunchX<Real, 32>::call; break; case 48: LaunchX<Real, 48>::call; break; \
+    case 64: LaunchX<Real, 64>::call; break; case 96: LaunchX<Real, 96>::call; break; \
+    case 128: LaunchX<Real, 128>::call; break; case 256: LaunchX<Real, 256>::call; break; \
+    default: LaunchX<Real, 0>::call; }
+#define DFT_SWITCH_Y(n, call) switch (n) { \
+    case 32: LaunchY<Real, 32>::call; break; case 48: LaunchY<Real, 48>::call; break; \
+    case 64: LaunchY<Real, 64>::call; break; case 96: LaunchY<Real, 96>::call; break; \
+    case 128: LaunchY<Real, 128>::call; break; case 256: LaunchY<Real, 256>::call; break; \
+    default: LaunchY<Real, 0>::call; }
+#define DFT_SWITCH_Z(n, call) switch (n) { \
+    case 32: LaunchZ<Real, 32>::call; break; case 48: LaunchZ<Real, 48>::call; break; \
+    case 64: LaunchZ<Real, 64>::call; break; case 96: LaunchZ<Real, 96>::call; break; \
+    case 128: LaunchZ<Real, 128>::call; break; case 256: LaunchZ<Real, 256>::call; break; \
+    default: LaunchZ<Real, 0>::call; }
+
+template <typename Real>
+cudaError_t Passes<Real>::init_attributes() {
+    cudaError_t e = cudaSuccess, r;
+#define DFT_INIT(N) \
+    if ((r = LaunchX<Real, N>::init()) != cudaSuccess) e = r; \
+    if ((r = LaunchY<Real, N>::init()) != cudaSuccess) e = r; \
+    if ((r = LaunchZ<Real, N>::init()) != cudaSuccess) e = r;
+    DFT_CT_SIZES(DFT_INIT)
+    DFT_INIT(0)
+#undef DFT_INIT
+    return e;
+}
+
+template <typename Real>
+int Passes<Real>::tile_y(int n, size_t budget) {
+    if (dft_is_ct_size(n)) return dft_tile_y<Real>(n);
+    for (int T = 16; T >= 1; T /= 2)
+        if (smem_col(n, T, 2) <= budget) return T;
+    return 1;
+}
+
+template <typename Real>
+int Passes<Real>::tile_z(int n, size_t budget) {
+    if (dft_is_ct_size(n)) return dft_tile_z<Real>(n);
+    for (int T = 16; T >= 1; T /= 2)
+        if (smem_col(n, T, 7) <= budget) return T;
+    return 1;
+}
+
+template <typename Real>
+void Passes<Real>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+                        C* out, const C* tw) {
+    DFT_SWITCH_X(g.nx, xfwd(st, g, px, ncomp, lx, in, out, tw))
+}
+
+template <typename Real>
+void Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
+                        const C* tw) {
+    DFT_SWITCH_Y(g.ny, yfft(st, inv, g, py, T, ncomp, data, tw))
+}
+
+template <typename Real>
+void Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+                             int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
+                             const C* tw) {
+    DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw))
+}
+
+template <typename Real>
+void Passes<Real>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+                        const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
+    DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, tw))
+}
+
+template <typename Real>
+void Passes<Real>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+                             int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
+                             const C* esA, const C* esB, C* es_mat, const C* tw) {
+    DFT_SWITCH_Z(g.nz, zconv_bwd(st, g, pz, sp, T, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw))
+}
+
+template <typename Real>
+void Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+                           const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
+                           Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw) {
+    DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw))
+}
+
+template <typename Real>
+void Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+                        Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw) {
+    DFT_SWITCH_X(g.nx, xinv(st, g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw))
+}
+
+template struct Passes<float>;
+template struct Passes<double>;
+
+void launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
+                     int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor) {
+    dftk::k_finalize<<<1, dftk::kThreads, 0, st>>>(ctl, red_sum, nsum, red_max, nmax, op, inv_count, alpha_fixed,
+                                                  n3_bound, alpha_floor);
+}

@@ -154,3 +154,82 @@ __device__ C* smem_fft(C* a, C* b, const AxisPlan& p, int lines, int es, int ls,
     }
     return a;
 }
+
+// ------------------------------------------------------------------------------------
+// Compile-time transforms.  The same Stockham stages with the length, the radix plan and
+// (for column tiles) the tile width known at compile time, so that index arithmetic is by
+// constants and every loop unrolls.  Radix plan of n: the factors 3 first, then 16s, then
+// one of 2/4/8 -- the same order as the run-time AxisPlan.
+// ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int ct_radix_at(int n, int s) {
+    int m = n, k = 0;
+    while (m % 3 == 0) { if (k == s) return 3; m /= 3; ++k; }
+    while (m >= 16 && m % 16 == 0) { if (k == s) return 16; m /= 16; ++k; }
+    if (m > 1) { if (k == s) return m; ++k; }
+    return 0;
+}
+__host__ __device__ constexpr int ct_nstages(int n) { int s = 0; while (ct_radix_at(n, s) != 0) ++s; return s; }
+__host__ __device__ constexpr int ct_ns_at(int n, int s) { int p = 1; for (int i = 0; i < s; ++i) p *= ct_radix_at(n, i); return p; }
+
+constexpr int kFftThreads = 256;
+
+// One stage.  COLS: lines are tile columns (element e of line l at e*T + l, line index fastest
+// across threads); otherwise lines are rows (element e of line l at e + l*ls, e fastest).
+template <int N, int R, int NS, bool INV, bool COLS, int T, typename C>
+__device__ __forceinline__ void ct_stage(const C* __restrict__ src, C* __restrict__ dst, int lines, int ls,
+                                         const C* __restrict__ tw) {
+    constexpr int M = N / R;
+    constexpr int TWSTEP = N / (NS * R);
+    const int total = COLS ? M * T : M * lines;
+#pragma unroll 2
+    for (int task = threadIdx.x; task < total; task += kFftThreads) {
+        int line, j;
+        if constexpr (COLS) { line = task % T; j = task / T; }
+        else { j = task % M; line = task / M; }
+        const int k = j % NS;
+        const int off = COLS ? line : line * ls;
+        constexpr int ES = COLS ? T : 1;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * M) * ES + off];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[k * r * TWSTEP];
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_small<R, INV>(v);
+        const int base = (j / NS) * (NS * R) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(base + r * NS) * ES + off] = v[r];
+    }
+}
+
+template <int N, bool INV, bool COLS, int T, int S, typename C>
+__device__ __forceinline__ void ct_stages(C*& a, C*& b, int lines, int ls, const C* tw) {
+    if constexpr (S < ct_nstages(N)) {
+        constexpr int R = ct_radix_at(N, S);
+        constexpr int NS = ct_ns_at(N, S);
+        ct_stage<N, R, NS, INV, COLS, T>(a, b, lines, ls, tw);
+        __syncthreads();
+        C* t = a; a = b; b = t;
+        ct_stages<N, INV, COLS, T, S + 1>(a, b, lines, ls, tw);
+    }
+}
+
+// Compile-time counterpart of smem_fft (same contract).  COLS with tile width T, or rows
+// with `lines` rows of pitch ls.
+template <int N, bool INV, bool COLS, int T, typename C>
+__device__ __forceinline__ C* ct_fft(C* a, C* b, int lines, int ls, const C* tw) {
+    ct_stages<N, INV, COLS, T, 0>(a, b, lines, ls, tw);
+    return a;
+}
+
+// Length-generic front end: N > 0 uses the compile-time stages, N == 0 the run-time plan.
+template <int N, bool INV, bool COLS, int T, typename C>
+__device__ __forceinline__ C* any_fft(C* a, C* b, const AxisPlan& p, int lines, int es, int ls, const C* tw) {
+    if constexpr (N > 0) return ct_fft<N, INV, COLS, T>(a, b, lines, ls, tw);
+    else return smem_fft<INV>(a, b, p, lines, es, ls, tw);
+}

@@ -149,19 +149,67 @@ template <typename C> __device__ __forceinline__ C* align_ptr(unsigned char* p) 
     return reinterpret_cast<C*>(u);
 }
 
+// Copy a column tile (n rows of T complex, global row stride rs, columns t < valid) between
+// global and shared memory ([e][t] layout).  TT/NN > 0: compile-time tile, loads batched in
+// registers so that all of a thread's loads are in flight together.
+template <int TT, int NN, typename C>
+__device__ __forceinline__ void tile_load(C* __restrict__ dst, const C* __restrict__ src, long long rs, int valid,
+                                          int T, int n) {
+    if constexpr (TT > 0 && NN > 0) {
+        constexpr int TOTAL = TT * NN;
+        constexpr int PER = (TOTAL + kThreads - 1) / kThreads;
+        C tmp[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            const int e = idx / TT, t = idx % TT;
+            tmp[i] = cmake<C>(0, 0);
+            if ((TOTAL % kThreads == 0 || idx < TOTAL) && t < valid) tmp[i] = src[e * rs + t];
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (TOTAL % kThreads == 0 || idx < TOTAL) dst[idx] = tmp[i];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < T * n; idx += blockDim.x) {
+            const int e = idx / T, t = idx - (idx / T) * T;
+            dst[idx] = (t < valid) ? src[e * rs + t] : cmake<C>(0, 0);
+        }
+    }
+}
+
+template <int TT, int NN, typename C>
+__device__ __forceinline__ void tile_store(C* __restrict__ dst, const C* __restrict__ src, long long rs, int valid,
+                                           int T, int n) {
+    if constexpr (TT > 0 && NN > 0) {
+        constexpr int TOTAL = TT * NN;
+#pragma unroll
+        for (int idx = threadIdx.x; idx < TOTAL; idx += kThreads) {
+            const int e = idx / TT, t = idx % TT;
+            if (t < valid) dst[e * rs + t] = src[idx];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < T * n; idx += blockDim.x) {
+            const int e = idx / T, t = idx - (idx / T) * T;
+            if (t < valid) dst[e * rs + t] = src[idx];
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // x pass, forward: S real fields -> half spectra.  Two real rows a, b are packed as a + i b
 // into one complex transform of length nx and separated afterwards:
 //   X_a[k] = (Z[k] + conj Z[-k]) / 2,  X_b[k] = (Z[k] - conj Z[-k]) / (2 i).
 // ------------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int NX>
 __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int ncomp, int lx,
                                                    const Real* __restrict__ in,
                                                    typename Cplx<Real>::type* __restrict__ out,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
     C* B = A + lx * pitch;
@@ -176,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
         A[l * pitch + x] = cmake<C>(a, b);
     }
     __syncthreads();
-    C* R = smem_fft<false>(A, B, px, lx, 1, pitch, tw);
+    C* R = any_fft<NX, false, false, 0>(A, B, px, lx, 1, pitch, tw);
     for (int idx = threadIdx.x; idx < lx * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
         const long long ra = 2 * (pair0 + l), rb = ra + 1;
@@ -193,29 +241,24 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
 // y pass: in-place transform of ncomp half spectra along y, tiles of T kx columns.
 // grid (ceil(nxh/T), nz, ncomp)
 // ------------------------------------------------------------------------------------
-template <typename Real, bool INV>
-__global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int T,
+template <typename Real, bool INV, int NY, int TY>
+__global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int Trt,
                                                    typename Cplx<Real>::type* __restrict__ data,
                                                    const typename Cplx<Real>::type* __restrict__ twy) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int ny = g.ny, nxh = g.nxh;
+    const int ny = NY > 0 ? NY : g.ny, nxh = g.nxh;
+    const int T = TY > 0 ? TY : Trt;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + ny;
     C* B = A + T * ny;
     for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = twy[i];
     const int kx0 = blockIdx.x * T;
     C* base = data + (long long)blockIdx.z * g.nc + (long long)blockIdx.y * ny * nxh + kx0;
-    for (int idx = threadIdx.x; idx < T * ny; idx += blockDim.x) {
-        const int y = idx / T, t = idx - (idx / T) * T;
-        A[idx] = (kx0 + t < nxh) ? base[(long long)y * nxh + t] : cmake<C>(Real(0), Real(0));
-    }
+    tile_load<TY, NY>(A, base, nxh, nxh - kx0, T, ny);
     __syncthreads();
-    C* R = smem_fft<INV>(A, B, py, T, T, 1, tw);
-    for (int idx = threadIdx.x; idx < T * ny; idx += blockDim.x) {
-        const int y = idx / T, t = idx - (idx / T) * T;
-        if (kx0 + t < nxh) base[(long long)y * nxh + t] = R[idx];
-    }
+    C* R = any_fft<NY, INV, true, TY>(A, B, py, T, T, 1, tw);
+    tile_store<TY, NY>(base, R, nxh, nxh - kx0, T, ny);
 }
 
 // Wave vector components of tile point (kz index, t) in a z-pass tile at (kx0, ky index)
@@ -263,8 +306,8 @@ __device__ __forceinline__ Real inverse_laplacian(const KPoint<Real>& p, Real hx
 //   slot_es: S (+1 with psi) unnormalised bulk-fluid/Poisson spectra sum_j K_ij drho_hat_j (kx, ky, kz)
 // Shared pool of 7 tiles of T x nz.
 // ------------------------------------------------------------------------------------
-template <typename Real>
-__global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int T,
+template <typename Real, int NZ, int TZ>
+__global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int Trt,
                                                         Real kfx, Real kfy, Real kfz, int want_psi,
                                                         const typename Cplx<Real>::type* __restrict__ in,
                                                         typename Cplx<Real>::type* __restrict__ slot_n,
@@ -272,7 +315,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
                                                         const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int nz = g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int nz = NZ > 0 ? NZ : g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int T = TZ > 0 ? TZ : Trt;
     const int tile = T * nz;
     C* tw = align_ptr<C>(smem_raw);
     C* pool[7];
@@ -285,14 +329,10 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
 
     // phase 1: forward z transform of each species tile; results end in pool[0..S-1]
     for (int s = 0; s < S; ++s) {
-        const C* src = in + (long long)s * g.nc + col0;
         C* b = pool[s];
-        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-            const int z = idx / T, t = idx - (idx / T) * T;
-            b[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
-        }
+        tile_load<TZ, NZ>(b, in + (long long)s * g.nc + col0, zstride, nxh - kx0, T, nz);
         __syncthreads();
-        C* r = smem_fft<false>(b, pool[6], pz, T, T, 1, tw);
+        C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
         if (r != b) { pool[6] = b; pool[s] = r; }
     }
 
@@ -371,41 +411,43 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
                 W[idx] = nyq ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd * u.y, kd * u.x);
             }
             __syncthreads();
-            r = smem_fft<true>(W, pool[6], pz, T, T, 1, tw);
+            r = any_fft<NZ, true, true, TZ>(W, pool[6], pz, T, T, 1, tw);
         } else {
-            r = smem_fft<true>(pool[a], pool[5], pz, T, T, 1, tw);
+            r = any_fft<NZ, true, true, TZ>(pool[a], pool[5], pz, T, T, 1, tw);
         }
-        C* dst = slot_n + (long long)a * g.nc + col0;
-        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-            const int z = idx / T, t = idx - (idx / T) * T;
-            if (kx0 + t < nxh) dst[z * zstride + t] = r[idx];
-        }
+        tile_store<TZ, NZ>(slot_n + (long long)a * g.nc + col0, r, zstride, nxh - kx0, T, nz);
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------------------------
-// Pointwise derivatives of eq. Phi.  The log(1 - n3) and 1/(1 - n3)^m factors are formed
-// in FP64; xi = |nV2|^2/n2^2 is clamped to [0, 1] (Sec. "Numerical Stability"), and the
-// xi terms vanish where n2 <= 1e-30.  Returns false if n3 >= 1.
+// Pointwise derivatives of eq. Phi; xi = |nV2|^2/n2^2 is clamped to [0, 1] (Sec. "Numerical
+// Stability") and the xi terms vanish where n2 <= 1e-30.  log(1 - n3) and 1/(1 - n3)^m are
+// formed in FP64 where n3 >= 0.5, i.e. where n3 approaches 1; below, 1 - n3 is exact in the
+// working precision and log1p / the reciprocal are within 2 ulp.  Returns false if n3 >= 1.
 // ------------------------------------------------------------------------------------
 template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n) {
     const Real n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     const Real v1x = n[4], v1y = n[5], v1z = n[6], v2x = n[7], v2y = n[8], v2z = n[9];
-    const double D = 1.0 - double(n3);
-    const bool ok = D > 0.0;
-    const double lnD = log(D);
-    const double iD = 1.0 / D;
-    const double iD2 = iD * iD;
-    const double iD3 = iD2 * iD;
-    const Real fiD = Real(iD), fiD2 = Real(iD2), fiD3 = Real(iD3);
+    Real lnD, fiD;
+    bool ok = true;
+    if (n3 < Real(0.5)) {
+        lnD = log1p(-n3);
+        fiD = Real(1) / (Real(1) - n3);
+    } else {
+        const double D = 1.0 - double(n3);
+        ok = D > 0.0;
+        lnD = Real(log(D));
+        fiD = Real(1.0 / D);
+    }
+    const Real fiD2 = fiD * fiD, fiD3 = fiD2 * fiD;
     const Real q = v2x * v2x + v2y * v2y + v2z * v2z;
     Real xi = (n2 > Real(1e-30)) ? q / (n2 * n2) : Real(1);
     xi = xi < Real(0) ? Real(0) : (xi > Real(1) ? Real(1) : xi);
     const Real om = Real(1) - xi;
     const Real dot = v1x * v2x + v1y * v2y + v1z * v2z;
     const Real pi = Real(CUDART_PI);
-    n[0] = Real(-lnD);
+    n[0] = -lnD;
     n[1] = n2 * fiD;
     n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 / (Real(8) * pi);
     n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 / (Real(12) * pi);
@@ -421,7 +463,7 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
 
 // Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
 // full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
-template <typename Real>
+template <typename Real, int NX>
 __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
                                                long long nrows, int ncomp,
                                                const typename Cplx<Real>::type* A,
@@ -429,7 +471,7 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
                                                typename Cplx<Real>::type* mat_out,
                                                typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
-    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
     const bool even = (nx % 2) == 0;
     for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
@@ -457,12 +499,12 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
 }
 
 // Separate Z = FFT(a + i b) of two real rows into their half spectra and store them.
-template <typename Real>
+template <typename Real, int NX>
 __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
                                                 long long nrows, int ncomp, const typename Cplx<Real>::type* R,
                                                 typename Cplx<Real>::type* out) {
     using C = typename Cplx<Real>::type;
-    const int nx = g.nx, nxh = g.nxh, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
     for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
         const long long row = row0 + l / lines_per_row;
@@ -481,7 +523,7 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
 // x pass of the second half's start: n_alpha (mixed from slots A and B) -> real space ->
 // dPhi/dn_alpha -> half spectra.  grid: ceil(ny nz / LR); 5 lines (component pairs) per row.
 // ------------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int NX>
 __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int LR, const Ctl* __restrict__ ctl,
                                                    const typename Cplx<Real>::type* slotA,
                                                    const typename Cplx<Real>::type* slotB,
@@ -492,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
-    const int nx = g.nx, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1;
     const int lines = 5 * LR;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
@@ -501,9 +543,9 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
-    load_pair_rows<Real>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A);
+    load_pair_rows<Real, NX>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A);
     __syncthreads();
-    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
     bool bad = false;
     for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
@@ -525,8 +567,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     if (bad) atomicOr(status, DEV_N3BOUND);
     __syncthreads();
     C* other = (R == A) ? B : A;
-    C* F = smem_fft<false>(R, other, px, lines, 1, pitch, tw);
-    store_pair_rows<Real>(g, lines, 5, row0, nrows, DFT_NCOMP, F, phi_out);
+    C* F = any_fft<NX, false, false, 0>(R, other, px, lines, 1, pitch, tw);
+    store_pair_rows<Real, NX>(g, lines, 5, row0, nrows, DFT_NCOMP, F, phi_out);
     const float bm = block_max(mx, scratch_f);
     if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
 }
@@ -541,8 +583,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
 //   c_hat_i = (-mu_hat_i + wA es_A_i + wB es_B_i) / N.
 // flags: 1 = hard-sphere part, 2 = electrostatic part; ncomp_out = S (or S + 1 for psi).
 // ------------------------------------------------------------------------------------
-template <typename Real>
-__global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int T,
+template <typename Real, int NZ, int TZ>
+__global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int Trt,
                                                         Real kfx, Real kfy, Real kfz, int flags, int ncomp_out,
                                                         const Ctl* __restrict__ ctl,
                                                         typename Cplx<Real>::type* phi,
@@ -552,7 +594,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
                                                         const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int nz = g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int nz = NZ > 0 ? NZ : g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int T = TZ > 0 ? TZ : Trt;
     const int tile = T * nz;
     C* tw = align_ptr<C>(smem_raw);
     C* pool[7];
@@ -567,26 +610,18 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
 
     if (hs) {
         for (int a = 0; a < 4; ++a) {
-            const C* src = phi + (long long)a * g.nc + col0;
             C* b = pool[a];
-            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-                const int z = idx / T, t = idx - (idx / T) * T;
-                b[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
-            }
+            tile_load<TZ, NZ>(b, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
             __syncthreads();
-            C* r = smem_fft<false>(b, pool[6], pz, T, T, 1, tw);
+            C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
             if (r != b) { pool[6] = b; pool[a] = r; }
         }
         for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) pool[4][idx] = cmake<C>(Real(0), Real(0));
         for (int a = 4; a < 10; ++a) {
-            const C* src = phi + (long long)a * g.nc + col0;
             C* W = pool[5];
-            for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-                const int z = idx / T, t = idx - (idx / T) * T;
-                W[idx] = (kx0 + t < nxh) ? src[z * zstride + t] : cmake<C>(Real(0), Real(0));
-            }
+            tile_load<TZ, NZ>(W, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
             __syncthreads();
-            C* r = smem_fft<false>(W, pool[6], pz, T, T, 1, tw);
+            C* r = any_fft<NZ, false, true, TZ>(W, pool[6], pz, T, T, 1, tw);
             C* acc = (a < 7) ? pool[4] : pool[3];
             const int d = (a - 4) % 3;
             for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
@@ -641,12 +676,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     __syncthreads();
 
     for (int s = 0; s < ncomp_out; ++s) {
-        C* r = smem_fft<true>(pool[s], pool[5 + (s & 1)], pz, T, T, 1, tw);
-        C* dst = phi + (long long)s * g.nc + col0;
-        for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-            const int z = idx / T, t = idx - (idx / T) * T;
-            if (kx0 + t < nxh) dst[z * zstride + t] = r[idx];
-        }
+        C* r = any_fft<NZ, true, true, TZ>(pool[s], pool[5 + (s & 1)], pz, T, T, 1, tw);
+        tile_store<TZ, NZ>(phi + (long long)s * g.nc + col0, r, zstride, nxh - kx0, T, nz);
         __syncthreads();
     }
 }
@@ -658,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
 // accumulated in FP64.  grid: ceil(ny nz / LR); ceil(S/2) lines per row.
 // rho_out may alias rho0 and g_out may alias rho1 (each point is read before it is written).
 // ------------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int NX>
 __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR,
                                                       const Ctl* __restrict__ ctl,
                                                       const typename Cplx<Real>::type* __restrict__ cspec,
@@ -669,7 +700,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
-    const int nx = g.nx, pitch = nx + 1, S = sp.S;
+    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1, S = sp.S;
     const int lpr = (S + 1) / 2;
     const int lines = lpr * LR;
     C* tw = align_ptr<C>(smem_raw);
@@ -678,11 +709,13 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    load_pair_rows<Real>(g, lines, lpr, row0, nrows, S, cspec, nullptr, Real(1), Real(0), nullptr, A);
+    load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, S, cspec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
-    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
-    double acc = 0.0;
+    // per-thread partial sum in the working precision with Kahan compensation, then FP64
+    // across threads and blocks
+    Real acc = Real(0), comp = Real(0);
     bool bad = false;
     for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
         const int r = idx / nx, x = idx - (idx / nx) * nx;
@@ -700,13 +733,16 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
             else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
             if (!isfinite(gval) || !isfinite(rho)) bad = true;
             const Real e = (rho - gval) * sp.inv_rho_b[s];
-            acc += double(e) * double(e);
+            const Real y = e * e - comp;
+            const Real t = acc + y;
+            comp = (t - acc) - y;
+            acc = t;
             if (rho_out) rho_out[o] = rho;
             if (g_out) g_out[o] = gval;
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);
-    const double bs = block_sum(acc, scratch_d);
+    const double bs = block_sum(double(acc) - double(comp), scratch_d);
     if (threadIdx.x == 0) red_sum[blockIdx.x] = bs;
 }
 
@@ -714,7 +750,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
 // Plain x inverse of ncomp half spectra to real fields, out[c] = value + offset[c].
 // Optional max of component cmax into red_max.  grid: ceil(ny nz / LR).
 // ------------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int NX>
 __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int LR, int ncomp,
                                                    const typename Cplx<Real>::type* __restrict__ spec,
                                                    Real* __restrict__ out, Real* __restrict__ out_last,
@@ -724,7 +760,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
-    const int nx = g.nx, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1;
     const int lpr = (ncomp + 1) / 2;
     const int lines = lpr * LR;
     C* tw = align_ptr<C>(smem_raw);
@@ -733,9 +769,9 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    load_pair_rows<Real>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
+    load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
-    C* R = smem_fft<true>(A, B, px, lines, 1, pitch, tw);
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
     for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
         const int r = idx / nx, x = idx - (idx / nx) * nx;

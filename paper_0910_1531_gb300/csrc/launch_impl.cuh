@@ -1,0 +1,122 @@
+// Definitions of LaunchX / LaunchY / LaunchZ<Real, N> (included by kinst.cu once per pair).
+#pragma once
+
+#include "kernels.cuh"
+#include "passes.h"
+
+namespace {
+// Allow each kernel the device's opt-in shared memory per block minus its static shared memory.
+template <typename K> cudaError_t set_max_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <typename C> size_t smem_x_of(int nx, int lines) { return (size_t(nx) + 2 * size_t(lines) * (nx + 1)) * sizeof(C) + 16; }
+template <typename C> size_t smem_col_of(int n, int T, int nbuf) { return (size_t(n) + size_t(nbuf) * T * n) * sizeof(C) + 16; }
+}  // namespace
+
+// ---------------------------------------------------------------------------------- x
+template <typename Real, int N>
+cudaError_t LaunchX<Real, N>::init() {
+    cudaError_t e = cudaSuccess, r;
+    if ((r = set_max_smem(dftk::k_xfwd<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xphi<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xupdate<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xinv<Real, N>)) != cudaSuccess) e = r;
+    return e;
+}
+
+template <typename Real, int N>
+void LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx,
+                            const Real* in, C* out, const C* tw) {
+    const long long rows = (long long)ncomp * g.ny * g.nz;
+    const unsigned blocks = (unsigned)ceil_div((rows + 1) / 2, lx);
+    dftk::k_xfwd<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lx), st>>>(g, px, ncomp, lx, in, out, tw);
+}
+
+template <typename Real, int N>
+void LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
+                            const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
+                                                                                    red_max, status, tw);
+}
+
+template <typename Real, int N>
+void LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                               int LR, const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1,
+                               const Real* V, Real* rho_out, Real* g_out, double* red_sum, int* status,
+                               const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    const int lpr = (sp.S + 1) / 2;
+    dftk::k_xupdate<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lpr * LR), st>>>(
+        g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw);
+}
+
+template <typename Real, int N>
+void LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp,
+                            const C* spec, Real* out, Real* out_last, const Offsets<Real>& off, int cmax,
+                            float* red_max, const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    const int lpr = (ncomp + 1) / 2;
+    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lpr * LR), st>>>(
+        g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw);
+}
+
+// ---------------------------------------------------------------------------------- y
+template <typename Real, int N>
+cudaError_t LaunchY<Real, N>::init() {
+    constexpr int TY = N > 0 ? dft_tile_y<Real>(N) : 0;
+    cudaError_t e = cudaSuccess, r;
+    if ((r = set_max_smem(dftk::k_yfft<Real, false, N, TY>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_yfft<Real, true, N, TY>)) != cudaSuccess) e = r;
+    return e;
+}
+
+template <typename Real, int N>
+void LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
+                            C* data, const C* tw) {
+    constexpr int TY = N > 0 ? dft_tile_y<Real>(N) : 0;
+    const int Tu = TY > 0 ? TY : T;
+    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.nz, (unsigned)ncomp);
+    const size_t sm = smem_col_of<C>(g.ny, Tu, 2);
+    if (inv) dftk::k_yfft<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(g, py, Tu, data, tw);
+    else dftk::k_yfft<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(g, py, Tu, data, tw);
+}
+
+// ---------------------------------------------------------------------------------- z
+template <typename Real, int N>
+cudaError_t LaunchZ<Real, N>::init() {
+    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
+    cudaError_t e = cudaSuccess, r;
+    if ((r = set_max_smem(dftk::k_zconv_fwd<Real, N, TZ>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_zconv_bwd<Real, N, TZ>)) != cudaSuccess) e = r;
+    return e;
+}
+
+template <typename Real, int N>
+void LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+                                 int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
+                                 C* slot_es, const C* tw) {
+    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
+    const int Tu = TZ > 0 ? TZ : T;
+    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
+    dftk::k_zconv_fwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
+        g, pz, sp, Tu, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw);
+}
+
+template <typename Real, int N>
+void LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+                                 int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
+                                 const C* esA, const C* esB, C* es_mat, const C* tw) {
+    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
+    const int Tu = TZ > 0 ? TZ : T;
+    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
+    dftk::k_zconv_bwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
+        g, pz, sp, Tu, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
+}

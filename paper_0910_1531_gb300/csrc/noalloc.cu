@@ -85,12 +85,6 @@ bool valid_n_na(int n) {
     return m == 1;
 }
 
-int tile_for(int n, int nbuf, size_t budget) {
-    for (int T = 16; T >= 1; T /= 2)
-        if ((size_t(n) + size_t(nbuf) * T * n) * sizeof(float2) + 16 <= budget) return T;
-    return 1;
-}
-
 int lines_for(int nx, int per_unit, size_t budget, int cap) {
     const long long avail = (long long)(budget / sizeof(float2)) - nx;
     long long L = avail / (2LL * (nx + 1) * per_unit);
@@ -164,7 +158,7 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     const double two_pi = 6.28318530717958647692;
     const float kfx = float(two_pi / (g.nx * g.hx)), kfy = float(two_pi / (g.ny * g.hy)),
                 kfz = float(two_pi / (g.nz * g.hz));
-    const int Ty = tile_for(g.ny, 2, 100 * 1024), Tz = tile_for(g.nz, 7, 112 * 1024);
+    const int Ty = Passes<float>::tile_y(g.ny, 100 * 1024), Tz = Passes<float>::tile_z(g.nz, 112 * 1024);
     const int LX = lines_for(g.nx, 1, 48 * 1024, 32);
     const int LR = lines_for(g.nx, DFT_NCOMP / 2, 48 * 1024, 16);
 

@@ -1,12 +1,63 @@
-// Host-side launchers of the pass kernels, instantiated for float (kernels_f32.cu) and
-// double (kernels_f64.cu).  Each launcher sizes its grid from the grid descriptor and
-// the tile parameters and queues one kernel on `st`.
+// Host-side launchers of the pass kernels.
+//
+// Passes<Real> is the interface the plan code calls; it dispatches on the axis length to
+// LaunchX / LaunchY / LaunchZ<Real, N>, whose kernels have the transform length N (and the
+// column tile width) fixed at compile time.  N = 0 is the run-time path for any length.
+// Each (Real, N) pair is compiled in its own translation unit (kinst.cu).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 #include "common.cuh"
+
+// Axis lengths with compile-time kernels.
+#define DFT_CT_SIZES(X) X(32) X(48) X(64) X(96) X(128) X(256)
+
+__host__ __device__ constexpr bool dft_is_ct_size(int n) {
+    return n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 256;
+}
+
+// Column-tile widths of the compile-time y and z passes (kx columns per tile).
+template <typename Real> __host__ __device__ constexpr int dft_tile_y(int n) { return sizeof(Real) == 4 ? 16 : 8; }
+template <typename Real> __host__ __device__ constexpr int dft_tile_z(int n) {
+    return sizeof(Real) == 4 ? (n <= 64 ? 16 : (n <= 128 ? 8 : 4)) : (n <= 64 ? 8 : (n <= 128 ? 4 : 2));
+}
+
+template <typename Real, int N>
+struct LaunchX {
+    using C = typename Cplx<Real>::type;
+    static cudaError_t init();
+    static void xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+                     C* out, const C* tw);
+    static void xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+                     const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
+    static void xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+                        const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
+                        Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
+    static void xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+};
+
+template <typename Real, int N>
+struct LaunchY {
+    using C = typename Cplx<Real>::type;
+    static cudaError_t init();
+    static void yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
+                     const C* tw);
+};
+
+template <typename Real, int N>
+struct LaunchZ {
+    using C = typename Cplx<Real>::type;
+    static cudaError_t init();
+    static void zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+                          Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
+                          const C* tw);
+    static void zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+                          Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
+                          const C* esA, const C* esB, C* es_mat, const C* tw);
+};
 
 template <typename Real>
 struct Passes {
@@ -15,6 +66,9 @@ struct Passes {
     // dynamic shared memory of an x pass with `lines` lines and of a column pass with nbuf tiles
     static size_t smem_x(int nx, int lines) { return (size_t(nx) + 2 * size_t(lines) * (nx + 1)) * sizeof(C) + 16; }
     static size_t smem_col(int n, int T, int nbuf) { return (size_t(n) + size_t(nbuf) * T * n) * sizeof(C) + 16; }
+    // tile widths: the compile-time value for specialised lengths, else the largest that fits `budget`
+    static int tile_y(int n, size_t budget);
+    static int tile_z(int n, size_t budget);
 
     static void xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
@@ -35,7 +89,6 @@ struct Passes {
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
 };
 
-cudaError_t finalize_init_attributes();
 void launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
                      int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor);
 

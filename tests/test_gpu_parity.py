@@ -63,6 +63,8 @@ def to_dev(x, plan):
 
 CASES = [
     ((8, 8, 8), 0.1, 2),
+    ((128, 16, 96), (0.05, 0.1, 0.06), 2),   # compile-time z 128, x 96; run-time y 16
+    ((32, 256, 128), (0.08, 0.04, 0.1), 3),  # compile-time z 32, y 256, x 128
     ((16, 24, 32), (0.1, 0.08, 0.12), 2),
     ((12, 18, 24), 0.07, 3),
     ((27, 16, 9), 0.09, 2),        # odd x axis (no Nyquist), radix-3 z
@@ -118,6 +120,24 @@ def test_picard_map(shape, h, nspec, precision):
     r_ref = np.sqrt(P.residual_sq(prob, rho, g_ref))
     assert abs(r_gpu - r_ref) <= TOL[precision] * max(r_ref, 1e-30) * 10
     assert np.all(g_gpu.cpu().numpy()[np.isinf(V)] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_picard_map_full_size_obstacles(precision):
+    # The 128^3 three-species workload the benchmark times, in the same launch configuration.
+    w = workloads.obstacles_3species(n=128, h=0.05, seed=1)
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    plan = plan_for(prob, precision)
+    g_gpu, r_gpu = plan.picard_map(to_dev(rho, plan), to_dev(w.V, plan))
+    g_ref = F.picard_map(prob, rho, w.V)
+    assert relerr(g_gpu.cpu().numpy(), g_ref) < TOL[precision]
+    r_ref = np.sqrt(P.residual_sq(prob, rho, g_ref))
+    assert abs(r_gpu - r_ref) <= 1e-4 * r_ref
+    n_gpu = plan.weighted_densities(to_dev(rho, plan)).cpu().numpy()
+    n_ref = F.weighted_densities(prob, rho)
+    for a in range(10):
+        assert relerr(n_gpu[a], n_ref[a]) < TOL[precision], a
 
 
 def test_uniform_bath_is_fixed_point_fp32():
