@@ -47,7 +47,7 @@ typedef enum {
     DFT_EN3BOUND = -5,     /* local packing fraction n3 >= 1 somewhere (log(1-n3) undefined) */
     DFT_ENONFINITE = -6,   /* NaN or Inf appeared in a density */
     DFT_ENOCONV = -7,      /* dft_solve reached max_it without reaching tol */
-    DFT_ETIMEOUT = -8      /* reserved: a bounded device-side wait gave up */
+    DFT_ETIMEOUT = -8      /* a bounded device-side wait on an asynchronous (TMA) copy gave up */
 } dft_status;
 
 enum { DFT_FP32_STAB = 0, DFT_FP64 = 1 };

@@ -185,8 +185,9 @@ struct Prof {
     }
 };
 
-// bytes of one complex half-spectrum component and of one real field component
-double CB(const dft_plan* p) { return double(p->g.nc) * double(p->csize); }
+// bytes of one complex half-spectrum component (used elements, not the row padding) and of
+// one real field component
+double CB(const dft_plan* p) { return double(p->g.nz) * p->g.ny * p->g.nxh * double(p->csize); }
 double RB(const dft_plan* p) { return double(p->g.n) * double(p->rsize); }
 
 void collect_profile(dft_plan* p) {
@@ -208,11 +209,12 @@ void collect_profile(dft_plan* p) {
 // each output element written once), accumulated by the profiler.
 #define LAUNCH(p, kind, bytes, call)                                                          \
     do {                                                                                      \
+        cudaError_t _e;                                                                       \
         {                                                                                     \
             Prof _pr((p), (kind), double(bytes));                                             \
-            call;                                                                             \
+            _e = (call);                                                                      \
         }                                                                                     \
-        cudaError_t _e = cudaGetLastError();                                                  \
+        if (_e == cudaSuccess) _e = cudaGetLastError();                                       \
         if (_e != cudaSuccess)                                                                \
             return fail((p), DFT_ECUDA, std::string(kKindNames[kind]) + ": " + cudaGetErrorString(_e)); \
         if ((p)->prof && (p)->recs.size() > 4096) collect_profile(p);                         \
@@ -236,10 +238,10 @@ template <typename Real> struct Ops {
     static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_ZFWD, (p->S + DFT_NCOMP + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
                                        T1(p), slot_n(slot), slot_es(p, slot), tw(p, 2)));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), &p->ctl->status, tw(p, 1)));
         return DFT_OK;
     }
 
@@ -254,11 +256,11 @@ template <typename Real> struct Ops {
         LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NCOMP * CB(p),
                P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
                                   p->red_max, &p->ctl->status, tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
                                        p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
-        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0))),
                P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
                                      g_out, p->red_sum, &p->ctl->status, tw(p, 0)));
@@ -293,6 +295,7 @@ dft_status read_ctl(dft_plan* p) {
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("reading control block: ") + cudaGetErrorString(e));
     if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
     if (p->ctl_host->status & DEV_NONFINITE) return fail(p, DFT_ENONFINITE, "non-finite density or residual met");
+    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
     return DFT_OK;
 }
 
@@ -359,10 +362,10 @@ template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* 
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
                               O::T1(p), p->red_max, &p->ctl->status, O::tw(p, 0)));
-    LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), &p->ctl->status, O::tw(p, 1)));
     LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), &p->ctl->status, O::tw(p, 1)));
     TRY(O::xinv(p, p->S, O::T1(p), c1, nullptr, nullptr, -1, nullptr, nullptr));
     return DFT_OK;
 }
@@ -377,7 +380,7 @@ template <typename Real> dft_status c1_es_t(dft_plan* p, const Real* rho, Real* 
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     LAUNCH(p, K_ZBWD, 2.0 * nout * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 2, nout,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, 2.0 * (nout) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (nout) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), &p->ctl->status, O::tw(p, 1)));
     double offs[DFT_NCOMP + 2] = {0};
     for (int s = 0; s < p->S; ++s) offs[s] = -p->bath.mu_es[s];
     TRY(O::xinv(p, nout, O::T1(p), c1, psi, offs, -1, nullptr, nullptr));
@@ -446,8 +449,9 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     GridDesc& g = p->g;
     g.nx = prm->nx; g.ny = prm->ny; g.nz = prm->nz;
     g.nxh = g.nx / 2 + 1;
+    g.pxh = (g.nxh + 1) & ~1;
     g.n = (long long)g.nx * g.ny * g.nz;
-    g.nc = (long long)g.nz * g.ny * g.nxh;
+    g.nc = (long long)g.nz * g.ny * g.pxh;
     g.hx = prm->hx; g.hy = prm->hy; g.hz = prm->hz;
     const double two_pi = 6.28318530717958647692;
     p->kf[0] = two_pi / (g.nx * g.hx);

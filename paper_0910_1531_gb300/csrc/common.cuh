@@ -35,11 +35,13 @@ struct AxisPlan {
 };
 
 // Grid of one state point.  Real fields: [c][nz][ny][nx]; half spectra after the
-// x transform: [c][nz][ny][nxh], nxh = nx/2 + 1.
+// x transform: [c][nz][ny][pxh], of which kx < nxh = nx/2 + 1 are used; the row pitch
+// pxh is nxh rounded up to even so that every row starts on a 16-byte boundary (a TMA
+// requirement).
 struct GridDesc {
-    int nx, ny, nz, nxh;
+    int nx, ny, nz, nxh, pxh;
     long long n;     // nx * ny * nz
-    long long nc;    // nz * ny * nxh
+    long long nc;    // nz * ny * pxh (elements per half-spectrum component)
     double hx, hy, hz;
 };
 
@@ -88,7 +90,8 @@ struct Ctl {
 
 enum {
     DEV_N3BOUND = 1,        // n3 >= 1 met
-    DEV_NONFINITE = 2       // non-finite density or residual met
+    DEV_NONFINITE = 2,      // non-finite density or residual met
+    DEV_TIMEOUT = 4         // a bounded wait on an asynchronous copy gave up
 };
 
 // finalize() operations

@@ -16,20 +16,20 @@ DFT_DECLARE_EXTERN(0)
 
 #define DFT_CASE(N, L, call) case N: L<Real, N>::call; break;
 #define DFT_SWITCH_X(n, call) switch (n) { \
-    case 32: LaunchX<Real, 32>::call; break; case 48: LaunchX<Real, 48>::call; break; \
-    case 64: LaunchX<Real, 64>::call; break; case 96: LaunchX<Real, 96>::call; break; \
-    case 128: LaunchX<Real, 128>::call; break; case 256: LaunchX<Real, 256>::call; break; \
-    default: LaunchX<Real, 0>::call; }
+    case 32: return LaunchX<Real, 32>::call; case 48: return LaunchX<Real, 48>::call; \
+    case 64: return LaunchX<Real, 64>::call; case 96: return LaunchX<Real, 96>::call; \
+    case 128: return LaunchX<Real, 128>::call; case 256: return LaunchX<Real, 256>::call; \
+    default: return LaunchX<Real, 0>::call; }
 #define DFT_SWITCH_Y(n, call) switch (n) { \
-    case 32: LaunchY<Real, 32>::call; break; case 48: LaunchY<Real, 48>::call; break; \
-    case 64: LaunchY<Real, 64>::call; break; case 96: LaunchY<Real, 96>::call; break; \
-    case 128: LaunchY<Real, 128>::call; break; case 256: LaunchY<Real, 256>::call; break; \
-    default: LaunchY<Real, 0>::call; }
+    case 32: return LaunchY<Real, 32>::call; case 48: return LaunchY<Real, 48>::call; \
+    case 64: return LaunchY<Real, 64>::call; case 96: return LaunchY<Real, 96>::call; \
+    case 128: return LaunchY<Real, 128>::call; case 256: return LaunchY<Real, 256>::call; \
+    default: return LaunchY<Real, 0>::call; }
 #define DFT_SWITCH_Z(n, call) switch (n) { \
-    case 32: LaunchZ<Real, 32>::call; break; case 48: LaunchZ<Real, 48>::call; break; \
-    case 64: LaunchZ<Real, 64>::call; break; case 96: LaunchZ<Real, 96>::call; break; \
-    case 128: LaunchZ<Real, 128>::call; break; case 256: LaunchZ<Real, 256>::call; break; \
-    default: LaunchZ<Real, 0>::call; }
+    case 32: return LaunchZ<Real, 32>::call; case 48: return LaunchZ<Real, 48>::call; \
+    case 64: return LaunchZ<Real, 64>::call; case 96: return LaunchZ<Real, 96>::call; \
+    case 128: return LaunchZ<Real, 128>::call; case 256: return LaunchZ<Real, 256>::call; \
+    default: return LaunchZ<Real, 0>::call; }
 
 template <typename Real>
 cudaError_t Passes<Real>::init_attributes() {
@@ -61,46 +61,46 @@ int Passes<Real>::tile_z(int n, size_t budget) {
 }
 
 template <typename Real>
-void Passes<Real>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+cudaError_t Passes<Real>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                         C* out, const C* tw) {
     DFT_SWITCH_X(g.nx, xfwd(st, g, px, ncomp, lx, in, out, tw))
 }
 
 template <typename Real>
-void Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
-                        const C* tw) {
-    DFT_SWITCH_Y(g.ny, yfft(st, inv, g, py, T, ncomp, data, tw))
+cudaError_t Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
+                               C* data, int* status, const C* tw) {
+    DFT_SWITCH_Y(g.ny, yfft(st, inv, g, py, T, ncomp, data, status, tw))
 }
 
 template <typename Real>
-void Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+cudaError_t Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                              int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
                              const C* tw) {
     DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw))
 }
 
 template <typename Real>
-void Passes<Real>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+cudaError_t Passes<Real>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
                         const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
     DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, tw))
 }
 
 template <typename Real>
-void Passes<Real>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+cudaError_t Passes<Real>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                              int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                              const C* esA, const C* esB, C* es_mat, const C* tw) {
     DFT_SWITCH_Z(g.nz, zconv_bwd(st, g, pz, sp, T, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw))
 }
 
 template <typename Real>
-void Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                            const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                            Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw) {
     DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw))
 }
 
 template <typename Real>
-void Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+cudaError_t Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                         Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw) {
     DFT_SWITCH_X(g.nx, xinv(st, g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw))
 }
@@ -108,8 +108,48 @@ void Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, 
 template struct Passes<float>;
 template struct Passes<double>;
 
-void launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
+cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
                      int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor) {
     dftk::k_finalize<<<1, dftk::kThreads, 0, st>>>(ctl, red_sum, nsum, red_max, nmax, op, inv_count, alpha_fixed,
                                                   n3_bound, alpha_floor);
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------
+// TMA tensor-map encoding through the driver entry point (no link against libcuda).
+// ------------------------------------------------------------------------------------
+#include <cudaTypedefs.h>
+#include <mutex>
+
+#include "tma.cuh"
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+}  // namespace
+
+cudaError_t tma_encode_3d(CUtensorMap* map, void* base, unsigned long long d0, unsigned long long d1,
+                          unsigned long long d2, unsigned long long stride1_bytes, unsigned long long stride2_bytes,
+                          unsigned b0, unsigned b1, unsigned b2) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }

@@ -173,6 +173,19 @@ __host__ __device__ constexpr int ct_ns_at(int n, int s) { int p = 1; for (int i
 
 constexpr int kFftThreads = 256;
 
+// Row pitch (elements) of the compile-time x passes.  A stage with M < 16 butterflies per
+// row puts 16/M rows in one half-warp; a pitch congruent to M modulo 16 sends those rows to
+// disjoint bank groups (8-byte elements).  Lengths without such a stage use an odd pitch.
+__host__ __device__ constexpr int ct_row_pitch(int n) {
+    int msmall = 0;
+    for (int s = 0; s < ct_nstages(n); ++s) {
+        const int m = n / ct_radix_at(n, s);
+        if (m < 16) msmall = m;
+    }
+    if (msmall == 0) return n + 1;
+    return n + (((msmall - n) % 16) + 16) % 16;
+}
+
 // One stage.  COLS: lines are tile columns (element e of line l at e*T + l, line index fastest
 // across threads); otherwise lines are rows (element e of line l at e + l*ls, e fastest).
 template <int N, int R, int NS, bool INV, bool COLS, int T, typename C>

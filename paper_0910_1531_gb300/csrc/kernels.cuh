@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace dftk {
 
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
     C* B = A + lx * pitch;
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
         const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
         const C s = cadd(zk, cconj(znk));
         const C d = csub(zk, cconj(znk));
-        if (ra < rows) out[ra * nxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
-        if (rb < rows) out[rb * nxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+        if (ra < rows) out[ra * g.pxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+        if (rb < rows) out[rb * g.pxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
     }
 }
 
@@ -247,18 +248,92 @@ __global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int 
                                                    const typename Cplx<Real>::type* __restrict__ twy) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int ny = NY > 0 ? NY : g.ny, nxh = g.nxh;
+    const int ny = NY > 0 ? NY : g.ny, nxh = g.nxh, pxh = g.pxh;
     const int T = TY > 0 ? TY : Trt;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + ny;
     C* B = A + T * ny;
     for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = twy[i];
     const int kx0 = blockIdx.x * T;
-    C* base = data + (long long)blockIdx.z * g.nc + (long long)blockIdx.y * ny * nxh + kx0;
-    tile_load<TY, NY>(A, base, nxh, nxh - kx0, T, ny);
+    C* base = data + (long long)blockIdx.z * g.nc + (long long)blockIdx.y * ny * pxh + kx0;
+    tile_load<TY, NY>(A, base, pxh, nxh - kx0, T, ny);
     __syncthreads();
     C* R = any_fft<NY, INV, true, TY>(A, B, py, T, T, 1, tw);
-    tile_store<TY, NY>(base, R, nxh, nxh - kx0, T, ny);
+    tile_store<TY, NY>(base, R, pxh, nxh - kx0, T, ny);
+}
+
+// ------------------------------------------------------------------------------------
+// y pass with TMA tiles (compile-time length NY <= 256 and tile width TY).  Persistent: CTA b
+// handles tiles b, b + gridDim.x, ...  Two shared-memory stages are filled by TMA loads (one
+// cp.async.bulk.tensor per tile, completing on an mbarrier) while the previous tile is
+// transformed; results leave through a TMA store.  The tensor map views the half spectra as
+// (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements, E = sizeof(complex) / 8; a tile is the
+// box (TY * E, NY, 1).  A wait that runs out sets DEV_TIMEOUT and the CTA stops after draining
+// the loads it has in flight.
+// ------------------------------------------------------------------------------------
+template <typename Real, bool INV, int NY, int TY>
+__global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ CUtensorMap map, int ntiles_x,
+                                                       int ntiles, int* __restrict__ status,
+                                                       const typename Cplx<Real>::type* __restrict__ twy) {
+    static_assert(NY > 0 && NY <= 256 && TY > 0, "compile-time TMA y pass");
+    using C = typename Cplx<Real>::type;
+    constexpr int E = int(sizeof(C) / 8);
+    constexpr int TILE = TY * NY;
+    constexpr uint32_t BYTES = uint32_t(TILE * sizeof(C));
+    extern __shared__ unsigned char smem_raw[];
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
+    C* stage[2] = {reinterpret_cast<C*>(base), reinterpret_cast<C*>(base) + TILE};
+    C* X = stage[1] + TILE;
+    C* tw = X + TILE;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NY);
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < NY; i += kThreads) tw[i] = twy[i];
+    __syncthreads();
+    int issued[2] = {0, 0}, consumed[2] = {0, 0};   // meaningful in thread 0
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            const int tile = blockIdx.x + s * gridDim.x;
+            if (tile < ntiles) {
+                tma::mbar_expect_tx(&bar[s], BYTES);
+                tma::load_3d(stage[s], &map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, &bar[s]);
+                issued[s] = 1;
+            }
+        }
+    }
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, DEV_TIMEOUT);
+                for (int s = 0; s < 2; ++s)
+                    if (issued[s] > consumed[s]) tma::mbar_wait(&bar[s], (issued[s] - 1) & 1);
+            }
+            break;
+        }
+        consumed[cur] += 1;
+        C* R = ct_fft<NY, INV, true, TY>(stage[cur], X, 0, 0, tw);
+        tma::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::store_3d(&map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, R);
+            tma::commit();
+            tma::wait_read_all();
+            const int next = tile + 2 * gridDim.x;
+            if (next < ntiles) {
+                tma::mbar_expect_tx(&bar[cur], BYTES);
+                tma::load_3d(stage[cur], &map, (next % ntiles_x) * TY * E, 0, next / ntiles_x, &bar[cur]);
+                issued[cur] += 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tma::wait_all();
 }
 
 // Wave vector components of tile point (kz index, t) in a z-pass tile at (kx0, ky index)
@@ -324,8 +399,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
     for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twz[i];
     const int kx0 = blockIdx.x * T;
     const int kyi = blockIdx.y;
-    const long long zstride = (long long)ny * nxh;
-    const long long col0 = (long long)kyi * nxh + kx0;
+    const long long zstride = (long long)ny * g.pxh;
+    const long long col0 = (long long)kyi * g.pxh + kx0;
 
     // phase 1: forward z transform of each species tile; results end in pool[0..S-1]
     for (int s = 0; s < S; ++s) {
@@ -471,7 +546,7 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
                                                typename Cplx<Real>::type* mat_out,
                                                typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
-    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
     for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
@@ -479,8 +554,8 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
         const int ca = 2 * (l % lines_per_row), cb = ca + 1;
         C a = cmake<C>(Real(0), Real(0)), b = a;
         if (row < nrows) {
-            const long long oa = (long long)ca * g.nc + row * nxh + k;
-            const long long ob = (long long)cb * g.nc + row * nxh + k;
+            const long long oa = (long long)ca * g.nc + row * g.pxh + k;
+            const long long ob = (long long)cb * g.nc + row * g.pxh + k;
             a = cscale(A[oa], wA);
             if (Bm) a = cadd(a, cscale(Bm[oa], wB));
             if (cb < ncomp) {
@@ -504,7 +579,7 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
                                                 long long nrows, int ncomp, const typename Cplx<Real>::type* R,
                                                 typename Cplx<Real>::type* out) {
     using C = typename Cplx<Real>::type;
-    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
         const long long row = row0 + l / lines_per_row;
@@ -514,8 +589,8 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
         const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
         const C s = cadd(zk, cconj(znk));
         const C d = csub(zk, cconj(znk));
-        out[(long long)ca * g.nc + row * nxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
-        if (cb < ncomp) out[(long long)cb * g.nc + row * nxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+        out[(long long)ca * g.nc + row * g.pxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+        if (cb < ncomp) out[(long long)cb * g.nc + row * g.pxh + k] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
     }
 }
 
@@ -534,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
-    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const int lines = 5 * LR;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
@@ -603,8 +678,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twz[i];
     const int kx0 = blockIdx.x * T;
     const int kyi = blockIdx.y;
-    const long long zstride = (long long)ny * nxh;
-    const long long col0 = (long long)kyi * nxh + kx0;
+    const long long zstride = (long long)ny * g.pxh;
+    const long long col0 = (long long)kyi * g.pxh + kx0;
     const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
 
@@ -700,7 +775,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
-    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1, S = sp.S;
+    const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1, S = sp.S;
     const int lpr = (S + 1) / 2;
     const int lines = lpr * LR;
     C* tw = align_ptr<C>(smem_raw);
@@ -760,7 +835,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
-    const int nx = NX > 0 ? NX : g.nx, pitch = nx + 1;
+    const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const int lpr = (ncomp + 1) / 2;
     const int lines = lpr * LR;
     C* tw = align_ptr<C>(smem_raw);

@@ -16,7 +16,11 @@ template <typename K> cudaError_t set_max_smem(K kernel) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
-template <typename C> size_t smem_x_of(int nx, int lines) { return (size_t(nx) + 2 * size_t(lines) * (nx + 1)) * sizeof(C) + 16; }
+// x pass: twiddles (nx) + two buffers of `lines` rows at the kernel's row pitch
+template <typename C, int N> size_t smem_x_of(int nx, int lines) {
+    const int pitch = N > 0 ? ct_row_pitch(N) : nx + 1;
+    return (size_t(nx) + 2 * size_t(lines) * pitch) * sizeof(C) + 16;
+}
 template <typename C> size_t smem_col_of(int n, int T, int nbuf) { return (size_t(n) + size_t(nbuf) * T * n) * sizeof(C) + 16; }
 }  // namespace
 
@@ -32,40 +36,44 @@ cudaError_t LaunchX<Real, N>::init() {
 }
 
 template <typename Real, int N>
-void LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx,
+cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx,
                             const Real* in, C* out, const C* tw) {
     const long long rows = (long long)ncomp * g.ny * g.nz;
     const unsigned blocks = (unsigned)ceil_div((rows + 1) / 2, lx);
-    dftk::k_xfwd<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lx), st>>>(g, px, ncomp, lx, in, out, tw);
+    dftk::k_xfwd<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lx), st>>>(g, px, ncomp, lx, in, out, tw);
+    return cudaSuccess;
 }
 
 template <typename Real, int N>
-void LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
+cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
                             const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
+    dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
                                                                                     red_max, status, tw);
+    return cudaSuccess;
 }
 
 template <typename Real, int N>
-void LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                                int LR, const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1,
                                const Real* V, Real* rho_out, Real* g_out, double* red_sum, int* status,
                                const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
-    dftk::k_xupdate<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lpr * LR), st>>>(
+    dftk::k_xupdate<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
         g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw);
+    return cudaSuccess;
 }
 
 template <typename Real, int N>
-void LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp,
+cudaError_t LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp,
                             const C* spec, Real* out, Real* out_last, const Offsets<Real>& off, int cmax,
                             float* red_max, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (ncomp + 1) / 2;
-    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C>(g.nx, lpr * LR), st>>>(
+    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
         g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw);
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------------- y
@@ -75,18 +83,51 @@ cudaError_t LaunchY<Real, N>::init() {
     cudaError_t e = cudaSuccess, r;
     if ((r = set_max_smem(dftk::k_yfft<Real, false, N, TY>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_yfft<Real, true, N, TY>)) != cudaSuccess) e = r;
+    if constexpr (N > 0) {
+        if ((r = set_max_smem(dftk::k_yfft_tma<Real, false, N, TY>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_yfft_tma<Real, true, N, TY>)) != cudaSuccess) e = r;
+    }
     return e;
 }
 
 template <typename Real, int N>
-void LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
-                            C* data, const C* tw) {
-    constexpr int TY = N > 0 ? dft_tile_y<Real>(N) : 0;
-    const int Tu = TY > 0 ? TY : T;
-    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.nz, (unsigned)ncomp);
-    const size_t sm = smem_col_of<C>(g.ny, Tu, 2);
-    if (inv) dftk::k_yfft<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(g, py, Tu, data, tw);
-    else dftk::k_yfft<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(g, py, Tu, data, tw);
+cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
+                                   C* data, int* status, const C* tw) {
+    if constexpr (N > 0) {
+        // TMA path: persistent CTAs, two TMA-filled stages + one FFT scratch tile + twiddles + 2 mbarriers
+        constexpr int TY = dft_tile_y<Real>(N);
+        constexpr int E = int(sizeof(C) / 8);
+        CUtensorMap map;
+        cudaError_t e = tma_encode_3d(&map, data, (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
+                                      (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
+                                      (unsigned long long)g.ny * g.pxh * sizeof(C), TY * E, N, 1);
+        if (e != cudaSuccess) return e;
+        const int ntx = (int)ceil_div(g.nxh, TY);
+        const int ntiles = ntx * g.nz * ncomp;
+        const size_t sm = (3 * size_t(TY) * N + N) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+        static int per_sm[2] = {0, 0};
+        static int sms = 0;
+        int& occ = per_sm[inv ? 1 : 0];
+        if (occ == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (inv) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_yfft_tma<Real, true, N, TY>, dftk::kThreads, sm);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_yfft_tma<Real, false, N, TY>, dftk::kThreads, sm);
+            if (occ < 1) occ = 1;
+        }
+        const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
+        if (inv) dftk::k_yfft_tma<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw);
+        else dftk::k_yfft_tma<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw);
+        return cudaSuccess;
+    } else {
+        dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.nz, (unsigned)ncomp);
+        const size_t sm = smem_col_of<C>(g.ny, T, 2);
+        if (inv) dftk::k_yfft<Real, true, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
+        else dftk::k_yfft<Real, false, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
+        (void)status;
+        return cudaSuccess;
+    }
 }
 
 // ---------------------------------------------------------------------------------- z
@@ -100,7 +141,7 @@ cudaError_t LaunchZ<Real, N>::init() {
 }
 
 template <typename Real, int N>
-void LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
                                  C* slot_es, const C* tw) {
     constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
@@ -108,10 +149,11 @@ void LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisP
     dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
     dftk::k_zconv_fwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
         g, pz, sp, Tu, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw);
+    return cudaSuccess;
 }
 
 template <typename Real, int N>
-void LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
+cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                                  const C* esA, const C* esB, C* es_mat, const C* tw) {
     constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
@@ -119,4 +161,5 @@ void LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisP
     dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
     dftk::k_zconv_bwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
         g, pz, sp, Tu, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
+    return cudaSuccess;
 }

@@ -120,17 +120,19 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     GridDesc g{};
     g.nx = prm->nx; g.ny = prm->ny; g.nz = prm->nz;
     g.nxh = g.nx / 2 + 1;
+    g.pxh = (g.nxh + 1) & ~1;
     g.n = (long long)g.nx * g.ny * g.nz;
-    g.nc = (long long)g.nz * g.ny * g.nxh;
+    g.nc = (long long)g.nz * g.ny * g.pxh;
     g.hx = prm->hx; g.hy = prm->hy; g.hz = prm->hz;
     AxisPlan ax, ay, az;
     if (!radix_plan_na(g.nx, &ax) || !radix_plan_na(g.ny, &ay) || !radix_plan_na(g.nz, &az))
         FAIL(DFT_EINVAL, "no radix plan for the grid sizes");
 
-    // scratch layout (float2 elements): twiddles x, y, z | S spectra | 10 weighted densities |
-    // S + 1 bulk-fluid spectra (written by the z pass, not used here)
+    // scratch layout (float2 elements): status word | twiddles x, y, z | S spectra | 10 weighted
+    // densities | S + 1 bulk-fluid spectra (written by the z pass, not used here)
     auto up = [](size_t v) { return (v + 31) & ~size_t(31); };   // keep 256-byte alignment
-    const size_t o_twx = 0, o_twy = o_twx + up(g.nx), o_twz = o_twy + up(g.ny);
+    const size_t o_status = 0;
+    const size_t o_twx = o_status + up(1), o_twy = o_twx + up(g.nx), o_twz = o_twy + up(g.ny);
     const size_t o_spec = o_twz + up(g.nz);
     const size_t o_n = o_spec + up(size_t(S) * g.nc);
     const size_t o_es = o_n + up(size_t(DFT_NCOMP) * g.nc);
@@ -165,19 +167,23 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     // Every scratch element the pipeline reads is first written by this call, so nothing
     // needs clearing; the twiddles are rewritten every call (the previous call may have
     // used other grid sizes).
+    // the status word records a bounded wait that gave up inside the y pass (never expected)
+    int* status = reinterpret_cast<int*>(base + o_status);
     k_twiddles<<<4, 256, 0, st>>>(base + o_twx, g.nx);
     k_twiddles<<<4, 256, 0, st>>>(base + o_twy, g.ny);
     k_twiddles<<<4, 256, 0, st>>>(base + o_twz, g.nz);
-    Passes<float>::xfwd(st, g, ax, S, LX, static_cast<const float*>(rho), base + o_spec, base + o_twx);
-    Passes<float>::yfft(st, false, g, ay, Ty, S, base + o_spec, base + o_twy);
-    Passes<float>::zconv_fwd(st, g, az, sp, Tz, kfx, kfy, kfz, 0, base + o_spec, base + o_n, base + o_es,
-                             base + o_twz);
-    Passes<float>::yfft(st, true, g, ay, Ty, DFT_NCOMP, base + o_n, base + o_twy);
     Offsets<float> off;
     for (int c = 0; c < DFT_NCOMP + 2; ++c) off.v[c] = 0.f;
-    Passes<float>::xinv(st, g, ax, LR, DFT_NCOMP, base + o_n, static_cast<float*>(n_out), nullptr, off, -1, nullptr,
-                        base + o_twx);
-    e = cudaGetLastError();
+    e = Passes<float>::xfwd(st, g, ax, S, LX, static_cast<const float*>(rho), base + o_spec, base + o_twx);
+    if (e == cudaSuccess) e = Passes<float>::yfft(st, false, g, ay, Ty, S, base + o_spec, status, base + o_twy);
+    if (e == cudaSuccess)
+        e = Passes<float>::zconv_fwd(st, g, az, sp, Tz, kfx, kfy, kfz, 0, base + o_spec, base + o_n, base + o_es,
+                                     base + o_twz);
+    if (e == cudaSuccess) e = Passes<float>::yfft(st, true, g, ay, Ty, DFT_NCOMP, base + o_n, status, base + o_twy);
+    if (e == cudaSuccess)
+        e = Passes<float>::xinv(st, g, ax, LR, DFT_NCOMP, base + o_n, static_cast<float*>(n_out), nullptr, off, -1,
+                                nullptr, base + o_twx);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) FAIL(DFT_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (errbuf && errbuf_len > 0) errbuf[0] = '\0';
     return DFT_OK;

@@ -28,14 +28,14 @@ template <typename Real, int N>
 struct LaunchX {
     using C = typename Cplx<Real>::type;
     static cudaError_t init();
-    static void xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+    static cudaError_t xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
-    static void xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+    static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
                      const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
-    static void xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+    static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
-    static void xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+    static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
 };
 
@@ -43,18 +43,18 @@ template <typename Real, int N>
 struct LaunchY {
     using C = typename Cplx<Real>::type;
     static cudaError_t init();
-    static void yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
-                     const C* tw);
+    static cudaError_t yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
+                     int* status, const C* tw);
 };
 
 template <typename Real, int N>
 struct LaunchZ {
     using C = typename Cplx<Real>::type;
     static cudaError_t init();
-    static void zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+    static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
                           const C* tw);
-    static void zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+    static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
 };
@@ -70,26 +70,26 @@ struct Passes {
     static int tile_y(int n, size_t budget);
     static int tile_z(int n, size_t budget);
 
-    static void xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
+    static cudaError_t xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
-    static void yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
-                     const C* tw);
-    static void zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+    static cudaError_t yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
+                     int* status, const C* tw);
+    static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
                           const C* tw);
-    static void xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+    static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
                      const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
-    static void zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
+    static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
-    static void xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
+    static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
-    static void xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
+    static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
 };
 
-void launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
+cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
                      int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor);
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
