@@ -180,6 +180,35 @@ __device__ __forceinline__ void tile_load(C* __restrict__ dst, const C* __restri
     }
 }
 
+// Split form of tile_load for prefetching: fetch a compile-time tile into registers (loads in
+// flight while the caller works on the previous tile), then put it into shared memory.
+template <int TT, int NN> __host__ __device__ constexpr int tile_per_thread() { return (TT * NN + kThreads - 1) / kThreads; }
+
+template <int TT, int NN, typename C>
+__device__ __forceinline__ void tile_fetch(C (&tmp)[tile_per_thread<TT, NN>()], const C* __restrict__ src, long long rs,
+                                           int valid) {
+    constexpr int TOTAL = TT * NN;
+    constexpr int PER = tile_per_thread<TT, NN>();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        const int e = idx / TT, t = idx % TT;
+        tmp[i] = cmake<C>(0, 0);
+        if ((TOTAL % kThreads == 0 || idx < TOTAL) && t < valid) tmp[i] = src[e * rs + t];
+    }
+}
+
+template <int TT, int NN, typename C>
+__device__ __forceinline__ void tile_put(C* __restrict__ dst, const C (&tmp)[tile_per_thread<TT, NN>()]) {
+    constexpr int TOTAL = TT * NN;
+    constexpr int PER = tile_per_thread<TT, NN>();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if (TOTAL % kThreads == 0 || idx < TOTAL) dst[idx] = tmp[i];
+    }
+}
+
 template <int TT, int NN, typename C>
 __device__ __forceinline__ void tile_store(C* __restrict__ dst, const C* __restrict__ src, long long rs, int valid,
                                            int T, int n) {
@@ -402,13 +431,27 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
     const long long zstride = (long long)ny * g.pxh;
     const long long col0 = (long long)kyi * g.pxh + kx0;
 
-    // phase 1: forward z transform of each species tile; results end in pool[0..S-1]
-    for (int s = 0; s < S; ++s) {
-        C* b = pool[s];
-        tile_load<TZ, NZ>(b, in + (long long)s * g.nc + col0, zstride, nxh - kx0, T, nz);
-        __syncthreads();
-        C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
-        if (r != b) { pool[6] = b; pool[s] = r; }
+    // phase 1: forward z transform of each species tile; results end in pool[0..S-1].  With a
+    // compile-time tile the next species' loads are in flight during this one's transform.
+    if constexpr (NZ > 0 && TZ > 0) {
+        C pre[tile_per_thread<TZ, NZ>()];
+        tile_fetch<TZ, NZ>(pre, in + col0, zstride, nxh - kx0);
+        for (int s = 0; s < S; ++s) {
+            C* b = pool[s];
+            tile_put<TZ, NZ>(b, pre);
+            if (s + 1 < S) tile_fetch<TZ, NZ>(pre, in + (long long)(s + 1) * g.nc + col0, zstride, nxh - kx0);
+            __syncthreads();
+            C* r = ct_fft<NZ, false, true, TZ>(b, pool[6], T, 1, tw);
+            if (r != b) { pool[6] = b; pool[s] = r; }
+        }
+    } else {
+        for (int s = 0; s < S; ++s) {
+            C* b = pool[s];
+            tile_load<TZ, NZ>(b, in + (long long)s * g.nc + col0, zstride, nxh - kx0, T, nz);
+            __syncthreads();
+            C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
+            if (r != b) { pool[6] = b; pool[s] = r; }
+        }
     }
 
     // phase 2: k-space products at each tile point
@@ -538,6 +581,8 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
 
 // Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
 // full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
+// Loads are issued in batches of kBatch elements per thread before any store, so that several
+// are in flight at once.
 template <typename Real, int NX>
 __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
                                                long long nrows, int ncomp,
@@ -546,30 +591,49 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
                                                typename Cplx<Real>::type* mat_out,
                                                typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
+    constexpr int kBatch = 4;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
-    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
-        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
-        const long long row = row0 + l / lines_per_row;
-        const int ca = 2 * (l % lines_per_row), cb = ca + 1;
-        C a = cmake<C>(Real(0), Real(0)), b = a;
-        if (row < nrows) {
-            const long long oa = (long long)ca * g.nc + row * g.pxh + k;
-            const long long ob = (long long)cb * g.nc + row * g.pxh + k;
-            a = cscale(A[oa], wA);
-            if (Bm) a = cadd(a, cscale(Bm[oa], wB));
-            if (cb < ncomp) {
-                b = cscale(A[ob], wA);
-                if (Bm) b = cadd(b, cscale(Bm[ob], wB));
-            }
-            if (k == 0 || (even && 2 * k == nx)) { a.y = Real(0); b.y = Real(0); }
-            if (mat_out) {
-                mat_out[oa] = a;
-                if (cb < ncomp) mat_out[ob] = b;
+    const int total = lines * nxh;
+    for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
+        C av[kBatch], bv[kBatch], aB[kBatch], bB[kBatch];
+        long long oa[kBatch], ob[kBatch];
+        bool live[kBatch], hasb[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+            const long long row = row0 + l / lines_per_row;
+            const int ca = 2 * (l % lines_per_row), cb = ca + 1;
+            live[j] = idx < total && row < nrows;
+            hasb[j] = cb < ncomp;
+            oa[j] = (long long)ca * g.nc + row * g.pxh + k;
+            ob[j] = (long long)cb * g.nc + row * g.pxh + k;
+            av[j] = bv[j] = aB[j] = bB[j] = cmake<C>(Real(0), Real(0));
+            if (live[j]) {
+                av[j] = A[oa[j]];
+                if (hasb[j]) bv[j] = A[ob[j]];
+                if (Bm) {
+                    aB[j] = Bm[oa[j]];
+                    if (hasb[j]) bB[j] = Bm[ob[j]];
+                }
             }
         }
-        dst[l * pitch + k] = cmake<C>(a.x - b.y, a.y + b.x);
-        if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + (nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            if (idx >= total) continue;
+            const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+            C a = cadd(cscale(av[j], wA), cscale(aB[j], wB));
+            C b = cadd(cscale(bv[j], wA), cscale(bB[j], wB));
+            if (k == 0 || (even && 2 * k == nx)) { a.y = Real(0); b.y = Real(0); }
+            if (mat_out && live[j]) {
+                mat_out[oa[j]] = a;
+                if (hasb[j]) mat_out[ob[j]] = b;
+            }
+            dst[l * pitch + k] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + (nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+        }
     }
 }
 
@@ -684,19 +748,28 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
 
     if (hs) {
-        for (int a = 0; a < 4; ++a) {
-            C* b = pool[a];
-            tile_load<TZ, NZ>(b, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
-            __syncthreads();
-            C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
-            if (r != b) { pool[6] = b; pool[a] = r; }
-        }
+        // Phi_0..Phi_3 transform into accumulators 0..3; -i k_d Phi_V2d adds to accumulator 3,
+        // -i k_d Phi_V1d to accumulator 4.  With a compile-time tile the next component's loads
+        // are in flight during this one's transform.
         for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) pool[4][idx] = cmake<C>(Real(0), Real(0));
-        for (int a = 4; a < 10; ++a) {
-            C* W = pool[5];
-            tile_load<TZ, NZ>(W, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
+        constexpr bool kPre = NZ > 0 && TZ > 0;
+        constexpr int PER = kPre ? tile_per_thread<TZ, NZ>() : 1;
+        C pre[PER];
+        if constexpr (kPre) tile_fetch<TZ, NZ>(pre, phi + col0, zstride, nxh - kx0);
+        for (int a = 0; a < 10; ++a) {
+            C* dst = (a < 4) ? pool[a] : pool[5];
+            if constexpr (kPre) {
+                tile_put<TZ, NZ>(dst, pre);
+                if (a + 1 < 10) tile_fetch<TZ, NZ>(pre, phi + (long long)(a + 1) * g.nc + col0, zstride, nxh - kx0);
+            } else {
+                tile_load<TZ, NZ>(dst, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
+            }
             __syncthreads();
-            C* r = any_fft<NZ, false, true, TZ>(W, pool[6], pz, T, T, 1, tw);
+            C* r = any_fft<NZ, false, true, TZ>(dst, pool[6], pz, T, T, 1, tw);
+            if (a < 4) {
+                if (r != dst) { pool[6] = dst; pool[a] = r; }
+                continue;
+            }
             C* acc = (a < 7) ? pool[4] : pool[3];
             const int d = (a - 4) % 3;
             for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
@@ -796,13 +869,25 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
         const int r = idx / nx, x = idx - (idx / nx) * nx;
         const long long row = row0 + r;
         if (row >= nrows) continue;
-        for (int s = 0; s < S; ++s) {
+        // all loads of this point first (rho_out / g_out may alias rho0 / rho1)
+        Real r0[DFT_MAXS], r1[DFT_MAXS], vv[DFT_MAXS];
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            if (s < S) {
+                const long long o = (long long)s * g.n + row * nx + x;
+                r0[s] = rho0[o];
+                r1[s] = rho1 ? rho1[o] : Real(0);
+                vv[s] = V[o];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            if (s >= S) continue;
             const C pr = R[(r * lpr + s / 2) * pitch + x];
             const Real c = (s & 1) ? pr.y : pr.x;
             const long long o = (long long)s * g.n + row * nx + x;
-            Real rho = w0 * rho0[o];
-            if (rho1) rho += w1 * rho1[o];
-            const Real v = V[o];
+            const Real rho = w0 * r0[s] + w1 * r1[s];
+            const Real v = vv[s];
             Real gval;
             if (isinf(v) && v > Real(0)) gval = Real(0);
             else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
