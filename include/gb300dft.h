@@ -159,6 +159,31 @@ dft_status dft_iter_step(dft_plan* plan, void* rho_inout, const void* V, double 
                          double* resid_out, double* alpha_out);
 
 /*
+ * Grand potential and its gradients (differentiated form).  The paper asserts
+ * the functional (Sec. "Introduction") and its bulk-fluid expansion (eq.
+ * muESexpansion2); the discrete functional whose stationarity condition is
+ * eq. rhoEquation is, in kT units,
+ *   Omega = h^3 sum_x sum_i [rho_i (ln(rho_i/rho_bath_i) - 1) + rho_i (V_i - mu_ex_bath_i)]
+ *         + h^3 sum_x Phi(n(x))                                   (eq. Phi)
+ *         + h^3 sum_i mu_ES_bath_i sum_x drho_i
+ *         - (h^3/2) sum_i sum_x drho_i (DC_ij (*) drho_j - z_i psi)(x)
+ * with drho = rho - rho_bath over all voxels and an electroneutral bath.
+ * Outputs (any may be NULL):
+ *   omega_out     Omega (host double)
+ *   dOmega_drho   [S][N] device: h^3 [ln(rho_i/rho_bath_i) + V_i - mu_ex_bath_i + mu_ex_i(x)]
+ *                 = h^3 ln(rho_i / G_i), zero where V_i = +inf or rho_i = 0
+ *   dOmega_dV     [S][N] device: h^3 rho_i (the explicit partial; at a solution of
+ *                 eq. rhoEquation it is the total derivative, by stationarity)
+ *   dOmega_dbulk  [S] host: dOmega/drho_bath_k at fixed rho and V, kT nm^3 (bath
+ *                 derivatives of mu_ex, mu_ES and Gamma by extrapolated central
+ *                 differences of the App. A solver; the Gamma dependence of DC by
+ *                 its analytic derivative).
+ * Weighted densities are recomputed, not stored.  Synchronous.
+ */
+dft_status dft_grad(dft_plan* plan, const void* rho, const void* V, double* omega_out, void* dOmega_drho,
+                    void* dOmega_dV, double* dOmega_dbulk);
+
+/*
  * End-to-end convenience for host buffers: copies rho (and V) from HOST
  * memory to the plan's device scratch, performs one dft_picard_step, and
  * copies the updated rho back to HOST memory.  rho_host: [S][N], V_host:

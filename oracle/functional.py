@@ -45,7 +45,8 @@ second-order free-energy expansion about the bath):
              + (h^3/2) sum_x q(x) psi(x),             q = sum_i z_i rho_i
              + h^3 sum_i mu_ES_bath_i sum_x drho_i(x)
              - (h^3/2) sum_ij sum_x drho_i(x) (DC_ij (*) drho_j)(x)
-so that dOmega/drho_i(x) = h^3 [ln(rho_i/rho_bath_i) + V_i - mu_ex_bath_i + mu_ex_i(x)].
+so that dOmega/drho_i(x) = h^3 [ln(rho_i/rho_bath_i) + V_i - mu_ex_bath_i + mu_ex_i(x)],
+dOmega/dV_i(x) = h^3 rho_i(x), and dOmega/drho_bath_k follows by differentiating over the bath.
 
 Parity: pinned by tests/test_oracle_functional.py (uniform fluid -> the
 fundamental measures, E1/E2 of Sec. "Verification"; a single Fourier mode with
@@ -226,3 +227,24 @@ def grad_omega_rho(prob, rho, V):
 def grad_omega_v(prob, rho):
     """Explicit partial dOmega/dV_i(x) = h^3 rho_i(x)."""
     return prob.dv * rho
+
+
+def grad_omega_bulk(shape, h, radius, z, bulk_molar, rho, V, temperature_K=298.15, eps_r=78.5, rel=1e-3):
+    """dOmega/drho_bath_k / kT (kT nm^3) at fixed rho and V, by its definition: central differences
+    of Omega over the bath density with steps rel*c_k and rel*c_k/2, Richardson-extrapolated.  The
+    bath (mu_ex_bath, mu_ES_bath, Gamma) and the bulk-fluid kernel are recomputed at every
+    displaced bath; the step in mol/L converts to nm^-3 by the molar factor."""
+    c = np.asarray(bulk_molar, dtype=np.float64)
+    out = np.zeros(len(c))
+    for k in range(len(c)):
+        base = rel * c[k] if c[k] > 0 else 1e-9
+        est = []
+        for step in (base, 0.5 * base):
+            cp, cm = c.copy(), c.copy()
+            cp[k] += step
+            cm[k] = max(c[k] - step, 0.0)
+            op = grand_potential(Problem(shape, h, radius, z, cp, temperature_K, eps_r), rho, V)
+            om = grand_potential(Problem(shape, h, radius, z, cm, temperature_K, eps_r), rho, V)
+            est.append((op - om) / (cp[k] - cm[k]))
+        out[k] = (4.0 * est[1] - est[0]) / 3.0 / molar_to_per_nm3(1.0)
+    return out

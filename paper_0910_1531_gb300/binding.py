@@ -64,6 +64,7 @@ SIGNATURES = {
     "dft_iter_begin": (_I, [_P, _P, _P]),
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
+    "dft_grad": (_I, [_P, _P, _P, _PD, _P, _P, _PD]),
     "dft_profile_enable": (_I, [_P, _I]),
     "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
@@ -215,6 +216,19 @@ class Plan:
                                            self._field(V, self.nspecies, "V"), float(alpha),
                                            ctypes.byref(r) if sync else None, ctypes.byref(a) if sync else None))
         return (r.value, a.value) if sync else None
+
+    def grad(self, rho, V, want_rho=True, want_V=True, want_bulk=True):
+        """(Omega, dOmega/drho, dOmega/dV, dOmega/drho_bath) through dft_grad; gradients None if not wanted."""
+        om = _D()
+        d_rho = self.empty(self.nspecies) if want_rho else None
+        d_V = self.empty(self.nspecies) if want_V else None
+        d_bulk = np.zeros(self.nspecies) if want_bulk else None
+        self._check(self.lib.dft_grad(self.handle, self._field(rho, self.nspecies, "rho"),
+                                      self._field(V, self.nspecies, "V"), ctypes.byref(om),
+                                      self._field(d_rho, self.nspecies, "dOmega_drho") if want_rho else None,
+                                      self._field(d_V, self.nspecies, "dOmega_dV") if want_V else None,
+                                      d_bulk.ctypes.data_as(_PD) if want_bulk else None))
+        return om.value, d_rho, d_V, d_bulk
 
     def picard_step_host(self, rho_host, V_host, alpha=-1.0):
         """rho_host, V_host: host tensors/arrays (pinned recommended) of the plan dtype; rho updated in place."""

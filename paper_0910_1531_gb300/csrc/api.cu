@@ -64,6 +64,8 @@ struct dft_plan {
     double prof_ms[K_COUNT] = {0};
     double prof_bytes[K_COUNT] = {0};
     std::string err;
+    double* grad_red = nullptr;     // partial sums of dft_grad (allocated on first use)
+    size_t grad_red_len = 0;
     bool iter_ready = false;
     const void* iter_rho = nullptr;
     const void* iter_V = nullptr;
@@ -121,6 +123,7 @@ template <typename Real> void fill_species(dft_plan* p) {
         sp.rho_b[i] = Real(b.rho[i]);
         sp.inv_rho_b[i] = b.rho[i] > 0 ? Real(1.0 / b.rho[i]) : Real(0);
         sp.mu_hs_b[i] = Real(b.mu_hs[i]);
+        sp.mu_ex_b[i] = Real(b.mu_hs[i] + b.mu_es[i]);
         sp.n_rho_b[i] = Real(double(p->g.n) * b.rho[i]);
     }
     for (int i = 0; i < p->S; ++i)
@@ -137,6 +140,17 @@ template <typename Real> void fill_species(dft_plan* p) {
                 sp.es_c[i][j] = Real(2);
             }
             sp.es_R[i][j] = Real(p->R[i] + p->R[j]);
+            if (b.gamma > 0.0) {
+                // l = R + s, s = 1/(2 Gamma): d/dGamma = d/ds * (-1 / (2 Gamma^2))
+                const double dsdg = -0.5 / (b.gamma * b.gamma);
+                const double li2lj2 = li * li * lj * lj;
+                const double dR = p->R[i] - p->R[j];
+                sp.es_da[i][j] = Real(-(li + lj) / (2.0 * li2lj2) * dsdg);
+                sp.es_db[i][j] = Real(-(1.0 / (li * li) + 1.0 / (lj * lj)) * dsdg);
+                sp.es_dc[i][j] = Real(-dR * dR * (li + lj) / (2.0 * li2lj2) * dsdg);
+            } else {
+                sp.es_da[i][j] = sp.es_db[i][j] = sp.es_dc[i][j] = Real(0);
+            }
             sp.pois[i][j] = Real(4.0 * pi * b.lb * p->z[i] * p->z[j]);
         }
     sp.inv_n = Real(1.0 / double(p->g.n));
@@ -235,12 +249,13 @@ template <typename Real> struct Ops {
 
     // rho (S real fields) -> slot: ten weighted densities (kx, ky, z) and the S (+psi)
     // bulk-fluid / Poisson spectra (kx, ky, kz)
-    static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi) {
+    static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi,
+                                 double* red_energy = nullptr) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_ZFWD, (p->S + DFT_NCOMP + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
-                                       T1(p), slot_n(slot), slot_es(p, slot), tw(p, 2)));
+                                       T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2)));
         LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), &p->ctl->status, tw(p, 1)));
         return DFT_OK;
     }
@@ -255,7 +270,7 @@ template <typename Real> struct Ops {
         C* esB = use_B ? slot_es(p, p->slotB) : nullptr;
         LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NCOMP * CB(p),
                P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
-                                  p->red_max, &p->ctl->status, tw(p, 0)));
+                                  p->red_max, &p->ctl->status, nullptr, tw(p, 0)));
         LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
@@ -361,7 +376,7 @@ template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* 
     TRY(O::first_half(p, rho, p->slotA, 0));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
-                              O::T1(p), p->red_max, &p->ctl->status, O::tw(p, 0)));
+                              O::T1(p), p->red_max, &p->ctl->status, nullptr, O::tw(p, 0)));
     LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), &p->ctl->status, O::tw(p, 1)));
     LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
@@ -394,6 +409,151 @@ template <typename Real> dft_status picard_map_t(dft_plan* p, const Real* rho, c
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, g));
     TRY(finalize(p, FIN_F0 | FIN_N3CUR, (int)p->blocks_x(p->LRupd), (int)p->blocks_x(p->LRphi), -1.0));
+    return DFT_OK;
+}
+
+// Bath derivatives by central differences of the host bath solver, Richardson-extrapolated
+// (h and h/2), in units of the number density: d/drho_bath_k = d/dc_k / 0.602214076.
+struct BathDerivs {
+    std::vector<double> dmu_ex;   // [i * S + k] = d beta mu_ex_bath_i / d rho_bath_k
+    std::vector<double> dmu_es;   // [i * S + k]
+    std::vector<double> dgamma;   // [k]
+};
+
+bool bath_derivatives(dft_plan* p, BathDerivs* d, std::string* err) {
+    const int S = p->S;
+    d->dmu_ex.assign(S * S, 0.0);
+    d->dmu_es.assign(S * S, 0.0);
+    d->dgamma.assign(S, 0.0);
+    const double to_rho = 0.602214076;
+    for (int k = 0; k < S; ++k) {
+        const double c = p->molar[k];
+        const double h = c > 0.0 ? 1e-3 * c : 1e-9;
+        double dex[2][DFT_MAXS] = {}, des[2][DFT_MAXS] = {}, dg[2] = {};
+        for (int lev = 0; lev < 2; ++lev) {
+            const double hh = lev == 0 ? h : 0.5 * h;
+            BathState bp, bm;
+            std::vector<double> cp(p->molar), cm(p->molar);
+            cp[k] = c + hh;
+            cm[k] = c - hh;
+            if (cm[k] < 0.0) cm[k] = 0.0;
+            const double span = cp[k] - cm[k];
+            if (!compute_bath(S, p->R.data(), p->z.data(), cp.data(), p->T, p->eps_r, &bp, err) ||
+                !compute_bath(S, p->R.data(), p->z.data(), cm.data(), p->T, p->eps_r, &bm, err))
+                return false;
+            for (int i = 0; i < S; ++i) {
+                dex[lev][i] = ((bp.mu_hs[i] + bp.mu_es[i]) - (bm.mu_hs[i] + bm.mu_es[i])) / span;
+                des[lev][i] = (bp.mu_es[i] - bm.mu_es[i]) / span;
+            }
+            dg[lev] = (bp.gamma - bm.gamma) / span;
+        }
+        for (int i = 0; i < S; ++i) {
+            d->dmu_ex[i * S + k] = (4.0 * dex[1][i] - dex[0][i]) / 3.0 / to_rho;
+            d->dmu_es[i * S + k] = (4.0 * des[1][i] - des[0][i]) / 3.0 / to_rho;
+        }
+        d->dgamma[k] = (4.0 * dg[1] - dg[0]) / 3.0 / to_rho;
+    }
+    return true;
+}
+
+// Bulk-fluid kernel at k = 0 (limits of the ball integrals), in kT nm^3
+double delta_c_hat_zero(const dft_plan* p, int i, int j) {
+    const BathState& b = p->bath;
+    const double pi = 3.14159265358979323846;
+    const double R = p->R[i] + p->R[j];
+    const double pref = 0.5 * b.lb * p->z[i] * p->z[j];
+    double a = 0.0, bb = 0.0, c = 2.0;
+    if (b.gamma > 0.0) {
+        const double li = b.lam[i], lj = b.lam[j];
+        a = 1.0 / (2.0 * li * lj);
+        bb = (li + lj) / (li * lj);
+        c = (li - lj) * (li - lj) / (2.0 * li * lj) + 2.0;
+    }
+    return pref * (a * pi * R * R * R * R - bb * 4.0 * pi * R * R * R / 3.0 + c * 2.0 * pi * R * R);
+}
+
+template <typename Real>
+dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out, Real* d_rho, Real* d_V,
+                  double* d_bulk) {
+    using O = Ops<Real>;
+    using P = Passes<Real>;
+    const SpeciesDesc<Real>& sp = species<Real>(p);
+    const int S = p->S;
+    const long long n_zk = ceil_div(p->g.nxh, p->Tz) * p->g.ny;
+    const long long n_phi = p->blocks_x(p->LRphi);
+    const long long n_g = p->blocks_x(p->LRupd);
+    const size_t need = size_t(2 * n_zk + n_phi + n_g * (S + 1));
+    if (p->grad_red_len < need) {
+        cudaFree(p->grad_red);
+        p->grad_red = nullptr;
+        if (cudaMalloc(&p->grad_red, need * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            p->grad_red_len = 0;
+            return fail(p, DFT_ENOMEM, "gradient partial sums");
+        }
+        p->grad_red_len = need;
+    }
+    double* r_energy = p->grad_red;
+    double* r_phi = r_energy + 2 * n_zk;
+    double* r_g = r_phi + n_phi;
+    const double dv = p->g.hx * p->g.hy * p->g.hz;
+    TRY(reset_status(p));
+    TRY(O::first_half(p, rho, p->slotA, 0, r_energy));
+    TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA),
+                                                        nullptr, nullptr, O::T1(p), p->red_max, &p->ctl->status,
+                                                        r_phi, O::tw(p, 0)));
+    LAUNCH(p, K_YFFT, 2.0 * DFT_NCOMP * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p),
+                                                        &p->ctl->status, O::tw(p, 1)));
+    LAUNCH(p, K_ZBWD, (DFT_NCOMP + 2 * S) * CB(p),
+           P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 3, S, p->ctl,
+                        O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
+    LAUNCH(p, K_YFFT, 2.0 * S * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, S, O::T1(p), &p->ctl->status,
+                                                O::tw(p, 1)));
+    LAUNCH(p, K_XUPD, S * (CB(p) + RB(p) * (2 + (d_rho ? 1 : 0) + (d_V ? 1 : 0))),
+           P::xgrad(p->stream, p->g, p->ax, sp, p->LRupd, Real(dv), O::T1(p), rho, V, d_rho, d_V, r_g, O::tw(p, 0)));
+    std::vector<double> h(need);
+    cudaError_t e = cudaMemcpyAsync(h.data(), p->grad_red, need * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("reading gradient sums: ") + cudaGetErrorString(e));
+    if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
+    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
+    double energy = 0.0, qgam = 0.0, phisum = 0.0, ideal = 0.0;
+    std::vector<double> Ni(S, 0.0);
+    for (long long b = 0; b < n_zk; ++b) { energy += h[2 * b]; qgam += h[2 * b + 1]; }
+    for (long long b = 0; b < n_phi; ++b) phisum += h[2 * n_zk + b];
+    for (long long b = 0; b < n_g; ++b) {
+        const double* r = &h[2 * n_zk + n_phi + b * (S + 1)];
+        ideal += r[0];
+        for (int i = 0; i < S; ++i) Ni[i] += r[1 + i];
+    }
+    const double N = double(p->g.n);
+    const BathState& bt = p->bath;
+    std::vector<double> D(S);
+    for (int i = 0; i < S; ++i) D[i] = Ni[i] - N * bt.rho[i];
+    double lin = 0.0;
+    for (int i = 0; i < S; ++i) lin += bt.mu_es[i] * D[i];
+    // Omega/kT = h^3 [ideal + ext + sum Phi + sum_i mu_ES_bath_i D_i - (1/2) sum_i sum_x drho_i E_i],
+    // sum_x drho_i E_i = (1/N) sum_k conj(drho_hat_i) es_hat_i (Parseval)
+    const double omega = dv * (ideal + phisum + lin - 0.5 * energy / N);
+    if (!std::isfinite(omega)) return fail(p, DFT_ENONFINITE, "non-finite grand potential");
+    if (omega_out) *omega_out = omega;
+    if (d_bulk) {
+        BathDerivs bd;
+        std::string err;
+        if (!bath_derivatives(p, &bd, &err)) return fail(p, DFT_EINVAL, err);
+        for (int k = 0; k < S; ++k) {
+            double g = 0.0;
+            if (bt.rho[k] > 0.0) g -= Ni[k] / bt.rho[k];
+            for (int i = 0; i < S; ++i) g -= Ni[i] * bd.dmu_ex[i * S + k];
+            for (int i = 0; i < S; ++i) g += bd.dmu_es[i * S + k] * D[i];
+            g -= bt.mu_es[k] * N;
+            g -= 0.5 * bd.dgamma[k] * qgam / N;
+            for (int j = 0; j < S; ++j) g += delta_c_hat_zero(p, k, j) * D[j];
+            d_bulk[k] = dv * g;
+        }
+    }
     return DFT_OK;
 }
 
@@ -541,6 +701,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->stage_V);
     cudaFree(p->red_sum);
     cudaFree(p->red_max);
+    cudaFree(p->grad_red);
     cudaFree(p->ctl);
     if (p->ctl_host) cudaFreeHost(p->ctl_host);
     for (cudaEvent_t ev : p->evpool) cudaEventDestroy(ev);
@@ -685,6 +846,18 @@ dft_status dft_picard_step_host(dft_plan* p, void* rho_host, const void* V_host,
     if (resid_out) *resid_out = r;
     if (alpha_out) *alpha_out = a;
     return DFT_OK;
+}
+
+dft_status dft_grad(dft_plan* p, const void* rho, const void* V, double* omega_out, void* dOmega_drho,
+                    void* dOmega_dV, double* dOmega_dbulk) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    p->iter_ready = false;
+    if (is_fp64(p))
+        return grad_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), omega_out,
+                              static_cast<double*>(dOmega_drho), static_cast<double*>(dOmega_dV), dOmega_dbulk);
+    return grad_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), omega_out,
+                         static_cast<float*>(dOmega_drho), static_cast<float*>(dOmega_dV), dOmega_dbulk);
 }
 
 dft_status dft_profile_enable(dft_plan* p, int enable) {

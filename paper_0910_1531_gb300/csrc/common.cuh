@@ -54,6 +54,7 @@ struct SpeciesDesc {
     Real rho_b[DFT_MAXS];
     Real inv_rho_b[DFT_MAXS];   // residual weights 1 / rho_bath
     Real mu_hs_b[DFT_MAXS];     // beta mu^{HS,bath}
+    Real mu_ex_b[DFT_MAXS];     // beta mu^{ex,bath} = beta (mu^{HS,bath} + mu^{ES,bath})
     Real n_rho_b[DFT_MAXS];     // N * rho_bath: DFT of the bath density at k = 0
     // bulk-fluid kernel per pair (i, j), in kT units
     Real es_pref[DFT_MAXS][DFT_MAXS];   // lambda_B z_i z_j / 2
@@ -62,6 +63,9 @@ struct SpeciesDesc {
     Real es_c[DFT_MAXS][DFT_MAXS];      // (l_i - l_j)^2 / (2 l_i l_j) + 2
     Real es_R[DFT_MAXS][DFT_MAXS];      // R_ij = R_i + R_j
     Real pois[DFT_MAXS][DFT_MAXS];      // 4 pi lambda_B z_i z_j
+    Real es_da[DFT_MAXS][DFT_MAXS];     // d es_a / d Gamma  (gradient with respect to the bath)
+    Real es_db[DFT_MAXS][DFT_MAXS];     // d es_b / d Gamma
+    Real es_dc[DFT_MAXS][DFT_MAXS];     // d es_c / d Gamma
     Real inv_n;                         // 1 / N
     int coulomb_limit;                  // Gamma == 0: kernel is lambda_B z_i z_j / r inside R_ij
 };

@@ -75,14 +75,14 @@ cudaError_t Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, con
 template <typename Real>
 cudaError_t Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                              int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                             const C* tw) {
-    DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw))
+                             double* red_energy, const C* tw) {
+    DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw))
 }
 
 template <typename Real>
 cudaError_t Passes<Real>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                        const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
-    DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, tw))
+                        const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw) {
+    DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, red_phi, tw))
 }
 
 template <typename Real>
@@ -103,6 +103,13 @@ template <typename Real>
 cudaError_t Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                         Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw) {
     DFT_SWITCH_X(g.nx, xinv(st, g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw))
+}
+
+template <typename Real>
+cudaError_t Passes<Real>::xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                                int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
+                                Real* grad_V, double* red, const C* tw) {
+    DFT_SWITCH_X(g.nx, xgrad(st, g, px, sp, LR, dv, cspec, rho, V, grad_rho, grad_V, red, tw))
 }
 
 template struct Passes<float>;

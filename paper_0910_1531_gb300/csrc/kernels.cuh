@@ -88,7 +88,8 @@ template <typename Real> __device__ __forceinline__ void fmt_weights(Real kmag, 
 // Bulk-fluid kernel DC_ij_hat(|k|) of eq. CplusPsiHat (prefactor 2 pi lambda_B z_i z_j / k, i.e.
 // (lambda_B z_i z_j / 2)(4 pi / k) I_n) in kT units.
 template <typename Real>
-__device__ __forceinline__ Real delta_c_hat(Real kmag, Real R, Real pref, Real a, Real b, Real c) {
+__device__ __forceinline__ Real delta_c_hat(Real kmag, Real R, Real pref, Real a, Real b, Real c,
+                                           Real* dGamma = nullptr, Real da = 0, Real db = 0, Real dc = 0) {
     const Real y = kmag * R;
     Real bm1, b0, b1;   // (4 pi / k) I_n / (4 pi R^(n+3))
     if (y < series_cut<Real>()) {
@@ -110,6 +111,8 @@ __device__ __forceinline__ Real delta_c_hat(Real kmag, Real R, Real pref, Real a
     }
     const Real R2 = R * R;
     const Real fourpi = Real(4.0 * CUDART_PI);
+    // the Gamma dependence sits in the coefficients only (l_k = R_k + 1/(2 Gamma))
+    if (dGamma) *dGamma = pref * fourpi * R2 * (da * R2 * b1 - db * R * b0 + dc * bm1);
     return pref * fourpi * R2 * (a * R2 * b1 - b * R * b0 + c * bm1);
 }
 
@@ -389,8 +392,10 @@ __device__ __forceinline__ KPoint<Real> kpoint(const GridDesc& g, int kxi, int k
 // Bulk-fluid + mean-field kernel K_ij(k) = DC_ij_hat(k) - 4 pi lambda_B z_i z_j / lap(k) (k != 0),
 // lap(k) = sum_d 4 sin^2(k_d h_d / 2) / h_d^2 (eq. potentialSolution), psi_hat(0) = 0.
 template <typename Real>
-__device__ __forceinline__ Real es_kernel(const SpeciesDesc<Real>& sp, int i, int j, const KPoint<Real>& p, Real inv_lap) {
-    Real K = delta_c_hat<Real>(p.kmag, sp.es_R[i][j], sp.es_pref[i][j], sp.es_a[i][j], sp.es_b[i][j], sp.es_c[i][j]);
+__device__ __forceinline__ Real es_kernel(const SpeciesDesc<Real>& sp, int i, int j, const KPoint<Real>& p, Real inv_lap,
+                                         Real* dGamma = nullptr) {
+    Real K = delta_c_hat<Real>(p.kmag, sp.es_R[i][j], sp.es_pref[i][j], sp.es_a[i][j], sp.es_b[i][j], sp.es_c[i][j],
+                               dGamma, sp.es_da[i][j], sp.es_db[i][j], sp.es_dc[i][j]);
     if (!p.zero) K -= sp.pois[i][j] * inv_lap;
     return K;
 }
@@ -416,10 +421,16 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
                                                         const typename Cplx<Real>::type* __restrict__ in,
                                                         typename Cplx<Real>::type* __restrict__ slot_n,
                                                         typename Cplx<Real>::type* __restrict__ slot_es,
+                                                        double* __restrict__ red_energy,
                                                         const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
+    __shared__ double scratch_d[32];
     const int nz = NZ > 0 ? NZ : g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
+    // red_energy (optional): per block, [0] = sum_k w Re(conj(drho_hat_i) es_hat_i) and
+    // [1] = sum_k w Re(conj(drho_hat_i) dK_ij/dGamma drho_hat_j), w = 1 on the kx = 0 and Nyquist
+    // planes and 2 elsewhere (the half spectrum standing for the full one)
+    double e_acc = 0.0, q_acc = 0.0;
     const int T = TZ > 0 ? TZ : Trt;
     const int tile = T * nz;
     C* tw = align_ptr<C>(smem_raw);
@@ -484,13 +495,21 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
             }
             C es[DFT_MAXS];
             for (int s = 0; s < S; ++s) es[s] = cmake<C>(Real(0), Real(0));
+            const double wk = (kxi == 0 || (g.nx % 2 == 0 && 2 * kxi == g.nx)) ? 1.0 : 2.0;
             for (int i = 0; i < S; ++i) {
                 for (int j = i; j < S; ++j) {
-                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap);
+                    Real dK = Real(0);
+                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap, red_energy ? &dK : nullptr);
                     es[i] = cadd(es[i], cscale(dv[j], K));
                     if (j != i) es[j] = cadd(es[j], cscale(dv[i], K));
+                    if (red_energy) {
+                        const double re = double(dv[i].x) * dv[j].x + double(dv[i].y) * dv[j].y;
+                        q_acc += wk * double(dK) * re * (j != i ? 2.0 : 1.0);
+                    }
                 }
             }
+            if (red_energy)
+                for (int i = 0; i < S; ++i) e_acc += wk * (double(dv[i].x) * es[i].x + double(dv[i].y) * es[i].y);
             const long long o = (long long)kzi * zstride + col0 + t;
             for (int s = 0; s < S; ++s) slot_es[(long long)s * g.nc + o] = es[s];
             if (want_psi) {
@@ -504,6 +523,15 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
             }
         }
         for (int a = 0; a < 5; ++a) pool[a][idx] = cscale(acc[a], sp.inv_n);
+    }
+    if (red_energy) {
+        const double be = block_sum(e_acc, scratch_d);
+        const double bq = block_sum(q_acc, scratch_d);
+        if (threadIdx.x == 0) {
+            const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            red_energy[2 * b] = be;
+            red_energy[2 * b + 1] = bq;
+        }
     }
     __syncthreads();
 
@@ -544,6 +572,18 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
 // formed in FP64 where n3 >= 0.5, i.e. where n3 approaches 1; below, 1 - n3 is exact in the
 // working precision and log1p / the reciprocal are within 2 ulp.  Returns false if n3 >= 1.
 // ------------------------------------------------------------------------------------
+// Phi itself (eq. Phi), in FP64, for the grand potential; same clamp as the derivatives.
+template <typename Real> __device__ __forceinline__ double phi_value(const Real* n) {
+    const double n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
+    const double D = 1.0 - n3;
+    const double q = double(n[7]) * n[7] + double(n[8]) * n[8] + double(n[9]) * n[9];
+    double xi = (n2 > 1e-30) ? q / (n2 * n2) : 1.0;
+    xi = xi < 0.0 ? 0.0 : (xi > 1.0 ? 1.0 : xi);
+    const double om = 1.0 - xi;
+    const double dot = double(n[4]) * n[7] + double(n[5]) * n[8] + double(n[6]) * n[9];
+    return -n0 * log(D) + (n1 * n2 - dot) / D + n2 * n2 * n2 * om * om * om / (24.0 * CUDART_PI * D * D);
+}
+
 template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n) {
     const Real n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     const Real v1x = n[4], v1y = n[5], v1z = n[6], v2x = n[7], v2y = n[8], v2z = n[9];
@@ -669,10 +709,13 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
                                                    typename Cplx<Real>::type* mat_out,
                                                    typename Cplx<Real>::type* __restrict__ phi_out,
                                                    float* __restrict__ red_max, int* __restrict__ status,
+                                                   double* __restrict__ red_phi,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
+    __shared__ double scratch_d[32];
+    double phi_acc = 0.0;   // sum of Phi(n) over the block's points (grand potential only)
     const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const int lines = 5 * LR;
     C* tw = align_ptr<C>(smem_raw);
@@ -698,6 +741,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
             n[2 * p + 1] = v.y;
         }
         if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
+        if (red_phi && row0 + r < nrows) phi_acc += phi_value<Real>(n);
         const bool ok = phi_derivatives<Real>(n);
         if (!ok && row0 + r < nrows) bad = true;
 #pragma unroll
@@ -710,6 +754,10 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     store_pair_rows<Real, NX>(g, lines, 5, row0, nrows, DFT_NCOMP, F, phi_out);
     const float bm = block_max(mx, scratch_f);
     if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
+    if (red_phi) {
+        const double bp = block_sum(phi_acc, scratch_d);
+        if (threadIdx.x == 0) red_phi[blockIdx.x] = bp;
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -904,6 +952,65 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     if (bad) atomicOr(status, DEV_NONFINITE);
     const double bs = block_sum(double(acc) - double(comp), scratch_d);
     if (threadIdx.x == 0) red_sum[blockIdx.x] = bs;
+}
+
+// ------------------------------------------------------------------------------------
+// Gradient pass: x inverse of the one-body correlations c_i, then at each point
+//   dOmega/drho_i = h^3 [ln(rho_i / rho_bath_i) + V_i - beta mu_HS_bath_i - c_i]   (accessible, rho > 0)
+//   dOmega/dV_i   = h^3 rho_i
+// and per-block sums red[b (S + 1) + 0] = sum_i sum_x [rho_i (ln(rho_i/rho_bath_i) - 1) + rho_i (V_i -
+// beta mu_ex_bath_i)] (accessible points), red[b (S + 1) + 1 + i] = sum_x rho_i, all in FP64.
+// ------------------------------------------------------------------------------------
+template <typename Real, int NX>
+__global__ void __launch_bounds__(kThreads) k_xgrad(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR, Real dv,
+                                                    const typename Cplx<Real>::type* __restrict__ cspec,
+                                                    const Real* __restrict__ rho, const Real* __restrict__ V,
+                                                    Real* __restrict__ grad_rho, Real* __restrict__ grad_V,
+                                                    double* __restrict__ red,
+                                                    const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double scratch_d[32];
+    const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1, S = sp.S;
+    const int lpr = (S + 1) / 2;
+    const int lines = lpr * LR;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lines * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long nrows = (long long)g.ny * g.nz;
+    const long long row0 = (long long)blockIdx.x * LR;
+    load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, S, cspec, nullptr, Real(1), Real(0), nullptr, A);
+    __syncthreads();
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
+    double acc[DFT_MAXS + 1];
+    for (int s = 0; s <= DFT_MAXS; ++s) acc[s] = 0.0;
+    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        const long long row = row0 + r;
+        if (row >= nrows) continue;
+        for (int s = 0; s < S; ++s) {
+            const C pr = R[(r * lpr + s / 2) * pitch + x];
+            const Real c = (s & 1) ? pr.y : pr.x;
+            const long long o = (long long)s * g.n + row * nx + x;
+            const Real rv = rho[o];
+            const Real v = V[o];
+            const bool acc_ok = !(isinf(v) && v > Real(0)) && rv > Real(0);
+            Real gr = Real(0);
+            if (acc_ok) {
+                const double lr = log(double(rv) * double(sp.inv_rho_b[s]));
+                gr = Real(dv * (lr + double(v) - double(sp.mu_hs_b[s]) - double(c)));
+                acc[0] += double(rv) * (lr - 1.0) + double(rv) * (double(v) - double(sp.mu_ex_b[s]));
+            }
+            acc[1 + s] += double(rv);
+            if (grad_rho) grad_rho[o] = gr;
+            if (grad_V) grad_V[o] = dv * rv;
+        }
+    }
+    for (int s = 0; s <= S; ++s) {
+        const double b = block_sum(acc[s], scratch_d);
+        if (threadIdx.x == 0) red[(long long)blockIdx.x * (S + 1) + s] = b;
+    }
 }
 
 // ------------------------------------------------------------------------------------

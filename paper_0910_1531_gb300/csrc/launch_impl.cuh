@@ -32,6 +32,7 @@ cudaError_t LaunchX<Real, N>::init() {
     if ((r = set_max_smem(dftk::k_xphi<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xupdate<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xinv<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xgrad<Real, N>)) != cudaSuccess) e = r;
     return e;
 }
 
@@ -46,10 +47,11 @@ cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const Axi
 
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
-                            const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw) {
+                            const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi,
+                            const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
-                                                                                    red_max, status, tw);
+                                                                                    red_max, status, red_phi, tw);
     return cudaSuccess;
 }
 
@@ -73,6 +75,17 @@ cudaError_t LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const Axi
     const int lpr = (ncomp + 1) / 2;
     dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
         g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw);
+    return cudaSuccess;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchX<Real, N>::xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px,
+                                    const SpeciesDesc<Real>& sp, int LR, Real dv, const C* cspec, const Real* rho,
+                                    const Real* V, Real* grad_rho, Real* grad_V, double* red, const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    const int lpr = (sp.S + 1) / 2;
+    dftk::k_xgrad<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
+        g, px, sp, LR, dv, cspec, rho, V, grad_rho, grad_V, red, tw);
     return cudaSuccess;
 }
 
@@ -143,12 +156,12 @@ cudaError_t LaunchZ<Real, N>::init() {
 template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
-                                 C* slot_es, const C* tw) {
+                                 C* slot_es, double* red_energy, const C* tw) {
     constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
     const int Tu = TZ > 0 ? TZ : T;
     dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
     dftk::k_zconv_fwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
-        g, pz, sp, Tu, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, tw);
+        g, pz, sp, Tu, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
     return cudaSuccess;
 }
 

@@ -31,12 +31,15 @@ struct LaunchX {
     static cudaError_t xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
     static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                     const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
+                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw);
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+    static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                             int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
+                             Real* grad_V, double* red, const C* tw);
 };
 
 template <typename Real, int N>
@@ -53,7 +56,7 @@ struct LaunchZ {
     static cudaError_t init();
     static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                          const C* tw);
+                          double* red_energy, const C* tw);
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
@@ -76,9 +79,9 @@ struct Passes {
                      int* status, const C* tw);
     static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                          const C* tw);
+                          double* red_energy, const C* tw);
     static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                     const C* B, C* mat, C* phi, float* red_max, int* status, const C* tw);
+                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw);
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
@@ -87,6 +90,9 @@ struct Passes {
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+    static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                             int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
+                             Real* grad_V, double* red, const C* tw);
 };
 
 cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
