@@ -193,6 +193,27 @@ dft_status dft_picard_step_host(dft_plan* plan, void* rho_host, const void* V_ho
                                 double* resid_out, double* alpha_out);
 
 /*
+ * Batched state points.  A batch holds `count` independent state points (each
+ * with its own grid -- ragged sizes allowed --, species, bath and precision, as
+ * in dft_plan_create; each owns a plan and a CUDA stream).  dft_batch_begin
+ * takes per-state DEVICE pointers rho[i] ([S_i][N_i], updated in place) and V[i]
+ * and evaluates G for every state.  dft_batch_iterate then advances every state
+ * by `iters` Picard iterations (alpha_or_neg as in dft_picard_step); one
+ * iteration of all states is captured once into a CUDA graph (fork/join across
+ * the state streams) and replayed, so the states run concurrently and the host
+ * does one graph launch per iteration.  resid_out ([count], may be NULL)
+ * receives each state's r after the last iteration (synchronises).
+ * cuda_stream: stream the batch orders its work after (NULL: an internal one).
+ * The rho and V pointers must stay valid and unmoved between begin and iterate.
+ */
+typedef struct dft_batch dft_batch;
+dft_status dft_batch_create(const dft_params* params, int count, void* cuda_stream, dft_batch** out);
+dft_status dft_batch_destroy(dft_batch* batch);
+const char* dft_batch_last_error(const dft_batch* batch);
+dft_status dft_batch_begin(dft_batch* batch, void* const* rho, const void* const* V);
+dft_status dft_batch_iterate(dft_batch* batch, int iters, double alpha_or_neg, double* resid_out);
+
+/*
  * Per-kernel timing with CUDA events recorded on the plan's stream around
  * each launch.  enable != 0 starts collection (and clears totals).
  * dft_profile_read returns, for the kernel kind named by `name`, the number

@@ -65,6 +65,11 @@ SIGNATURES = {
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_grad": (_I, [_P, _P, _P, _PD, _P, _P, _PD]),
+    "dft_batch_create": (_I, [ctypes.POINTER(DftParams), _I, _P, ctypes.POINTER(_P)]),
+    "dft_batch_destroy": (_I, [_P]),
+    "dft_batch_last_error": (ctypes.c_char_p, [_P]),
+    "dft_batch_begin": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "dft_batch_iterate": (_I, [_P, _I, _D, _PD]),
     "dft_profile_enable": (_I, [_P, _I]),
     "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
@@ -256,6 +261,75 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.dft_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Ragged batch of state points advanced together (one CUDA-graph launch per iteration).
+
+    states: list of dicts with keys shape, h, radius, valence, bulk_molar (and optionally
+    temperature_K, eps_r); all share `precision`.
+    """
+
+    def __init__(self, states, precision="fp32", stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.precision = DFT_FP64 if precision in ("fp64", DFT_FP64) else DFT_FP32_STAB
+        self.dtype = torch.float64 if self.precision == DFT_FP64 else torch.float32
+        self.states = []
+        self._keep = []
+        prms = (DftParams * len(states))()
+        for i, st in enumerate(states):
+            nz, ny, nx = st["shape"]
+            h = st["h"]
+            h = (h, h, h) if np.isscalar(h) else h
+            arrs = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("radius", "valence", "bulk_molar")]
+            self._keep.append(arrs)
+            pd = lambda a: a.ctypes.data_as(_PD)
+            prms[i] = DftParams(nx, ny, nz, h[0], h[1], h[2], len(arrs[0]), pd(arrs[0]), pd(arrs[1]), pd(arrs[2]),
+                                float(st.get("temperature_K", 298.15)), float(st.get("eps_r", 78.5)), self.precision)
+            self.states.append((int(nz), int(ny), int(nx), len(arrs[0])))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        handle = ctypes.c_void_p()
+        st = self.lib.dft_batch_create(prms, len(states), ctypes.c_void_p(s.cuda_stream), ctypes.byref(handle))
+        if st != 0:
+            raise DftError(st, self.lib.dft_batch_last_error(None).decode())
+        self.handle = handle
+        self._ptrs = None
+
+    def _check(self, st):
+        if st != 0:
+            raise DftError(st, self.lib.dft_batch_last_error(self.handle).decode())
+
+    def begin(self, rhos, Vs):
+        torch = self._torch
+        for (nz, ny, nx, S), r, v in zip(self.states, rhos, Vs):
+            for t in (r, v):
+                if t.device.type != "cuda" or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != S * nz * ny * nx:
+                    raise ValueError("batch field has the wrong shape, dtype or device")
+        n = len(self.states)
+        rp = (_P * n)(*[r.data_ptr() for r in rhos])
+        vp = (_P * n)(*[v.data_ptr() for v in Vs])
+        self._ptrs = (rp, vp, list(rhos), list(Vs))
+        self._check(self.lib.dft_batch_begin(self.handle, rp, vp))
+
+    def iterate(self, iters, alpha=-1.0, resid=True):
+        out = np.zeros(len(self.states)) if resid else None
+        self._check(self.lib.dft_batch_iterate(self.handle, int(iters), float(alpha),
+                                               out.ctypes.data_as(_PD) if resid else None))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.dft_batch_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -362,6 +362,8 @@ template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Re
 
 dft_status check_plan(dft_plan* p) {
     if (!p) return fail(nullptr, DFT_EINVAL, "NULL plan");
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur == p->device) return DFT_OK;
     cudaError_t e = cudaSetDevice(p->device);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     return DFT_OK;
@@ -858,6 +860,161 @@ dft_status dft_grad(dft_plan* p, const void* rho, const void* V, double* omega_o
                               static_cast<double*>(dOmega_drho), static_cast<double*>(dOmega_dV), dOmega_dbulk);
     return grad_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), omega_out,
                          static_cast<float*>(dOmega_drho), static_cast<float*>(dOmega_dV), dOmega_dbulk);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched state points
+// ---------------------------------------------------------------------------------------
+}  // extern "C"
+
+struct dft_batch {
+    std::vector<dft_plan*> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t main = nullptr;
+    bool own_main = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double graph_alpha = 0.0;
+    std::vector<void*> rho;
+    std::vector<const void*> V;
+    bool begun = false;
+    std::string err;
+};
+
+namespace {
+dft_status bfail(dft_batch* b, dft_status code, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+void batch_release_graph(dft_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+dft_status dft_batch_create(const dft_params* params, int count, void* cuda_stream, dft_batch** out) {
+    if (!params || !out || count < 1) return bfail(nullptr, DFT_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    dft_batch* b = new dft_batch();
+    if (cuda_stream) {
+        b->main = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, DFT_ECUDA, "stream creation failed");
+        }
+        b->own_main = true;
+    }
+    cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            dft_batch_destroy(b);
+            return bfail(nullptr, DFT_ECUDA, "stream creation failed");
+        }
+        b->streams.push_back(st);
+        b->joins.push_back(ev);
+        dft_plan* p = nullptr;
+        dft_status s = dft_plan_create(&params[i], st, &p);
+        if (s != DFT_OK) {
+            const std::string msg = "state " + std::to_string(i) + ": " + g_create_error;
+            dft_batch_destroy(b);
+            return bfail(nullptr, s, msg);
+        }
+        b->plans.push_back(p);
+    }
+    *out = b;
+    return DFT_OK;
+}
+
+dft_status dft_batch_destroy(dft_batch* b) {
+    if (!b) return DFT_OK;
+    batch_release_graph(b);
+    for (dft_plan* p : b->plans) dft_plan_destroy(p);
+    for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->joins) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->own_main) cudaStreamDestroy(b->main);
+    delete b;
+    return DFT_OK;
+}
+
+const char* dft_batch_last_error(const dft_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+dft_status dft_batch_begin(dft_batch* b, void* const* rho, const void* const* V) {
+    if (!b || !rho || !V) return bfail(b, DFT_EINVAL, "NULL argument");
+    batch_release_graph(b);
+    b->rho.assign(rho, rho + b->plans.size());
+    b->V.assign(V, V + b->plans.size());
+    // all states start after work already queued on the main stream
+    cudaEventRecord(b->fork, b->main);
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        dft_status s = dft_iter_begin(b->plans[i], b->rho[i], b->V[i]);
+        if (s != DFT_OK) return bfail(b, s, "state " + std::to_string(i) + ": " + b->plans[i]->err);
+        cudaEventRecord(b->joins[i], b->streams[i]);
+        cudaStreamWaitEvent(b->main, b->joins[i], 0);
+    }
+    b->begun = true;
+    return DFT_OK;
+}
+
+dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, double* resid_out) {
+    if (!b || !b->begun) return bfail(b, DFT_EINVAL, "dft_batch_iterate needs a preceding dft_batch_begin");
+    if (iters < 0) return bfail(b, DFT_EINVAL, "negative iteration count");
+    if (b->exec && b->graph_alpha != alpha_or_neg) batch_release_graph(b);
+    if (!b->exec) {
+        // capture one iteration of every state: fork from the main stream, join back
+        cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        cudaEventRecord(b->fork, b->main);
+        dft_status st = DFT_OK;
+        for (size_t i = 0; i < b->plans.size() && st == DFT_OK; ++i) {
+            cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+            st = dft_iter_step(b->plans[i], b->rho[i], b->V[i], alpha_or_neg, nullptr, nullptr);
+            if (st != DFT_OK) b->err = "state " + std::to_string(i) + ": " + b->plans[i]->err;
+            cudaEventRecord(b->joins[i], b->streams[i]);
+            cudaStreamWaitEvent(b->main, b->joins[i], 0);
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(b->main, &g);
+        if (st != DFT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) {
+            batch_release_graph(b);
+            return bfail(b, DFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        b->graph_alpha = alpha_or_neg;
+    }
+    for (int it = 0; it < iters; ++it) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    }
+    if (resid_out) {
+        cudaError_t e = cudaStreamSynchronize(b->main);
+        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            dft_status s = read_ctl(b->plans[i]);
+            if (s != DFT_OK) return bfail(b, s, "state " + std::to_string(i) + ": " + b->plans[i]->err);
+            resid_out[i] = b->plans[i]->ctl_host->resid;
+        }
+    }
+    return DFT_OK;
 }
 
 dft_status dft_profile_enable(dft_plan* p, int enable) {
