@@ -129,7 +129,9 @@ dft_status dft_picard_map(dft_plan* plan, const void* rho, const void* V, void* 
  * One Picard iteration (eq. picard) with the line search of Sec. "Nonlinear
  * solver": rho <- (1 - alpha) rho + alpha G(rho).  alpha_or_neg >= 0 gives
  * fixed mixing alpha = min(alpha_or_neg, alpha_max); a negative value selects
- * the quadratic line search on r^2 sampled at alpha_max/2 and alpha_max.
+ * the quadratic line search on r^2 sampled at alpha_s/2 and alpha_s, with
+ * alpha_s = min(alpha_max, 2 alpha_prev) (alpha_prev: the previous step's alpha
+ * within dft_solve / dft_iter_step; alpha_s = alpha_max on a first step).
  * alpha_max = min(1, (0.9 - max n3(rho)) / (max n3(G) - max n3(rho))) when
  * max n3(G) > max n3(rho), else 1.  rho_inout: [S][N] device, updated in place.
  * resid_out receives r(rho) before the update, alpha_out the alpha used (either may be NULL).

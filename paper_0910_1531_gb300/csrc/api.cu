@@ -4,6 +4,7 @@
 // control block so an iteration needs no host round trip.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -97,6 +98,14 @@ bool valid_n(int n) {
     while (m % 2 == 0) m /= 2;
     while (m % 3 == 0) m /= 3;
     return m == 1;
+}
+
+// Shared-memory budget of a pass's row block (bytes); a positive environment value overrides it.
+size_t env_budget(const char* name, size_t dflt) {
+    const char* v = std::getenv(name);
+    if (!v) return dflt;
+    const long long x = std::atoll(v);
+    return x > 0 ? size_t(x) : dflt;
 }
 
 int pick_lines(int nx, size_t csize, int lines_per_unit, size_t budget, int cap) {
@@ -630,9 +639,9 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->rsize = f64 ? sizeof(double) : sizeof(float);
     p->Ty = f64 ? Passes<double>::tile_y(g.ny, 100 * 1024) : Passes<float>::tile_y(g.ny, 100 * 1024);
     p->Tz = f64 ? Passes<double>::tile_z(g.nz, 112 * 1024) : Passes<float>::tile_z(g.nz, 112 * 1024);
-    p->LX = pick_lines(g.nx, p->csize, 1, 48 * 1024, 32);
-    p->LRphi = pick_lines(g.nx, p->csize, 5, 64 * 1024, 16);
-    p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, 48 * 1024, 16);
+    p->LX = pick_lines(g.nx, p->csize, 1, env_budget("DFT_XFWD_SMEM", 48 * 1024), 32);
+    p->LRphi = pick_lines(g.nx, p->csize, 5, env_budget("DFT_XPHI_SMEM", 64 * 1024), 16);
+    p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, env_budget("DFT_XUPD_SMEM", 48 * 1024), 16);
     if (f64) fill_species<double>(p);
     else fill_species<float>(p);
 

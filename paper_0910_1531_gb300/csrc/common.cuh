@@ -80,8 +80,9 @@ struct Ctl {
     double wA, wB;          // weights of slot A / slot B weighted densities (XPHI, ZK2)
     double w0, w1;          // weights of rho^(0) / rho^(1) (XU)
     double f[4];            // squared residuals: f0 = r^2(rho0), f1, f2 samples, f3 = accepted point
-    double alpha_max;
-    double alpha;           // accepted alpha of the last step
+    double alpha_max;       // n3 bound of the step
+    double alpha_s;         // sampled interval min(alpha_max, 2 alpha_prev)
+    double alpha;           // accepted alpha of the last step (alpha_prev of the next)
     double alpha_fixed;     // < 0: line search
     double n3max_cur;       // max n3 of the current iterate
     double n3max_next;      // max n3 of G(current)

@@ -1081,7 +1081,10 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* ctl, const double* _
     if (threadIdx.x != 0) return;
     Ctl* c = ctl;
     const double f = tot * inv_count;
-    if (op & FIN_IDENTITY) set_weights(c, 0.0);
+    if (op & FIN_IDENTITY) {
+        set_weights(c, 0.0);
+        c->alpha = 0.5;   // no previous step: the first sampled interval is alpha_max (<= 1 = 2 * 0.5)
+    }
     if (op & FIN_F0) {
         c->f[0] = f;
         c->resid = sqrt(f);
@@ -1101,18 +1104,20 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Ctl* ctl, const double* _
             c->alpha = a;
             set_weights(c, a);
         } else {
-            c->sample_alpha[0] = 0.5 * am;
-            set_weights(c, 0.5 * am);
+            const double as = fmin(am, 2.0 * c->alpha);
+            c->alpha_s = as;
+            c->sample_alpha[0] = 0.5 * as;
+            set_weights(c, 0.5 * as);
         }
     }
     if (op & FIN_F1) {
         c->f[1] = f;
-        c->sample_alpha[1] = c->alpha_max;
-        set_weights(c, c->alpha_max);
+        c->sample_alpha[1] = c->alpha_s;
+        set_weights(c, c->alpha_s);
     }
     if (op & FIN_F2_CHOOSE) {
         c->f[2] = f;
-        const double am = c->alpha_max, a = 0.5 * am;
+        const double am = c->alpha_s, a = 0.5 * am;
         const double f0 = c->f[0], f1 = c->f[1], f2 = f;
         const double c2 = (f0 - 2.0 * f1 + f2) / (2.0 * a * a);
         const double c1 = (-3.0 * f0 + 4.0 * f1 - f2) / (2.0 * a);

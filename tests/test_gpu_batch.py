@@ -53,3 +53,19 @@ def test_batch_matches_independent_plans(precision, alpha):
         assert torch.equal(ref, rho)
         assert np.isfinite(r)
     batch.close()
+
+
+def test_batch_state_with_steep_residual_converges():
+    # 0.87 M NaCl around a 0.95 nm sphere in a 9.6 nm box: the residual grows much faster than
+    # quadratically along the Picard segment; the adaptive sampled interval keeps the line search
+    # converging (with the interval fixed at alpha_max it diverged).
+    from paper_0910_1531_gb300 import binding
+    w = workloads.batch_state_points(count=64, seed=4)[6]
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32")
+    rho = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=torch.float32, device="cuda")
+    V = torch.tensor(w.V, dtype=torch.float32, device="cuda")
+    plan.iter_begin(rho, V)
+    res = [plan.iter_step(rho, V, -1.0)[0] for _ in range(40)]
+    assert all(np.isfinite(res))
+    assert res[-1] < 0.05 * res[0]
+    plan.close()

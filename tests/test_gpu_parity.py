@@ -65,6 +65,8 @@ CASES = [
     ((8, 8, 8), 0.1, 2),
     ((128, 16, 96), (0.05, 0.1, 0.06), 2),   # compile-time z 128, x 96; run-time y 16
     ((32, 256, 128), (0.08, 0.04, 0.1), 3),  # compile-time z 32, y 256, x 128
+    ((96, 96, 16), 0.1, 2),                  # compile-time z 96 and y 96 (TMA), run-time x 16
+    ((48, 64, 48), 0.1, 2),                  # compile-time z 48, y 64, x 48
     ((16, 24, 32), (0.1, 0.08, 0.12), 2),
     ((12, 18, 24), 0.07, 3),
     ((27, 16, 9), 0.09, 2),        # odd x axis (no Nyquist), radix-3 z
@@ -174,9 +176,11 @@ def test_line_search_steps_fp64():
     V = to_dev(w.V, plan)
     ref = rho0.copy()
     plan.iter_begin(rho, V)
+    alpha_prev = None
     for it in range(4):
         r_gpu, a_gpu = plan.iter_step(rho, V, -1.0)
-        ref, info = P.picard_step(prob, ref, w.V)
+        ref, info = P.picard_step(prob, ref, w.V, alpha_prev=alpha_prev)
+        alpha_prev = info["alpha"]
         assert r_gpu == pytest.approx(info["resid"], rel=1e-9)
         assert a_gpu == pytest.approx(info["alpha"], rel=1e-8)
         assert relerr(rho.cpu().numpy(), ref) < 1e-10
