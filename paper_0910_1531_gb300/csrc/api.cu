@@ -640,7 +640,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->Ty = f64 ? Passes<double>::tile_y(g.ny, 100 * 1024) : Passes<float>::tile_y(g.ny, 100 * 1024);
     p->Tz = f64 ? Passes<double>::tile_z(g.nz, 112 * 1024) : Passes<float>::tile_z(g.nz, 112 * 1024);
     p->LX = pick_lines(g.nx, p->csize, 1, env_budget("DFT_XFWD_SMEM", 48 * 1024), 32);
-    p->LRphi = pick_lines(g.nx, p->csize, 5, env_budget("DFT_XPHI_SMEM", 64 * 1024), 16);
+    p->LRphi = pick_lines(g.nx, p->csize, 5, env_budget("DFT_XPHI_SMEM", 32 * 1024), 16);
     p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, env_budget("DFT_XUPD_SMEM", 48 * 1024), 16);
     if (f64) fill_species<double>(p);
     else fill_species<float>(p);

@@ -173,17 +173,23 @@ __host__ __device__ constexpr int ct_ns_at(int n, int s) { int p = 1; for (int i
 
 constexpr int kFftThreads = 256;
 
-// Row pitch (elements) of the compile-time x passes.  A stage with M < 16 butterflies per
-// row puts 16/M rows in one half-warp; a pitch congruent to M modulo 16 sends those rows to
-// disjoint bank groups (8-byte elements).  Lengths without such a stage use an odd pitch.
+// Compile-time x passes keep element e of a row at position e + floor(e / 16): the first
+// Stockham stage writes its outputs with a stride of R (16) elements across threads, which the
+// pad turns into 17 so the eight-byte stores of a half-warp hit distinct banks.
+__host__ __device__ constexpr int ct_xpad(int e) { return e + (e >> 4); }
+
+// Row pitch (elements) of the compile-time x passes: at least the padded row length, and,
+// when a stage has M < 16 butterflies per row (16/M rows in one half-warp), congruent to M
+// modulo 16 so that those rows fall into disjoint bank groups.
 __host__ __device__ constexpr int ct_row_pitch(int n) {
     int msmall = 0;
     for (int s = 0; s < ct_nstages(n); ++s) {
         const int m = n / ct_radix_at(n, s);
         if (m < 16) msmall = m;
     }
-    if (msmall == 0) return n + 1;
-    return n + (((msmall - n) % 16) + 16) % 16;
+    const int len = ct_xpad(n - 1) + 1;
+    if (msmall == 0) return len | 1;
+    return len + (((msmall - len) % 16) + 16) % 16;
 }
 
 // One stage.  COLS: lines are tile columns (element e of line l at e*T + l, line index fastest
@@ -204,7 +210,10 @@ __device__ __forceinline__ void ct_stage(const C* __restrict__ src, C* __restric
         constexpr int ES = COLS ? T : 1;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * M) * ES + off];
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * M;
+            v[r] = src[(COLS ? e * ES : ct_xpad(e)) + off];
+        }
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -216,7 +225,10 @@ __device__ __forceinline__ void ct_stage(const C* __restrict__ src, C* __restric
         dft_small<R, INV>(v);
         const int base = (j / NS) * (NS * R) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * NS) * ES + off] = v[r];
+        for (int r = 0; r < R; ++r) {
+            const int e = base + r * NS;
+            dst[(COLS ? e * ES : ct_xpad(e)) + off] = v[r];
+        }
     }
 }
 
@@ -245,4 +257,66 @@ template <int N, bool INV, bool COLS, int T, typename C>
 __device__ __forceinline__ C* any_fft(C* a, C* b, const AxisPlan& p, int lines, int es, int ls, const C* tw) {
     if constexpr (N > 0) return ct_fft<N, INV, COLS, T>(a, b, lines, ls, tw);
     else return smem_fft<INV>(a, b, p, lines, es, ls, tw);
+}
+
+// ------------------------------------------------------------------------------------
+// Grouped column transforms: `groups` tiles of T columns x N rows, stored one after another
+// (tile g at offset g * ct_gtile(N, T)), transformed together so that every stage has
+// groups * T * N / R butterflies for the CTA's threads.  Element e of column t sits at
+// T * ct_xpad(e) + t: the first stage's outputs, R rows apart across threads, then fall into
+// distinct bank groups (the same pad as the x-pass rows).
+// ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int ct_gpos(int e, int T) { return T * ct_xpad(e); }
+__host__ __device__ constexpr int ct_gtile(int n, int T) { return T * (ct_xpad(n - 1) + 1); }
+
+template <int N, int R, int NS, bool INV, int T, typename C>
+__device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* __restrict__ dst, int groups,
+                                                 const C* __restrict__ tw) {
+    constexpr int M = N / R;
+    constexpr int TWSTEP = N / (NS * R);
+    constexpr int PERG = M * T;
+    constexpr int GS = ct_gtile(N, T);
+    const int total = PERG * groups;
+    for (int task = threadIdx.x; task < total; task += kFftThreads) {
+        const int g = task / PERG;
+        const int rem = task - g * PERG;
+        const int t = rem % T, j = rem / T;
+        const int k = j % NS;
+        const int off = g * GS + t;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[ct_gpos(j + r * M, T) + off];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[k * r * TWSTEP];
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_small<R, INV>(v);
+        const int base = (j / NS) * (NS * R) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[ct_gpos(base + r * NS, T) + off] = v[r];
+    }
+}
+
+template <int N, bool INV, int T, int S, typename C>
+__device__ __forceinline__ void ct_stages_grouped(C*& a, C*& b, int groups, const C* tw) {
+    if constexpr (S < ct_nstages(N)) {
+        constexpr int R = ct_radix_at(N, S);
+        constexpr int NS = ct_ns_at(N, S);
+        ct_stage_grouped<N, R, NS, INV, T>(a, b, groups, tw);
+        __syncthreads();
+        C* t = a; a = b; b = t;
+        ct_stages_grouped<N, INV, T, S + 1>(a, b, groups, tw);
+    }
+}
+
+// Transform `groups` consecutive column tiles held in a (b: scratch of the same size); the
+// caller syncs before; returns the buffer holding the result.
+template <int N, bool INV, int T, typename C>
+__device__ __forceinline__ C* ct_fft_grouped(C* a, C* b, int groups, const C* tw) {
+    ct_stages_grouped<N, INV, T, 0>(a, b, groups, tw);
+    return a;
 }

@@ -147,6 +147,9 @@ __device__ __forceinline__ float block_max(float v, float* scratch) {
     return r;
 }
 
+// Position of element e within an x-pass row: padded in the compile-time passes (see ct_xpad).
+template <int NX> __device__ __forceinline__ int xo(int e) { return NX > 0 ? ct_xpad(e) : e; }
+
 template <typename C> __device__ __forceinline__ C* align_ptr(unsigned char* p) {
     uintptr_t u = reinterpret_cast<uintptr_t>(p);
     u = (u + 15) & ~uintptr_t(15);
@@ -254,15 +257,15 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
         const long long ra = 2 * (pair0 + l), rb = ra + 1;
         const Real a = (ra < rows) ? in[ra * nx + x] : Real(0);
         const Real b = (rb < rows) ? in[rb * nx + x] : Real(0);
-        A[l * pitch + x] = cmake<C>(a, b);
+        A[l * pitch + xo<NX>(x)] = cmake<C>(a, b);
     }
     __syncthreads();
     C* R = any_fft<NX, false, false, 0>(A, B, px, lx, 1, pitch, tw);
     for (int idx = threadIdx.x; idx < lx * nxh; idx += blockDim.x) {
         const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
         const long long ra = 2 * (pair0 + l), rb = ra + 1;
-        const C zk = R[l * pitch + k];
-        const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
+        const C zk = R[l * pitch + xo<NX>(k)];
+        const C znk = R[l * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
         const C s = cadd(zk, cconj(znk));
         const C d = csub(zk, cconj(znk));
         if (ra < rows) out[ra * g.pxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
@@ -415,7 +418,7 @@ __device__ __forceinline__ Real inverse_laplacian(const KPoint<Real>& p, Real hx
 //   slot_es: S (+1 with psi) unnormalised bulk-fluid/Poisson spectra sum_j K_ij drho_hat_j (kx, ky, kz)
 // Shared pool of 7 tiles of T x nz.
 // ------------------------------------------------------------------------------------
-template <typename Real, int NZ, int TZ>
+template <typename Real, int NZ, int TZ, bool GRAD>
 __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz, SpeciesDesc<Real> sp, int Trt,
                                                         Real kfx, Real kfy, Real kfz, int want_psi,
                                                         const typename Cplx<Real>::type* __restrict__ in,
@@ -495,20 +498,20 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
             }
             C es[DFT_MAXS];
             for (int s = 0; s < S; ++s) es[s] = cmake<C>(Real(0), Real(0));
-            const double wk = (kxi == 0 || (g.nx % 2 == 0 && 2 * kxi == g.nx)) ? 1.0 : 2.0;
+            const double wk = GRAD ? ((kxi == 0 || (g.nx % 2 == 0 && 2 * kxi == g.nx)) ? 1.0 : 2.0) : 0.0;
             for (int i = 0; i < S; ++i) {
                 for (int j = i; j < S; ++j) {
                     Real dK = Real(0);
-                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap, red_energy ? &dK : nullptr);
+                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap, GRAD ? &dK : nullptr);
                     es[i] = cadd(es[i], cscale(dv[j], K));
                     if (j != i) es[j] = cadd(es[j], cscale(dv[i], K));
-                    if (red_energy) {
+                    if constexpr (GRAD) {
                         const double re = double(dv[i].x) * dv[j].x + double(dv[i].y) * dv[j].y;
                         q_acc += wk * double(dK) * re * (j != i ? 2.0 : 1.0);
                     }
                 }
             }
-            if (red_energy)
+            if constexpr (GRAD)
                 for (int i = 0; i < S; ++i) e_acc += wk * (double(dv[i].x) * es[i].x + double(dv[i].y) * es[i].y);
             const long long o = (long long)kzi * zstride + col0 + t;
             for (int s = 0; s < S; ++s) slot_es[(long long)s * g.nc + o] = es[s];
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
         }
         for (int a = 0; a < 5; ++a) pool[a][idx] = cscale(acc[a], sp.inv_n);
     }
-    if (red_energy) {
+    if constexpr (GRAD) {
         const double be = block_sum(e_acc, scratch_d);
         const double bq = block_sum(q_acc, scratch_d);
         if (threadIdx.x == 0) {
@@ -564,6 +567,260 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
         tile_store<TZ, NZ>(slot_n + (long long)a * g.nc + col0, r, zstride, nxh - kx0, T, nz);
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------------------------------
+// Grouped z passes (compile-time length NZ, tile width TZ), grid (ceil(nxh/TZ), ny).  All
+// components of a column tile are loaded in one batch of in-flight loads and transformed by
+// one grouped FFT (ct_fft_grouped), so every stage keeps the CTA's threads busy and a tile
+// costs a handful of barriers instead of a dozen transforms of one component each.
+// Shared memory: twiddles | 10 tiles | 10 tiles (ct_gtile(NZ, TZ) elements each).
+// ------------------------------------------------------------------------------------
+template <int TT, int NN> __host__ __device__ constexpr size_t zg_smem_bytes(size_t csize) {
+    return (size_t(NN) + 2 * size_t(DFT_NCOMP) * ct_gtile(NN, TT)) * csize + 16;
+}
+
+// Load `groups` column tiles (component c at src + c * cstride, global row stride rs, columns
+// t < valid, zero elsewhere) into the grouped layout; every load of a thread is issued before
+// its first shared-memory store.
+template <int TT, int NN, int GMAX, typename C>
+__device__ __forceinline__ void tiles_load_grouped(C* __restrict__ dst, const C* __restrict__ src, long long cstride,
+                                                   int groups, long long rs, int valid) {
+    constexpr int TILE = TT * NN;
+    constexpr int PER = (TILE + kThreads - 1) / kThreads;
+    constexpr int GS = ct_gtile(NN, TT);
+    C reg[GMAX][PER];
+#pragma unroll
+    for (int gi = 0; gi < GMAX; ++gi) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            const int e = idx / TT, t = idx % TT;
+            reg[gi][i] = cmake<C>(0, 0);
+            if (gi < groups && (TILE % kThreads == 0 || idx < TILE) && t < valid)
+                reg[gi][i] = src[gi * cstride + e * rs + t];
+        }
+    }
+#pragma unroll
+    for (int gi = 0; gi < GMAX; ++gi) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            const int e = idx / TT, t = idx % TT;
+            if (gi < groups && (TILE % kThreads == 0 || idx < TILE)) dst[gi * GS + ct_gpos(e, TT) + t] = reg[gi][i];
+        }
+    }
+}
+
+template <int TT, int NN, typename C>
+__device__ __forceinline__ void tiles_store_grouped(C* __restrict__ dst, const C* __restrict__ src, long long cstride,
+                                                    int groups, long long rs, int valid) {
+    constexpr int TILE = TT * NN;
+    constexpr int GS = ct_gtile(NN, TT);
+    for (int gi = 0; gi < groups; ++gi) {
+#pragma unroll
+        for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
+            const int e = idx / TT, t = idx % TT;
+            if (t < valid) dst[gi * cstride + e * rs + t] = src[gi * GS + ct_gpos(e, TT) + t];
+        }
+    }
+}
+
+// First-half z pass (same contract as k_zconv_fwd): S species spectra in, the ten weighted
+// densities (z inverse, 1/N applied) and the bulk-fluid/Poisson spectra out.
+template <typename Real, int NZ, int TZ, bool GRAD>
+__global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
+                                                          Real kfz, int want_psi,
+                                                          const typename Cplx<Real>::type* __restrict__ in,
+                                                          typename Cplx<Real>::type* __restrict__ slot_n,
+                                                          typename Cplx<Real>::type* __restrict__ slot_es,
+                                                          double* __restrict__ red_energy,
+                                                          const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    constexpr int TILE = TZ * NZ;
+    constexpr int GS = ct_gtile(NZ, TZ);
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double scratch_d[32];
+    const int ny = g.ny, nxh = g.nxh, S = sp.S;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + NZ;
+    C* B = A + DFT_NCOMP * GS;
+    for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = twz[i];
+    const int kx0 = blockIdx.x * TZ;
+    const int kyi = blockIdx.y;
+    const long long zstride = (long long)ny * g.pxh;
+    const long long col0 = (long long)kyi * g.pxh + kx0;
+    tiles_load_grouped<TZ, NZ, DFT_MAXS>(A, in + col0, g.nc, S, zstride, nxh - kx0);
+    __syncthreads();
+    C* R = ct_fft_grouped<NZ, false, TZ>(A, B, S, tw);
+    C* O = (R == A) ? B : A;
+
+    const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    double e_acc = 0.0, q_acc = 0.0;
+    for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
+        const int kzi = idx / TZ, t = idx % TZ;
+        const int pos = ct_gpos(kzi, TZ) + t;
+        const int kxi = kx0 + t;
+        const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+        C v[DFT_MAXS];
+        for (int s = 0; s < S; ++s) v[s] = R[s * GS + pos];
+        C acc[5];
+        for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
+        for (int s = 0; s < S; ++s) {
+            Real w0, j3;
+            fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
+            const Real Rs = sp.R[s];
+            acc[0] = cadd(acc[0], cscale(v[s], w0));
+            acc[1] = cadd(acc[1], cscale(v[s], Rs * w0));
+            acc[2] = cadd(acc[2], cscale(v[s], fourpi * Rs * Rs * w0));
+            acc[3] = cadd(acc[3], cscale(v[s], fourpi * Rs * Rs * Rs * j3));
+            acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
+        }
+        if (kxi < nxh) {
+            const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+            C dv[DFT_MAXS];
+            for (int s = 0; s < S; ++s) {
+                dv[s] = v[s];
+                if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+            }
+            C es[DFT_MAXS];
+            for (int s = 0; s < S; ++s) es[s] = cmake<C>(Real(0), Real(0));
+            const double wk = GRAD ? ((kxi == 0 || (g.nx % 2 == 0 && 2 * kxi == g.nx)) ? 1.0 : 2.0) : 0.0;
+            for (int i = 0; i < S; ++i) {
+                for (int j = i; j < S; ++j) {
+                    Real dK = Real(0);
+                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap, GRAD ? &dK : nullptr);
+                    es[i] = cadd(es[i], cscale(dv[j], K));
+                    if (j != i) es[j] = cadd(es[j], cscale(dv[i], K));
+                    if constexpr (GRAD) {
+                        const double re = double(dv[i].x) * dv[j].x + double(dv[i].y) * dv[j].y;
+                        q_acc += wk * double(dK) * re * (j != i ? 2.0 : 1.0);
+                    }
+                }
+            }
+            if constexpr (GRAD)
+                for (int i = 0; i < S; ++i) e_acc += wk * (double(dv[i].x) * es[i].x + double(dv[i].y) * es[i].y);
+            const long long o = (long long)kzi * zstride + col0 + t;
+            for (int s = 0; s < S; ++s) slot_es[(long long)s * g.nc + o] = es[s];
+            if (want_psi) {
+                C q = cmake<C>(Real(0), Real(0));
+                for (int s = 0; s < S; ++s) q = cadd(q, cscale(v[s], sp.z[s]));
+                // psi_hat = 4 pi lambda_B q_hat / lap; pois[s][s] / z_s^2 = 4 pi lambda_B
+                Real flb = Real(0);
+                for (int s = 0; s < S; ++s)
+                    if (sp.z[s] != Real(0)) { flb = sp.pois[s][s] / (sp.z[s] * sp.z[s]); break; }
+                slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
+            }
+        }
+        // the ten weighted-density spectra, 1/N applied; vector components are i k_d m_hat
+        // (n_V1) and i k_d n3_hat (n_V2), zero on the Nyquist index of axis d
+        for (int a = 0; a < 4; ++a) O[a * GS + pos] = cscale(acc[a], sp.inv_n);
+        const Real kd[3] = {p.kx, p.ky, p.kz};
+        const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
+        const C m = cscale(acc[4], sp.inv_n), n3 = cscale(acc[3], sp.inv_n);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            O[(4 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * m.y, kd[d] * m.x);
+            O[(7 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * n3.y, kd[d] * n3.x);
+        }
+    }
+    if constexpr (GRAD) {
+        const double be = block_sum(e_acc, scratch_d);
+        const double bq = block_sum(q_acc, scratch_d);
+        if (threadIdx.x == 0) {
+            const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            red_energy[2 * b] = be;
+            red_energy[2 * b + 1] = bq;
+        }
+    }
+    __syncthreads();
+    C* Q = ct_fft_grouped<NZ, true, TZ>(O, R, DFT_NCOMP, tw);
+    tiles_store_grouped<TZ, NZ>(slot_n + col0, Q, g.nc, DFT_NCOMP, zstride, nxh - kx0);
+}
+
+// Second-half z pass (same contract as k_zconv_bwd): the ten Phi' spectra in (flags & 1), the
+// bulk-fluid/Poisson spectra mixed in (flags & 2), ncomp_out one-body correlation spectra out.
+template <typename Real, int NZ, int TZ>
+__global__ void __launch_bounds__(kThreads) k_zconv_bwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
+                                                          Real kfz, int flags, int ncomp_out,
+                                                          const Ctl* __restrict__ ctl,
+                                                          typename Cplx<Real>::type* phi,
+                                                          const typename Cplx<Real>::type* esA,
+                                                          const typename Cplx<Real>::type* esB,
+                                                          typename Cplx<Real>::type* es_mat,
+                                                          const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    constexpr int TILE = TZ * NZ;
+    constexpr int GS = ct_gtile(NZ, TZ);
+    extern __shared__ unsigned char smem_raw[];
+    const int ny = g.ny, nxh = g.nxh, S = sp.S;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + NZ;
+    C* B = A + DFT_NCOMP * GS;
+    for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = twz[i];
+    const int kx0 = blockIdx.x * TZ;
+    const int kyi = blockIdx.y;
+    const long long zstride = (long long)ny * g.pxh;
+    const long long col0 = (long long)kyi * g.pxh + kx0;
+    const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
+    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+    C* R = A;
+    if (hs) {
+        tiles_load_grouped<TZ, NZ, DFT_NCOMP>(A, phi + col0, g.nc, DFT_NCOMP, zstride, nxh - kx0);
+        __syncthreads();
+        R = ct_fft_grouped<NZ, false, TZ>(A, B, DFT_NCOMP, tw);
+    }
+    C* O = (R == A) ? B : A;
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
+        const int kzi = idx / TZ, t = idx % TZ;
+        const int pos = ct_gpos(kzi, TZ) + t;
+        const int kxi = kx0 + t;
+        C out[DFT_MAXS + 1];
+        for (int s = 0; s < DFT_MAXS + 1; ++s) out[s] = cmake<C>(Real(0), Real(0));
+        if (hs) {
+            const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+            // species-independent sums: Phi_0..Phi_3, with -i k_d Phi_V2d added to the third and
+            // -i k_d Phi_V1d summed into a fifth (Nyquist components of axis d dropped)
+            const C a0 = R[0 * GS + pos], a1 = R[1 * GS + pos], a2 = R[2 * GS + pos];
+            C a3 = R[3 * GS + pos];
+            C a4 = cmake<C>(Real(0), Real(0));
+            const Real kd[3] = {p.kx, p.ky, p.kz};
+            const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (nyq[d]) continue;
+                const C u1 = R[(4 + d) * GS + pos], u2 = R[(7 + d) * GS + pos];
+                a4 = cadd(a4, cmake<C>(kd[d] * u1.y, -kd[d] * u1.x));
+                a3 = cadd(a3, cmake<C>(kd[d] * u2.y, -kd[d] * u2.x));
+            }
+            for (int s = 0; s < S; ++s) {
+                Real w0, j3;
+                const Real Rs = sp.R[s];
+                fmt_weights<Real>(p.kmag, Rs, &w0, &j3);
+                C mu = cscale(a0, w0);
+                mu = cadd(mu, cscale(a1, Rs * w0));
+                mu = cadd(mu, cscale(a2, fourpi * Rs * Rs * w0));
+                mu = cadd(mu, cscale(a3, fourpi * Rs * Rs * Rs * j3));
+                mu = cadd(mu, cscale(a4, Rs * Rs * j3));
+                out[s] = cmake<C>(-mu.x, -mu.y);
+            }
+        }
+        if (es_on && kxi < nxh) {
+            const long long o = (long long)kzi * zstride + col0 + t;
+            for (int s = 0; s < ncomp_out; ++s) {
+                C e = cscale(esA[(long long)s * g.nc + o], wA);
+                if (esB) e = cadd(e, cscale(esB[(long long)s * g.nc + o], wB));
+                if (es_mat) es_mat[(long long)s * g.nc + o] = e;
+                out[s] = cadd(out[s], e);
+            }
+        }
+        for (int s = 0; s < ncomp_out; ++s) O[s * GS + pos] = cscale(out[s], sp.inv_n);
+    }
+    __syncthreads();
+    C* Q = ct_fft_grouped<NZ, true, TZ>(O, R, ncomp_out, tw);
+    tiles_store_grouped<TZ, NZ>(phi + col0, Q, g.nc, ncomp_out, zstride, nxh - kx0);
 }
 
 // ------------------------------------------------------------------------------------
@@ -671,8 +928,8 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
                 mat_out[oa[j]] = a;
                 if (hasb[j]) mat_out[ob[j]] = b;
             }
-            dst[l * pitch + k] = cmake<C>(a.x - b.y, a.y + b.x);
-            if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + (nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
         }
     }
 }
@@ -689,8 +946,8 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
         const long long row = row0 + l / lines_per_row;
         if (row >= nrows) continue;
         const int ca = 2 * (l % lines_per_row), cb = ca + 1;
-        const C zk = R[l * pitch + k];
-        const C znk = R[l * pitch + (k == 0 ? 0 : nx - k)];
+        const C zk = R[l * pitch + xo<NX>(k)];
+        const C znk = R[l * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
         const C s = cadd(zk, cconj(znk));
         const C d = csub(zk, cconj(znk));
         out[(long long)ca * g.nc + row * g.pxh + k] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
@@ -732,7 +989,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     bool bad = false;
     for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
         const int r = idx / nx, x = idx - (idx / nx) * nx;
-        C* base = R + (r * 5) * pitch + x;
+        C* base = R + (r * 5) * pitch + xo<NX>(x);
         Real n[DFT_NCOMP];
 #pragma unroll
         for (int p = 0; p < 5; ++p) {
@@ -931,7 +1188,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
 #pragma unroll
         for (int s = 0; s < DFT_MAXS; ++s) {
             if (s >= S) continue;
-            const C pr = R[(r * lpr + s / 2) * pitch + x];
+            const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
             const Real c = (s & 1) ? pr.y : pr.x;
             const long long o = (long long)s * g.n + row * nx + x;
             const Real rho = w0 * r0[s] + w1 * r1[s];
@@ -990,7 +1247,7 @@ __global__ void __launch_bounds__(kThreads) k_xgrad(GridDesc g, AxisPlan px, Spe
         const long long row = row0 + r;
         if (row >= nrows) continue;
         for (int s = 0; s < S; ++s) {
-            const C pr = R[(r * lpr + s / 2) * pitch + x];
+            const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
             const Real c = (s & 1) ? pr.y : pr.x;
             const long long o = (long long)s * g.n + row * nx + x;
             const Real rv = rho[o];
@@ -1045,7 +1302,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
         const long long row = row0 + r;
         if (row >= nrows) continue;
         for (int c = 0; c < ncomp; ++c) {
-            const C pr = R[(r * lpr + c / 2) * pitch + x];
+            const C pr = R[(r * lpr + c / 2) * pitch + xo<NX>(x)];
             const Real v = ((c & 1) ? pr.y : pr.x) + off.v[c];
             if (out_last && c == ncomp - 1) out_last[row * nx + x] = v;
             else if (out) out[(long long)c * g.n + row * nx + x] = v;

@@ -144,12 +144,20 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
 }
 
 // ---------------------------------------------------------------------------------- z
+// N > 0: grouped kernels (all components of a tile in one transform); N == 0: run-time path.
 template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::init() {
-    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
     cudaError_t e = cudaSuccess, r;
-    if ((r = set_max_smem(dftk::k_zconv_fwd<Real, N, TZ>)) != cudaSuccess) e = r;
-    if ((r = set_max_smem(dftk::k_zconv_bwd<Real, N, TZ>)) != cudaSuccess) e = r;
+    if constexpr (N > 0) {
+        constexpr int TZ = dft_tile_z<Real>(N);
+        if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, false>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, true>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_zconv_bwd_g<Real, N, TZ>)) != cudaSuccess) e = r;
+    } else {
+        if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_zconv_bwd<Real, 0, 0>)) != cudaSuccess) e = r;
+    }
     return e;
 }
 
@@ -157,11 +165,26 @@ template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
                                  C* slot_es, double* red_energy, const C* tw) {
-    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
-    const int Tu = TZ > 0 ? TZ : T;
-    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
-    dftk::k_zconv_fwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
-        g, pz, sp, Tu, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
+    if constexpr (N > 0) {
+        constexpr int TZ = dft_tile_z<Real>(N);
+        const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
+        dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
+        if (red_energy)
+            dftk::k_zconv_fwd_g<Real, N, TZ, true><<<grid, dftk::kThreads, sm, st>>>(
+                g, sp, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
+        else
+            dftk::k_zconv_fwd_g<Real, N, TZ, false><<<grid, dftk::kThreads, sm, st>>>(
+                g, sp, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, nullptr, tw);
+    } else {
+        dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.ny);
+        const size_t sm = smem_col_of<C>(g.nz, T, 7);
+        if (red_energy)
+            dftk::k_zconv_fwd<Real, 0, 0, true><<<grid, dftk::kThreads, sm, st>>>(
+                g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
+        else
+            dftk::k_zconv_fwd<Real, 0, 0, false><<<grid, dftk::kThreads, sm, st>>>(
+                g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, nullptr, tw);
+    }
     return cudaSuccess;
 }
 
@@ -169,10 +192,16 @@ template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                                  const C* esA, const C* esB, C* es_mat, const C* tw) {
-    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 0;
-    const int Tu = TZ > 0 ? TZ : T;
-    dim3 grid((unsigned)ceil_div(g.nxh, Tu), (unsigned)g.ny);
-    dftk::k_zconv_bwd<Real, N, TZ><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, Tu, 7), st>>>(
-        g, pz, sp, Tu, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
+    if constexpr (N > 0) {
+        constexpr int TZ = dft_tile_z<Real>(N);
+        const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
+        dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
+        dftk::k_zconv_bwd_g<Real, N, TZ><<<grid, dftk::kThreads, sm, st>>>(
+            g, sp, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
+    } else {
+        dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.ny);
+        dftk::k_zconv_bwd<Real, 0, 0><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, T, 7), st>>>(
+            g, pz, sp, T, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
+    }
     return cudaSuccess;
 }

@@ -20,8 +20,15 @@ __host__ __device__ constexpr bool dft_is_ct_size(int n) {
 
 // Column-tile widths of the compile-time y and z passes (kx columns per tile).
 template <typename Real> __host__ __device__ constexpr int dft_tile_y(int n) { return sizeof(Real) == 4 ? 16 : 8; }
+// The compile-time z passes transform all components of a tile together (two pools of ten
+// tiles in shared memory): the width keeps a CTA near 86 KB (FP32) so that two fit on an SM.
+// DFT_TILE_ZG_SHIFT (build flag, default 0) narrows the tiles by that power of two.
+#ifndef DFT_TILE_ZG_SHIFT
+#define DFT_TILE_ZG_SHIFT 0
+#endif
 template <typename Real> __host__ __device__ constexpr int dft_tile_z(int n) {
-    return sizeof(Real) == 4 ? (n <= 64 ? 16 : (n <= 128 ? 8 : 4)) : (n <= 64 ? 8 : (n <= 128 ? 4 : 2));
+    const int t = (n <= 32 ? 16 : (n <= 64 ? 8 : (n <= 128 ? 4 : 2))) / (sizeof(Real) == 4 ? 1 : 2);
+    return (t >> DFT_TILE_ZG_SHIFT) > 0 ? (t >> DFT_TILE_ZG_SHIFT) : 1;
 }
 
 template <typename Real, int N>
