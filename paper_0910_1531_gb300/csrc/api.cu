@@ -65,6 +65,7 @@ struct dft_plan {
     double prof_ms[K_COUNT] = {0};
     double prof_bytes[K_COUNT] = {0};
     std::string err;
+    void* ktab = nullptr;           // |k| tables of the compile-time z passes (cubic boxes)
     double* grad_red = nullptr;     // partial sums of dft_grad (allocated on first use)
     size_t grad_red_len = 0;
     bool iter_ready = false;
@@ -684,6 +685,38 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         }
     }
     cudaMemset(p->ctl, 0, sizeof(Ctl));
+    // On a cubic box |k| = kf sqrt(mx^2 + my^2 + mz^2) takes one value per integer m2, so the
+    // compile-time z passes read the FMT weights and bulk-fluid kernels from per-m2 tables
+    // instead of evaluating them at every point.
+    if (dft_is_ct_size(g.nz) && p->kf[0] == p->kf[1] && p->kf[1] == p->kf[2]) {
+        const long long m2max = (long long)(g.nx / 2) * (g.nx / 2) + (long long)(g.ny / 2) * (g.ny / 2) +
+                                (long long)(g.nz / 2) * (g.nz / 2);
+        const long long P = (long long)S * (S + 1) / 2;
+        const long long rows = m2max + 1;
+        if (cudaMalloc(&p->ktab, size_t(rows * (2 * S + 2 * P)) * p->rsize) != cudaSuccess) {
+            cudaGetLastError();
+            dft_plan_destroy(p);
+            return fail(nullptr, DFT_ENOMEM, "cudaMalloc failed: |k| tables");
+        }
+        cudaError_t te;
+        if (f64) {
+            SpeciesDesc<double>& sp = p->spd;
+            double* base = static_cast<double*>(p->ktab);
+            sp.tab_w = base; sp.tab_k = base + rows * 2 * S; sp.tab_dk = base + rows * (2 * S + P);
+            sp.tab_m2max = (int)m2max;
+            te = Passes<double>::build_ktab(nullptr, sp, p->kf[0]);
+        } else {
+            SpeciesDesc<float>& sp = p->spf;
+            float* base = static_cast<float*>(p->ktab);
+            sp.tab_w = base; sp.tab_k = base + rows * 2 * S; sp.tab_dk = base + rows * (2 * S + P);
+            sp.tab_m2max = (int)m2max;
+            te = Passes<float>::build_ktab(nullptr, sp, p->kf[0]);
+        }
+        if (te != cudaSuccess) {
+            dft_plan_destroy(p);
+            return fail(nullptr, DFT_ECUDA, std::string("|k| tables: ") + cudaGetErrorString(te));
+        }
+    }
     if (cudaMallocHost(&p->ctl_host, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
         dft_plan_destroy(p);
@@ -713,6 +746,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->red_sum);
     cudaFree(p->red_max);
     cudaFree(p->grad_red);
+    cudaFree(p->ktab);
     cudaFree(p->ctl);
     if (p->ctl_host) cudaFreeHost(p->ctl_host);
     for (cudaEvent_t ev : p->evpool) cudaEventDestroy(ev);

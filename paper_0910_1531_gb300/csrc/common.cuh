@@ -68,7 +68,16 @@ struct SpeciesDesc {
     Real es_dc[DFT_MAXS][DFT_MAXS];     // d es_c / d Gamma
     Real inv_n;                         // 1 / N
     int coulomb_limit;                  // Gamma == 0: kernel is lambda_B z_i z_j / r inside R_ij
+    // Optional tables of the |k|-only factors on a cubic box, indexed by the integer
+    // m2 = mx^2 + my^2 + mz^2 (|k| = kf sqrt(m2)); null: the kernels evaluate them per point.
+    const Real* tab_w;                  // [m2][2 S]: w0_s at 2 s, j3_s at 2 s + 1
+    const Real* tab_k;                  // [m2][S (S + 1) / 2]: DC_ij_hat at j (j + 1) / 2 + i, i <= j
+    const Real* tab_dk;                 // [m2][S (S + 1) / 2]: d DC_ij_hat / d Gamma, same order
+    int tab_m2max;
 };
+
+// Index of the pair (i, j), i <= j, in a table record (independent of S).
+__host__ __device__ constexpr int dft_pair(int i, int j) { return j * (j + 1) / 2 + i; }
 
 // Per-component additive constants of the plain x inverse.
 template <typename Real> struct Offsets { Real v[DFT_NCOMP + 2]; };

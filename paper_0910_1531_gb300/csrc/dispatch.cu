@@ -45,6 +45,14 @@ cudaError_t Passes<Real>::init_attributes() {
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf) {
+    const int n = sp.tab_m2max + 1;
+    dftk::k_ktab<Real><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(sp, kf, sp.tab_m2max, const_cast<Real*>(sp.tab_w),
+                                                                  const_cast<Real*>(sp.tab_k), const_cast<Real*>(sp.tab_dk));
+    return cudaGetLastError();
+}
+
+template <typename Real>
 int Passes<Real>::tile_y(int n, size_t budget) {
     if (dft_is_ct_size(n)) return dft_tile_y<Real>(n);
     for (int T = 16; T >= 1; T /= 2)

@@ -626,22 +626,53 @@ __device__ __forceinline__ void tiles_store_grouped(C* __restrict__ dst, const C
     }
 }
 
+// Tables of the |k|-only factors for a cubic box (kf equal on the three axes): the FMT weights
+// w0, j3 of each species and the bulk-fluid kernel DC_ij_hat with its Gamma derivative, at
+// |k| = kf sqrt(m2) for every integer m2 in [0, m2max].  Evaluated once per plan with the same
+// functions the z passes call per point.
+template <typename Real>
+__global__ void k_ktab(SpeciesDesc<Real> sp, double kf, int m2max, Real* tab_w, Real* tab_k, Real* tab_dk) {
+    const int m2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m2 > m2max) return;
+    const int S = sp.S, P = S * (S + 1) / 2;
+    const Real kmag = Real(kf * sqrt(double(m2)));
+    for (int s = 0; s < S; ++s) {
+        Real w0, j3;
+        fmt_weights<Real>(kmag, sp.R[s], &w0, &j3);
+        tab_w[(long long)m2 * 2 * S + 2 * s] = w0;
+        tab_w[(long long)m2 * 2 * S + 2 * s + 1] = j3;
+    }
+    for (int j = 0; j < S; ++j)
+        for (int i = 0; i <= j; ++i) {
+            Real dG = Real(0);
+            const Real K = delta_c_hat<Real>(kmag, sp.es_R[i][j], sp.es_pref[i][j], sp.es_a[i][j], sp.es_b[i][j],
+                                             sp.es_c[i][j], &dG, sp.es_da[i][j], sp.es_db[i][j], sp.es_dc[i][j]);
+            tab_k[(long long)m2 * P + dft_pair(i, j)] = K;
+            tab_dk[(long long)m2 * P + dft_pair(i, j)] = dG;
+        }
+}
+
+__device__ __forceinline__ int signed_index(int j, int n) { return (2 * j <= n) ? j : j - n; }
+
 // First-half z pass (same contract as k_zconv_fwd): S species spectra in, the ten weighted
-// densities (z inverse, 1/N applied) and the bulk-fluid/Poisson spectra out.
+// densities (z inverse, 1/N applied) and the bulk-fluid/Poisson spectra out.  Per-species loops
+// run to DFT_MAXS with guards so that every per-point array stays in registers.
 template <typename Real, int NZ, int TZ, bool GRAD>
-__global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
-                                                          Real kfz, int want_psi,
-                                                          const typename Cplx<Real>::type* __restrict__ in,
-                                                          typename Cplx<Real>::type* __restrict__ slot_n,
-                                                          typename Cplx<Real>::type* __restrict__ slot_es,
-                                                          double* __restrict__ red_energy,
-                                                          const typename Cplx<Real>::type* __restrict__ twz) {
+__global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
+                                                             Real kfz, int want_psi,
+                                                             const typename Cplx<Real>::type* __restrict__ in,
+                                                             typename Cplx<Real>::type* __restrict__ slot_n,
+                                                             typename Cplx<Real>::type* __restrict__ slot_es,
+                                                             double* __restrict__ red_energy,
+                                                             const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gtile(NZ, TZ);
+    constexpr int P = DFT_MAXS * (DFT_MAXS + 1) / 2;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
     const int ny = g.ny, nxh = g.nxh, S = sp.S;
+    const int Pn = S * (S + 1) / 2;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + NZ;
     C* B = A + DFT_NCOMP * GS;
@@ -657,19 +688,49 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDes
 
     const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
     const Real fourpi = Real(4.0 * CUDART_PI);
+    const bool tab = sp.tab_w != nullptr;
+    const int my = signed_index(kyi, ny);
+    Real flb = Real(0);      // 4 pi lambda_B = pois[s][s] / z_s^2 of a charged species
+    for (int s = 0; s < S; ++s)
+        if (sp.z[s] != Real(0)) { flb = sp.pois[s][s] / (sp.z[s] * sp.z[s]); break; }
     double e_acc = 0.0, q_acc = 0.0;
     for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
         const int kzi = idx / TZ, t = idx % TZ;
         const int pos = ct_gpos(kzi, TZ) + t;
         const int kxi = kx0 + t;
+        const bool live = kxi < nxh;
         const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+        int m2 = 0;
+        if (tab && live) { const int mz = signed_index(kzi, g.nz); m2 = kxi * kxi + my * my + mz * mz; }
+        Real wr[2 * DFT_MAXS];
+        Real kr[P], dkr[P];
+        if (tab) {
+#pragma unroll
+            for (int q = 0; q < 2 * DFT_MAXS; ++q)
+                if (q < 2 * S) wr[q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+            if (live) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    if (q < Pn) {
+                        kr[q] = __ldg(sp.tab_k + (long long)m2 * Pn + q);
+                        if (GRAD) dkr[q] = __ldg(sp.tab_dk + (long long)m2 * Pn + q);
+                    }
+                }
+            }
+        }
         C v[DFT_MAXS];
-        for (int s = 0; s < S; ++s) v[s] = R[s * GS + pos];
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s)
+            if (s < S) v[s] = R[s * GS + pos];
         C acc[5];
+#pragma unroll
         for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
-        for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            if (s >= S) break;
             Real w0, j3;
-            fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
+            if (tab) { w0 = wr[2 * s]; j3 = wr[2 * s + 1]; }
+            else fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
             const Real Rs = sp.R[s];
             acc[0] = cadd(acc[0], cscale(v[s], w0));
             acc[1] = cadd(acc[1], cscale(v[s], Rs * w0));
@@ -677,20 +738,31 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDes
             acc[3] = cadd(acc[3], cscale(v[s], fourpi * Rs * Rs * Rs * j3));
             acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
         }
-        if (kxi < nxh) {
+        if (live) {
             const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
-            C dv[DFT_MAXS];
-            for (int s = 0; s < S; ++s) {
-                dv[s] = v[s];
-                if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+            C dv[DFT_MAXS], es[DFT_MAXS];
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s < S) {
+                    dv[s] = v[s];
+                    if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+                }
+                es[s] = cmake<C>(Real(0), Real(0));
             }
-            C es[DFT_MAXS];
-            for (int s = 0; s < S; ++s) es[s] = cmake<C>(Real(0), Real(0));
             const double wk = GRAD ? ((kxi == 0 || (g.nx % 2 == 0 && 2 * kxi == g.nx)) ? 1.0 : 2.0) : 0.0;
-            for (int i = 0; i < S; ++i) {
-                for (int j = i; j < S; ++j) {
-                    Real dK = Real(0);
-                    const Real K = es_kernel<Real>(sp, i, j, p, inv_lap, GRAD ? &dK : nullptr);
+#pragma unroll
+            for (int j = 0; j < DFT_MAXS; ++j) {
+#pragma unroll
+                for (int i = 0; i <= j; ++i) {
+                    if (j >= S) continue;
+                    Real K, dK = Real(0);
+                    if (tab) {
+                        K = kr[dft_pair(i, j)];
+                        if (!p.zero) K -= sp.pois[i][j] * inv_lap;
+                        if (GRAD) dK = dkr[dft_pair(i, j)];
+                    } else {
+                        K = es_kernel<Real>(sp, i, j, p, inv_lap, GRAD ? &dK : nullptr);
+                    }
                     es[i] = cadd(es[i], cscale(dv[j], K));
                     if (j != i) es[j] = cadd(es[j], cscale(dv[i], K));
                     if constexpr (GRAD) {
@@ -699,22 +771,25 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDes
                     }
                 }
             }
-            if constexpr (GRAD)
-                for (int i = 0; i < S; ++i) e_acc += wk * (double(dv[i].x) * es[i].x + double(dv[i].y) * es[i].y);
             const long long o = (long long)kzi * zstride + col0 + t;
-            for (int s = 0; s < S; ++s) slot_es[(long long)s * g.nc + o] = es[s];
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s >= S) break;
+                if constexpr (GRAD) e_acc += wk * (double(dv[s].x) * es[s].x + double(dv[s].y) * es[s].y);
+                slot_es[(long long)s * g.nc + o] = es[s];
+            }
             if (want_psi) {
                 C q = cmake<C>(Real(0), Real(0));
-                for (int s = 0; s < S; ++s) q = cadd(q, cscale(v[s], sp.z[s]));
-                // psi_hat = 4 pi lambda_B q_hat / lap; pois[s][s] / z_s^2 = 4 pi lambda_B
-                Real flb = Real(0);
-                for (int s = 0; s < S; ++s)
-                    if (sp.z[s] != Real(0)) { flb = sp.pois[s][s] / (sp.z[s] * sp.z[s]); break; }
+#pragma unroll
+                for (int s = 0; s < DFT_MAXS; ++s)
+                    if (s < S) q = cadd(q, cscale(v[s], sp.z[s]));
+                // psi_hat = 4 pi lambda_B q_hat / lap
                 slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
             }
         }
         // the ten weighted-density spectra, 1/N applied; vector components are i k_d m_hat
         // (n_V1) and i k_d n3_hat (n_V2), zero on the Nyquist index of axis d
+#pragma unroll
         for (int a = 0; a < 4; ++a) O[a * GS + pos] = cscale(acc[a], sp.inv_n);
         const Real kd[3] = {p.kx, p.ky, p.kz};
         const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
@@ -741,18 +816,22 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd_g(GridDesc g, SpeciesDes
 
 // Second-half z pass (same contract as k_zconv_bwd): the ten Phi' spectra in (flags & 1), the
 // bulk-fluid/Poisson spectra mixed in (flags & 2), ncomp_out one-body correlation spectra out.
+// The points of a thread are handled together so that all of their global and table loads are
+// in flight at once.
 template <typename Real, int NZ, int TZ>
-__global__ void __launch_bounds__(kThreads) k_zconv_bwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
-                                                          Real kfz, int flags, int ncomp_out,
-                                                          const Ctl* __restrict__ ctl,
-                                                          typename Cplx<Real>::type* phi,
-                                                          const typename Cplx<Real>::type* esA,
-                                                          const typename Cplx<Real>::type* esB,
-                                                          typename Cplx<Real>::type* es_mat,
-                                                          const typename Cplx<Real>::type* __restrict__ twz) {
+__global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy,
+                                                             Real kfz, int flags, int ncomp_out,
+                                                             const Ctl* __restrict__ ctl,
+                                                             typename Cplx<Real>::type* phi,
+                                                             const typename Cplx<Real>::type* esA,
+                                                             const typename Cplx<Real>::type* esB,
+                                                             typename Cplx<Real>::type* es_mat,
+                                                             const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gtile(NZ, TZ);
+    constexpr int PER = (TILE + kThreads - 1) / kThreads;
+    constexpr int EMAX = DFT_MAXS + 1;
     extern __shared__ unsigned char smem_raw[];
     const int ny = g.ny, nxh = g.nxh, S = sp.S;
     C* tw = align_ptr<C>(smem_raw);
@@ -773,12 +852,53 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd_g(GridDesc g, SpeciesDes
     }
     C* O = (R == A) ? B : A;
     const Real fourpi = Real(4.0 * CUDART_PI);
-    for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
+    const bool tab = sp.tab_w != nullptr;
+    const int my = signed_index(kyi, ny);
+
+    // loads first: bulk-fluid/Poisson spectra and table records of all of this thread's points
+    C ea[PER][EMAX];
+    Real wr[PER][2 * DFT_MAXS];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        const int kzi = idx / TZ, t = idx % TZ;
+        const int kxi = kx0 + t;
+        const bool in_tile = (TILE % kThreads == 0) || idx < TILE;
+        const bool live = in_tile && kxi < nxh;
+        const long long o = (long long)kzi * zstride + col0 + t;
+#pragma unroll
+        for (int s = 0; s < EMAX; ++s) {
+            ea[i][s] = cmake<C>(Real(0), Real(0));
+            if (es_on && live && s < ncomp_out) {
+                C e = cscale(esA[(long long)s * g.nc + o], wA);
+                if (esB) e = cadd(e, cscale(esB[(long long)s * g.nc + o], wB));
+                ea[i][s] = e;
+            }
+        }
+        if (hs && tab) {
+            int m2 = 0;
+            if (live) { const int mz = signed_index(kzi, g.nz); m2 = kxi * kxi + my * my + mz * mz; }
+#pragma unroll
+            for (int q = 0; q < 2 * DFT_MAXS; ++q)
+                if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if ((TILE % kThreads != 0) && idx >= TILE) break;
         const int kzi = idx / TZ, t = idx % TZ;
         const int pos = ct_gpos(kzi, TZ) + t;
         const int kxi = kx0 + t;
-        C out[DFT_MAXS + 1];
-        for (int s = 0; s < DFT_MAXS + 1; ++s) out[s] = cmake<C>(Real(0), Real(0));
+        C out[EMAX];
+#pragma unroll
+        for (int s = 0; s < EMAX; ++s) out[s] = ea[i][s];
+        if (es_on && es_mat && kxi < nxh) {
+            const long long o = (long long)kzi * zstride + col0 + t;
+#pragma unroll
+            for (int s = 0; s < EMAX; ++s)
+                if (s < ncomp_out) es_mat[(long long)s * g.nc + o] = ea[i][s];
+        }
         if (hs) {
             const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
             // species-independent sums: Phi_0..Phi_3, with -i k_d Phi_V2d added to the third and
@@ -795,28 +915,24 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd_g(GridDesc g, SpeciesDes
                 a4 = cadd(a4, cmake<C>(kd[d] * u1.y, -kd[d] * u1.x));
                 a3 = cadd(a3, cmake<C>(kd[d] * u2.y, -kd[d] * u2.x));
             }
-            for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s >= S) break;
                 Real w0, j3;
                 const Real Rs = sp.R[s];
-                fmt_weights<Real>(p.kmag, Rs, &w0, &j3);
+                if (tab) { w0 = wr[i][2 * s]; j3 = wr[i][2 * s + 1]; }
+                else fmt_weights<Real>(p.kmag, Rs, &w0, &j3);
                 C mu = cscale(a0, w0);
                 mu = cadd(mu, cscale(a1, Rs * w0));
                 mu = cadd(mu, cscale(a2, fourpi * Rs * Rs * w0));
                 mu = cadd(mu, cscale(a3, fourpi * Rs * Rs * Rs * j3));
                 mu = cadd(mu, cscale(a4, Rs * Rs * j3));
-                out[s] = cmake<C>(-mu.x, -mu.y);
+                out[s] = cmake<C>(out[s].x - mu.x, out[s].y - mu.y);
             }
         }
-        if (es_on && kxi < nxh) {
-            const long long o = (long long)kzi * zstride + col0 + t;
-            for (int s = 0; s < ncomp_out; ++s) {
-                C e = cscale(esA[(long long)s * g.nc + o], wA);
-                if (esB) e = cadd(e, cscale(esB[(long long)s * g.nc + o], wB));
-                if (es_mat) es_mat[(long long)s * g.nc + o] = e;
-                out[s] = cadd(out[s], e);
-            }
-        }
-        for (int s = 0; s < ncomp_out; ++s) O[s * GS + pos] = cscale(out[s], sp.inv_n);
+#pragma unroll
+        for (int s = 0; s < EMAX; ++s)
+            if (s < ncomp_out) O[s * GS + pos] = cscale(out[s], sp.inv_n);
     }
     __syncthreads();
     C* Q = ct_fft_grouped<NZ, true, TZ>(O, R, ncomp_out, tw);

@@ -47,6 +47,9 @@ struct LaunchX {
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);
+    // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
+    // number kf of a cubic box
+    static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
 };
 
 template <typename Real, int N>
@@ -100,6 +103,9 @@ struct Passes {
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);
+    // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
+    // number kf of a cubic box
+    static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
 };
 
 cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
