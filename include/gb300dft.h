@@ -161,6 +161,18 @@ dft_status dft_iter_step(dft_plan* plan, void* rho_inout, const void* V, double 
                          double* resid_out, double* alpha_out);
 
 /*
+ * `iters` consecutive dft_iter_step iterations (same arithmetic, same order) queued as
+ * replays of a CUDA graph of one iteration, captured on the first call for these
+ * (rho_inout, V, alpha_or_neg) and kept in the plan until they change, dft_iter_begin is
+ * called or the plan is destroyed.  Requires a preceding dft_iter_begin on the same
+ * buffers.  resid_out (may be NULL; NULL skips the synchronisation) receives r of rho
+ * after the last iteration.  While kernel profiling is enabled the iterations are
+ * launched one by one instead (the per-kernel events are not captured).
+ */
+dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iters, double alpha_or_neg,
+                        double* resid_out);
+
+/*
  * Grand potential and its gradients (differentiated form).  The paper asserts
  * the functional (Sec. "Introduction") and its bulk-fluid expansion (eq.
  * muESexpansion2); the discrete functional whose stationarity condition is

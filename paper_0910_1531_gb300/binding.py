@@ -63,6 +63,7 @@ SIGNATURES = {
     "dft_solve": (_I, [_P, _P, _P, _D, _D, _I, _PI, _PD]),
     "dft_iter_begin": (_I, [_P, _P, _P]),
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
+    "dft_iter_run": (_I, [_P, _P, _P, _I, _D, _PD]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_grad": (_I, [_P, _P, _P, _PD, _P, _P, _PD]),
     "dft_batch_create": (_I, [ctypes.POINTER(DftParams), _I, _P, ctypes.POINTER(_P)]),
@@ -221,6 +222,14 @@ class Plan:
                                            self._field(V, self.nspecies, "V"), float(alpha),
                                            ctypes.byref(r) if sync else None, ctypes.byref(a) if sync else None))
         return (r.value, a.value) if sync else None
+
+    def iter_run(self, rho, V, iters, alpha=-1.0, sync=True):
+        """`iters` iterations of iter_step as CUDA-graph replays; returns r after them (sync)."""
+        r = _D()
+        self._check(self.lib.dft_iter_run(self.handle, self._field(rho, self.nspecies, "rho"),
+                                          self._field(V, self.nspecies, "V"), int(iters), float(alpha),
+                                          ctypes.byref(r) if sync else None))
+        return r.value if sync else None
 
     def grad(self, rho, V, want_rho=True, want_V=True, want_bulk=True):
         """(Omega, dOmega/drho, dOmega/dV, dOmega/drho_bath) through dft_grad; gradients None if not wanted."""

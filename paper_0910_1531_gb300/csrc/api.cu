@@ -66,6 +66,12 @@ struct dft_plan {
     double prof_bytes[K_COUNT] = {0};
     std::string err;
     void* ktab = nullptr;           // |k| tables of the compile-time z passes (cubic boxes)
+    cudaStream_t cap = nullptr;     // capture stream of the one-iteration graph (dft_iter_run)
+    cudaGraph_t igraph = nullptr;
+    cudaGraphExec_t iexec = nullptr;
+    const void* graph_rho = nullptr;
+    const void* graph_V = nullptr;
+    double graph_alpha = 0.0;
     double* grad_red = nullptr;     // partial sums of dft_grad (allocated on first use)
     size_t grad_red_len = 0;
     bool iter_ready = false;
@@ -574,6 +580,16 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
 // ======================================================================================
 // C ABI
 // ======================================================================================
+namespace {
+void release_iter_graph(dft_plan* p) {
+    if (p->iexec) cudaGraphExecDestroy(p->iexec);
+    if (p->igraph) cudaGraphDestroy(p->igraph);
+    p->iexec = nullptr;
+    p->igraph = nullptr;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* dft_version(void) { return "gb300dft 0.1 (sm_103a)"; }
@@ -747,6 +763,8 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->red_max);
     cudaFree(p->grad_red);
     cudaFree(p->ktab);
+    release_iter_graph(p);
+    if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->ctl);
     if (p->ctl_host) cudaFreeHost(p->ctl_host);
     for (cudaEvent_t ev : p->evpool) cudaEventDestroy(ev);
@@ -827,6 +845,7 @@ dft_status dft_picard_map(dft_plan* p, const void* rho, const void* V, void* g_o
 dft_status dft_iter_begin(dft_plan* p, void* rho, const void* V) {
     TRY(check_plan(p));
     if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    release_iter_graph(p);
     if (is_fp64(p)) return iter_begin_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V));
     return iter_begin_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V));
 }
@@ -842,6 +861,59 @@ dft_status dft_iter_step(dft_plan* p, void* rho, const void* V, double alpha, do
         TRY(read_ctl(p));
         if (resid_out) *resid_out = p->ctl_host->resid_prev;
         if (alpha_out) *alpha_out = p->ctl_host->alpha;
+    }
+    return DFT_OK;
+}
+
+dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double alpha, double* resid_out) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (iters < 0) return fail(p, DFT_EINVAL, "negative iteration count");
+    if (!p->iter_ready || p->iter_rho != rho || p->iter_V != V)
+        return fail(p, DFT_EINVAL, "dft_iter_run needs a preceding dft_iter_begin on the same rho and V");
+    if (p->prof) {
+        for (int it = 0; it < iters; ++it) TRY(dft_iter_step(p, rho, V, alpha, nullptr, nullptr));
+    } else {
+        if (p->iexec && (p->graph_rho != rho || p->graph_V != V || p->graph_alpha != alpha)) release_iter_graph(p);
+        if (!p->iexec && iters > 0) {
+            if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(p, DFT_ECUDA, "capture stream creation failed");
+            cudaStream_t user = p->stream;
+            p->stream = p->cap;
+            cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                p->stream = user;
+                return fail(p, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+            }
+            dft_status st = is_fp64(p)
+                ? iter_step_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V), alpha)
+                : iter_step_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V), alpha);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(p->cap, &g);
+            p->stream = user;
+            if (st != DFT_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+            p->igraph = g;
+            e = cudaGraphInstantiate(&p->iexec, p->igraph, 0);
+            if (e != cudaSuccess) {
+                release_iter_graph(p);
+                return fail(p, DFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            }
+            p->graph_rho = rho;
+            p->graph_V = V;
+            p->graph_alpha = alpha;
+        }
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = cudaGraphLaunch(p->iexec, p->stream);
+            if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        }
+    }
+    if (resid_out) {
+        TRY(read_ctl(p));
+        *resid_out = p->ctl_host->resid;
     }
     return DFT_OK;
 }

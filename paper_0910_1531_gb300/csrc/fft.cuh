@@ -260,32 +260,39 @@ __device__ __forceinline__ C* any_fft(C* a, C* b, const AxisPlan& p, int lines, 
 }
 
 // ------------------------------------------------------------------------------------
-// Grouped column transforms: `groups` tiles of T columns x N rows, stored one after another
-// (tile g at offset g * ct_gtile(N, T)), transformed together so that every stage has
-// groups * T * N / R butterflies for the CTA's threads.  Element e of column t sits at
-// T * ct_xpad(e) + t: the first stage's outputs, R rows apart across threads, then fall into
-// distinct bank groups (the same pad as the x-pass rows).
+// Grouped column transforms: `groups` tiles of T columns x N rows, tile g at offset g * GSTR,
+// transformed together so that every stage has groups * T * N / R butterflies for the CTA's
+// NT threads.  Inside a tile, element e of column t sits at T * ct_xpad(e) + t (padded: the
+// first stage's outputs, R rows apart across threads, then fall into distinct bank groups);
+// SRC_DENSE / DST_DENSE make the first stage read, or the last stage write, the dense layout
+// e * T + t of a TMA box instead.
 // ------------------------------------------------------------------------------------
 __host__ __device__ constexpr int ct_gpos(int e, int T) { return T * ct_xpad(e); }
 __host__ __device__ constexpr int ct_gtile(int n, int T) { return T * (ct_xpad(n - 1) + 1); }
+// group stride: the padded tile rounded up to 128 bytes (TMA destinations are 128-byte aligned)
+__host__ __device__ constexpr int ct_gstride(int n, int T, int csize) {
+    return (ct_gtile(n, T) + 128 / csize - 1) / (128 / csize) * (128 / csize);
+}
 
-template <int N, int R, int NS, bool INV, int T, typename C>
+template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, typename C>
 __device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* __restrict__ dst, int groups,
                                                  const C* __restrict__ tw) {
     constexpr int M = N / R;
     constexpr int TWSTEP = N / (NS * R);
     constexpr int PERG = M * T;
-    constexpr int GS = ct_gtile(N, T);
     const int total = PERG * groups;
-    for (int task = threadIdx.x; task < total; task += kFftThreads) {
+    for (int task = threadIdx.x; task < total; task += NT) {
         const int g = task / PERG;
         const int rem = task - g * PERG;
         const int t = rem % T, j = rem / T;
         const int k = j % NS;
-        const int off = g * GS + t;
+        const int off = g * GSTR + t;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[ct_gpos(j + r * M, T) + off];
+        for (int r = 0; r < R; ++r) {
+            const int e = j + r * M;
+            v[r] = src[(SD ? e * T : ct_gpos(e, T)) + off];
+        }
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -297,26 +304,30 @@ __device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* _
         dft_small<R, INV>(v);
         const int base = (j / NS) * (NS * R) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[ct_gpos(base + r * NS, T) + off] = v[r];
+        for (int r = 0; r < R; ++r) {
+            const int e = base + r * NS;
+            dst[(DD ? e * T : ct_gpos(e, T)) + off] = v[r];
+        }
     }
 }
 
-template <int N, bool INV, int T, int S, typename C>
+template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, typename C>
 __device__ __forceinline__ void ct_stages_grouped(C*& a, C*& b, int groups, const C* tw) {
     if constexpr (S < ct_nstages(N)) {
         constexpr int R = ct_radix_at(N, S);
         constexpr int NS = ct_ns_at(N, S);
-        ct_stage_grouped<N, R, NS, INV, T>(a, b, groups, tw);
+        constexpr bool last = (S + 1 == ct_nstages(N));
+        ct_stage_grouped<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT>(a, b, groups, tw);
         __syncthreads();
         C* t = a; a = b; b = t;
-        ct_stages_grouped<N, INV, T, S + 1>(a, b, groups, tw);
+        ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, S + 1>(a, b, groups, tw);
     }
 }
 
-// Transform `groups` consecutive column tiles held in a (b: scratch of the same size); the
-// caller syncs before; returns the buffer holding the result.
-template <int N, bool INV, int T, typename C>
+// Transform `groups` tiles held in a (b: scratch of the same size); the caller syncs before;
+// returns the buffer holding the result (synced).
+template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads, typename C>
 __device__ __forceinline__ C* ct_fft_grouped(C* a, C* b, int groups, const C* tw) {
-    ct_stages_grouped<N, INV, T, 0>(a, b, groups, tw);
+    ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, 0>(a, b, groups, tw);
     return a;
 }

@@ -574,10 +574,10 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
 // components of a column tile are loaded in one batch of in-flight loads and transformed by
 // one grouped FFT (ct_fft_grouped), so every stage keeps the CTA's threads busy and a tile
 // costs a handful of barriers instead of a dozen transforms of one component each.
-// Shared memory: twiddles | 10 tiles | 10 tiles (ct_gtile(NZ, TZ) elements each).
+// Shared memory: twiddles | 10 tiles | 10 tiles (ct_gstride(NZ, TZ, csize) elements each).
 // ------------------------------------------------------------------------------------
 template <int TT, int NN> __host__ __device__ constexpr size_t zg_smem_bytes(size_t csize) {
-    return (size_t(NN) + 2 * size_t(DFT_NCOMP) * ct_gtile(NN, TT)) * csize + 16;
+    return (size_t(NN) + 2 * size_t(DFT_NCOMP) * ct_gstride(NN, TT, int(csize))) * csize + 16;
 }
 
 // Load `groups` column tiles (component c at src + c * cstride, global row stride rs, columns
@@ -588,7 +588,7 @@ __device__ __forceinline__ void tiles_load_grouped(C* __restrict__ dst, const C*
                                                    int groups, long long rs, int valid) {
     constexpr int TILE = TT * NN;
     constexpr int PER = (TILE + kThreads - 1) / kThreads;
-    constexpr int GS = ct_gtile(NN, TT);
+    constexpr int GS = ct_gstride(NN, TT, int(sizeof(C)));
     C reg[GMAX][PER];
 #pragma unroll
     for (int gi = 0; gi < GMAX; ++gi) {
@@ -616,7 +616,7 @@ template <int TT, int NN, typename C>
 __device__ __forceinline__ void tiles_store_grouped(C* __restrict__ dst, const C* __restrict__ src, long long cstride,
                                                     int groups, long long rs, int valid) {
     constexpr int TILE = TT * NN;
-    constexpr int GS = ct_gtile(NN, TT);
+    constexpr int GS = ct_gstride(NN, TT, int(sizeof(C)));
     for (int gi = 0; gi < groups; ++gi) {
 #pragma unroll
         for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
                                                              const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
-    constexpr int GS = ct_gtile(NZ, TZ);
+    constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
     constexpr int P = DFT_MAXS * (DFT_MAXS + 1) / 2;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
     const long long col0 = (long long)kyi * g.pxh + kx0;
     tiles_load_grouped<TZ, NZ, DFT_MAXS>(A, in + col0, g.nc, S, zstride, nxh - kx0);
     __syncthreads();
-    C* R = ct_fft_grouped<NZ, false, TZ>(A, B, S, tw);
+    C* R = ct_fft_grouped<NZ, false, TZ, GS>(A, B, S, tw);
     C* O = (R == A) ? B : A;
 
     const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
         }
     }
     __syncthreads();
-    C* Q = ct_fft_grouped<NZ, true, TZ>(O, R, DFT_NCOMP, tw);
+    C* Q = ct_fft_grouped<NZ, true, TZ, GS>(O, R, DFT_NCOMP, tw);
     tiles_store_grouped<TZ, NZ>(slot_n + col0, Q, g.nc, DFT_NCOMP, zstride, nxh - kx0);
 }
 
@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
                                                              const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
-    constexpr int GS = ct_gtile(NZ, TZ);
+    constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
     constexpr int PER = (TILE + kThreads - 1) / kThreads;
     constexpr int EMAX = DFT_MAXS + 1;
     extern __shared__ unsigned char smem_raw[];
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
     if (hs) {
         tiles_load_grouped<TZ, NZ, DFT_NCOMP>(A, phi + col0, g.nc, DFT_NCOMP, zstride, nxh - kx0);
         __syncthreads();
-        R = ct_fft_grouped<NZ, false, TZ>(A, B, DFT_NCOMP, tw);
+        R = ct_fft_grouped<NZ, false, TZ, GS>(A, B, DFT_NCOMP, tw);
     }
     C* O = (R == A) ? B : A;
     const Real fourpi = Real(4.0 * CUDART_PI);
@@ -935,8 +935,207 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
             if (s < ncomp_out) O[s * GS + pos] = cscale(out[s], sp.inv_n);
     }
     __syncthreads();
-    C* Q = ct_fft_grouped<NZ, true, TZ>(O, R, ncomp_out, tw);
+    C* Q = ct_fft_grouped<NZ, true, TZ, GS>(O, R, ncomp_out, tw);
     tiles_store_grouped<TZ, NZ>(phi + col0, Q, g.nc, ncomp_out, zstride, nxh - kx0);
+}
+
+// ------------------------------------------------------------------------------------
+// Second-half z pass with TMA tiles (same contract as k_zconv_bwd), persistent: CTA b handles
+// tiles b, b + gridDim.x, ...  Two shared-memory stages, each holding one tile's ten Phi'
+// components and its bulk-fluid/Poisson spectra, are filled by TMA loads (one
+// cp.async.bulk.tensor per component, completing on the stage's mbarrier) while the previous
+// tile is transformed; the ncomp_out results leave through TMA stores.  A tensor map views a
+// half-spectrum array as (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements, E =
+// sizeof(complex) / 8; a component tile is the box (TZ * E, 1, NZ) at plane c * nz.  Columns
+// past nxh read as zero and are not written.  A wait that runs out sets DEV_TIMEOUT and the
+// CTA stops after draining the loads it has in flight.
+// Shared memory: stage 0 | stage 1 (each ten padded groups, then the dense ES tiles) |
+// W (ten padded groups) | twiddles | two mbarriers.
+// ------------------------------------------------------------------------------------
+template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zbwd_tma_smem(int nes) {
+    using C = typename Cplx<Real>::type;
+    constexpr size_t GS = size_t(ct_gstride(NZ, TZ, int(sizeof(C))));
+    return (2 * (DFT_NCOMP * GS + size_t(nes) * TZ * NZ) + DFT_NCOMP * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+}
+
+template <typename Real, int NZ, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const __grid_constant__ CUtensorMap map_phi,
+                                                         const __grid_constant__ CUtensorMap map_esA,
+                                                         const __grid_constant__ CUtensorMap map_esB, GridDesc g,
+                                                         SpeciesDesc<Real> sp, Real kfx, Real kfy, Real kfz, int flags,
+                                                         int ncomp_out, int has_esB, const Ctl* __restrict__ ctl,
+                                                         typename Cplx<Real>::type* es_mat, int ntiles_x, int ntiles,
+                                                         int* __restrict__ status,
+                                                         const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    constexpr int E = int(sizeof(C) / 8);
+    constexpr int TILE = TZ * NZ;
+    constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
+    constexpr int PER = (TILE + NT - 1) / NT;
+    constexpr int EMAX = DFT_MAXS + 1;
+    constexpr uint32_t BOX = uint32_t(TILE * sizeof(C));
+    static_assert(NZ > 0 && NZ <= 256 && (TZ * sizeof(C)) % 16 == 0 && BOX % 128 == 0, "z TMA tile");
+    extern __shared__ unsigned char smem_raw[];
+    const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
+    const int nes = es_on ? ncomp_out * (has_esB ? 2 : 1) : 0;
+    const int stage_elems = DFT_NCOMP * GS + nes * TILE;
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
+    C* const stage0 = reinterpret_cast<C*>(base);
+    C* W = stage0 + 2 * stage_elems;
+    C* tw = W + DFT_NCOMP * GS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
+    const uint32_t tile_bytes = uint32_t((hs ? DFT_NCOMP : 0) + nes) * BOX;
+    const int S = sp.S, ny = g.ny, nxh = g.nxh;
+    const long long zstride = (long long)ny * g.pxh;
+
+    auto issue = [&](int tile, int s) {
+        C* st = stage0 + s * stage_elems;
+        const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
+        tma::mbar_expect_tx(&bar[s], tile_bytes);
+        if (hs)
+            for (int c = 0; c < DFT_NCOMP; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
+        if (es_on) {
+            for (int c = 0; c < ncomp_out; ++c)
+                tma::load_3d(st + DFT_NCOMP * GS + c * TILE, &map_esA, x, y, c * NZ, &bar[s]);
+            if (has_esB)
+                for (int c = 0; c < ncomp_out; ++c)
+                    tma::load_3d(st + DFT_NCOMP * GS + (ncomp_out + c) * TILE, &map_esB, x, y, c * NZ, &bar[s]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < NZ; i += NT) tw[i] = twz[i];
+    __syncthreads();
+    // loads issued / consumed per stage, packed as (stage 1 << 16) | stage 0; meaningful in thread 0
+    int issued = 0, consumed = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            const int tile = blockIdx.x + s * gridDim.x;
+            if (tile < ntiles) { issue(tile, s); issued += 1 << (16 * s); }
+        }
+    }
+    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    const bool tab = sp.tab_w != nullptr;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
+        const int my = signed_index(kyi, ny);
+        // table records of this thread's points, in flight while the tile arrives
+        Real wr[PER][2 * DFT_MAXS];
+        if (hs && tab) {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = threadIdx.x + i * NT;
+                const int kzi = idx / TZ, kxi = kx0 + idx % TZ;
+                int m2 = 0;
+                if (((TILE % NT == 0) || idx < TILE) && kxi < nxh) {
+                    const int mz = signed_index(kzi, g.nz);
+                    m2 = kxi * kxi + my * my + mz * mz;
+                }
+#pragma unroll
+                for (int q = 0; q < 2 * DFT_MAXS; ++q)
+                    if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+            }
+        }
+        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        // the previous tile's TMA stores have finished reading shared memory (W is written next)
+        if (threadIdx.x == 0) tma::wait_read_all();
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, DEV_TIMEOUT);
+                for (int s = 0; s < 2; ++s) {
+                    const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
+                    if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
+                }
+            }
+            break;
+        }
+        consumed += 1 << (16 * cur);
+        C* st = stage0 + cur * stage_elems;
+        const C* es_t = st + DFT_NCOMP * GS;
+        C* X = st;
+        C* Y = W;
+        if (hs) {
+            X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NCOMP, tw);
+            Y = (X == st) ? W : st;
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * NT;
+            if ((TILE % NT != 0) && idx >= TILE) break;
+            const int kzi = idx / TZ, t = idx % TZ;
+            const int pos = ct_gpos(kzi, TZ) + t;
+            const int kxi = kx0 + t;
+            C out[EMAX];
+#pragma unroll
+            for (int s = 0; s < EMAX; ++s) {
+                out[s] = cmake<C>(Real(0), Real(0));
+                if (es_on && s < ncomp_out) {
+                    C e = cscale(es_t[s * TILE + idx], wA);
+                    if (has_esB) e = cadd(e, cscale(es_t[(ncomp_out + s) * TILE + idx], wB));
+                    out[s] = e;
+                }
+            }
+            if (es_on && es_mat && kxi < nxh) {
+                const long long o = (long long)kzi * zstride + (long long)kyi * g.pxh + kxi;
+#pragma unroll
+                for (int s = 0; s < EMAX; ++s)
+                    if (s < ncomp_out) es_mat[(long long)s * g.nc + o] = out[s];
+            }
+            if (hs) {
+                const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+                const C a0 = X[0 * GS + pos], a1 = X[1 * GS + pos], a2 = X[2 * GS + pos];
+                C a3 = X[3 * GS + pos];
+                C a4 = cmake<C>(Real(0), Real(0));
+                const Real kd[3] = {p.kx, p.ky, p.kz};
+                const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (nyq[d]) continue;
+                    const C u1 = X[(4 + d) * GS + pos], u2 = X[(7 + d) * GS + pos];
+                    a4 = cadd(a4, cmake<C>(kd[d] * u1.y, -kd[d] * u1.x));
+                    a3 = cadd(a3, cmake<C>(kd[d] * u2.y, -kd[d] * u2.x));
+                }
+#pragma unroll
+                for (int s = 0; s < DFT_MAXS; ++s) {
+                    if (s >= S) break;
+                    Real w0, j3;
+                    const Real Rs = sp.R[s];
+                    if (tab) { w0 = wr[i][2 * s]; j3 = wr[i][2 * s + 1]; }
+                    else fmt_weights<Real>(p.kmag, Rs, &w0, &j3);
+                    C mu = cscale(a0, w0);
+                    mu = cadd(mu, cscale(a1, Rs * w0));
+                    mu = cadd(mu, cscale(a2, fourpi * Rs * Rs * w0));
+                    mu = cadd(mu, cscale(a3, fourpi * Rs * Rs * Rs * j3));
+                    mu = cadd(mu, cscale(a4, Rs * Rs * j3));
+                    out[s] = cmake<C>(out[s].x - mu.x, out[s].y - mu.y);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < EMAX; ++s)
+                if (s < ncomp_out) Y[s * GS + pos] = cscale(out[s], sp.inv_n);
+        }
+        __syncthreads();
+        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(Y, X, ncomp_out, tw);
+        tma::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < ncomp_out; ++s) tma::store_3d(&map_phi, kx0 * E, kyi, s * NZ, Q + s * GS);
+            tma::commit();
+            // the stage may be refilled at once unless the stores read from it; otherwise their
+            // shared-memory reads are awaited before the next tile writes W
+            if (Q == st) tma::wait_read_all();
+            const int next = tile + 2 * gridDim.x;
+            if (next < ntiles) { issue(next, cur); issued += 1 << (16 * cur); }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tma::wait_all();
 }
 
 // ------------------------------------------------------------------------------------

@@ -153,6 +153,9 @@ cudaError_t LaunchZ<Real, N>::init() {
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_bwd_g<Real, N, TZ>)) != cudaSuccess) e = r;
+        constexpr int TB = dft_tile_zb<Real>(N);
+        if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0)
+            if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
     } else {
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
@@ -192,8 +195,54 @@ template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                                  const C* esA, const C* esB, C* es_mat, const C* tw) {
+    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 1;
+    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
+    constexpr bool kTma = N > 0 && (TB * sizeof(C)) % 16 == 0;
+    const bool es_on = (flags & 2) != 0;
+    const int nes = es_on ? ncomp_out * (esB ? 2 : 1) : 0;
+    static int optin = 0;
+    if (optin == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    if constexpr (kTma) {
+        if (dftk::zbwd_tma_smem<Real, N, TB>(nes) <= size_t(optin)) {
+            // TMA path: persistent CTAs, two TMA-filled stages (ten Phi' tiles + the ES tiles each)
+            constexpr int NT = dft_zbwd_threads<Real>(N);
+            constexpr int E = int(sizeof(C) / 8);
+            CUtensorMap map_phi, map_esA, map_esB;
+            auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
+                return tma_encode_3d(m, const_cast<C*>(data), (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
+                                     (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
+                                     (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
+            };
+            cudaError_t e = encode(&map_phi, phi, DFT_NCOMP);
+            if (e == cudaSuccess) e = encode(&map_esA, es_on ? esA : phi, es_on ? ncomp_out : DFT_NCOMP);
+            if (e == cudaSuccess) e = encode(&map_esB, (es_on && esB) ? esB : phi, (es_on && esB) ? ncomp_out : DFT_NCOMP);
+            if (e != cudaSuccess) return e;
+            const int ntx = (int)ceil_div(g.nxh, TB);
+            const int ntiles = ntx * g.ny;
+            const size_t sm = dftk::zbwd_tma_smem<Real, N, TB>(nes);
+            static int sms = 0;
+            if (sms == 0) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            }
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_bwd_tma<Real, N, TB, NT>, NT, sm);
+            if (occ < 1) occ = 1;
+            const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
+            // the status word of the device control block records a TMA wait that ran out
+            int* status = const_cast<int*>(&ctl->status);
+            dftk::k_zconv_bwd_tma<Real, N, TB, NT><<<grid, NT, sm, st>>>(
+                map_phi, map_esA, map_esB, g, sp, kfx, kfy, kfz, flags, ncomp_out, esB ? 1 : 0, ctl, es_mat, ntx, ntiles,
+                status, tw);
+            return cudaSuccess;
+        }
+    }
     if constexpr (N > 0) {
-        constexpr int TZ = dft_tile_z<Real>(N);
         const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
         dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
         dftk::k_zconv_bwd_g<Real, N, TZ><<<grid, dftk::kThreads, sm, st>>>(

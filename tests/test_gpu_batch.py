@@ -69,3 +69,29 @@ def test_batch_state_with_steep_residual_converges():
     assert all(np.isfinite(res))
     assert res[-1] < 0.05 * res[0]
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("alpha", [-1.0, 0.1])
+def test_iter_run_graph_matches_iter_step(precision, alpha):
+    # dft_iter_run replays a captured graph of one iteration: the iterate must equal, bit for
+    # bit, the same number of dft_iter_step calls (same kernels in the same order)
+    from paper_0910_1531_gb300 import binding
+    w = workloads.centred_sphere(n=32, h=0.1, molar=0.5, sphere_radius=0.5, mixing=None)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=precision)
+    r0 = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=dt, device="cuda")
+    V = torch.tensor(w.V, dtype=dt, device="cuda")
+    ref = r0.clone()
+    plan.iter_begin(ref, V)
+    for _ in range(5):
+        plan.iter_step(ref, V, alpha, sync=False)
+    r_ref = plan.iter_run(ref, V, 0)          # zero iterations: only the residual read-back
+    got = r0.clone()
+    plan.iter_begin(got, V)
+    plan.iter_run(got, V, 2, alpha, sync=False)
+    r_got = plan.iter_run(got, V, 3, alpha)   # graph reused across calls
+    torch.cuda.synchronize()
+    assert torch.equal(ref, got)
+    assert r_ref == r_got and np.isfinite(r_got)
+    plan.close()
