@@ -271,7 +271,7 @@ template <typename Real> struct Ops {
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
         LAUNCH(p, K_ZFWD, (p->S + DFT_NCOMP + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
-                                       T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2)));
+                                       T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
         LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), &p->ctl->status, tw(p, 1)));
         return DFT_OK;
     }

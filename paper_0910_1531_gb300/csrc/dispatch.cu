@@ -83,8 +83,8 @@ cudaError_t Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, con
 template <typename Real>
 cudaError_t Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                              int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                             double* red_energy, const C* tw) {
-    DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw))
+                             double* red_energy, const C* tw, int* status) {
+    DFT_SWITCH_Z(g.nz, zconv_fwd(st, g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw, status))
 }
 
 template <typename Real>

@@ -940,6 +940,219 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
 }
 
 // ------------------------------------------------------------------------------------
+// First-half z pass with TMA tiles (same contract as k_zconv_fwd without the grand-potential
+// sums), persistent like k_zconv_bwd_tma: two stages of S species tiles are filled by TMA loads
+// while the previous tile is transformed; the ten weighted densities leave through TMA stores,
+// the bulk-fluid/Poisson spectra through plain stores.  A tensor map views a half-spectrum
+// array as (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements; a tile is the box
+// (TZ * E, 1, NZ) at plane c * nz.  A wait that runs out sets DEV_TIMEOUT and the CTA stops
+// after draining the loads it has in flight.
+// Shared memory: stage 0 | stage 1 (S padded groups each) | W | V (ten padded groups each) |
+// twiddles | two mbarriers.
+// ------------------------------------------------------------------------------------
+template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zfwd_tma_smem(int S) {
+    using C = typename Cplx<Real>::type;
+    constexpr size_t GS = size_t(ct_gstride(NZ, TZ, int(sizeof(C))));
+    return ((2 * size_t(S) + 2 * DFT_NCOMP) * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+}
+
+template <typename Real, int NZ, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const __grid_constant__ CUtensorMap map_in,
+                                                                         const __grid_constant__ CUtensorMap map_n,
+                                                                         GridDesc g, SpeciesDesc<Real> sp, Real kfx,
+                                                                         Real kfy, Real kfz, int want_psi,
+                                                                         typename Cplx<Real>::type* __restrict__ slot_es,
+                                                                         int ntiles_x, int ntiles,
+                                                                         int* __restrict__ status,
+                                                                         const typename Cplx<Real>::type* __restrict__ twz) {
+    using C = typename Cplx<Real>::type;
+    constexpr int E = int(sizeof(C) / 8);
+    constexpr int TILE = TZ * NZ;
+    constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
+    constexpr int PER = (TILE + NT - 1) / NT;
+    constexpr int P = DFT_MAXS * (DFT_MAXS + 1) / 2;
+    constexpr uint32_t BOX = uint32_t(TILE * sizeof(C));
+    static_assert(NZ > 0 && NZ <= 256 && (TZ * sizeof(C)) % 16 == 0 && BOX % 128 == 0, "z TMA tile");
+    extern __shared__ unsigned char smem_raw[];
+    const int S = sp.S, ny = g.ny, nxh = g.nxh;
+    const int Pn = S * (S + 1) / 2;
+    const int stage_elems = S * GS;
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
+    C* const stage0 = reinterpret_cast<C*>(base);
+    C* W = stage0 + 2 * stage_elems;
+    C* Vb = W + DFT_NCOMP * GS;
+    C* tw = Vb + DFT_NCOMP * GS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
+    const uint32_t tile_bytes = uint32_t(S) * BOX;
+    const long long zstride = (long long)ny * g.pxh;
+
+    auto issue = [&](int tile, int s) {
+        C* st = stage0 + s * stage_elems;
+        const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
+        tma::mbar_expect_tx(&bar[s], tile_bytes);
+        for (int c = 0; c < S; ++c) tma::load_3d(st + c * GS, &map_in, x, y, c * NZ, &bar[s]);
+    };
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < NZ; i += NT) tw[i] = twz[i];
+    __syncthreads();
+    int issued = 0, consumed = 0;   // per stage, packed (stage 1 << 16) | stage 0; thread 0
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            const int tile = blockIdx.x + s * gridDim.x;
+            if (tile < ntiles) { issue(tile, s); issued += 1 << (16 * s); }
+        }
+    }
+    const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    const bool tab = sp.tab_w != nullptr;
+    Real flb = Real(0);      // 4 pi lambda_B = pois[s][s] / z_s^2 of a charged species
+    for (int s = 0; s < S; ++s)
+        if (sp.z[s] != Real(0)) { flb = sp.pois[s][s] / (sp.z[s] * sp.z[s]); break; }
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
+        const int my = signed_index(kyi, ny);
+        // table records of this thread's points, in flight while the tile arrives
+        Real wr[PER][2 * DFT_MAXS];
+        Real kr[PER][P];
+        if (tab) {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = threadIdx.x + i * NT;
+                const int kzi = idx / TZ, kxi = kx0 + idx % TZ;
+                int m2 = 0;
+                if (((TILE % NT == 0) || idx < TILE) && kxi < nxh) {
+                    const int mz = signed_index(kzi, g.nz);
+                    m2 = kxi * kxi + my * my + mz * mz;
+                }
+#pragma unroll
+                for (int q = 0; q < 2 * DFT_MAXS; ++q)
+                    if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    if (q < Pn) kr[i][q] = __ldg(sp.tab_k + (long long)m2 * Pn + q);
+            }
+        }
+        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        // the previous tile's TMA stores have finished reading shared memory
+        if (threadIdx.x == 0) tma::wait_read_all();
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, DEV_TIMEOUT);
+                for (int s = 0; s < 2; ++s) {
+                    const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
+                    if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
+                }
+            }
+            break;
+        }
+        consumed += 1 << (16 * cur);
+        C* st = stage0 + cur * stage_elems;
+        C* X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, Vb, S, tw);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * NT;
+            if ((TILE % NT != 0) && idx >= TILE) break;
+            const int kzi = idx / TZ, t = idx % TZ;
+            const int pos = ct_gpos(kzi, TZ) + t;
+            const int kxi = kx0 + t;
+            const bool live = kxi < nxh;
+            const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+            C v[DFT_MAXS];
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s)
+                if (s < S) v[s] = X[s * GS + pos];
+            C acc[5];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s >= S) break;
+                Real w0, j3;
+                if (tab) { w0 = wr[i][2 * s]; j3 = wr[i][2 * s + 1]; }
+                else fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
+                const Real Rs = sp.R[s];
+                acc[0] = cadd(acc[0], cscale(v[s], w0));
+                acc[1] = cadd(acc[1], cscale(v[s], Rs * w0));
+                acc[2] = cadd(acc[2], cscale(v[s], fourpi * Rs * Rs * w0));
+                acc[3] = cadd(acc[3], cscale(v[s], fourpi * Rs * Rs * Rs * j3));
+                acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
+            }
+            if (live) {
+                const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+                C dv[DFT_MAXS], es[DFT_MAXS];
+#pragma unroll
+                for (int s = 0; s < DFT_MAXS; ++s) {
+                    if (s < S) {
+                        dv[s] = v[s];
+                        if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+                    }
+                    es[s] = cmake<C>(Real(0), Real(0));
+                }
+#pragma unroll
+                for (int j = 0; j < DFT_MAXS; ++j) {
+#pragma unroll
+                    for (int i2 = 0; i2 <= j; ++i2) {
+                        if (j >= S) continue;
+                        Real K;
+                        if (tab) {
+                            K = kr[i][dft_pair(i2, j)];
+                            if (!p.zero) K -= sp.pois[i2][j] * inv_lap;
+                        } else {
+                            K = es_kernel<Real>(sp, i2, j, p, inv_lap, nullptr);
+                        }
+                        es[i2] = cadd(es[i2], cscale(dv[j], K));
+                        if (j != i2) es[j] = cadd(es[j], cscale(dv[i2], K));
+                    }
+                }
+                const long long o = (long long)kzi * zstride + (long long)kyi * g.pxh + kxi;
+#pragma unroll
+                for (int s = 0; s < DFT_MAXS; ++s)
+                    if (s < S) slot_es[(long long)s * g.nc + o] = es[s];
+                if (want_psi) {
+                    C q = cmake<C>(Real(0), Real(0));
+#pragma unroll
+                    for (int s = 0; s < DFT_MAXS; ++s)
+                        if (s < S) q = cadd(q, cscale(v[s], sp.z[s]));
+                    slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
+                }
+            }
+            // the ten weighted-density spectra, 1/N applied; vector components are i k_d m_hat
+            // (n_V1) and i k_d n3_hat (n_V2), zero on the Nyquist index of axis d
+#pragma unroll
+            for (int a = 0; a < 4; ++a) W[a * GS + pos] = cscale(acc[a], sp.inv_n);
+            const Real kd[3] = {p.kx, p.ky, p.kz};
+            const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
+            const C m = cscale(acc[4], sp.inv_n), n3 = cscale(acc[3], sp.inv_n);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                W[(4 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * m.y, kd[d] * m.x);
+                W[(7 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * n3.y, kd[d] * n3.x);
+            }
+        }
+        __syncthreads();
+        // the stage is free now: refill it with the tile after next while the inverse runs
+        if (threadIdx.x == 0) {
+            const int next = tile + 2 * gridDim.x;
+            if (next < ntiles) { issue(next, cur); issued += 1 << (16 * cur); }
+        }
+        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(W, Vb, DFT_NCOMP, tw);
+        tma::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int a = 0; a < DFT_NCOMP; ++a) tma::store_3d(&map_n, kx0 * E, kyi, a * NZ, Q + a * GS);
+            tma::commit();
+        }
+    }
+    if (threadIdx.x == 0) tma::wait_all();
+}
+
+// ------------------------------------------------------------------------------------
 // Second-half z pass with TMA tiles (same contract as k_zconv_bwd), persistent: CTA b handles
 // tiles b, b + gridDim.x, ...  Two shared-memory stages, each holding one tile's ten Phi'
 // components and its bulk-fluid/Poisson spectra, are filled by TMA loads (one

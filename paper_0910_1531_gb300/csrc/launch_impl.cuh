@@ -154,8 +154,10 @@ cudaError_t LaunchZ<Real, N>::init() {
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_bwd_g<Real, N, TZ>)) != cudaSuccess) e = r;
         constexpr int TB = dft_tile_zb<Real>(N);
-        if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0)
+        if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0) {
             if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
+            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
+        }
     } else {
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
@@ -167,9 +169,44 @@ cudaError_t LaunchZ<Real, N>::init() {
 template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
-                                 C* slot_es, double* red_energy, const C* tw) {
+                                 C* slot_es, double* red_energy, const C* tw, int* status) {
+    constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 1;
+    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
+    constexpr bool kTma = N > 0 && (TB * sizeof(C)) % 16 == 0;
+    if constexpr (kTma) {
+        static int optin = 0, sms = 0;
+        if (optin == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        const size_t sm = dftk::zfwd_tma_smem<Real, N, TB>(sp.S);
+        if (!red_energy && status && sm <= size_t(optin)) {
+            // TMA path (the grand-potential sums keep the one-tile-per-CTA kernel below)
+            constexpr int NT = dft_zbwd_threads<Real>(N);
+            constexpr int E = int(sizeof(C) / 8);
+            CUtensorMap map_in, map_n;
+            auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
+                return tma_encode_3d(m, const_cast<C*>(data), (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
+                                     (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
+                                     (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
+            };
+            cudaError_t e = encode(&map_in, in, sp.S);
+            if (e == cudaSuccess) e = encode(&map_n, slot_n, DFT_NCOMP);
+            if (e != cudaSuccess) return e;
+            const int ntx = (int)ceil_div(g.nxh, TB);
+            const int ntiles = ntx * g.ny;
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_fwd_tma<Real, N, TB, NT>, NT, sm);
+            if (occ < 1) occ = 1;
+            const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
+            dftk::k_zconv_fwd_tma<Real, N, TB, NT><<<grid, NT, sm, st>>>(map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
+                                                                         slot_es, ntx, ntiles, status, tw);
+            return cudaSuccess;
+        }
+    }
     if constexpr (N > 0) {
-        constexpr int TZ = dft_tile_z<Real>(N);
         const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
         dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
         if (red_energy)

@@ -178,7 +178,7 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     if (e == cudaSuccess) e = Passes<float>::yfft(st, false, g, ay, Ty, S, base + o_spec, status, base + o_twy);
     if (e == cudaSuccess)
         e = Passes<float>::zconv_fwd(st, g, az, sp, Tz, kfx, kfy, kfz, 0, base + o_spec, base + o_n, base + o_es,
-                                     nullptr, base + o_twz);
+                                     nullptr, base + o_twz, status);
     if (e == cudaSuccess) e = Passes<float>::yfft(st, true, g, ay, Ty, DFT_NCOMP, base + o_n, status, base + o_twy);
     if (e == cudaSuccess)
         e = Passes<float>::xinv(st, g, ax, LR, DFT_NCOMP, base + o_n, static_cast<float*>(n_out), nullptr, off, -1,

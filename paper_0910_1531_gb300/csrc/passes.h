@@ -78,7 +78,7 @@ struct LaunchZ {
     static cudaError_t init();
     static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                          double* red_energy, const C* tw);
+                          double* red_energy, const C* tw, int* status);
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
@@ -101,7 +101,7 @@ struct Passes {
                      int* status, const C* tw);
     static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
-                          double* red_energy, const C* tw);
+                          double* red_energy, const C* tw, int* status);
     static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
                      const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw);
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
