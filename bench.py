@@ -329,8 +329,10 @@ def run_ours(args):
     plan.profile_enable(True)
     ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ep0.record(stream)
+    torch.cuda.nvtx.range_push("profiled_steps")     # ncu --nvtx-include "profiled_steps/"
     for _ in range(args.steps):
         plan.iter_step(rho, V, -1.0, sync=False)
+    torch.cuda.nvtx.range_pop()
     ep1.record(stream)
     torch.cuda.synchronize()
     ms_prof = ep0.elapsed_time(ep1)

@@ -35,6 +35,11 @@ namespace dftk {
 
 constexpr int kThreads = 256;
 
+// Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
+#ifndef DFT_XUPD_KP
+#define DFT_XUPD_KP 1
+#endif
+
 template <typename Real> __device__ __forceinline__ void sc(Real x, Real* s, Real* c);
 template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { sincosf(x, s, c); }
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
@@ -131,6 +136,34 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
         for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     }
     return r;   // valid in thread 0
+}
+
+// Block sum of per-thread FP32 pairs (hi, lo) kept as a double-single (hi + lo) through the
+// warp shuffles (error-free TwoSum of the high parts, Knuth), then in FP64 across the warps:
+// about 48 significant bits at FP32 cost, where FP64 shuffles and adds would queue on the
+// narrow FP64 pipe.  Result valid in thread 0.
+__device__ __forceinline__ void ds_add(float& hi, float& lo, float bhi, float blo) {
+    const float s = hi + bhi;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bhi - bb);
+    const float l = err + lo + blo;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+__device__ __forceinline__ double block_sum_ds(float hi, float lo, double* scratch) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        ds_add(hi, lo, bh, bl);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = double(hi) + double(lo);
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += scratch[i];
+    return r;
 }
 
 __device__ __forceinline__ float block_max(float v, float* scratch) {
@@ -1694,48 +1727,64 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
-    // per-thread partial sum in the working precision with Kahan compensation, then FP64
-    // across threads and blocks
+    // per-thread partial sum in the working precision with Kahan compensation, then
+    // double-single (FP32) or FP64 across threads, FP64 across blocks
     Real acc = Real(0), comp = Real(0);
     bool bad = false;
-    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
-        const int r = idx / nx, x = idx - (idx / nx) * nx;
-        const long long row = row0 + r;
-        if (row >= nrows) continue;
-        // all loads of this point first (rho_out / g_out may alias rho0 / rho1)
-        Real r0[DFT_MAXS], r1[DFT_MAXS], vv[DFT_MAXS];
+    // KP points per thread at a time: every load of the KP points is issued before the first
+    // store (rho_out / g_out may alias rho0 / rho1; the points are distinct)
+    constexpr int KP = DFT_XUPD_KP;
+    const int total = LR * nx;
+    for (int base = threadIdx.x; base < total; base += KP * kThreads) {
+        Real r0[KP][DFT_MAXS], r1[KP][DFT_MAXS], vv[KP][DFT_MAXS];
 #pragma unroll
-        for (int s = 0; s < DFT_MAXS; ++s) {
-            if (s < S) {
-                const long long o = (long long)s * g.n + row * nx + x;
-                r0[s] = rho0[o];
-                r1[s] = rho1 ? rho1[o] : Real(0);
-                vv[s] = V[o];
+        for (int q = 0; q < KP; ++q) {
+            const int idx = base + q * kThreads;
+            const long long row = row0 + idx / nx;
+            const bool live = idx < total && row < nrows;
+            const long long pt = row0 * nx + idx;
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s < S && live) {
+                    const long long o = (long long)s * g.n + pt;
+                    r0[q][s] = rho0[o];
+                    r1[q][s] = rho1 ? rho1[o] : Real(0);
+                    vv[q][s] = V[o];
+                }
             }
         }
 #pragma unroll
-        for (int s = 0; s < DFT_MAXS; ++s) {
-            if (s >= S) continue;
-            const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
-            const Real c = (s & 1) ? pr.y : pr.x;
-            const long long o = (long long)s * g.n + row * nx + x;
-            const Real rho = w0 * r0[s] + w1 * r1[s];
-            const Real v = vv[s];
-            Real gval;
-            if (isinf(v) && v > Real(0)) gval = Real(0);
-            else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
-            if (!isfinite(gval) || !isfinite(rho)) bad = true;
-            const Real e = (rho - gval) * sp.inv_rho_b[s];
-            const Real y = e * e - comp;
-            const Real t = acc + y;
-            comp = (t - acc) - y;
-            acc = t;
-            if (rho_out) rho_out[o] = rho;
-            if (g_out) g_out[o] = gval;
+        for (int q = 0; q < KP; ++q) {
+            const int idx = base + q * kThreads;
+            const int r = idx / nx, x = idx - (idx / nx) * nx;
+            if (idx >= total || row0 + r >= nrows) continue;
+            const long long pt = row0 * nx + idx;
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s >= S) continue;
+                const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
+                const Real c = (s & 1) ? pr.y : pr.x;
+                const long long o = (long long)s * g.n + pt;
+                const Real rho = w0 * r0[q][s] + w1 * r1[q][s];
+                const Real v = vv[q][s];
+                Real gval;
+                if (isinf(v) && v > Real(0)) gval = Real(0);
+                else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
+                if (!isfinite(gval) || !isfinite(rho)) bad = true;
+                const Real e = (rho - gval) * sp.inv_rho_b[s];
+                const Real y = e * e - comp;
+                const Real t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+                if (rho_out) rho_out[o] = rho;
+                if (g_out) g_out[o] = gval;
+            }
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);
-    const double bs = block_sum(double(acc) - double(comp), scratch_d);
+    double bs;
+    if constexpr (sizeof(Real) == 4) bs = block_sum_ds(acc, -comp, scratch_d);
+    else bs = block_sum(double(acc) - double(comp), scratch_d);
     if (threadIdx.x == 0) red_sum[blockIdx.x] = bs;
 }
 
