@@ -333,12 +333,22 @@ __global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int 
 // ------------------------------------------------------------------------------------
 // y pass with TMA tiles (compile-time length NY <= 256 and tile width TY).  Persistent: CTA b
 // handles tiles b, b + gridDim.x, ...  Two shared-memory stages are filled by TMA loads (one
-// cp.async.bulk.tensor per tile, completing on an mbarrier) while the previous tile is
-// transformed; results leave through a TMA store.  The tensor map views the half spectra as
-// (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements, E = sizeof(complex) / 8; a tile is the
-// box (TY * E, NY, 1).  A wait that runs out sets DEV_TIMEOUT and the CTA stops after draining
-// the loads it has in flight.
+// cp.async.bulk.tensor per tile, completing on an mbarrier).  The first FFT stage moves a
+// tile out of its TMA stage into scratch X, so the stage is refilled with the tile after next
+// at once; the remaining stages run between X and Y (padded layout) and the last writes the
+// dense box that leaves through a TMA store, whose shared-memory reads are awaited only before
+// that buffer is written again.  The tensor map views the half spectra as (x: nxh * E, y: ny,
+// plane: nz * ncomp) 8-byte elements, E = sizeof(complex) / 8; a tile is the box (TY * E, NY,
+// 1).  A wait that runs out sets DEV_TIMEOUT and the CTA stops after draining the loads it has
+// in flight.
+// Shared memory: stage 0 | stage 1 (dense tiles) | X | Y (padded) | twiddles | 2 mbarriers.
 // ------------------------------------------------------------------------------------
+template <typename Real, int NY, int TY> __host__ __device__ constexpr size_t yfft_tma_smem() {
+    using C = typename Cplx<Real>::type;
+    return (2 * size_t(TY) * NY + 2 * size_t(ct_gstride(NY, TY, int(sizeof(C)))) + NY) * sizeof(C) +
+           2 * sizeof(uint64_t) + 128;
+}
+
 template <typename Real, bool INV, int NY, int TY>
 __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ CUtensorMap map, int ntiles_x,
                                                        int ntiles, int* __restrict__ status,
@@ -347,12 +357,16 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
     constexpr int TILE = TY * NY;
+    constexpr int GS = ct_gstride(NY, TY, int(sizeof(C)));
+    constexpr int NST = ct_nstages(NY);
     constexpr uint32_t BYTES = uint32_t(TILE * sizeof(C));
+    static_assert(BYTES % 128 == 0, "TMA stage alignment");
     extern __shared__ unsigned char smem_raw[];
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
-    C* stage[2] = {reinterpret_cast<C*>(base), reinterpret_cast<C*>(base) + TILE};
-    C* X = stage[1] + TILE;
-    C* tw = X + TILE;
+    C* const stage0 = reinterpret_cast<C*>(base);
+    C* X = stage0 + 2 * TILE;
+    C* Y = X + GS;
+    C* tw = Y + GS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NY);
     if (threadIdx.x == 0) {
         tma::mbar_init(&bar[0], 1);
@@ -361,45 +375,57 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
     }
     for (int i = threadIdx.x; i < NY; i += kThreads) tw[i] = twy[i];
     __syncthreads();
-    int issued[2] = {0, 0}, consumed[2] = {0, 0};   // meaningful in thread 0
+    int issued = 0, consumed = 0;   // per stage, packed (stage 1 << 16) | stage 0; thread 0
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
             const int tile = blockIdx.x + s * gridDim.x;
             if (tile < ntiles) {
                 tma::mbar_expect_tx(&bar[s], BYTES);
-                tma::load_3d(stage[s], &map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, &bar[s]);
-                issued[s] = 1;
+                tma::load_3d(stage0 + s * TILE, &map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, &bar[s]);
+                issued += 1 << (16 * s);
             }
         }
     }
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int cur = it & 1;
+        C* st = stage0 + cur * TILE;
         const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        // an odd stage count leaves the result in X, which the first stage writes next
+        if (NST % 2 == 1 && threadIdx.x == 0) tma::wait_read_all();
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicOr(status, DEV_TIMEOUT);
-                for (int s = 0; s < 2; ++s)
-                    if (issued[s] > consumed[s]) tma::mbar_wait(&bar[s], (issued[s] - 1) & 1);
+                for (int s = 0; s < 2; ++s) {
+                    const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
+                    if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
+                }
             }
             break;
         }
-        consumed[cur] += 1;
-        C* R = ct_fft<NY, INV, true, TY>(stage[cur], X, 0, 0, tw);
-        tma::fence_proxy_async();
+        consumed += 1 << (16 * cur);
+        ct_stage_grouped<NY, ct_radix_at(NY, 0), ct_ns_at(NY, 0), INV, TY, GS, true, NST == 1, kThreads>(st, X, 1,
+                                                                                                       tw);
+        // an even stage count leaves the result in Y, which the second stage writes next
+        if (NST % 2 == 0 && threadIdx.x == 0) tma::wait_read_all();
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma::store_3d(&map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, R);
-            tma::commit();
-            tma::wait_read_all();
             const int next = tile + 2 * gridDim.x;
             if (next < ntiles) {
                 tma::mbar_expect_tx(&bar[cur], BYTES);
-                tma::load_3d(stage[cur], &map, (next % ntiles_x) * TY * E, 0, next / ntiles_x, &bar[cur]);
-                issued[cur] += 1;
+                tma::load_3d(st, &map, (next % ntiles_x) * TY * E, 0, next / ntiles_x, &bar[cur]);
+                issued += 1 << (16 * cur);
             }
         }
+        C* a = X;
+        C* b = Y;
+        ct_stages_grouped<NY, INV, TY, GS, false, true, kThreads, 1>(a, b, 1, tw);
+        tma::fence_proxy_async();
         __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::store_3d(&map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, a);
+            tma::commit();
+        }
     }
     if (threadIdx.x == 0) tma::wait_all();
 }

@@ -117,7 +117,7 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
         if (e != cudaSuccess) return e;
         const int ntx = (int)ceil_div(g.nxh, TY);
         const int ntiles = ntx * g.nz * ncomp;
-        const size_t sm = (3 * size_t(TY) * N + N) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+        const size_t sm = dftk::yfft_tma_smem<Real, N, TY>();
         static int per_sm[2] = {0, 0};
         static int sms = 0;
         int& occ = per_sm[inv ? 1 : 0];

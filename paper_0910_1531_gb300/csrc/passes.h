@@ -19,7 +19,12 @@ __host__ __device__ constexpr bool dft_is_ct_size(int n) {
 }
 
 // Column-tile widths of the compile-time y and z passes (kx columns per tile).
-template <typename Real> __host__ __device__ constexpr int dft_tile_y(int n) { return sizeof(Real) == 4 ? 16 : 8; }
+#ifndef DFT_TILE_Y_SHIFT
+#define DFT_TILE_Y_SHIFT 0
+#endif
+template <typename Real> __host__ __device__ constexpr int dft_tile_y(int n) {
+    return (sizeof(Real) == 4 ? 16 : 8) >> DFT_TILE_Y_SHIFT;
+}
 // The compile-time z passes transform all components of a tile together (two pools of ten
 // tiles in shared memory): the width keeps a CTA near 86 KB (FP32) so that two fit on an SM.
 // DFT_TILE_ZG_SHIFT (build flag, default 0) narrows the tiles by that power of two.
