@@ -260,7 +260,7 @@ template <typename Real> struct Ops {
     static const C* tw(dft_plan* p, int a) { return static_cast<const C*>(p->tw[a]); }
     static C* T1(dft_plan* p) { return static_cast<C*>(p->T1); }
     static C* slot_n(void* s) { return static_cast<C*>(s); }
-    static C* slot_es(dft_plan* p, void* s) { return static_cast<C*>(s) + DFT_NCOMP * p->g.nc; }
+    static C* slot_es(dft_plan* p, void* s) { return static_cast<C*>(s) + DFT_NSPEC * p->g.nc; }
     static Real kf(dft_plan* p, int a) { return Real(p->kf[a]); }
 
     // rho (S real fields) -> slot: ten weighted densities (kx, ky, z) and the S (+psi)
@@ -270,9 +270,9 @@ template <typename Real> struct Ops {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
-        LAUNCH(p, K_ZFWD, (p->S + DFT_NCOMP + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
+        LAUNCH(p, K_ZFWD, (p->S + DFT_NSPEC + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
                                        T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NCOMP, slot_n(slot), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 1)));
         return DFT_OK;
     }
 
@@ -284,11 +284,11 @@ template <typename Real> struct Ops {
         C* B = use_B ? slot_n(p->slotB) : nullptr;
         C* esA = slot_es(p, p->slotA);
         C* esB = use_B ? slot_es(p, p->slotB) : nullptr;
-        LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NCOMP * CB(p),
+        LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NSPEC * CB(p),
                P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
-                                  p->red_max, &p->ctl->status, nullptr, tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, T1(p), &p->ctl->status, tw(p, 1)));
-        LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
+                                  p->red_max, &p->ctl->status, nullptr, kf(p, 0), tw(p, 0)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, T1(p), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
                                        p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
@@ -306,8 +306,11 @@ template <typename Real> struct Ops {
         for (int c = 0; c < DFT_NCOMP + 2; ++c) off.v[c] = Real(0);
         if (offs)
             for (int c = 0; c < ncomp; ++c) off.v[c] = Real(offs[c]);
-        LAUNCH(p, K_XINV, ncomp * (CB(p) + (out || out_last ? RB(p) : 0.0)), P::xinv(p->stream, p->g, p->ax, LR, ncomp, spec, out, out_last, off, cmax, red_max,
-                                  tw(p, 0)));
+        // ten real rows are the weighted densities, built from the nine kept spectra
+        const int wd = ncomp == DFT_NCOMP ? 1 : 0;
+        LAUNCH(p, K_XINV, ((wd ? DFT_NSPEC : ncomp) * CB(p) + (out || out_last ? ncomp * RB(p) : 0.0)),
+               P::xinv(p->stream, p->g, p->ax, LR, ncomp, spec, out, out_last, off, cmax, red_max, wd, kf(p, 0),
+                       tw(p, 0)));
         if (blocks_out) *blocks_out = (int)p->blocks_x(LR);
         return DFT_OK;
     }
@@ -393,10 +396,10 @@ template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* 
     const SpeciesDesc<Real>& sp = species<Real>(p);
     TRY(O::first_half(p, rho, p->slotA, 0));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
-    LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
-                              O::T1(p), p->red_max, &p->ctl->status, nullptr, O::tw(p, 0)));
-    LAUNCH(p, K_YFFT, 2.0 * (DFT_NCOMP) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p), &p->ctl->status, O::tw(p, 1)));
-    LAUNCH(p, K_ZBWD, (DFT_NCOMP + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
+    LAUNCH(p, K_XPHI, 2.0 * DFT_NSPEC * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
+                              O::T1(p), p->red_max, &p->ctl->status, nullptr, O::kf(p, 0), O::tw(p, 0)));
+    LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p), &p->ctl->status, O::tw(p, 1)));
+    LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
     LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), &p->ctl->status, O::tw(p, 1)));
     TRY(O::xinv(p, p->S, O::T1(p), c1, nullptr, nullptr, -1, nullptr, nullptr));
@@ -518,12 +521,12 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
     TRY(reset_status(p));
     TRY(O::first_half(p, rho, p->slotA, 0, r_energy));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
-    LAUNCH(p, K_XPHI, 2.0 * DFT_NCOMP * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA),
+    LAUNCH(p, K_XPHI, 2.0 * DFT_NSPEC * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA),
                                                         nullptr, nullptr, O::T1(p), p->red_max, &p->ctl->status,
-                                                        r_phi, O::tw(p, 0)));
-    LAUNCH(p, K_YFFT, 2.0 * DFT_NCOMP * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NCOMP, O::T1(p),
+                                                        r_phi, O::kf(p, 0), O::tw(p, 0)));
+    LAUNCH(p, K_YFFT, 2.0 * DFT_NSPEC * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p),
                                                         &p->ctl->status, O::tw(p, 1)));
-    LAUNCH(p, K_ZBWD, (DFT_NCOMP + 2 * S) * CB(p),
+    LAUNCH(p, K_ZBWD, (DFT_NSPEC + 2 * S) * CB(p),
            P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 3, S, p->ctl,
                         O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
     LAUNCH(p, K_YFFT, 2.0 * S * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, S, O::T1(p), &p->ctl->status,
@@ -682,7 +685,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
             cudaMemcpy(p->tw[a], t.data(), bytes, cudaMemcpyHostToDevice);
         }
     }
-    const size_t slot_comps = DFT_NCOMP + S + 1;
+    const size_t slot_comps = DFT_NSPEC + S + 1;
     const size_t nred = size_t(g.ny) * g.nz + 1;
     struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
         {&p->T1, size_t(DFT_NCOMP) * g.nc * p->csize, "work spectra"},

@@ -8,6 +8,11 @@
 #define DFT_MAXS 5          // species (the back-convolution keeps 5 k-space accumulators)
 #define DFT_MAXSTAGES 8     // radix stages per axis
 #define DFT_NCOMP 10        // n0 n1 n2 n3 nV1(xyz) nV2(xyz)
+// Weighted-density spectra kept between the passes: n0 n1 n2 n3, m (n_V1 = grad m), then
+// i k_y m, i k_z m, i k_y n3, i k_z n3.  The x components i k_x m and i k_x n3 are formed in
+// the x pass that takes the spectra to real space (and the divergence terms of the back
+// convolution in the x pass that leaves it), so the y and z passes carry nine components.
+#define DFT_NSPEC 9
 
 template <typename Real> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };

@@ -89,8 +89,9 @@ cudaError_t Passes<Real>::zconv_fwd(cudaStream_t st, const GridDesc& g, const Ax
 
 template <typename Real>
 cudaError_t Passes<Real>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                        const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw) {
-    DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, red_phi, tw))
+                        const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, Real kfx,
+                        const C* tw) {
+    DFT_SWITCH_X(g.nx, xphi(st, g, px, LR, ctl, A, B, mat, phi, red_max, status, red_phi, kfx, tw))
 }
 
 template <typename Real>
@@ -109,8 +110,9 @@ cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const Axis
 
 template <typename Real>
 cudaError_t Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
-                        Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw) {
-    DFT_SWITCH_X(g.nx, xinv(st, g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw))
+                        Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
+                        Real kfx, const C* tw) {
+    DFT_SWITCH_X(g.nx, xinv(st, g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, wd, kfx, tw))
 }
 
 template <typename Real>

@@ -35,6 +35,11 @@ namespace dftk {
 
 constexpr int kThreads = 256;
 
+// Elements per thread whose loads the weighted-density row loader issues together (build flag).
+#ifndef DFT_WD_BATCH
+#define DFT_WD_BATCH 2
+#endif
+
 // Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
 #ifndef DFT_XUPD_KP
 #define DFT_XUPD_KP 1
@@ -597,23 +602,22 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
     }
     __syncthreads();
 
-    // phase 3: inverse z of the ten weighted densities.  Vector spectra are i k_d n3_hat and
-    // i k_d m_hat (n_V2 = grad n3, n_V1 = grad m), zero on the Nyquist index of axis d.
-    const int order[10] = {4, 5, 6, 7, 8, 9, 3, 0, 1, 2};
-    for (int oi = 0; oi < 10; ++oi) {
+    // phase 3: inverse z of the nine weighted-density spectra: n0..n3, m, then i k_y m, i k_z m,
+    // i k_y n3, i k_z n3 (zero on the Nyquist index of their axis); the derived ones first,
+    // while m and n3 are still in k space.
+    const int order[DFT_NSPEC] = {5, 6, 7, 8, 4, 3, 0, 1, 2};
+    for (int oi = 0; oi < DFT_NSPEC; ++oi) {
         const int a = order[oi];
         C* r;
-        if (a >= 4) {
+        if (a >= 5) {
             const C* src = (a < 7) ? pool[4] : pool[3];
-            const int d = (a - 4) % 3;
+            const int d = (a == 5 || a == 7) ? 1 : 2;
             C* W = pool[5];
             for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-                const int kzi = idx / T, t = idx - (idx / T) * T;
-                const int kxi = kx0 + t;
+                const int kzi = idx / T;
                 Real kd;
                 bool nyq;
-                if (d == 0) { kd = kval<Real>(kxi, g.nx, kfx); nyq = (g.nx % 2 == 0) && (2 * kxi == g.nx); }
-                else if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
+                if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
                 else { kd = kval<Real>(kzi, g.nz, kfz); nyq = (g.nz % 2 == 0) && (2 * kzi == g.nz); }
                 const C u = src[idx];
                 W[idx] = nyq ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd * u.y, kd * u.x);
@@ -635,8 +639,51 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
 // costs a handful of barriers instead of a dozen transforms of one component each.
 // Shared memory: twiddles | 10 tiles | 10 tiles (ct_gstride(NZ, TZ, csize) elements each).
 // ------------------------------------------------------------------------------------
+// The nine weighted-density spectra of one k point into grouped tiles (group stride GS,
+// position pos), 1/N applied: acc = (n0, n1, n2, n3, m) spectra; i k_y and i k_z of m and n3
+// are zero on the Nyquist index of their axis.
+template <typename Real>
+__device__ __forceinline__ void store_wd_spectra(typename Cplx<Real>::type* O, int GS, int pos,
+                                                 const typename Cplx<Real>::type* acc, Real inv_n,
+                                                 const KPoint<Real>& p) {
+    using C = typename Cplx<Real>::type;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) O[a * GS + pos] = cscale(acc[a], inv_n);
+    const C m = cscale(acc[4], inv_n), n3 = cscale(acc[3], inv_n);
+    const C zero = cmake<C>(Real(0), Real(0));
+    O[5 * GS + pos] = p.nyq_y ? zero : cmake<C>(-p.ky * m.y, p.ky * m.x);
+    O[6 * GS + pos] = p.nyq_z ? zero : cmake<C>(-p.kz * m.y, p.kz * m.x);
+    O[7 * GS + pos] = p.nyq_y ? zero : cmake<C>(-p.ky * n3.y, p.ky * n3.x);
+    O[8 * GS + pos] = p.nyq_z ? zero : cmake<C>(-p.kz * n3.y, p.kz * n3.x);
+}
+
+// Species-independent sums of the back convolution at one k point from the nine Phi' spectra
+// of the x and y passes (group stride GS, position pos): a0..a2 = Phi_0..Phi_2,
+// a3 = B3 - i k_y Phi_V2y - i k_z Phi_V2z, a4 = B4 - i k_y Phi_V1y - i k_z Phi_V1z, where the
+// x pass formed B3 = Phi_3 - i k_x Phi_V2x and B4 = -i k_x Phi_V1x (Nyquist terms dropped).
+template <typename Real>
+__device__ __forceinline__ void bwd_sums(const typename Cplx<Real>::type* X, int GS, int pos, const KPoint<Real>& p,
+                                         typename Cplx<Real>::type* a) {
+    using C = typename Cplx<Real>::type;
+    a[0] = X[0 * GS + pos];
+    a[1] = X[1 * GS + pos];
+    a[2] = X[2 * GS + pos];
+    a[3] = X[3 * GS + pos];
+    a[4] = X[4 * GS + pos];
+    if (!p.nyq_y) {
+        const C u1 = X[5 * GS + pos], u2 = X[7 * GS + pos];
+        a[4] = cadd(a[4], cmake<C>(p.ky * u1.y, -p.ky * u1.x));
+        a[3] = cadd(a[3], cmake<C>(p.ky * u2.y, -p.ky * u2.x));
+    }
+    if (!p.nyq_z) {
+        const C u1 = X[6 * GS + pos], u2 = X[8 * GS + pos];
+        a[4] = cadd(a[4], cmake<C>(p.kz * u1.y, -p.kz * u1.x));
+        a[3] = cadd(a[3], cmake<C>(p.kz * u2.y, -p.kz * u2.x));
+    }
+}
+
 template <int TT, int NN> __host__ __device__ constexpr size_t zg_smem_bytes(size_t csize) {
-    return (size_t(NN) + 2 * size_t(DFT_NCOMP) * ct_gstride(NN, TT, int(csize))) * csize + 16;
+    return (size_t(NN) + 2 * size_t(DFT_NSPEC) * ct_gstride(NN, TT, int(csize))) * csize + 16;
 }
 
 // Load `groups` column tiles (component c at src + c * cstride, global row stride rs, columns
@@ -734,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
     const int Pn = S * (S + 1) / 2;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + NZ;
-    C* B = A + DFT_NCOMP * GS;
+    C* B = A + DFT_NSPEC * GS;
     for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = twz[i];
     const int kx0 = blockIdx.x * TZ;
     const int kyi = blockIdx.y;
@@ -846,18 +893,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
                 slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
             }
         }
-        // the ten weighted-density spectra, 1/N applied; vector components are i k_d m_hat
-        // (n_V1) and i k_d n3_hat (n_V2), zero on the Nyquist index of axis d
-#pragma unroll
-        for (int a = 0; a < 4; ++a) O[a * GS + pos] = cscale(acc[a], sp.inv_n);
-        const Real kd[3] = {p.kx, p.ky, p.kz};
-        const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
-        const C m = cscale(acc[4], sp.inv_n), n3 = cscale(acc[3], sp.inv_n);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            O[(4 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * m.y, kd[d] * m.x);
-            O[(7 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * n3.y, kd[d] * n3.x);
-        }
+        // the nine weighted-density spectra, 1/N applied (DFT_NSPEC order)
+        store_wd_spectra<Real>(O, GS, pos, acc, sp.inv_n, p);
     }
     if constexpr (GRAD) {
         const double be = block_sum(e_acc, scratch_d);
@@ -869,8 +906,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
         }
     }
     __syncthreads();
-    C* Q = ct_fft_grouped<NZ, true, TZ, GS>(O, R, DFT_NCOMP, tw);
-    tiles_store_grouped<TZ, NZ>(slot_n + col0, Q, g.nc, DFT_NCOMP, zstride, nxh - kx0);
+    C* Q = ct_fft_grouped<NZ, true, TZ, GS>(O, R, DFT_NSPEC, tw);
+    tiles_store_grouped<TZ, NZ>(slot_n + col0, Q, g.nc, DFT_NSPEC, zstride, nxh - kx0);
 }
 
 // Second-half z pass (same contract as k_zconv_bwd): the ten Phi' spectra in (flags & 1), the
@@ -895,7 +932,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
     const int ny = g.ny, nxh = g.nxh, S = sp.S;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + NZ;
-    C* B = A + DFT_NCOMP * GS;
+    C* B = A + DFT_NSPEC * GS;
     for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = twz[i];
     const int kx0 = blockIdx.x * TZ;
     const int kyi = blockIdx.y;
@@ -905,9 +942,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
     C* R = A;
     if (hs) {
-        tiles_load_grouped<TZ, NZ, DFT_NCOMP>(A, phi + col0, g.nc, DFT_NCOMP, zstride, nxh - kx0);
+        tiles_load_grouped<TZ, NZ, DFT_NSPEC>(A, phi + col0, g.nc, DFT_NSPEC, zstride, nxh - kx0);
         __syncthreads();
-        R = ct_fft_grouped<NZ, false, TZ, GS>(A, B, DFT_NCOMP, tw);
+        R = ct_fft_grouped<NZ, false, TZ, GS>(A, B, DFT_NSPEC, tw);
     }
     C* O = (R == A) ? B : A;
     const Real fourpi = Real(4.0 * CUDART_PI);
@@ -960,20 +997,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
         }
         if (hs) {
             const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
-            // species-independent sums: Phi_0..Phi_3, with -i k_d Phi_V2d added to the third and
-            // -i k_d Phi_V1d summed into a fifth (Nyquist components of axis d dropped)
-            const C a0 = R[0 * GS + pos], a1 = R[1 * GS + pos], a2 = R[2 * GS + pos];
-            C a3 = R[3 * GS + pos];
-            C a4 = cmake<C>(Real(0), Real(0));
-            const Real kd[3] = {p.kx, p.ky, p.kz};
-            const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (nyq[d]) continue;
-                const C u1 = R[(4 + d) * GS + pos], u2 = R[(7 + d) * GS + pos];
-                a4 = cadd(a4, cmake<C>(kd[d] * u1.y, -kd[d] * u1.x));
-                a3 = cadd(a3, cmake<C>(kd[d] * u2.y, -kd[d] * u2.x));
-            }
+            C asum[5];
+            bwd_sums<Real>(R, GS, pos, p, asum);
+            const C a0 = asum[0], a1 = asum[1], a2 = asum[2], a3 = asum[3], a4 = asum[4];
 #pragma unroll
             for (int s = 0; s < DFT_MAXS; ++s) {
                 if (s >= S) break;
@@ -1012,7 +1038,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
 template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zfwd_tma_smem(int S) {
     using C = typename Cplx<Real>::type;
     constexpr size_t GS = size_t(ct_gstride(NZ, TZ, int(sizeof(C))));
-    return ((2 * size_t(S) + 2 * DFT_NCOMP) * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+    return ((2 * size_t(S) + 2 * DFT_NSPEC) * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
 }
 
 template <typename Real, int NZ, int TZ, int NT>
@@ -1039,8 +1065,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
     C* const stage0 = reinterpret_cast<C*>(base);
     C* W = stage0 + 2 * stage_elems;
-    C* Vb = W + DFT_NCOMP * GS;
-    C* tw = Vb + DFT_NCOMP * GS;
+    C* Vb = W + DFT_NSPEC * GS;
+    C* tw = Vb + DFT_NSPEC * GS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
     const uint32_t tile_bytes = uint32_t(S) * BOX;
     const long long zstride = (long long)ny * g.pxh;
@@ -1181,18 +1207,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
                     slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
                 }
             }
-            // the ten weighted-density spectra, 1/N applied; vector components are i k_d m_hat
-            // (n_V1) and i k_d n3_hat (n_V2), zero on the Nyquist index of axis d
-#pragma unroll
-            for (int a = 0; a < 4; ++a) W[a * GS + pos] = cscale(acc[a], sp.inv_n);
-            const Real kd[3] = {p.kx, p.ky, p.kz};
-            const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
-            const C m = cscale(acc[4], sp.inv_n), n3 = cscale(acc[3], sp.inv_n);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                W[(4 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * m.y, kd[d] * m.x);
-                W[(7 + d) * GS + pos] = nyq[d] ? cmake<C>(Real(0), Real(0)) : cmake<C>(-kd[d] * n3.y, kd[d] * n3.x);
-            }
+            // the nine weighted-density spectra, 1/N applied (DFT_NSPEC order)
+            store_wd_spectra<Real>(W, GS, pos, acc, sp.inv_n, p);
         }
         __syncthreads();
         // the stage is free now: refill it with the tile after next while the inverse runs
@@ -1200,11 +1216,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
             const int next = tile + 2 * gridDim.x;
             if (next < ntiles) { issue(next, cur); issued += 1 << (16 * cur); }
         }
-        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(W, Vb, DFT_NCOMP, tw);
+        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(W, Vb, DFT_NSPEC, tw);
         tma::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int a = 0; a < DFT_NCOMP; ++a) tma::store_3d(&map_n, kx0 * E, kyi, a * NZ, Q + a * GS);
+            for (int a = 0; a < DFT_NSPEC; ++a) tma::store_3d(&map_n, kx0 * E, kyi, a * NZ, Q + a * GS);
             tma::commit();
         }
     }
@@ -1227,7 +1243,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
 template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zbwd_tma_smem(int nes) {
     using C = typename Cplx<Real>::type;
     constexpr size_t GS = size_t(ct_gstride(NZ, TZ, int(sizeof(C))));
-    return (2 * (DFT_NCOMP * GS + size_t(nes) * TZ * NZ) + DFT_NCOMP * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+    return (2 * (DFT_NSPEC * GS + size_t(nes) * TZ * NZ) + DFT_NSPEC * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
 }
 
 template <typename Real, int NZ, int TZ, int NT>
@@ -1250,13 +1266,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
     extern __shared__ unsigned char smem_raw[];
     const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
     const int nes = es_on ? ncomp_out * (has_esB ? 2 : 1) : 0;
-    const int stage_elems = DFT_NCOMP * GS + nes * TILE;
+    const int stage_elems = DFT_NSPEC * GS + nes * TILE;
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
     C* const stage0 = reinterpret_cast<C*>(base);
     C* W = stage0 + 2 * stage_elems;
-    C* tw = W + DFT_NCOMP * GS;
+    C* tw = W + DFT_NSPEC * GS;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
-    const uint32_t tile_bytes = uint32_t((hs ? DFT_NCOMP : 0) + nes) * BOX;
+    const uint32_t tile_bytes = uint32_t((hs ? DFT_NSPEC : 0) + nes) * BOX;
     const int S = sp.S, ny = g.ny, nxh = g.nxh;
     const long long zstride = (long long)ny * g.pxh;
 
@@ -1265,13 +1281,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
         tma::mbar_expect_tx(&bar[s], tile_bytes);
         if (hs)
-            for (int c = 0; c < DFT_NCOMP; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
+            for (int c = 0; c < DFT_NSPEC; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
         if (es_on) {
             for (int c = 0; c < ncomp_out; ++c)
-                tma::load_3d(st + DFT_NCOMP * GS + c * TILE, &map_esA, x, y, c * NZ, &bar[s]);
+                tma::load_3d(st + DFT_NSPEC * GS + c * TILE, &map_esA, x, y, c * NZ, &bar[s]);
             if (has_esB)
                 for (int c = 0; c < ncomp_out; ++c)
-                    tma::load_3d(st + DFT_NCOMP * GS + (ncomp_out + c) * TILE, &map_esB, x, y, c * NZ, &bar[s]);
+                    tma::load_3d(st + DFT_NSPEC * GS + (ncomp_out + c) * TILE, &map_esB, x, y, c * NZ, &bar[s]);
         }
     };
     if (threadIdx.x == 0) {
@@ -1329,11 +1345,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
         }
         consumed += 1 << (16 * cur);
         C* st = stage0 + cur * stage_elems;
-        const C* es_t = st + DFT_NCOMP * GS;
+        const C* es_t = st + DFT_NSPEC * GS;
         C* X = st;
         C* Y = W;
         if (hs) {
-            X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NCOMP, tw);
+            X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NSPEC, tw);
             Y = (X == st) ? W : st;
         }
 #pragma unroll
@@ -1361,18 +1377,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
             }
             if (hs) {
                 const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
-                const C a0 = X[0 * GS + pos], a1 = X[1 * GS + pos], a2 = X[2 * GS + pos];
-                C a3 = X[3 * GS + pos];
-                C a4 = cmake<C>(Real(0), Real(0));
-                const Real kd[3] = {p.kx, p.ky, p.kz};
-                const bool nyq[3] = {p.nyq_x, p.nyq_y, p.nyq_z};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    if (nyq[d]) continue;
-                    const C u1 = X[(4 + d) * GS + pos], u2 = X[(7 + d) * GS + pos];
-                    a4 = cadd(a4, cmake<C>(kd[d] * u1.y, -kd[d] * u1.x));
-                    a3 = cadd(a3, cmake<C>(kd[d] * u2.y, -kd[d] * u2.x));
-                }
+                C asum[5];
+                bwd_sums<Real>(X, GS, pos, p, asum);
+                const C a0 = asum[0], a1 = asum[1], a2 = asum[2], a3 = asum[3], a4 = asum[4];
 #pragma unroll
                 for (int s = 0; s < DFT_MAXS; ++s) {
                     if (s >= S) break;
@@ -1463,19 +1470,39 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
     return ok;
 }
 
+// The ten weighted densities in the x passes: five complex lines of two real rows each,
+// (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z), so that n3 and nV2x = d/dx n3
+// come from one spectrum read by one thread.  wd_comp(l, j): component of slot j of line l;
+// wd_line / wd_slot: the inverse; wd_spec: the kept spectrum (DFT_NSPEC order) behind a slot,
+// wd_dx: the slot is i k_x times that spectrum (nV1x = i k_x m, nV2x = i k_x n3).
+__host__ __device__ constexpr int wd_comp(int l, int j) {
+    return l == 0 ? j : (l == 1 ? (j ? 5 : 2) : (l == 2 ? (j ? 7 : 3) : (l == 3 ? (j ? 6 : 4) : 8 + j)));
+}
+__host__ __device__ constexpr int wd_line(int c) {
+    return c < 2 ? 0 : (c == 2 || c == 5 ? 1 : (c == 3 || c == 7 ? 2 : (c == 4 || c == 6 ? 3 : 4)));
+}
+__host__ __device__ constexpr int wd_slot(int c) { return (c == 1 || c == 5 || c == 7 || c == 6 || c == 9) ? 1 : 0; }
+__host__ __device__ constexpr int wd_spec(int l, int j) {
+    return l == 0 ? j : (l == 1 ? (j ? 5 : 2) : (l == 2 ? 3 : (l == 3 ? (j ? 6 : 4) : 7 + j)));
+}
+__host__ __device__ constexpr bool wd_dx(int l, int j) { return (l == 2 && j == 1) || (l == 3 && j == 0); }
+
 // Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
 // full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
-// Loads are issued in batches of kBatch elements per thread before any store, so that several
-// are in flight at once.
-template <typename Real, int NX>
+// wd: the ten rows are the weighted densities built from the nine kept spectra (wd_src), rows
+// 4 and 7 multiplied by i k_x (zero on the Nyquist index); mat_out then receives the nine mixed
+// spectra.  Loads are issued in batches of kBatch elements per thread before any store, so that
+// several are in flight at once.
+template <typename Real, int NX, bool WD = false>
 __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
                                                long long nrows, int ncomp,
                                                const typename Cplx<Real>::type* A,
                                                const typename Cplx<Real>::type* Bm, Real wA, Real wB,
                                                typename Cplx<Real>::type* mat_out,
-                                               typename Cplx<Real>::type* dst) {
+                                               typename Cplx<Real>::type* dst, Real kfx = Real(0)) {
     using C = typename Cplx<Real>::type;
-    constexpr int kBatch = 4;
+    constexpr bool wd = WD;
+    constexpr int kBatch = WD ? DFT_WD_BATCH : 4;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
     const int total = lines * nxh;
@@ -1488,11 +1515,12 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
             const int idx = base + j * kThreads;
             const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
             const long long row = row0 + l / lines_per_row;
-            const int ca = 2 * (l % lines_per_row), cb = ca + 1;
+            const int lr = l % lines_per_row, ca = 2 * lr, cb = ca + 1;
             live[j] = idx < total && row < nrows;
             hasb[j] = cb < ncomp;
-            oa[j] = (long long)ca * g.nc + row * g.pxh + k;
-            ob[j] = (long long)cb * g.nc + row * g.pxh + k;
+            const int sa = wd ? wd_spec(lr, 0) : ca, sb = wd ? wd_spec(lr, 1) : cb;
+            oa[j] = (long long)sa * g.nc + row * g.pxh + k;
+            ob[j] = (long long)sb * g.nc + row * g.pxh + k;
             av[j] = bv[j] = aB[j] = bB[j] = cmake<C>(Real(0), Real(0));
             if (live[j]) {
                 av[j] = A[oa[j]];
@@ -1508,15 +1536,23 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
             const int idx = base + j * kThreads;
             if (idx >= total) continue;
             const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+            const int lr = l % lines_per_row;
             C a = cadd(cscale(av[j], wA), cscale(aB[j], wB));
             C b = cadd(cscale(bv[j], wA), cscale(bB[j], wB));
-            if (k == 0 || (even && 2 * k == nx)) { a.y = Real(0); b.y = Real(0); }
+            const bool edge = k == 0 || (even && 2 * k == nx);
+            if (edge) { a.y = Real(0); b.y = Real(0); }
             if (mat_out && live[j]) {
                 mat_out[oa[j]] = a;
-                if (hasb[j]) mat_out[ob[j]] = b;
+                if (hasb[j] && !(wd && lr == 2)) mat_out[ob[j]] = b;   // line 2 reads n3 twice
+            }
+            if (wd) {
+                const Real kx = Real(k) * kfx;
+                const C zero = cmake<C>(Real(0), Real(0));
+                if (wd_dx(lr, 0)) a = (even && 2 * k == nx) ? zero : cmake<C>(-kx * a.y, kx * a.x);
+                if (wd_dx(lr, 1)) b = (even && 2 * k == nx) ? zero : cmake<C>(-kx * b.y, kx * b.x);
             }
             dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
-            if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            if (!edge) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
         }
     }
 }
@@ -1542,6 +1578,41 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
     }
 }
 
+// Half spectra of the ten dPhi/dn_alpha rows of `rows` grid rows (five complex lines each, in the
+// wd_comp arrangement of load_pair_rows) into the nine spectra the y and z passes carry:
+// Phi_0..Phi_2, B3 = Phi_3 - i k_x Phi_V2x, B4 = -i k_x Phi_V1x, Phi_V1y, Phi_V1z, Phi_V2y,
+// Phi_V2z (the -i k_x terms dropped on the Nyquist index).  Each line maps to its own outputs:
+// line 2 holds Phi_3 and Phi_V2x, line 3 Phi_V1x and Phi_V1z.
+template <typename Real, int NX>
+__device__ __forceinline__ void store_phi_spectra(const GridDesc& g, int rows, long long row0, long long nrows,
+                                                  Real kfx, const typename Cplx<Real>::type* R,
+                                                  typename Cplx<Real>::type* out) {
+    using C = typename Cplx<Real>::type;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
+    const bool even = (nx % 2) == 0;
+    for (int idx = threadIdx.x; idx < rows * 5 * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const int r = l / 5, lr = l - (l / 5) * 5;
+        const long long row = row0 + r;
+        if (row >= nrows) continue;
+        const C zk = R[l * pitch + xo<NX>(k)];
+        const C znk = R[l * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
+        const C s = cadd(zk, cconj(znk));
+        const C d = csub(zk, cconj(znk));
+        const C a = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+        const C b = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+        const Real kx = (even && 2 * k == nx) ? Real(0) : Real(k) * kfx;
+        const long long o = row * g.pxh + k;
+        switch (lr) {
+            case 0: out[0 * g.nc + o] = a; out[1 * g.nc + o] = b; break;
+            case 1: out[2 * g.nc + o] = a; out[5 * g.nc + o] = b; break;
+            case 2: out[3 * g.nc + o] = cadd(a, cmake<C>(kx * b.y, -kx * b.x)); break;
+            case 3: out[4 * g.nc + o] = cmake<C>(kx * a.y, -kx * a.x); out[6 * g.nc + o] = b; break;
+            default: out[7 * g.nc + o] = a; out[8 * g.nc + o] = b; break;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // x pass of the second half's start: n_alpha (mixed from slots A and B) -> real space ->
 // dPhi/dn_alpha -> half spectra.  grid: ceil(ny nz / LR); 5 lines (component pairs) per row.
@@ -1553,7 +1624,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
                                                    typename Cplx<Real>::type* mat_out,
                                                    typename Cplx<Real>::type* __restrict__ phi_out,
                                                    float* __restrict__ red_max, int* __restrict__ status,
-                                                   double* __restrict__ red_phi,
+                                                   double* __restrict__ red_phi, Real kfx,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -1569,7 +1640,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
-    load_pair_rows<Real, NX>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A);
+    load_pair_rows<Real, NX, true>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A, kfx);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
@@ -1581,21 +1652,21 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
 #pragma unroll
         for (int p = 0; p < 5; ++p) {
             const C v = base[p * pitch];
-            n[2 * p] = v.x;
-            n[2 * p + 1] = v.y;
+            n[wd_comp(p, 0)] = v.x;
+            n[wd_comp(p, 1)] = v.y;
         }
         if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
         if (red_phi && row0 + r < nrows) phi_acc += phi_value<Real>(n);
         const bool ok = phi_derivatives<Real>(n);
         if (!ok && row0 + r < nrows) bad = true;
 #pragma unroll
-        for (int p = 0; p < 5; ++p) base[p * pitch] = cmake<C>(n[2 * p], n[2 * p + 1]);
+        for (int p = 0; p < 5; ++p) base[p * pitch] = cmake<C>(n[wd_comp(p, 0)], n[wd_comp(p, 1)]);
     }
     if (bad) atomicOr(status, DEV_N3BOUND);
     __syncthreads();
     C* other = (R == A) ? B : A;
     C* F = any_fft<NX, false, false, 0>(R, other, px, lines, 1, pitch, tw);
-    store_pair_rows<Real, NX>(g, lines, 5, row0, nrows, DFT_NCOMP, F, phi_out);
+    store_phi_spectra<Real, NX>(g, LR, row0, nrows, kfx, F, phi_out);
     const float bm = block_max(mx, scratch_f);
     if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
     if (red_phi) {
@@ -1640,19 +1711,20 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
 
     if (hs) {
-        // Phi_0..Phi_3 transform into accumulators 0..3; -i k_d Phi_V2d adds to accumulator 3,
-        // -i k_d Phi_V1d to accumulator 4.  With a compile-time tile the next component's loads
-        // are in flight during this one's transform.
+        // nine Phi' spectra (DFT_NSPEC order): 0..3 transform into accumulators 0..3, B4 into
+        // accumulator 4; -i k_y / -i k_z of Phi_V1y, Phi_V1z add to accumulator 4 and of Phi_V2y,
+        // Phi_V2z to accumulator 3 (Nyquist components of their axis dropped).  With a
+        // compile-time tile the next component's loads are in flight during this one's transform.
         for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) pool[4][idx] = cmake<C>(Real(0), Real(0));
         constexpr bool kPre = NZ > 0 && TZ > 0;
         constexpr int PER = kPre ? tile_per_thread<TZ, NZ>() : 1;
         C pre[PER];
         if constexpr (kPre) tile_fetch<TZ, NZ>(pre, phi + col0, zstride, nxh - kx0);
-        for (int a = 0; a < 10; ++a) {
+        for (int a = 0; a < DFT_NSPEC; ++a) {
             C* dst = (a < 4) ? pool[a] : pool[5];
             if constexpr (kPre) {
                 tile_put<TZ, NZ>(dst, pre);
-                if (a + 1 < 10) tile_fetch<TZ, NZ>(pre, phi + (long long)(a + 1) * g.nc + col0, zstride, nxh - kx0);
+                if (a + 1 < DFT_NSPEC) tile_fetch<TZ, NZ>(pre, phi + (long long)(a + 1) * g.nc + col0, zstride, nxh - kx0);
             } else {
                 tile_load<TZ, NZ>(dst, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
             }
@@ -1663,19 +1735,16 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
                 continue;
             }
             C* acc = (a < 7) ? pool[4] : pool[3];
-            const int d = (a - 4) % 3;
+            const int d = (a == 4) ? 0 : ((a == 5 || a == 7) ? 1 : 2);
             for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-                const int kzi = idx / T, t = idx - (idx / T) * T;
-                const int kxi = kx0 + t;
+                const int kzi = idx / T;
+                const C u = r[idx];
+                if (d == 0) { acc[idx] = cadd(acc[idx], u); continue; }
                 Real kd;
                 bool nyq;
-                if (d == 0) { kd = kval<Real>(kxi, g.nx, kfx); nyq = (g.nx % 2 == 0) && (2 * kxi == g.nx); }
-                else if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
+                if (d == 1) { kd = kval<Real>(kyi, g.ny, kfy); nyq = (g.ny % 2 == 0) && (2 * kyi == g.ny); }
                 else { kd = kval<Real>(kzi, g.nz, kfz); nyq = (g.nz % 2 == 0) && (2 * kzi == g.nz); }
-                if (!nyq) {
-                    const C u = r[idx];
-                    acc[idx] = cadd(acc[idx], cmake<C>(kd * u.y, -kd * u.x));    // -i k_d u
-                }
+                if (!nyq) acc[idx] = cadd(acc[idx], cmake<C>(kd * u.y, -kd * u.x));    // -i k_d u
             }
             __syncthreads();
         }
@@ -1882,7 +1951,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
                                                    const typename Cplx<Real>::type* __restrict__ spec,
                                                    Real* __restrict__ out, Real* __restrict__ out_last,
                                                    Offsets<Real> off, int cmax,
-                                                   float* __restrict__ red_max,
+                                                   float* __restrict__ red_max, int wd, Real kfx,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -1896,7 +1965,8 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
+    if (wd) load_pair_rows<Real, NX, true>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A, kfx);
+    else load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
@@ -1905,8 +1975,9 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
         const long long row = row0 + r;
         if (row >= nrows) continue;
         for (int c = 0; c < ncomp; ++c) {
-            const C pr = R[(r * lpr + c / 2) * pitch + xo<NX>(x)];
-            const Real v = ((c & 1) ? pr.y : pr.x) + off.v[c];
+            const int l = wd ? wd_line(c) : c / 2, j = wd ? wd_slot(c) : (c & 1);
+            const C pr = R[(r * lpr + l) * pitch + xo<NX>(x)];
+            const Real v = (j ? pr.y : pr.x) + off.v[c];
             if (out_last && c == ncomp - 1) out_last[row * nx + x] = v;
             else if (out) out[(long long)c * g.n + row * nx + x] = v;
             if (c == cmax) mx = fmaxf(mx, float(v));

@@ -48,10 +48,10 @@ cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const Axi
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
                             const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi,
-                            const C* tw) {
+                            Real kfx, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
-                                                                                    red_max, status, red_phi, tw);
+                                                                                    red_max, status, red_phi, kfx, tw);
     return cudaSuccess;
 }
 
@@ -70,11 +70,11 @@ cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const 
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp,
                             const C* spec, Real* out, Real* out_last, const Offsets<Real>& off, int cmax,
-                            float* red_max, const C* tw) {
+                            float* red_max, int wd, Real kfx, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (ncomp + 1) / 2;
     dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
-        g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, tw);
+        g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, wd, kfx, tw);
     return cudaSuccess;
 }
 
@@ -193,7 +193,7 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
                                      (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
             };
             cudaError_t e = encode(&map_in, in, sp.S);
-            if (e == cudaSuccess) e = encode(&map_n, slot_n, DFT_NCOMP);
+            if (e == cudaSuccess) e = encode(&map_n, slot_n, DFT_NSPEC);
             if (e != cudaSuccess) return e;
             const int ntx = (int)ceil_div(g.nxh, TB);
             const int ntiles = ntx * g.ny;
@@ -254,9 +254,9 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
                                      (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
                                      (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
             };
-            cudaError_t e = encode(&map_phi, phi, DFT_NCOMP);
-            if (e == cudaSuccess) e = encode(&map_esA, es_on ? esA : phi, es_on ? ncomp_out : DFT_NCOMP);
-            if (e == cudaSuccess) e = encode(&map_esB, (es_on && esB) ? esB : phi, (es_on && esB) ? ncomp_out : DFT_NCOMP);
+            cudaError_t e = encode(&map_phi, phi, DFT_NSPEC);
+            if (e == cudaSuccess) e = encode(&map_esA, es_on ? esA : phi, es_on ? ncomp_out : DFT_NSPEC);
+            if (e == cudaSuccess) e = encode(&map_esB, (es_on && esB) ? esB : phi, (es_on && esB) ? ncomp_out : DFT_NSPEC);
             if (e != cudaSuccess) return e;
             const int ntx = (int)ceil_div(g.nxh, TB);
             const int ntiles = ntx * g.ny;

@@ -135,7 +135,7 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     const size_t o_twx = o_status + up(1), o_twy = o_twx + up(g.nx), o_twz = o_twy + up(g.ny);
     const size_t o_spec = o_twz + up(g.nz);
     const size_t o_n = o_spec + up(size_t(S) * g.nc);
-    const size_t o_es = o_n + up(size_t(DFT_NCOMP) * g.nc);
+    const size_t o_es = o_n + up(size_t(DFT_NSPEC) * g.nc);
     const size_t need = o_es + up(size_t(S + 1) * g.nc);
     if (need > kNoAllocElems)
         FAIL(DFT_EINVAL, "grid and species need " + std::to_string(need * sizeof(float2)) +
@@ -179,10 +179,10 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     if (e == cudaSuccess)
         e = Passes<float>::zconv_fwd(st, g, az, sp, Tz, kfx, kfy, kfz, 0, base + o_spec, base + o_n, base + o_es,
                                      nullptr, base + o_twz, status);
-    if (e == cudaSuccess) e = Passes<float>::yfft(st, true, g, ay, Ty, DFT_NCOMP, base + o_n, status, base + o_twy);
+    if (e == cudaSuccess) e = Passes<float>::yfft(st, true, g, ay, Ty, DFT_NSPEC, base + o_n, status, base + o_twy);
     if (e == cudaSuccess)
         e = Passes<float>::xinv(st, g, ax, LR, DFT_NCOMP, base + o_n, static_cast<float*>(n_out), nullptr, off, -1,
-                                nullptr, base + o_twx);
+                                nullptr, 1, kfx, base + o_twx);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) FAIL(DFT_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (errbuf && errbuf_len > 0) errbuf[0] = '\0';

@@ -55,12 +55,14 @@ struct LaunchX {
     static cudaError_t xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
     static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw);
+                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, Real kfx,
+                     const C* tw);
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
-                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
+                     Real kfx, const C* tw);
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);
@@ -108,7 +110,8 @@ struct Passes {
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
                           double* red_energy, const C* tw, int* status);
     static cudaError_t xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
-                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, const C* tw);
+                     const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi, Real kfx,
+                     const C* tw);
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
@@ -116,7 +119,8 @@ struct Passes {
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
-                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, const C* tw);
+                     Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
+                     Real kfx, const C* tw);
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);

@@ -224,6 +224,6 @@ def test_profile_counts_launches():
     n, ms, by = plan.profile_read("xphi")
     assert n == 1 and ms > 0
     nc = 16 * 16 * 9
-    assert by == 2 * 10 * nc * 8
+    assert by == 2 * 9 * nc * 8     # nine weighted-density spectra in and out
     n, ms, by = plan.profile_read("yfft")
     assert n == 4
