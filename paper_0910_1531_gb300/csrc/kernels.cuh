@@ -35,11 +35,6 @@ namespace dftk {
 
 constexpr int kThreads = 256;
 
-// Elements per thread whose loads the weighted-density row loader issues together (build flag).
-#ifndef DFT_WD_BATCH
-#define DFT_WD_BATCH 2
-#endif
-
 // Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
 #ifndef DFT_XUPD_KP
 #define DFT_XUPD_KP 1
@@ -1471,10 +1466,9 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
 }
 
 // The ten weighted densities in the x passes: five complex lines of two real rows each,
-// (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z), so that n3 and nV2x = d/dx n3
-// come from one spectrum read by one thread.  wd_comp(l, j): component of slot j of line l;
-// wd_line / wd_slot: the inverse; wd_spec: the kept spectrum (DFT_NSPEC order) behind a slot,
-// wd_dx: the slot is i k_x times that spectrum (nV1x = i k_x m, nV2x = i k_x n3).
+// (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z) (line 2 carries n3 and
+// nV2x = i k_x n3, line 3 nV1x = i k_x m; on the way back, line 2 gives B3 and line 3 B4).
+// wd_comp(l, j): component of slot j of line l; wd_line / wd_slot: the inverse.
 __host__ __device__ constexpr int wd_comp(int l, int j) {
     return l == 0 ? j : (l == 1 ? (j ? 5 : 2) : (l == 2 ? (j ? 7 : 3) : (l == 3 ? (j ? 6 : 4) : 8 + j)));
 }
@@ -1482,27 +1476,20 @@ __host__ __device__ constexpr int wd_line(int c) {
     return c < 2 ? 0 : (c == 2 || c == 5 ? 1 : (c == 3 || c == 7 ? 2 : (c == 4 || c == 6 ? 3 : 4)));
 }
 __host__ __device__ constexpr int wd_slot(int c) { return (c == 1 || c == 5 || c == 7 || c == 6 || c == 9) ? 1 : 0; }
-__host__ __device__ constexpr int wd_spec(int l, int j) {
-    return l == 0 ? j : (l == 1 ? (j ? 5 : 2) : (l == 2 ? 3 : (l == 3 ? (j ? 6 : 4) : 7 + j)));
-}
-__host__ __device__ constexpr bool wd_dx(int l, int j) { return (l == 2 && j == 1) || (l == 3 && j == 0); }
 
 // Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
 // full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
-// wd: the ten rows are the weighted densities built from the nine kept spectra (wd_src), rows
-// 4 and 7 multiplied by i k_x (zero on the Nyquist index); mat_out then receives the nine mixed
-// spectra.  Loads are issued in batches of kBatch elements per thread before any store, so that
-// several are in flight at once.
-template <typename Real, int NX, bool WD = false>
+// Loads are issued in batches of kBatch elements per thread before any store, so that several
+// are in flight at once.
+template <typename Real, int NX>
 __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int lines_per_row, long long row0,
                                                long long nrows, int ncomp,
                                                const typename Cplx<Real>::type* A,
                                                const typename Cplx<Real>::type* Bm, Real wA, Real wB,
                                                typename Cplx<Real>::type* mat_out,
-                                               typename Cplx<Real>::type* dst, Real kfx = Real(0)) {
+                                               typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
-    constexpr bool wd = WD;
-    constexpr int kBatch = WD ? DFT_WD_BATCH : 4;
+    constexpr int kBatch = 4;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
     const int total = lines * nxh;
@@ -1515,12 +1502,11 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
             const int idx = base + j * kThreads;
             const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
             const long long row = row0 + l / lines_per_row;
-            const int lr = l % lines_per_row, ca = 2 * lr, cb = ca + 1;
+            const int ca = 2 * (l % lines_per_row), cb = ca + 1;
             live[j] = idx < total && row < nrows;
             hasb[j] = cb < ncomp;
-            const int sa = wd ? wd_spec(lr, 0) : ca, sb = wd ? wd_spec(lr, 1) : cb;
-            oa[j] = (long long)sa * g.nc + row * g.pxh + k;
-            ob[j] = (long long)sb * g.nc + row * g.pxh + k;
+            oa[j] = (long long)ca * g.nc + row * g.pxh + k;
+            ob[j] = (long long)cb * g.nc + row * g.pxh + k;
             av[j] = bv[j] = aB[j] = bB[j] = cmake<C>(Real(0), Real(0));
             if (live[j]) {
                 av[j] = A[oa[j]];
@@ -1536,23 +1522,67 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
             const int idx = base + j * kThreads;
             if (idx >= total) continue;
             const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
-            const int lr = l % lines_per_row;
             C a = cadd(cscale(av[j], wA), cscale(aB[j], wB));
             C b = cadd(cscale(bv[j], wA), cscale(bB[j], wB));
-            const bool edge = k == 0 || (even && 2 * k == nx);
-            if (edge) { a.y = Real(0); b.y = Real(0); }
+            if (k == 0 || (even && 2 * k == nx)) { a.y = Real(0); b.y = Real(0); }
             if (mat_out && live[j]) {
                 mat_out[oa[j]] = a;
-                if (hasb[j] && !(wd && lr == 2)) mat_out[ob[j]] = b;   // line 2 reads n3 twice
-            }
-            if (wd) {
-                const Real kx = Real(k) * kfx;
-                const C zero = cmake<C>(Real(0), Real(0));
-                if (wd_dx(lr, 0)) a = (even && 2 * k == nx) ? zero : cmake<C>(-kx * a.y, kx * a.x);
-                if (wd_dx(lr, 1)) b = (even && 2 * k == nx) ? zero : cmake<C>(-kx * b.y, kx * b.x);
+                if (hasb[j]) mat_out[ob[j]] = b;
             }
             dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
-            if (!edge) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            if (k != 0 && !(even && 2 * k == nx)) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+        }
+    }
+}
+
+// The ten weighted-density rows of `rows` grid rows as five complex lines each (wd_comp
+// arrangement), built from the nine kept spectra mixed as wA * A + wB * B (B optional), with
+// n_V1x = i k_x m and n_V2x = i k_x n3 (zero on the Nyquist index); mat_out (optional) receives
+// the nine mixed spectra.  One thread handles all lines of one (row, k): the index arithmetic is
+// shared and its eighteen loads are in flight together.
+template <typename Real, int NX>
+__device__ __forceinline__ void load_wd_rows(const GridDesc& g, int rows, long long row0, long long nrows,
+                                             const typename Cplx<Real>::type* A,
+                                             const typename Cplx<Real>::type* Bm, Real wA, Real wB,
+                                             typename Cplx<Real>::type* mat_out, Real kfx,
+                                             typename Cplx<Real>::type* dst) {
+    using C = typename Cplx<Real>::type;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
+    const bool even = (nx % 2) == 0;
+    for (int idx = threadIdx.x; idx < rows * nxh; idx += blockDim.x) {
+        const int r = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const long long row = row0 + r;
+        const bool live = row < nrows;
+        const long long o = row * g.pxh + k;
+        C v[DFT_NSPEC], vb[DFT_NSPEC];
+#pragma unroll
+        for (int c = 0; c < DFT_NSPEC; ++c) {
+            v[c] = vb[c] = cmake<C>(Real(0), Real(0));
+            if (live) {
+                v[c] = A[(long long)c * g.nc + o];
+                if (Bm) vb[c] = Bm[(long long)c * g.nc + o];
+            }
+        }
+        const bool edge = k == 0 || (even && 2 * k == nx);
+        const bool nyq = even && 2 * k == nx;
+        const Real kx = Real(k) * kfx;
+#pragma unroll
+        for (int c = 0; c < DFT_NSPEC; ++c) {
+            v[c] = cadd(cscale(v[c], wA), cscale(vb[c], wB));
+            if (edge) v[c].y = Real(0);
+            if (mat_out && live) mat_out[(long long)c * g.nc + o] = v[c];
+        }
+        const C zero = cmake<C>(Real(0), Real(0));
+        const C dm = nyq ? zero : cmake<C>(-kx * v[4].y, kx * v[4].x);     // i k_x m
+        const C dn3 = nyq ? zero : cmake<C>(-kx * v[3].y, kx * v[3].x);    // i k_x n3
+        // line l holds (a, b) = (wd_comp(l, 0), wd_comp(l, 1))
+        const C la[5] = {v[0], v[2], v[3], dm, v[7]};
+        const C lb[5] = {v[1], v[5], dn3, v[6], v[8]};
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const C a = la[l], b = lb[l];
+            dst[(r * 5 + l) * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (!edge) dst[(r * 5 + l) * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
         }
     }
 }
@@ -1590,26 +1620,31 @@ __device__ __forceinline__ void store_phi_spectra(const GridDesc& g, int rows, l
     using C = typename Cplx<Real>::type;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
-    for (int idx = threadIdx.x; idx < rows * 5 * nxh; idx += blockDim.x) {
-        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
-        const int r = l / 5, lr = l - (l / 5) * 5;
+    for (int idx = threadIdx.x; idx < rows * nxh; idx += blockDim.x) {
+        const int r = idx / nxh, k = idx - (idx / nxh) * nxh;
         const long long row = row0 + r;
         if (row >= nrows) continue;
-        const C zk = R[l * pitch + xo<NX>(k)];
-        const C znk = R[l * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
-        const C s = cadd(zk, cconj(znk));
-        const C d = csub(zk, cconj(znk));
-        const C a = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
-        const C b = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+        C a[5], b[5];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const C zk = R[(r * 5 + l) * pitch + xo<NX>(k)];
+            const C znk = R[(r * 5 + l) * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
+            const C s = cadd(zk, cconj(znk));
+            const C d = csub(zk, cconj(znk));
+            a[l] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
+            b[l] = cmake<C>(Real(0.5) * d.y, Real(-0.5) * d.x);
+        }
         const Real kx = (even && 2 * k == nx) ? Real(0) : Real(k) * kfx;
         const long long o = row * g.pxh + k;
-        switch (lr) {
-            case 0: out[0 * g.nc + o] = a; out[1 * g.nc + o] = b; break;
-            case 1: out[2 * g.nc + o] = a; out[5 * g.nc + o] = b; break;
-            case 2: out[3 * g.nc + o] = cadd(a, cmake<C>(kx * b.y, -kx * b.x)); break;
-            case 3: out[4 * g.nc + o] = cmake<C>(kx * a.y, -kx * a.x); out[6 * g.nc + o] = b; break;
-            default: out[7 * g.nc + o] = a; out[8 * g.nc + o] = b; break;
-        }
+        out[0 * g.nc + o] = a[0];
+        out[1 * g.nc + o] = b[0];
+        out[2 * g.nc + o] = a[1];
+        out[5 * g.nc + o] = b[1];
+        out[3 * g.nc + o] = cadd(a[2], cmake<C>(kx * b[2].y, -kx * b[2].x));   // Phi_3 - i k_x Phi_V2x
+        out[4 * g.nc + o] = cmake<C>(kx * a[3].y, -kx * a[3].x);               // -i k_x Phi_V1x
+        out[6 * g.nc + o] = b[3];
+        out[7 * g.nc + o] = a[4];
+        out[8 * g.nc + o] = b[4];
     }
 }
 
@@ -1640,7 +1675,7 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
-    load_pair_rows<Real, NX, true>(g, lines, 5, row0, nrows, DFT_NCOMP, slotA, slotB, wA, wB, mat_out, A, kfx);
+    load_wd_rows<Real, NX>(g, LR, row0, nrows, slotA, slotB, wA, wB, mat_out, kfx, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
@@ -1649,18 +1684,20 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
         const int r = idx / nx, x = idx - (idx / nx) * nx;
         C* base = R + (r * 5) * pitch + xo<NX>(x);
         Real n[DFT_NCOMP];
-#pragma unroll
-        for (int p = 0; p < 5; ++p) {
-            const C v = base[p * pitch];
-            n[wd_comp(p, 0)] = v.x;
-            n[wd_comp(p, 1)] = v.y;
+        {   // lines (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z): see wd_comp
+            const C v0 = base[0], v1 = base[pitch], v2 = base[2 * pitch], v3 = base[3 * pitch], v4 = base[4 * pitch];
+            n[0] = v0.x; n[1] = v0.y; n[2] = v1.x; n[5] = v1.y; n[3] = v2.x;
+            n[7] = v2.y; n[4] = v3.x; n[6] = v3.y; n[8] = v4.x; n[9] = v4.y;
         }
         if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
         if (red_phi && row0 + r < nrows) phi_acc += phi_value<Real>(n);
         const bool ok = phi_derivatives<Real>(n);
         if (!ok && row0 + r < nrows) bad = true;
-#pragma unroll
-        for (int p = 0; p < 5; ++p) base[p * pitch] = cmake<C>(n[wd_comp(p, 0)], n[wd_comp(p, 1)]);
+        base[0] = cmake<C>(n[0], n[1]);
+        base[pitch] = cmake<C>(n[2], n[5]);
+        base[2 * pitch] = cmake<C>(n[3], n[7]);
+        base[3 * pitch] = cmake<C>(n[4], n[6]);
+        base[4 * pitch] = cmake<C>(n[8], n[9]);
     }
     if (bad) atomicOr(status, DEV_N3BOUND);
     __syncthreads();
@@ -1965,7 +2002,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    if (wd) load_pair_rows<Real, NX, true>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A, kfx);
+    if (wd) load_wd_rows<Real, NX>(g, LR, row0, nrows, spec, nullptr, Real(1), Real(0), nullptr, kfx, A);
     else load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
