@@ -64,6 +64,7 @@ SIGNATURES = {
     "dft_iter_begin": (_I, [_P, _P, _P]),
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_iter_run": (_I, [_P, _P, _P, _I, _D, _PD]),
+    "dft_autotune": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_int)]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_grad": (_I, [_P, _P, _P, _PD, _P, _P, _PD]),
     "dft_batch_create": (_I, [ctypes.POINTER(DftParams), _I, _P, ctypes.POINTER(_P)]),
@@ -222,6 +223,13 @@ class Plan:
                                            self._field(V, self.nspecies, "V"), float(alpha),
                                            ctypes.byref(r) if sync else None, ctypes.byref(a) if sync else None))
         return (r.value, a.value) if sync else None
+
+    def autotune(self, rho, V, reps=5):
+        """Time the x-pass rows per block on these fields; returns {xfwd, xphi, xupdate} choices."""
+        out = (ctypes.c_int * 3)()
+        self._check(self.lib.dft_autotune(self.handle, self._field(rho, self.nspecies, "rho"),
+                                          self._field(V, self.nspecies, "V"), int(reps), out))
+        return {"xfwd": out[0], "xphi": out[1], "xupdate": out[2]}
 
     def iter_run(self, rho, V, iters, alpha=-1.0, sync=True):
         """`iters` iterations of iter_step as CUDA-graph replays; returns r after them (sync)."""

@@ -6,7 +6,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "bulk.h"
@@ -584,6 +588,91 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
 // C ABI
 // ======================================================================================
 namespace {
+// --------------------------------------------------------------------------------------
+// x-pass autotuner: rows per block of the three x passes that stream every iteration
+// (xfwd, xphi, xupdate), timed on the plan's own data and cached per grid, species count
+// and precision for the life of the process.
+// --------------------------------------------------------------------------------------
+struct TuneKey {
+    int nx, ny, nz, S, prec;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nx, ny, nz, S, prec) < std::tie(o.nx, o.ny, o.nz, o.S, o.prec);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 3>> g_tune_cache;
+
+template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, const Real* V, int reps) {
+    using O = Ops<Real>;
+    using P = Passes<Real>;
+    using C = typename Cplx<Real>::type;
+    const SpeciesDesc<Real>& sp = species<Real>(p);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool prof = p->prof;
+    p->prof = false;
+    // realistic spectra in slot A (weighted densities of rho) and T1
+    TRY(reset_status(p));
+    TRY(O::first_half(p, rho, p->slotA, 0));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand[] = {1, 2, 3, 4, 6, 8, 11, 16};
+    // a candidate whose launch is refused (shared memory) is skipped
+    auto time_it = [&](auto&& launch) -> float {
+        cudaGetLastError();
+        launch();   // warm
+        if (cudaGetLastError() != cudaSuccess) return 1e30f;
+        cudaEventRecord(e0, p->stream);
+        for (int r = 0; r < reps; ++r) launch();
+        cudaEventRecord(e1, p->stream);
+        cudaEventSynchronize(e1);
+        if (cudaGetLastError() != cudaSuccess) return 1e30f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const int lpr_upd = (p->S + 1) / 2;
+    int best[3] = {p->LX, p->LRphi, p->LRupd};
+    float best_ms[3] = {1e30f, 1e30f, 1e30f};
+    const C* A = O::slot_n(p->slotA);
+    for (int L : cand) {
+        if (P::smem_x(p->g.nx, L) <= size_t(optin)) {
+            const float ms = time_it([&] {
+                P::xfwd(p->stream, p->g, p->ax, p->S, L, rho, O::T1(p), O::tw(p, 0));
+            });
+            if (ms < best_ms[0]) { best_ms[0] = ms; best[0] = L; }
+        }
+        if (P::smem_x(p->g.nx, 5 * L) <= size_t(optin)) {
+            const float ms = time_it([&] {
+                P::xphi(p->stream, p->g, p->ax, L, p->ctl, A, A, nullptr, O::T1(p), p->red_max, &p->ctl->status,
+                        nullptr, O::kf(p, 0), O::tw(p, 0));
+            });
+            if (ms < best_ms[1]) { best_ms[1] = ms; best[1] = L; }
+        }
+        if (P::smem_x(p->g.nx, lpr_upd * L) <= size_t(optin)) {
+            const float ms = time_it([&] {
+                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, p->red_sum,
+                           &p->ctl->status, O::tw(p, 0));
+            });
+            if (ms < best_ms[2]) { best_ms[2] = ms; best[2] = L; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    p->prof = prof;
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    TRY(reset_status(p));
+    p->LX = best[0];
+    p->LRphi = best[1];
+    p->LRupd = best[2];
+    return DFT_OK;
+}
+}  // namespace
+
+namespace {
 void release_iter_graph(dft_plan* p) {
     if (p->iexec) cudaGraphExecDestroy(p->iexec);
     if (p->igraph) cudaGraphDestroy(p->igraph);
@@ -917,6 +1006,39 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
     if (resid_out) {
         TRY(read_ctl(p));
         *resid_out = p->ctl_host->resid;
+    }
+    return DFT_OK;
+}
+
+dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, int lines_out[3]) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (reps < 1) reps = 5;
+    const TuneKey key{p->g.nx, p->g.ny, p->g.nz, p->S, p->precision};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->LX = it->second[0];
+            p->LRphi = it->second[1];
+            p->LRupd = it->second[2];
+            cached = true;
+        }
+    }
+    if (!cached) {
+        if (is_fp64(p)) TRY(autotune_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), reps));
+        else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd};
+    }
+    // the iteration state and its graph depend on the block counts
+    p->iter_ready = false;
+    release_iter_graph(p);
+    if (lines_out) {
+        lines_out[0] = p->LX;
+        lines_out[1] = p->LRphi;
+        lines_out[2] = p->LRupd;
     }
     return DFT_OK;
 }

@@ -36,17 +36,20 @@ template <typename Real> __host__ __device__ constexpr int dft_tile_z(int n) {
     return (t >> DFT_TILE_ZG_SHIFT) > 0 ? (t >> DFT_TILE_ZG_SHIFT) : 1;
 }
 
-// Persistent TMA second-half z pass: half the grouped width (at least 16 bytes of a row, the
-// TMA minimum) and 256 threads, so that two CTAs share an SM; DFT_ZBWD_THREADS (build flag)
-// overrides the thread count.
+// Persistent TMA z passes: half the grouped width (at least 16 bytes of a row, the TMA
+// minimum); 256 threads (two CTAs per SM) up to length 128, 512 at 256 where the two stages
+// leave room for one CTA per SM; DFT_ZBWD_THREADS (build flag) overrides the thread count.
 template <typename Real> __host__ __device__ constexpr int dft_tile_zb(int n) {
     const int t = dft_tile_z<Real>(n) / 2, tmin = sizeof(Real) == 4 ? 2 : 1;
     return t > tmin ? t : tmin;
 }
-#ifndef DFT_ZBWD_THREADS
-#define DFT_ZBWD_THREADS 256
+template <typename Real> __host__ __device__ constexpr int dft_zbwd_threads(int n) {
+#ifdef DFT_ZBWD_THREADS
+    return DFT_ZBWD_THREADS;
+#else
+    return n >= 256 ? 512 : 256;
 #endif
-template <typename Real> __host__ __device__ constexpr int dft_zbwd_threads(int n) { return DFT_ZBWD_THREADS; }
+}
 
 template <typename Real, int N>
 struct LaunchX {

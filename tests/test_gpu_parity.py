@@ -227,3 +227,26 @@ def test_profile_counts_launches():
     assert by == 2 * 9 * nc * 8     # nine weighted-density spectra in and out
     n, ms, by = plan.profile_read("yfft")
     assert n == 4
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotune_keeps_results(precision):
+    # the x-pass rows per block change only the partition of the rows among blocks: G is
+    # bitwise unchanged, the residual only by the grouping of its partial sums (per-thread
+    # compensated FP32 partials in the FP32 form: a few ulp of FP32)
+    prob, rho, V = make_case((32, 32, 32), 0.1, 3, seed=11)
+    plan = plan_for(prob, precision)
+    rd, Vd = to_dev(rho, plan), to_dev(V, plan)
+    g0, r0 = plan.picard_map(rd, Vd)
+    g0 = g0.clone()
+    lines = plan.autotune(rd, Vd, reps=2)
+    assert set(lines) == {"xfwd", "xphi", "xupdate"}
+    assert all(v in (1, 2, 3, 4, 6, 8, 11, 16) for v in lines.values())
+    g1, r1 = plan.picard_map(rd, Vd)
+    assert torch.equal(g0, g1)
+    assert abs(r1 - r0) <= (1e-6 if precision == "fp32" else 1e-12) * abs(r0)
+    # a second plan of the same shape takes the cached choice
+    plan2 = plan_for(prob, precision)
+    assert plan2.autotune(rd, Vd, reps=2) == lines
+    plan.close()
+    plan2.close()
