@@ -73,7 +73,7 @@ class Problem:
     bulk_molar in mol/L.
     """
 
-    def __init__(self, shape, h, radius, z, bulk_molar, temperature_K=298.15, eps_r=78.5):
+    def __init__(self, shape, h, radius, z, bulk_molar, temperature_K=298.15, eps_r=78.5, n_fixed=None):
         self.shape = tuple(int(s) for s in shape)
         if np.isscalar(h):
             h = (h, h, h)
@@ -86,6 +86,12 @@ class Problem:
         self.bath = make_bath(rho_b, self.radius, self.z, self.lb)
         self.npoints = self.shape[0] * self.shape[1] * self.shape[2]
         self.dv = self.h[0] * self.h[1] * self.h[2]
+        # Fixed-number (canonical) species: n_fixed[i] > 0 particles in the box, not in the bath
+        # (bulk_molar[i] = 0).  rho_ref: the residual weights (bath density, or the species'
+        # mean density N_i / (N h^3) for a fixed-number species).
+        self.n_fixed = np.zeros(self.nspecies) if n_fixed is None else np.asarray(n_fixed, dtype=np.float64)
+        self.canonical = self.n_fixed > 0.0
+        self.rho_ref = np.where(self.canonical, self.n_fixed / (self.npoints * self.dv), self.bath.rho)
         kz, ky, kx = fourier.kgrid(self.shape, self.h)
         self.kvec = (kz, ky, kx)
         self.kmag = np.sqrt(kx * kx + ky * ky + kz * kz)
@@ -185,20 +191,37 @@ def excess_mu(prob, rho):
 
 
 def picard_map(prob, rho, V):
-    """G(rho) of eq. rhoEquation; V is beta mu_ext (S, Nz, Ny, Nx), +inf for hard exclusion."""
+    """G(rho) of eq. rhoEquation; V is beta mu_ext (S, Nz, Ny, Nx), +inf for hard exclusion.
+
+    A fixed-number species i (n_fixed[i] > 0; the paper is silent on it, reading: the
+    canonical form of eq. rhoEquation) has the same Boltzmann factor normalised to its
+    particle number instead of the bath: G_i = N_i e_i / (h^3 sum_x e_i),
+    e_i = exp(-V_i - beta mu_ex_i(x)).
+    """
     mu = excess_mu(prob, rho)
     expo = prob.bath.mu_ex[:, None, None, None] - V - mu
     with np.errstate(over="ignore"):
         g = prob.bath.rho[:, None, None, None] * np.exp(expo)
-    return np.where(np.isinf(V), 0.0, g)
+    g = np.where(np.isinf(V), 0.0, g)
+    for i in np.flatnonzero(prob.canonical):
+        with np.errstate(over="ignore"):
+            e = np.where(np.isinf(V[i]), 0.0, np.exp(-V[i] - mu[i]))
+        g[i] = prob.n_fixed[i] * e / (prob.dv * np.sum(e))
+    return g
 
 
 def _accessible(V):
     return ~np.isinf(V)
 
 
+def _require_grand_canonical(prob):
+    if prob.canonical.any():
+        raise NotImplementedError("the grand potential here is for species in contact with the bath only")
+
+
 def grand_potential(prob, rho, V):
     """Omega / kT of the module docstring; rho must vanish where V = +inf."""
+    _require_grand_canonical(prob)
     acc = _accessible(V)
     rb = prob.bath.rho[:, None, None, None]
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -216,6 +239,7 @@ def grand_potential(prob, rho, V):
 
 def grad_omega_rho(prob, rho, V):
     """dOmega/drho_i(x) / kT on accessible voxels (0 elsewhere)."""
+    _require_grand_canonical(prob)
     acc = _accessible(V)
     rb = prob.bath.rho[:, None, None, None]
     mu = excess_mu(prob, rho)

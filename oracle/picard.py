@@ -11,7 +11,8 @@ Readings (the paper is ambiguous or silent on these):
   rho(alpha) = (1 - alpha) rho^(0) + alpha rho^(1); "mixing 0.1" means alpha = 0.1.
 * Residual norm: r(rho)^2 = (1/(S N)) sum_i sum_x ((rho_i - G_i) / rho_bath_i)^2,
   the squared L2 norm with each species scaled by its bath density (so that a
-  0.001 M species is not invisible next to a 0.1 M one).
+  0.001 M species is not invisible next to a 0.1 M one); a fixed-number species
+  is scaled by its mean density N_i / (N h^3).
 * Samples: r^2 at alpha in {0, alpha_s/2, alpha_s}, alpha_s = min(alpha_max,
   2 alpha_prev) with alpha_prev the previous iteration's alpha (alpha_s =
   alpha_max on the first iteration); the parabola through the three points is
@@ -44,7 +45,7 @@ ALPHA_FLOOR = 1e-3
 
 
 def residual_sq(prob, rho, g):
-    rb = prob.bath.rho[:, None, None, None]
+    rb = prob.rho_ref[:, None, None, None]
     return float(np.sum(((rho - g) / rb) ** 2)) / (prob.nspecies * prob.npoints)
 
 

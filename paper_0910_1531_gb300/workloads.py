@@ -41,6 +41,7 @@ class Workload:
     mixing: float = None         # fixed Picard mixing, or None for line search
     max_it: int = 50
     tol: float = 0.0
+    n_fixed: np.ndarray = None   # particles of fixed-number species (0: species in the bath)
     notes: dict = field(default_factory=dict)
 
     @property
@@ -48,9 +49,16 @@ class Workload:
         return len(self.radius)
 
     def initial_rho_nm3(self, per_nm3_bulk):
-        """Bulk density on accessible voxels, 0 on excluded ones (per_nm3_bulk: (S,) nm^-3)."""
+        """Bulk density on accessible voxels, 0 on excluded ones (per_nm3_bulk: (S,) nm^-3); a
+        fixed-number species starts uniform over its accessible voxels with its particle number."""
         acc = ~np.isinf(self.V)
-        return np.where(acc, np.asarray(per_nm3_bulk)[:, None, None, None], 0.0)
+        rho = np.where(acc, np.asarray(per_nm3_bulk, dtype=np.float64)[:, None, None, None], 0.0)
+        if self.n_fixed is not None:
+            dv = self.h[0] * self.h[1] * self.h[2]
+            for i, n in enumerate(self.n_fixed):
+                if n > 0:
+                    rho[i] = np.where(acc[i], n / (np.count_nonzero(acc[i]) * dv), 0.0)
+        return rho
 
 
 def grid_coordinates(shape, h):
@@ -125,6 +133,39 @@ def obstacles_3species(n=128, h=0.05, n_obstacles=16, r_lo=0.3, r_hi=0.6, seed=1
     return Workload(name=f"3species_16obstacles_{n}^3", shape=shape, h=hh, species=names, radius=radius,
                     z=z, bulk_molar=np.array([0.1, 0.01, 0.12]), V=V, mixing=None, max_it=max_it, tol=tol,
                     notes={"centres": centres, "radii": radii, "seed": seed})
+
+
+def pore_slab_4species(n=256, h=0.05, slab_half=1.0, pore_radius=0.5, pore_half=0.5, o_count=8,
+                       tol=1e-6, max_it=2000):
+    """Na+ 0.1 M, Ca2+ 0.001 M, Cl- 0.102 M and o_count half-charged O confined to a pore.
+
+    A hard slab |z - z0| < slab_half (nm) across the box, pierced along z by a cylindrical hole
+    of radius pore_radius about the box axis (x0, y0) = (L/2, L/2), z0 = L/2.  A bath species i
+    is excluded where |z - z0| < slab_half + R_i and r_perp > pore_radius - R_i (r_perp: the
+    minimum-image distance from the axis).  The O particles (fixed number, not in the bath) are
+    confined to r_perp <= pore_radius - R_O and |z - z0| <= pore_half - R_O, the central
+    2 pore_half of the hole.
+    """
+    names, radius, z = _species([NA, CA, CL, O_HALF])
+    shape = (n, n, n)
+    hh = (h, h, h)
+    L = n * h
+    zc, yc, xc = grid_coordinates(shape, hh)
+    dx = _min_image(xc - L / 2.0, L)
+    dy = _min_image(yc - L / 2.0, L)
+    dz = _min_image(zc - L / 2.0, L)
+    r_perp = np.sqrt(dx * dx + dy * dy)
+    V = np.zeros((4,) + shape, dtype=np.float64)
+    for i in range(3):
+        excl = (np.abs(dz) < slab_half + radius[i]) & (r_perp > pore_radius - radius[i])
+        V[i][np.broadcast_to(excl, shape)] = np.inf
+    Ro = radius[3]
+    allowed = (r_perp <= pore_radius - Ro) & (np.abs(dz) <= pore_half - Ro)
+    V[3][~np.broadcast_to(allowed, shape)] = np.inf
+    return Workload(name=f"pore_slab_4species_{n}^3", shape=shape, h=hh, species=names, radius=radius, z=z,
+                    bulk_molar=np.array([0.1, 0.001, 0.102, 0.0]), V=V, mixing=None, max_it=max_it, tol=tol,
+                    n_fixed=np.array([0.0, 0.0, 0.0, float(o_count)]),
+                    notes={"slab_half_nm": slab_half, "pore_radius_nm": pore_radius, "pore_half_nm": pore_half})
 
 
 def gaussian_random_field(shape, h, corr_len, std, seed):

@@ -81,3 +81,48 @@ def test_line_search_converges_to_fixed_point():
     # and the gradient of Omega vanishes there
     grad = F.grad_omega_rho(prob, rho, w.V)
     assert np.max(np.abs(grad)) < 1e-8 * prob.dv
+
+
+# ---- fixed-number (canonical) species: G_i = N_i e_i / (h^3 sum e_i) ----
+
+def _pore(n=16, h=0.2):
+    w = workloads.pore_slab_4species(n=n, h=h, o_count=8)
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar, n_fixed=w.n_fixed)
+    return w, prob
+
+
+def test_canonical_species_holds_its_particle_number():
+    w, prob = _pore()
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    assert np.sum(rho[3]) * prob.dv == pytest.approx(8.0, rel=1e-14)
+    g = F.picard_map(prob, rho, w.V)
+    assert np.sum(g[3]) * prob.dv == pytest.approx(8.0, rel=1e-13)
+    assert np.all(g[3][np.isinf(w.V[3])] == 0.0)
+    # bath species are untouched by the fixed-number form
+    gc = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    assert np.array_equal(g[:3], F.picard_map(gc, rho, w.V)[:3])
+
+
+def test_canonical_equals_grand_canonical_at_the_same_number():
+    # a species kept in the bath but marked fixed-number with N = h^3 sum of its grand-canonical
+    # G has, by the normalisation alone, exactly the grand-canonical G
+    w = workloads.centred_sphere(n=12, h=0.1, molar=0.3, sphere_radius=0.3)
+    gc = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    rho = workloads.random_density(w.shape, 2, gc.bath.rho, 0.3, seed=5)
+    rho = np.where(np.isinf(w.V), 0.0, rho)
+    g_gc = F.picard_map(gc, rho, w.V)
+    n1 = np.sum(g_gc[1]) * gc.dv
+    can = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar, n_fixed=[0.0, n1])
+    g_can = F.picard_map(can, rho, w.V)
+    assert np.array_equal(g_can[0], g_gc[0])
+    assert np.max(np.abs(g_can[1] - g_gc[1])) <= 1e-13 * np.max(g_gc[1])
+
+
+def test_canonical_iteration_conserves_number_and_converges():
+    w, prob = _pore()
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    rho, it, r = picard.solve(prob, rho, w.V, tol=1e-6, max_it=60)
+    assert np.sum(rho[3]) * prob.dv == pytest.approx(8.0, rel=1e-12)
+    assert r < 1e-6
+    # the weight of the residual is the species' mean density
+    assert prob.rho_ref[3] == pytest.approx(8.0 / (prob.npoints * prob.dv))
