@@ -63,6 +63,13 @@ typedef struct {
     double temperature_K;           /* T > 0 */
     double eps_r;                   /* relative permittivity > 0 */
     int precision;                  /* DFT_FP32_STAB or DFT_FP64 */
+    /* [nspecies] or NULL: n_fixed[i] > 0 makes species i a fixed-number (canonical)
+     * species of n_fixed[i] particles in the box (normally with bulk_molar[i] = 0, i.e.
+     * absent from the bath): G_i = n_fixed[i] e_i / (h^3 sum_x e_i), e_i its Boltzmann
+     * factor exp(-V_i - beta mu_ex_i(x)) (the paper has no such species; canonical reading
+     * of eq. rhoEquation); its residual weight is its mean density n_fixed[i] / (N h^3).
+     * dft_grad rejects plans with such species (DFT_EINVAL). */
+    const double* n_fixed;
 } dft_params;
 
 /*

@@ -40,7 +40,8 @@ class DftParams(ctypes.Structure):
                 ("valence", ctypes.POINTER(ctypes.c_double)),
                 ("bulk_molar", ctypes.POINTER(ctypes.c_double)),
                 ("temperature_K", ctypes.c_double), ("eps_r", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int),
+                ("n_fixed", ctypes.POINTER(ctypes.c_double))]
 
 
 _P = ctypes.c_void_p
@@ -108,7 +109,7 @@ class Plan:
     """One state point: grid, species and bath; owns the library plan and its scratch."""
 
     def __init__(self, shape, h, radius, valence, bulk_molar, temperature_K=298.15, eps_r=78.5,
-                 precision="fp32", stream=None, device=None):
+                 precision="fp32", stream=None, device=None, n_fixed=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -124,10 +125,13 @@ class Plan:
         self._arrays = [np.ascontiguousarray(radius, dtype=np.float64),
                         np.ascontiguousarray(valence, dtype=np.float64),
                         np.ascontiguousarray(bulk_molar, dtype=np.float64)]
+        if n_fixed is not None:
+            self._arrays.append(np.ascontiguousarray(n_fixed, dtype=np.float64))
         pd = lambda a: a.ctypes.data_as(_PD)
         prm = DftParams(nx, ny, nz, self.h[0], self.h[1], self.h[2], self.nspecies,
                         pd(self._arrays[0]), pd(self._arrays[1]), pd(self._arrays[2]),
-                        float(temperature_K), float(eps_r), self.precision)
+                        float(temperature_K), float(eps_r), self.precision,
+                        pd(self._arrays[3]) if n_fixed is not None else None)
         with torch.cuda.device(self.device):
             if stream is None:
                 stream = torch.cuda.current_stream(self.device)
@@ -308,10 +312,13 @@ class Batch:
             h = st["h"]
             h = (h, h, h) if np.isscalar(h) else h
             arrs = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("radius", "valence", "bulk_molar")]
+            if st.get("n_fixed") is not None:
+                arrs.append(np.ascontiguousarray(st["n_fixed"], dtype=np.float64))
             self._keep.append(arrs)
             pd = lambda a: a.ctypes.data_as(_PD)
             prms[i] = DftParams(nx, ny, nz, h[0], h[1], h[2], len(arrs[0]), pd(arrs[0]), pd(arrs[1]), pd(arrs[2]),
-                                float(st.get("temperature_K", 298.15)), float(st.get("eps_r", 78.5)), self.precision)
+                                float(st.get("temperature_K", 298.15)), float(st.get("eps_r", 78.5)), self.precision,
+                                pd(arrs[3]) if len(arrs) > 3 else None)
             self.states.append((int(nz), int(ny), int(nx), len(arrs[0])))
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s

@@ -39,6 +39,9 @@ struct dft_plan {
     int S = 0;
     int precision = DFT_FP32_STAB;
     std::vector<double> R, z, molar;
+    std::vector<double> n_fixed;    // particles of fixed-number species (0: bath species)
+    int ncanon = 0;
+    double* red_canon = nullptr;    // [blocks][DFT_MAXS] normalisation partial sums
     double T = 0, eps_r = 0;
     BathState bath;
     GridDesc g{};
@@ -145,6 +148,13 @@ template <typename Real> void fill_species(dft_plan* p) {
         sp.mu_hs_b[i] = Real(b.mu_hs[i]);
         sp.mu_ex_b[i] = Real(b.mu_hs[i] + b.mu_es[i]);
         sp.n_rho_b[i] = Real(double(p->g.n) * b.rho[i]);
+        if (p->n_fixed[i] > 0.0) {
+            const double dv = p->g.hx * p->g.hy * p->g.hz;
+            sp.canon[i] = 1;
+            sp.nfix_dv[i] = p->n_fixed[i] / dv;
+            sp.inv_rho_b[i] = Real(double(p->g.n) * dv / p->n_fixed[i]);   // 1 / mean density
+            sp.ncanon += 1;
+        }
     }
     for (int i = 0; i < p->S; ++i)
         for (int j = 0; j < p->S; ++j) {
@@ -296,6 +306,14 @@ template <typename Real> struct Ops {
                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
                                        p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
+        if (p->ncanon > 0) {
+            // fixed-number species: the sum of their Boltzmann factors first (its reciprocal
+            // scales G in the update pass)
+            LAUNCH(p, K_XUPD, p->ncanon * (CB(p) + RB(p)),
+                   P::xcanon(p->stream, p->g, p->ax, sp, p->LRupd, T1(p), V, p->red_canon, tw(p, 0)));
+            LAUNCH(p, K_FIN, p->blocks_x(p->LRupd) * DFT_MAXS * 8.0,
+                   P::canon_scale(p->stream, p->ctl, sp, p->red_canon, (int)p->blocks_x(p->LRupd)));
+        }
         LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0))),
                P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
                                      g_out, p->red_sum, &p->ctl->status, tw(p, 0)));
@@ -719,6 +737,16 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->R.assign(prm->radius_nm, prm->radius_nm + S);
     p->z.assign(prm->valence, prm->valence + S);
     p->molar.assign(prm->bulk_molar, prm->bulk_molar + S);
+    p->n_fixed.assign(S, 0.0);
+    if (prm->n_fixed)
+        for (int i = 0; i < S; ++i) {
+            if (!(prm->n_fixed[i] >= 0.0)) {
+                delete p;
+                return fail(nullptr, DFT_EINVAL, "n_fixed must be >= 0");
+            }
+            p->n_fixed[i] = prm->n_fixed[i];
+            if (p->n_fixed[i] > 0.0) p->ncanon += 1;
+        }
     p->T = prm->temperature_K;
     p->eps_r = prm->eps_r;
     std::string err;
@@ -793,6 +821,12 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         }
     }
     cudaMemset(p->ctl, 0, sizeof(Ctl));
+    if (p->ncanon > 0 &&
+        cudaMalloc(&p->red_canon, (size_t(g.ny) * g.nz + 1) * DFT_MAXS * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        dft_plan_destroy(p);
+        return fail(nullptr, DFT_ENOMEM, "cudaMalloc failed: normalisation sums");
+    }
     // On a cubic box |k| = kf sqrt(mx^2 + my^2 + mz^2) takes one value per integer m2, so the
     // compile-time z passes read the FMT weights and bulk-fluid kernels from per-m2 tables
     // instead of evaluating them at every point.
@@ -855,6 +889,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->red_max);
     cudaFree(p->grad_red);
     cudaFree(p->ktab);
+    cudaFree(p->red_canon);
     release_iter_graph(p);
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->ctl);
@@ -1094,6 +1129,7 @@ dft_status dft_grad(dft_plan* p, const void* rho, const void* V, double* omega_o
                     void* dOmega_dV, double* dOmega_dbulk) {
     TRY(check_plan(p));
     if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (p->ncanon > 0) return fail(p, DFT_EINVAL, "dft_grad: the plan has fixed-number species");
     p->iter_ready = false;
     if (is_fp64(p))
         return grad_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), omega_out,

@@ -79,6 +79,11 @@ struct SpeciesDesc {
     const Real* tab_k;                  // [m2][S (S + 1) / 2]: DC_ij_hat at j (j + 1) / 2 + i, i <= j
     const Real* tab_dk;                 // [m2][S (S + 1) / 2]: d DC_ij_hat / d Gamma, same order
     int tab_m2max;
+    // fixed-number species (canonical form of eq. rhoEquation): canon[i] != 0, target sum of G_i
+    // over the grid N_i / h^3; ncanon of them
+    int canon[DFT_MAXS];
+    double nfix_dv[DFT_MAXS];
+    int ncanon;
 };
 
 // Index of the pair (i, j), i <= j, in a table record (independent of S).
@@ -105,6 +110,8 @@ struct Ctl {
     double sample_alpha[2];
     int status;             // dft_status bits raised on the device (see DEV_* below)
     int iter;
+    // fixed-number species: G_i = canon_scale[i] exp(-V_i + c_i), canon_scale = N_i / (h^3 sum e)
+    double canon_scale[DFT_MAXS];
 };
 
 enum {

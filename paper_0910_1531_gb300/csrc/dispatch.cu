@@ -45,6 +45,19 @@ cudaError_t Passes<Real>::init_attributes() {
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::xcanon(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                                 int LR, const C* cspec, const Real* V, double* red, const C* tw) {
+    DFT_SWITCH_X(g.nx, xcanon(st, g, px, sp, LR, cspec, V, red, tw))
+}
+
+template <typename Real>
+cudaError_t Passes<Real>::canon_scale(cudaStream_t st, Ctl* ctl, const SpeciesDesc<Real>& sp, const double* red,
+                                      int nblocks) {
+    dftk::k_canon_scale<Real><<<1, dftk::kThreads, 0, st>>>(ctl, sp, red, nblocks);
+    return cudaSuccess;
+}
+
+template <typename Real>
 cudaError_t Passes<Real>::build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf) {
     const int n = sp.tab_m2max + 1;
     dftk::k_ktab<Real><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(sp, kf, sp.tab_m2max, const_cast<Real*>(sp.tab_w),

@@ -1829,6 +1829,105 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
 }
 
 // ------------------------------------------------------------------------------------
+// Normalisation of fixed-number species: per block, sum over accessible points of
+// e_i = exp(-V_i + c_i) for the species with canon[i] (c_i from the half spectra cspec),
+// red[block * DFT_MAXS + i].  Only the complex lines holding such species are transformed.
+// grid: ceil(ny nz / LR); nl lines per row (line l = species pair (2 line_of[l], +1)).
+// ------------------------------------------------------------------------------------
+template <typename Real, int NX>
+__global__ void __launch_bounds__(kThreads) k_xcanon(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR, int nl,
+                                                     int line0, int line1, int line2,
+                                                     const typename Cplx<Real>::type* __restrict__ cspec,
+                                                     const Real* __restrict__ V, double* __restrict__ red,
+                                                     const typename Cplx<Real>::type* __restrict__ twx) {
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double scratch_d[32];
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1, S = sp.S;
+    const bool even = (nx % 2) == 0;
+    const int lines = nl * LR;
+    C* tw = align_ptr<C>(smem_raw);
+    C* A = tw + nx;
+    C* B = A + lines * pitch;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
+    const long long nrows = (long long)g.ny * g.nz;
+    const long long row0 = (long long)blockIdx.x * LR;
+    const int line_of[3] = {line0, line1, line2};
+    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const int r = l / nl, j = l - (l / nl) * nl;
+        const long long row = row0 + r;
+        const int ca = 2 * line_of[j], cb = ca + 1;
+        C a = cmake<C>(Real(0), Real(0)), b = a;
+        if (row < nrows) {
+            a = cspec[(long long)ca * g.nc + row * g.pxh + k];
+            if (cb < S) b = cspec[(long long)cb * g.nc + row * g.pxh + k];
+        }
+        const bool edge = k == 0 || (even && 2 * k == nx);
+        if (edge) { a.y = Real(0); b.y = Real(0); }
+        A[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+        if (!edge) A[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+    }
+    __syncthreads();
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
+    Real acc[DFT_MAXS], comp[DFT_MAXS];
+#pragma unroll
+    for (int s = 0; s < DFT_MAXS; ++s) acc[s] = comp[s] = Real(0);
+    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        const long long row = row0 + r;
+        if (row >= nrows) continue;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= nl) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int s = 2 * line_of[j] + h;
+                if (s >= S || !sp.canon[s]) continue;
+                const C pr = R[(r * nl + j) * pitch + xo<NX>(x)];
+                const Real c = h ? pr.y : pr.x;
+                const Real v = V[(long long)s * g.n + row * nx + x];
+                const Real e = (isinf(v) && v > Real(0)) ? Real(0) : exp(-v + c);
+#pragma unroll
+                for (int q = 0; q < DFT_MAXS; ++q) {
+                    if (q != s) continue;
+                    const Real y = e - comp[q];
+                    const Real t = acc[q] + y;
+                    comp[q] = (t - acc[q]) - y;
+                    acc[q] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < DFT_MAXS; ++s) {
+        if (s >= S || !sp.canon[s]) continue;      // uniform across the block
+        double bs;
+        if constexpr (sizeof(Real) == 4) bs = block_sum_ds(acc[s], -comp[s], scratch_d);
+        else bs = block_sum(double(acc[s]) - double(comp[s]), scratch_d);
+        if (threadIdx.x == 0) red[(long long)blockIdx.x * DFT_MAXS + s] = bs;
+    }
+}
+
+// canon_scale_i = (N_i / h^3) / sum over blocks of the k_xcanon partial sums (one block).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) k_canon_scale(Ctl* ctl, SpeciesDesc<Real> sp, const double* __restrict__ red,
+                                                          int nblocks) {
+    __shared__ double scratch_d[32];
+    for (int s = 0; s < sp.S; ++s) {
+        if (!sp.canon[s]) continue;
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += red[(long long)b * DFT_MAXS + s];
+        const double tot = block_sum(t, scratch_d);
+        if (threadIdx.x == 0) {
+            ctl->canon_scale[s] = sp.nfix_dv[s] / tot;
+            if (!(tot > 0.0) || !isfinite(tot)) ctl->status |= DEV_NONFINITE;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Final x pass: one-body correlations c_i (half spectra) -> real space -> Picard map
 //   G_i = rho_bath_i exp(beta mu_HS_bath_i - V_i + c_i)   (0 where V_i = +inf)
 // at rho = w0 rho0 + w1 rho1, with the residual sum_i sum_x ((rho_i - G_i)/rho_bath_i)^2
@@ -1859,6 +1958,15 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
+    // G_i = pref_i exp(mu0_i - V_i + c_i): the bath (rho_b, beta mu_HS,b), or for a
+    // fixed-number species the normalisation of this evaluation and no bath constant
+    Real pref[DFT_MAXS], mu0[DFT_MAXS];
+#pragma unroll
+    for (int s = 0; s < DFT_MAXS; ++s) {
+        const bool cn = s < S && sp.canon[s];
+        pref[s] = cn ? Real(ctl->canon_scale[s]) : sp.rho_b[s];
+        mu0[s] = cn ? Real(0) : sp.mu_hs_b[s];
+    }
     // per-thread partial sum in the working precision with Kahan compensation, then
     // double-single (FP32) or FP64 across threads, FP64 across blocks
     Real acc = Real(0), comp = Real(0);
@@ -1901,7 +2009,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
                 const Real v = vv[q][s];
                 Real gval;
                 if (isinf(v) && v > Real(0)) gval = Real(0);
-                else gval = sp.rho_b[s] * exp(sp.mu_hs_b[s] - v + c);
+                else gval = pref[s] * exp(mu0[s] - v + c);
                 if (!isfinite(gval) || !isfinite(rho)) bad = true;
                 const Real e = (rho - gval) * sp.inv_rho_b[s];
                 const Real y = e * e - comp;

@@ -31,6 +31,7 @@ cudaError_t LaunchX<Real, N>::init() {
     if ((r = set_max_smem(dftk::k_xfwd<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xphi<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xupdate<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xcanon<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xinv<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xgrad<Real, N>)) != cudaSuccess) e = r;
     return e;
@@ -86,6 +87,27 @@ cudaError_t LaunchX<Real, N>::xgrad(cudaStream_t st, const GridDesc& g, const Ax
     const int lpr = (sp.S + 1) / 2;
     dftk::k_xgrad<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
         g, px, sp, LR, dv, cspec, rho, V, grad_rho, grad_V, red, tw);
+    return cudaSuccess;
+}
+
+// Lines (species pairs) of the x transform that hold a fixed-number species.
+template <typename Real> inline int canon_lines(const SpeciesDesc<Real>& sp, int* lines) {
+    int nl = 0;
+    for (int l = 0; 2 * l < sp.S; ++l)
+        if (sp.canon[2 * l] || (2 * l + 1 < sp.S && sp.canon[2 * l + 1])) lines[nl++] = l;
+    return nl;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchX<Real, N>::xcanon(cudaStream_t st, const GridDesc& g, const AxisPlan& px,
+                                     const SpeciesDesc<Real>& sp, int LR, const C* cspec, const Real* V,
+                                     double* red, const C* tw) {
+    int lines[3] = {0, 0, 0};
+    const int nl = canon_lines(sp, lines);
+    if (nl == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    dftk::k_xcanon<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, nl * LR), st>>>(
+        g, px, sp, LR, nl, lines[0], lines[1], lines[2], cspec, V, red, tw);
     return cudaSuccess;
 }
 

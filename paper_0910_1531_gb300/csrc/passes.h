@@ -69,9 +69,8 @@ struct LaunchX {
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);
-    // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
-    // number kf of a cubic box
-    static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
+    static cudaError_t xcanon(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                              int LR, const C* cspec, const Real* V, double* red, const C* tw);
 };
 
 template <typename Real, int N>
@@ -127,6 +126,12 @@ struct Passes {
     static cudaError_t xgrad(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                              int LR, Real dv, const C* cspec, const Real* rho, const Real* V, Real* grad_rho,
                              Real* grad_V, double* red, const C* tw);
+    // sums for the normalisation of fixed-number species (red: [blocks][DFT_MAXS]) and the
+    // scale factors they give (into ctl->canon_scale)
+    static cudaError_t xcanon(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                              int LR, const C* cspec, const Real* V, double* red, const C* tw);
+    static cudaError_t canon_scale(cudaStream_t st, Ctl* ctl, const SpeciesDesc<Real>& sp, const double* red,
+                                   int nblocks);
     // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
     // number kf of a cubic box
     static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
