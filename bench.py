@@ -36,9 +36,22 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 NCU_TRAFFIC = None
 
 
-def workload(n=128):
+def workload(args):
+    """The bench workload: 3-species obstacles (128^3 by default), or the pore/slab geometry
+    with eight confined half-charged O (fixed number; 256^3, h = 0.05 nm by default)."""
     from paper_0910_1531_gb300 import workloads
+    if args.workload == "pore256":
+        return workloads.pore_slab_4species(n=args.n or 256, h=0.05)
+    n = args.n or 128
     return workloads.obstacles_3species(n=n, h=0.05 * 128 / n, seed=1)
+
+
+def workload_config(w):
+    if w.n_fixed is not None:
+        return {"geometry": "hard slab |z - L/2| < 1 nm with a 0.5 nm-radius pore along z",
+                "n_fixed": list(map(float, w.n_fixed)),
+                "fixed_number_species": "O (R 0.14 nm, z -0.5) confined to the central 1 nm of the pore"}
+    return {"obstacles": 16, "seed": 1}
 
 
 def csrc_digest():
@@ -159,7 +172,7 @@ def oracle_sample(w, prob=None):
     import numpy as np
     from oracle import functional as F
     if prob is None:
-        prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+        prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar, n_fixed=w.n_fixed)
     rho = w.initial_rho_nm3(prob.bath.rho)
     t0 = time.perf_counter()
     F.picard_map(prob, rho, w.V)
@@ -174,7 +187,7 @@ def run_reference(args):
     world, rank, _ = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
     if rank != 0:
         return 0
-    w = workload(args.n)
+    w = workload(args)
     prob = None
     for _ in range(args.warmup):
         prob, *_ = oracle_sample(w, prob)
@@ -285,8 +298,8 @@ def run_ours(args):
     world, rank, local = dist_setup()
     build.build()
     torch.cuda.set_device(local)
-    w = workload(args.n)
-    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=args.precision)
+    w = workload(args)
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=args.precision, n_fixed=w.n_fixed)
     dt = plan.dtype
     rho_b = plan.bulk()["rho"]
     rho0 = w.initial_rho_nm3(rho_b)
@@ -297,11 +310,15 @@ def run_ours(args):
     nc = w.shape[0] * w.shape[1] * (w.shape[2] // 2 + 1)
     working_set = (2 * (10 + S + 1) + 10) * nc * 2 * elem + 3 * S * N * elem
 
+    # line search (alpha < 0) unless a fixed mixing is asked for or the workload needs one
+    alpha = args.alpha if args.alpha is not None else (0.05 if args.workload == "pore256" else -1.0)
+    if args.converge_tol is None:
+        args.converge_tol = 1e-6 if args.workload == "pore256" else 0.0
     # x-pass rows per block timed on this workload (cached per shape inside the library)
     x_lines = plan.autotune(rho, V)
     plan.iter_begin(rho, V)
     # warm-up through the same call as the timed region (captures the one-iteration graph)
-    plan.iter_run(rho, V, args.warmup, -1.0, sync=False)
+    plan.iter_run(rho, V, args.warmup, alpha, sync=False)
     torch.cuda.synchronize()
 
     uuid = None
@@ -311,14 +328,14 @@ def run_ours(args):
         pass
     sampler = ClockSampler(uuid)
     # warm the sampler window with a few untimed iterations
-    plan.iter_run(rho, V, max(1, args.warmup), -1.0, sync=False)
+    plan.iter_run(rho, V, max(1, args.warmup), alpha, sync=False)
     stream = torch.cuda.current_stream()
     barrier(world)
     torch.cuda.synchronize()
     # timed region: K iterations as replays of the plan's one-iteration CUDA graph
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    plan.iter_run(rho, V, args.steps, -1.0, sync=False)
+    plan.iter_run(rho, V, args.steps, alpha, sync=False)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -333,14 +350,33 @@ def run_ours(args):
     ep0.record(stream)
     torch.cuda.nvtx.range_push("profiled_steps")     # ncu --nvtx-include "profiled_steps/"
     for _ in range(args.steps):
-        plan.iter_step(rho, V, -1.0, sync=False)
+        plan.iter_step(rho, V, alpha, sync=False)
     torch.cuda.nvtx.range_pop()
     ep1.record(stream)
     torch.cuda.synchronize()
     ms_prof = ep0.elapsed_time(ep1)
     prof = {k: plan.profile_read(k) for k in KERNELS}
     plan.profile_enable(False)
-    resid_after, alpha_after = plan.iter_step(rho, V, -1.0, sync=True)
+    resid_after, alpha_after = plan.iter_step(rho, V, alpha, sync=True)
+
+    # time to tolerance from the initial density (chunks of graph replays, residual read
+    # between chunks)
+    convergence = None
+    if args.converge_tol > 0:
+        rho_c = torch.tensor(rho0, dtype=dt, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.iter_begin(rho_c, V)
+        it_c, r_c = 0, float("inf")
+        while it_c < args.converge_max:
+            r_c = plan.iter_run(rho_c, V, 50, alpha)
+            it_c += 50
+            if r_c < args.converge_tol:
+                break
+        t_c = time.perf_counter() - t0
+        convergence = {"tol": args.converge_tol, "iterations": it_c, "resid": r_c, "seconds": t_c,
+                       "converged": bool(r_c < args.converge_tol), "checked_every": 50}
+        del rho_c
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     peak, peak_kind = measured_peaks()
@@ -363,11 +399,11 @@ def run_ours(args):
     # end to end: public host-buffer entry point, pinned buffers, copies inside the timed region
     rho_h = torch.tensor(rho0, dtype=dt).pin_memory()
     V_h = torch.tensor(w.V, dtype=dt).pin_memory()
-    plan.picard_step_host(rho_h, V_h, -1.0)
+    plan.picard_step_host(rho_h, V_h, alpha)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        plan.picard_step_host(rho_h, V_h, -1.0)
+        plan.picard_step_host(rho_h, V_h, alpha)
     t_e2e = time.perf_counter() - t0
     t_e2e = max_over_ranks(t_e2e, world)
     e2e = {"value": args.e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * S * N * elem,
@@ -388,11 +424,13 @@ def run_ours(args):
                 "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
                 "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
-                           "bulk_molar": list(map(float, w.bulk_molar)), "obstacles": 16, "seed": 1,
+                           "bulk_molar": list(map(float, w.bulk_molar)), **workload_config(w),
                            "precision": "FP32 fields, FP64 log(1-n3)/(1-n3)^-m, residual and line-search sums"
                            if args.precision == "fp32" else "all FP64",
-                           "step": "one Picard iteration with quadratic line search (dft_iter_run: "
-                                   "CUDA-graph replay of the dft_iter_step kernels)",
+                           "step": ("one Picard iteration with quadratic line search" if alpha < 0 else
+                                    f"one Picard iteration with fixed mixing {alpha}")
+                                   + " (dft_iter_run: CUDA-graph replay of the dft_iter_step kernels)",
+                           "convergence": convergence,
                            "ms_per_step_launched": ms_prof / args.steps,
                            "x_rows_per_block": x_lines,
                            "parallelism": f"replicas x{world}",
@@ -415,11 +453,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "batch64"])
+    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64"])
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--alpha", type=float, default=None,
+                    help="fixed Picard mixing (default: line search; 0.05 for pore256, where the line search stalls)")
+    ap.add_argument("--converge-tol", type=float, default=None,
+                    help="also time iterations to this residual from the initial density (default 1e-6 for pore256)")
+    ap.add_argument("--converge-max", type=int, default=5000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
