@@ -835,7 +835,10 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
                                 (long long)(g.nz / 2) * (g.nz / 2);
         const long long P = (long long)S * (S + 1) / 2;
         const long long rows = m2max + 1;
-        if (cudaMalloc(&p->ktab, size_t(rows * (2 * S + 2 * P)) * p->rsize) != cudaSuccess) {
+        // records padded to 16 bytes (read with 16-byte loads)
+        const long long V = 16 / (long long)p->rsize;
+        const long long ws = (2 * S + V - 1) / V * V, ks = (P + V - 1) / V * V;
+        if (cudaMalloc(&p->ktab, size_t(rows * (ws + 2 * ks)) * p->rsize) != cudaSuccess) {
             cudaGetLastError();
             dft_plan_destroy(p);
             return fail(nullptr, DFT_ENOMEM, "cudaMalloc failed: |k| tables");
@@ -844,14 +847,16 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         if (f64) {
             SpeciesDesc<double>& sp = p->spd;
             double* base = static_cast<double*>(p->ktab);
-            sp.tab_w = base; sp.tab_k = base + rows * 2 * S; sp.tab_dk = base + rows * (2 * S + P);
+            sp.tab_w = base; sp.tab_k = base + rows * ws; sp.tab_dk = base + rows * (ws + ks);
             sp.tab_m2max = (int)m2max;
+            sp.tab_ws = (int)ws; sp.tab_ks = (int)ks;
             te = Passes<double>::build_ktab(nullptr, sp, p->kf[0]);
         } else {
             SpeciesDesc<float>& sp = p->spf;
             float* base = static_cast<float*>(p->ktab);
-            sp.tab_w = base; sp.tab_k = base + rows * 2 * S; sp.tab_dk = base + rows * (2 * S + P);
+            sp.tab_w = base; sp.tab_k = base + rows * ws; sp.tab_dk = base + rows * (ws + ks);
             sp.tab_m2max = (int)m2max;
+            sp.tab_ws = (int)ws; sp.tab_ks = (int)ks;
             te = Passes<float>::build_ktab(nullptr, sp, p->kf[0]);
         }
         if (te != cudaSuccess) {

@@ -75,10 +75,11 @@ struct SpeciesDesc {
     int coulomb_limit;                  // Gamma == 0: kernel is lambda_B z_i z_j / r inside R_ij
     // Optional tables of the |k|-only factors on a cubic box, indexed by the integer
     // m2 = mx^2 + my^2 + mz^2 (|k| = kf sqrt(m2)); null: the kernels evaluate them per point.
-    const Real* tab_w;                  // [m2][2 S]: w0_s at 2 s, j3_s at 2 s + 1
-    const Real* tab_k;                  // [m2][S (S + 1) / 2]: DC_ij_hat at j (j + 1) / 2 + i, i <= j
-    const Real* tab_dk;                 // [m2][S (S + 1) / 2]: d DC_ij_hat / d Gamma, same order
+    const Real* tab_w;                  // [m2][tab_ws]: w0_s at 2 s, j3_s at 2 s + 1
+    const Real* tab_k;                  // [m2][tab_ks]: DC_ij_hat at j (j + 1) / 2 + i, i <= j
+    const Real* tab_dk;                 // [m2][tab_ks]: d DC_ij_hat / d Gamma, same order
     int tab_m2max;
+    int tab_ws, tab_ks;                 // record lengths: 2 S and S (S + 1) / 2 rounded up to 16 bytes
     // fixed-number species (canonical form of eq. rhoEquation): canon[i] != 0, target sum of G_i
     // over the grid N_i / h^3; ncanon of them
     int canon[DFT_MAXS];
@@ -88,6 +89,10 @@ struct SpeciesDesc {
 
 // Index of the pair (i, j), i <= j, in a table record (independent of S).
 __host__ __device__ constexpr int dft_pair(int i, int j) { return j * (j + 1) / 2 + i; }
+
+// Register capacity of a table record (a multiple of 16 bytes of either precision).
+#define DFT_TAB_W 12        // >= 2 DFT_MAXS
+#define DFT_TAB_K 16        // >= DFT_MAXS (DFT_MAXS + 1) / 2
 
 // Per-component additive constants of the plain x inverse.
 template <typename Real> struct Offsets { Real v[DFT_NCOMP + 2]; };

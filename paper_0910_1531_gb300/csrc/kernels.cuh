@@ -727,6 +727,25 @@ __device__ __forceinline__ void tiles_store_grouped(C* __restrict__ dst, const C
     }
 }
 
+// Load the first n entries of a table record (16-byte aligned) with 16-byte loads.
+template <typename Real, int MAXN>
+__device__ __forceinline__ void load_record(Real (&dst)[MAXN], const Real* __restrict__ rec, int n) {
+    constexpr int V = int(16 / sizeof(Real));
+    static_assert(MAXN % V == 0, "record capacity");
+#pragma unroll
+    for (int v = 0; v < MAXN / V; ++v) {
+        if (v * V < n) {
+            if constexpr (sizeof(Real) == 4) {
+                const float4 t = __ldg(reinterpret_cast<const float4*>(rec) + v);
+                dst[4 * v] = t.x; dst[4 * v + 1] = t.y; dst[4 * v + 2] = t.z; dst[4 * v + 3] = t.w;
+            } else {
+                const double2 t = __ldg(reinterpret_cast<const double2*>(rec) + v);
+                dst[2 * v] = t.x; dst[2 * v + 1] = t.y;
+            }
+        }
+    }
+}
+
 // Tables of the |k|-only factors for a cubic box (kf equal on the three axes): the FMT weights
 // w0, j3 of each species and the bulk-fluid kernel DC_ij_hat with its Gamma derivative, at
 // |k| = kf sqrt(m2) for every integer m2 in [0, m2max].  Evaluated once per plan with the same
@@ -735,21 +754,21 @@ template <typename Real>
 __global__ void k_ktab(SpeciesDesc<Real> sp, double kf, int m2max, Real* tab_w, Real* tab_k, Real* tab_dk) {
     const int m2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (m2 > m2max) return;
-    const int S = sp.S, P = S * (S + 1) / 2;
+    const int S = sp.S;
     const Real kmag = Real(kf * sqrt(double(m2)));
     for (int s = 0; s < S; ++s) {
         Real w0, j3;
         fmt_weights<Real>(kmag, sp.R[s], &w0, &j3);
-        tab_w[(long long)m2 * 2 * S + 2 * s] = w0;
-        tab_w[(long long)m2 * 2 * S + 2 * s + 1] = j3;
+        tab_w[(long long)m2 * sp.tab_ws + 2 * s] = w0;
+        tab_w[(long long)m2 * sp.tab_ws + 2 * s + 1] = j3;
     }
     for (int j = 0; j < S; ++j)
         for (int i = 0; i <= j; ++i) {
             Real dG = Real(0);
             const Real K = delta_c_hat<Real>(kmag, sp.es_R[i][j], sp.es_pref[i][j], sp.es_a[i][j], sp.es_b[i][j],
                                              sp.es_c[i][j], &dG, sp.es_da[i][j], sp.es_db[i][j], sp.es_dc[i][j]);
-            tab_k[(long long)m2 * P + dft_pair(i, j)] = K;
-            tab_dk[(long long)m2 * P + dft_pair(i, j)] = dG;
+            tab_k[(long long)m2 * sp.tab_ks + dft_pair(i, j)] = K;
+            tab_dk[(long long)m2 * sp.tab_ks + dft_pair(i, j)] = dG;
         }
 }
 
@@ -803,20 +822,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
         const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
         int m2 = 0;
         if (tab && live) { const int mz = signed_index(kzi, g.nz); m2 = kxi * kxi + my * my + mz * mz; }
-        Real wr[2 * DFT_MAXS];
-        Real kr[P], dkr[P];
+        Real wr[DFT_TAB_W];
+        Real kr[DFT_TAB_K], dkr[DFT_TAB_K];
         if (tab) {
-#pragma unroll
-            for (int q = 0; q < 2 * DFT_MAXS; ++q)
-                if (q < 2 * S) wr[q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+            load_record(wr, sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
             if (live) {
-#pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    if (q < Pn) {
-                        kr[q] = __ldg(sp.tab_k + (long long)m2 * Pn + q);
-                        if (GRAD) dkr[q] = __ldg(sp.tab_dk + (long long)m2 * Pn + q);
-                    }
-                }
+                load_record(kr, sp.tab_k + (long long)m2 * sp.tab_ks, Pn);
+                if (GRAD) load_record(dkr, sp.tab_dk + (long long)m2 * sp.tab_ks, Pn);
             }
         }
         C v[DFT_MAXS];
@@ -948,7 +960,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
 
     // loads first: bulk-fluid/Poisson spectra and table records of all of this thread's points
     C ea[PER][EMAX];
-    Real wr[PER][2 * DFT_MAXS];
+    Real wr[PER][DFT_TAB_W];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int idx = threadIdx.x + i * kThreads;
@@ -969,9 +981,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
         if (hs && tab) {
             int m2 = 0;
             if (live) { const int mz = signed_index(kzi, g.nz); m2 = kxi * kxi + my * my + mz * mz; }
-#pragma unroll
-            for (int q = 0; q < 2 * DFT_MAXS; ++q)
-                if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+            load_record(wr[i], sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
         }
     }
 #pragma unroll
@@ -1098,8 +1108,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
         // table records of this thread's points, in flight while the tile arrives
-        Real wr[PER][2 * DFT_MAXS];
-        Real kr[PER][P];
+        Real wr[PER][DFT_TAB_W];
+        Real kr[PER][DFT_TAB_K];
         if (tab) {
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
@@ -1110,12 +1120,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
                     const int mz = signed_index(kzi, g.nz);
                     m2 = kxi * kxi + my * my + mz * mz;
                 }
-#pragma unroll
-                for (int q = 0; q < 2 * DFT_MAXS; ++q)
-                    if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
-#pragma unroll
-                for (int q = 0; q < P; ++q)
-                    if (q < Pn) kr[i][q] = __ldg(sp.tab_k + (long long)m2 * Pn + q);
+                load_record(wr[i], sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
+                load_record(kr[i], sp.tab_k + (long long)m2 * sp.tab_ks, Pn);
             }
         }
         const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
@@ -1309,7 +1315,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
         // table records of this thread's points, in flight while the tile arrives
-        Real wr[PER][2 * DFT_MAXS];
+        Real wr[PER][DFT_TAB_W];
         if (hs && tab) {
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
@@ -1320,9 +1326,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
                     const int mz = signed_index(kzi, g.nz);
                     m2 = kxi * kxi + my * my + mz * mz;
                 }
-#pragma unroll
-                for (int q = 0; q < 2 * DFT_MAXS; ++q)
-                    if (q < 2 * S) wr[i][q] = __ldg(sp.tab_w + (long long)m2 * (2 * S) + q);
+                load_record(wr[i], sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
             }
         }
         const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
