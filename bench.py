@@ -154,13 +154,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over the ranks (the timed region ends with the slowest replica)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    device = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job units per second: every replica processed units_per_rank in at most ms_max."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 # ----------------------------------------------------------------------------------------
@@ -265,7 +272,7 @@ def run_batch(args):
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     resid = batch.iterate(1, -1.0, resid=True)
     n_states = len(ws)
-    value = n_states * args.steps * world / (ms / 1e3)
+    value = job_throughput(n_states * args.steps, world, ms)
     peak, peak_kind = measured_peaks()
     achieved = byte_per_it * args.steps / (ms * 1e-3) / 1e9
     sizes = {}
@@ -342,7 +349,7 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms, world)
-    value = args.steps * world / (ms_max / 1e3)
+    value = job_throughput(args.steps, world, ms_max)
     # per-kernel table: the same K iterations launched one by one with CUDA events around
     # every kernel (untimed for the headline)
     plan.profile_enable(True)
