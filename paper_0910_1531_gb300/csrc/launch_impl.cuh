@@ -175,11 +175,11 @@ cudaError_t LaunchZ<Real, N>::init() {
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_bwd_g<Real, N, TZ>)) != cudaSuccess) e = r;
-        constexpr int TB = dft_tile_zb<Real>(N);
-        if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0) {
+        constexpr int TB = dft_tile_zb<Real>(N), TF = dft_tile_zf<Real>(N);
+        if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0)
             if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
-            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
-        }
+        if constexpr ((TF * sizeof(typename Cplx<Real>::type)) % 16 == 0)
+            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
     } else {
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
@@ -193,7 +193,7 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
                                  int T, Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n,
                                  C* slot_es, double* red_energy, const C* tw, int* status) {
     constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 1;
-    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
+    constexpr int TB = N > 0 ? dft_tile_zf<Real>(N) : 1;
     constexpr bool kTma = N > 0 && (TB * sizeof(C)) % 16 == 0;
     if constexpr (kTma) {
         static int optin = 0, sms = 0;

@@ -43,6 +43,16 @@ template <typename Real> __host__ __device__ constexpr int dft_tile_zb(int n) {
     const int t = dft_tile_z<Real>(n) / 2, tmin = sizeof(Real) == 4 ? 2 : 1;
     return t > tmin ? t : tmin;
 }
+// Tile width of the persistent TMA first-half z pass: the second half's (DFT_ZFWD_WIDE: the
+// grouped width, two CTAs per SM still fitting at length 128 with three species).
+template <typename Real> __host__ __device__ constexpr int dft_tile_zf(int n) {
+#ifdef DFT_ZFWD_WIDE
+    return dft_tile_z<Real>(n);
+#else
+    return dft_tile_zb<Real>(n);
+#endif
+}
+
 template <typename Real> __host__ __device__ constexpr int dft_zbwd_threads(int n) {
 #ifdef DFT_ZBWD_THREADS
     return DFT_ZBWD_THREADS;
