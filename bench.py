@@ -33,7 +33,14 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 
 # DRAM traffic per launch (bytes) of the kernels measured by ncu on this workload, keyed by
 # kernel name, with the source digest of csrc/ at capture time; None until captured.
-NCU_TRAFFIC = None
+# DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of three
+# profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, command in
+# profiles/launches_obstacles128_fp32.md); valid while the kernel sources hash to `digest`.
+NCU_TRAFFIC = {
+    "digest": "061caf355d5c6b82",
+    "per_launch": {"xfwd": 25352789, "yfft": 61256907, "zconv_fwd": 76225963, "xinv": 8710400,
+                   "finalize": 36629, "xphi": 213681920, "zconv_bwd": 137440427, "xupdate": 103318613},
+}
 
 
 def workload(args):

@@ -219,35 +219,6 @@ __device__ __forceinline__ void tile_load(C* __restrict__ dst, const C* __restri
     }
 }
 
-// Split form of tile_load for prefetching: fetch a compile-time tile into registers (loads in
-// flight while the caller works on the previous tile), then put it into shared memory.
-template <int TT, int NN> __host__ __device__ constexpr int tile_per_thread() { return (TT * NN + kThreads - 1) / kThreads; }
-
-template <int TT, int NN, typename C>
-__device__ __forceinline__ void tile_fetch(C (&tmp)[tile_per_thread<TT, NN>()], const C* __restrict__ src, long long rs,
-                                           int valid) {
-    constexpr int TOTAL = TT * NN;
-    constexpr int PER = tile_per_thread<TT, NN>();
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int e = idx / TT, t = idx % TT;
-        tmp[i] = cmake<C>(0, 0);
-        if ((TOTAL % kThreads == 0 || idx < TOTAL) && t < valid) tmp[i] = src[e * rs + t];
-    }
-}
-
-template <int TT, int NN, typename C>
-__device__ __forceinline__ void tile_put(C* __restrict__ dst, const C (&tmp)[tile_per_thread<TT, NN>()]) {
-    constexpr int TOTAL = TT * NN;
-    constexpr int PER = tile_per_thread<TT, NN>();
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        if (TOTAL % kThreads == 0 || idx < TOTAL) dst[idx] = tmp[i];
-    }
-}
-
 template <int TT, int NN, typename C>
 __device__ __forceinline__ void tile_store(C* __restrict__ dst, const C* __restrict__ src, long long rs, int valid,
                                            int T, int n) {
@@ -504,27 +475,13 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
     const long long zstride = (long long)ny * g.pxh;
     const long long col0 = (long long)kyi * g.pxh + kx0;
 
-    // phase 1: forward z transform of each species tile; results end in pool[0..S-1].  With a
-    // compile-time tile the next species' loads are in flight during this one's transform.
-    if constexpr (NZ > 0 && TZ > 0) {
-        C pre[tile_per_thread<TZ, NZ>()];
-        tile_fetch<TZ, NZ>(pre, in + col0, zstride, nxh - kx0);
-        for (int s = 0; s < S; ++s) {
-            C* b = pool[s];
-            tile_put<TZ, NZ>(b, pre);
-            if (s + 1 < S) tile_fetch<TZ, NZ>(pre, in + (long long)(s + 1) * g.nc + col0, zstride, nxh - kx0);
-            __syncthreads();
-            C* r = ct_fft<NZ, false, true, TZ>(b, pool[6], T, 1, tw);
-            if (r != b) { pool[6] = b; pool[s] = r; }
-        }
-    } else {
-        for (int s = 0; s < S; ++s) {
-            C* b = pool[s];
-            tile_load<TZ, NZ>(b, in + (long long)s * g.nc + col0, zstride, nxh - kx0, T, nz);
-            __syncthreads();
-            C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
-            if (r != b) { pool[6] = b; pool[s] = r; }
-        }
+    // phase 1: forward z transform of each species tile; results end in pool[0..S-1]
+    for (int s = 0; s < S; ++s) {
+        C* b = pool[s];
+        tile_load<TZ, NZ>(b, in + (long long)s * g.nc + col0, zstride, nxh - kx0, T, nz);
+        __syncthreads();
+        C* r = any_fft<NZ, false, true, TZ>(b, pool[6], pz, T, T, 1, tw);
+        if (r != b) { pool[6] = b; pool[s] = r; }
     }
 
     // phase 2: k-space products at each tile point
@@ -1754,21 +1711,11 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     if (hs) {
         // nine Phi' spectra (DFT_NSPEC order): 0..3 transform into accumulators 0..3, B4 into
         // accumulator 4; -i k_y / -i k_z of Phi_V1y, Phi_V1z add to accumulator 4 and of Phi_V2y,
-        // Phi_V2z to accumulator 3 (Nyquist components of their axis dropped).  With a
-        // compile-time tile the next component's loads are in flight during this one's transform.
+        // Phi_V2z to accumulator 3 (Nyquist components of their axis dropped)
         for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) pool[4][idx] = cmake<C>(Real(0), Real(0));
-        constexpr bool kPre = NZ > 0 && TZ > 0;
-        constexpr int PER = kPre ? tile_per_thread<TZ, NZ>() : 1;
-        C pre[PER];
-        if constexpr (kPre) tile_fetch<TZ, NZ>(pre, phi + col0, zstride, nxh - kx0);
         for (int a = 0; a < DFT_NSPEC; ++a) {
             C* dst = (a < 4) ? pool[a] : pool[5];
-            if constexpr (kPre) {
-                tile_put<TZ, NZ>(dst, pre);
-                if (a + 1 < DFT_NSPEC) tile_fetch<TZ, NZ>(pre, phi + (long long)(a + 1) * g.nc + col0, zstride, nxh - kx0);
-            } else {
-                tile_load<TZ, NZ>(dst, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
-            }
+            tile_load<TZ, NZ>(dst, phi + (long long)a * g.nc + col0, zstride, nxh - kx0, T, nz);
             __syncthreads();
             C* r = any_fft<NZ, false, true, TZ>(dst, pool[6], pz, T, T, 1, tw);
             if (a < 4) {

@@ -114,13 +114,14 @@ cudaError_t LaunchX<Real, N>::xcanon(cudaStream_t st, const GridDesc& g, const A
 // ---------------------------------------------------------------------------------- y
 template <typename Real, int N>
 cudaError_t LaunchY<Real, N>::init() {
-    constexpr int TY = N > 0 ? dft_tile_y<Real>(N) : 0;
     cudaError_t e = cudaSuccess, r;
-    if ((r = set_max_smem(dftk::k_yfft<Real, false, N, TY>)) != cudaSuccess) e = r;
-    if ((r = set_max_smem(dftk::k_yfft<Real, true, N, TY>)) != cudaSuccess) e = r;
     if constexpr (N > 0) {
+        constexpr int TY = dft_tile_y<Real>(N);
         if ((r = set_max_smem(dftk::k_yfft_tma<Real, false, N, TY>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_yfft_tma<Real, true, N, TY>)) != cudaSuccess) e = r;
+    } else {
+        if ((r = set_max_smem(dftk::k_yfft<Real, false, 0, 0>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_yfft<Real, true, 0, 0>)) != cudaSuccess) e = r;
     }
     return e;
 }
