@@ -1095,9 +1095,8 @@ dft_status dft_solve(dft_plan* p, void* rho, const void* V, double alpha, double
     double r = p->ctl_host->resid;
     int it = 0;
     while (it < max_it && !(r < tol)) {
-        TRY(dft_iter_step(p, rho, V, alpha, nullptr, nullptr));
-        TRY(read_ctl(p));
-        r = p->ctl_host->resid;
+        // one iteration as a replay of the plan's one-iteration graph, then its residual
+        TRY(dft_iter_run(p, rho, V, 1, alpha, &r));
         ++it;
     }
     if (iters_out) *iters_out = it;

@@ -1496,6 +1496,39 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
     }
 }
 
+// The S species' half rows of `rows` grid rows as ceil(S/2) complex lines each (species 2l and
+// 2l + 1 in line l), one thread per (row, k) with all its loads issued first.
+template <typename Real, int NX>
+__device__ __forceinline__ void load_species_rows(const GridDesc& g, int rows, long long row0, long long nrows, int S,
+                                                  const typename Cplx<Real>::type* __restrict__ spec,
+                                                  typename Cplx<Real>::type* dst) {
+    using C = typename Cplx<Real>::type;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
+    const bool even = (nx % 2) == 0;
+    const int lpr = (S + 1) / 2;
+    for (int idx = threadIdx.x; idx < rows * nxh; idx += blockDim.x) {
+        const int r = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const long long row = row0 + r;
+        const bool live = row < nrows;
+        const long long o = row * g.pxh + k;
+        C v[DFT_MAXS + 1];
+#pragma unroll
+        for (int c = 0; c < DFT_MAXS + 1; ++c) {
+            v[c] = cmake<C>(Real(0), Real(0));
+            if (live && c < S) v[c] = spec[(long long)c * g.nc + o];
+        }
+        const bool edge = k == 0 || (even && 2 * k == nx);
+#pragma unroll
+        for (int l = 0; l < (DFT_MAXS + 1) / 2; ++l) {
+            if (l >= lpr) break;
+            C a = v[2 * l], b = v[2 * l + 1];
+            if (edge) { a.y = Real(0); b.y = Real(0); }
+            dst[(r * lpr + l) * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (!edge) dst[(r * lpr + l) * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+        }
+    }
+}
+
 // The ten weighted-density rows of `rows` grid rows as five complex lines each (wd_comp
 // arrangement), built from the nine kept spectra mixed as wA * A + wB * B (B optional), with
 // n_V1x = i k_x m and n_V2x = i k_x n3 (zero on the Nyquist index); mat_out (optional) receives
@@ -1905,7 +1938,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, S, cspec, nullptr, Real(1), Real(0), nullptr, A);
+    load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
