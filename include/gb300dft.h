@@ -180,13 +180,13 @@ dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iter
                         double* resid_out);
 
 /*
- * Autotuner (no counterpart in the paper): times the rows per block of the three x passes
- * that run every iteration (forward x transform of the densities; the Phi' pass; the update
- * pass) over candidates 1..16 on the plan's own data (rho, V: [S][N] device, read only;
+ * Autotuner (no counterpart in the paper): times the rows per block of the x passes that run
+ * every iteration (forward x transform of the densities; the Phi' pass; the update pass over
+ * candidates 1..16; the n3-maximum pass of the line search over 8..64) on the plan's own data (rho, V: [S][N] device, read only;
  * `reps` timed launches per candidate, < 1 selects 5) and keeps the fastest in the plan.
  * Results are cached per (grid, species count, precision) for the life of the process, so
  * later plans of the same shape reuse them without timing.  Invalidates a preceding
- * dft_iter_begin (call it again).  lines_out (may be NULL) receives the three choices.
+ * dft_iter_begin (call it again).  lines_out (may be NULL) receives the first three choices.
  * Runs on the plan's stream and synchronises it.
  */
 dft_status dft_autotune(dft_plan* plan, const void* rho, const void* V, int reps, int lines_out[3]);

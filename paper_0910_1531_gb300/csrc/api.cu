@@ -61,7 +61,8 @@ struct dft_plan {
     float* red_max = nullptr;
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;
-    int Ty = 1, Tz = 1, LX = 1, LRphi = 1, LRupd = 1, LRn3 = 1, LR10 = 1;
+    int Ty = 1, Tz = 1, LX = 1, LRphi = 1, LRupd = 1;
+    int LRn3 = 0;                   // rows per block of the n3-maximum x pass (0: from the budget)
     SpeciesDesc<float> spf{};
     SpeciesDesc<double> spd{};
     bool prof = false;
@@ -323,7 +324,7 @@ template <typename Real> struct Ops {
     static dft_status xinv(dft_plan* p, int ncomp, const C* spec, Real* out, Real* out_last, const double* offs,
                            int cmax, float* red_max, int* blocks_out) {
         const int lpr = (ncomp + 1) / 2;
-        const int LR = pick_lines(p->g.nx, sizeof(C), lpr, 48 * 1024, 16);
+        const int LR = (ncomp == 1 && p->LRn3 > 0) ? p->LRn3 : pick_lines(p->g.nx, sizeof(C), lpr, 48 * 1024, 16);
         Offsets<Real> off;
         for (int c = 0; c < DFT_NCOMP + 2; ++c) off.v[c] = Real(0);
         if (offs)
@@ -618,7 +619,7 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 3>> g_tune_cache;
+std::map<TuneKey, std::array<int, 4>> g_tune_cache;
 
 template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, const Real* V, int reps) {
     using O = Ops<Real>;
@@ -652,9 +653,20 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
         return ms;
     };
     const int lpr_upd = (p->S + 1) / 2;
-    int best[3] = {p->LX, p->LRphi, p->LRupd};
-    float best_ms[3] = {1e30f, 1e30f, 1e30f};
+    int best[4] = {p->LX, p->LRphi, p->LRupd, p->LRn3};
+    float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     const C* A = O::slot_n(p->slotA);
+    Offsets<Real> off0;
+    for (int c = 0; c < DFT_NCOMP + 2; ++c) off0.v[c] = Real(0);
+    const int cand_n3[] = {8, 16, 24, 32, 48, 64};
+    for (int L : cand_n3) {
+        if (P::smem_x(p->g.nx, L) > size_t(optin)) continue;
+        const float ms = time_it([&] {
+            P::xinv(p->stream, p->g, p->ax, L, 1, A + 3 * p->g.nc, nullptr, nullptr, off0, 0, p->red_max, 0,
+                    O::kf(p, 0), O::tw(p, 0));
+        });
+        if (ms < best_ms[3]) { best_ms[3] = ms; best[3] = L; }
+    }
     for (int L : cand) {
         if (P::smem_x(p->g.nx, L) <= size_t(optin)) {
             const float ms = time_it([&] {
@@ -686,6 +698,7 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     p->LX = best[0];
     p->LRphi = best[1];
     p->LRupd = best[2];
+    p->LRn3 = best[3];
     return DFT_OK;
 }
 }  // namespace
@@ -1063,6 +1076,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
             p->LX = it->second[0];
             p->LRphi = it->second[1];
             p->LRupd = it->second[2];
+            p->LRn3 = it->second[3];
             cached = true;
         }
     }
@@ -1070,7 +1084,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         if (is_fp64(p)) TRY(autotune_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), reps));
         else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd};
+        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd, p->LRn3};
     }
     // the iteration state and its graph depend on the block counts
     p->iter_ready = false;

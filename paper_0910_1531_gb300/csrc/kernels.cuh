@@ -256,12 +256,27 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long rows = (long long)ncomp * g.ny * g.nz;
     const long long pair0 = (long long)blockIdx.x * lx;
-    for (int idx = threadIdx.x; idx < lx * nx; idx += blockDim.x) {
-        const int l = idx / nx, x = idx - (idx / nx) * nx;
-        const long long ra = 2 * (pair0 + l), rb = ra + 1;
-        const Real a = (ra < rows) ? in[ra * nx + x] : Real(0);
-        const Real b = (rb < rows) ? in[rb * nx + x] : Real(0);
-        A[l * pitch + xo<NX>(x)] = cmake<C>(a, b);
+    // rows 2(pair0 + l) and 2(pair0 + l) + 1 as the real and imaginary parts of line l; the loads
+    // of kU elements per thread are issued before their shared-memory stores
+    constexpr int kU = 4;
+    const int total = lx * nx;
+    for (int base = threadIdx.x; base < total; base += kU * kThreads) {
+        Real av[kU], bv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * kThreads;
+            const int l = idx / nx, x = idx - (idx / nx) * nx;
+            const long long ra = 2 * (pair0 + l), rb = ra + 1;
+            av[u] = (idx < total && ra < rows) ? in[ra * nx + x] : Real(0);
+            bv[u] = (idx < total && rb < rows) ? in[rb * nx + x] : Real(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * kThreads;
+            if (idx >= total) break;
+            const int l = idx / nx, x = idx - (idx / nx) * nx;
+            A[l * pitch + xo<NX>(x)] = cmake<C>(av[u], bv[u]);
+        }
     }
     __syncthreads();
     C* R = any_fft<NX, false, false, 0>(A, B, px, lx, 1, pitch, tw);
