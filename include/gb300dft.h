@@ -155,6 +155,23 @@ dft_status dft_solve(dft_plan* plan, void* rho_inout, const void* V, double alph
                      int max_it, int* iters_out, double* resid_out);
 
 /*
+ * Newton-Krylov alternative to dft_solve (the paper reports trying Newton-GMRES; Sec.
+ * "Nonlinear solver"): Newton on F(u) = u - log G(e^u) over the accessible voxels
+ * (u = log rho), each Newton step solving J d = -F by restarted-free GMRES with at most
+ * krylov_dim (1..200) Jacobian-vector products J v = (F(u + eps v) - F(u)) / eps (one G
+ * evaluation each; eps = sqrt(machine epsilon) sqrt(S N) for unit v) to relative residual
+ * 0.1, then a backtracking line search (u + lam d, lam = 1, 1/2, ... 1/128) requiring
+ * |F| to decrease; a trial whose G meets n3 >= 1 or a non-finite value is shortened.
+ * Stops when the Picard residual r(rho) of dft_picard_step is below tol (DFT_OK) or after
+ * max_newton steps / a line search that finds no decrease (DFT_ENOCONV, rho = the last
+ * accepted iterate).  rho_inout: [S][N] device, positive on accessible voxels.  Work
+ * vectors ((krylov_dim + 7) S N reals) are allocated for the call.  newton_out,
+ * gevals_out (G evaluations), resid_out may be NULL.
+ */
+dft_status dft_solve_newton(dft_plan* plan, void* rho_inout, const void* V, double tol, int max_newton,
+                            int krylov_dim, int* newton_out, int* gevals_out, double* resid_out);
+
+/*
  * Stateful iteration for callers that drive the loop themselves (and for
  * timing): dft_iter_begin evaluates G(rho) and keeps it, with the weighted
  * densities of rho, inside the plan; each dft_iter_step then performs one

@@ -65,6 +65,7 @@ SIGNATURES = {
     "dft_iter_begin": (_I, [_P, _P, _P]),
     "dft_iter_step": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_iter_run": (_I, [_P, _P, _P, _I, _D, _PD]),
+    "dft_solve_newton": (_I, [_P, _P, _P, _D, _I, _I, _PI, _PI, _PD]),
     "dft_autotune": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_int)]),
     "dft_picard_step_host": (_I, [_P, _P, _P, _D, _PD, _PD]),
     "dft_grad": (_I, [_P, _P, _P, _PD, _P, _P, _PD]),
@@ -216,6 +217,17 @@ class Plan:
             return it.value, r.value, False
         self._check(st)
         return it.value, r.value, True
+
+    def solve_newton(self, rho, V, tol, max_newton=50, krylov_dim=30, raise_on_noconv=False):
+        """Newton-Krylov solve in place; returns (newton steps, G evaluations, r, converged)."""
+        it, ge, r = _I(), _I(), _D()
+        st = self.lib.dft_solve_newton(self.handle, self._field(rho, self.nspecies, "rho"),
+                                       self._field(V, self.nspecies, "V"), float(tol), int(max_newton),
+                                       int(krylov_dim), ctypes.byref(it), ctypes.byref(ge), ctypes.byref(r))
+        if st == -7 and not raise_on_noconv:
+            return it.value, ge.value, r.value, False
+        self._check(st)
+        return it.value, ge.value, r.value, True
 
     def iter_begin(self, rho, V):
         self._check(self.lib.dft_iter_begin(self.handle, self._field(rho, self.nspecies, "rho"),

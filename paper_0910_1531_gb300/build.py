@@ -19,7 +19,7 @@ LIB_NAME = "libgb300dft.so"
 # (source, object name, extra defines); kinst.cu is compiled once per (precision, axis length)
 CT_SIZES = (0, 32, 48, 64, 96, 128, 256)
 SOURCES = ([("api.cu", "api", []), ("bulk.cpp", "bulk", []), ("noalloc.cu", "noalloc", []),
-            ("dispatch.cu", "dispatch", [])]
+            ("dispatch.cu", "dispatch", []), ("newton.cu", "newton", [])]
            + [("kinst.cu", f"kinst_{r}_{n}", [f"-DDFT_INST_REAL={r}", f"-DDFT_INST_N={n}"])
               for r in ("float", "double") for n in CT_SIZES])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

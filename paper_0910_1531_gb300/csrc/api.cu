@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <array>
 #include <map>
 #include <mutex>
@@ -15,6 +16,7 @@
 
 #include "bulk.h"
 #include "gb300dft.h"
+#include "newton.h"
 #include "passes.h"
 
 namespace {
@@ -608,6 +610,153 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
 // ======================================================================================
 namespace {
 // --------------------------------------------------------------------------------------
+// Newton-Krylov solver (see newton.cu): u = log rho on the accessible voxels,
+// F(u) = u - log G(e^u); GMRES(m) on J d = -F with finite-difference products J v, a
+// backtracking line search on |F|; stops on the Picard residual r(rho) < tol.
+// --------------------------------------------------------------------------------------
+template <typename Real>
+dft_status newton_t(dft_plan* p, Real* rho, const Real* V, double tol, int max_newton, int m, int* iters_out,
+                    int* gevals_out, double* resid_out) {
+    const long long n = (long long)p->S * p->g.n;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = 2 * sms;
+    NkVec<Real> vk(p->stream, n, grid);
+    std::vector<Real*> buf;
+    auto alloc = [&](size_t count) -> Real* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(Real)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        buf.push_back(static_cast<Real*>(q));
+        return static_cast<Real*>(q);
+    };
+    double* part_dev = nullptr;
+    std::vector<double> part_host(grid);
+    struct Cleanup {
+        std::vector<Real*>& b;
+        double*& pd;
+        ~Cleanup() { for (Real* q : b) cudaFree(q); cudaFree(pd); }
+    } cleanup{buf, part_dev};
+    Real* F = alloc(n);
+    Real* Ft = alloc(n);
+    Real* g = alloc(n);
+    Real* gt = alloc(n);
+    Real* rt = alloc(n);
+    Real* d = alloc(n);
+    Real* basis = alloc(size_t(m + 1) * n);
+    if (!F || !Ft || !g || !gt || !rt || !d || !basis || cudaMalloc(&part_dev, sizeof(double) * grid) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(p, DFT_ENOMEM, "Newton-Krylov work vectors");
+    }
+    auto Vk = [&](int i) { return basis + size_t(i) * n; };
+    int gevals = 0;
+    // G(x) into gout and the Picard residual r(x); a status error (n3 >= 1, non-finite) is returned
+    auto evalG = [&](const Real* x, Real* gout, double* r) -> dft_status {
+        ++gevals;
+        dft_status st = picard_map_t<Real>(p, x, V, gout);
+        if (st != DFT_OK) return st;
+        st = read_ctl(p);
+        if (st != DFT_OK) return st;
+        if (r) *r = p->ctl_host->resid;
+        return DFT_OK;
+    };
+    auto dot = [&](const Real* a, const Real* b, double* out) -> dft_status {
+        cudaError_t e = vk.dot(a, b, part_dev, part_host.data(), out);
+        return e == cudaSuccess ? DFT_OK : fail(p, DFT_ECUDA, std::string("Newton-Krylov: ") + cudaGetErrorString(e));
+    };
+#define NK_CUDA(x)                                                                                       \
+    do {                                                                                                 \
+        cudaError_t _e = (x);                                                                            \
+        if (_e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("Newton-Krylov: ") + cudaGetErrorString(_e)); \
+    } while (0)
+    double r = 0.0, fn2 = 0.0;
+    TRY(evalG(rho, g, &r));
+    NK_CUDA(vk.residual(rho, g, V, F));
+    TRY(dot(F, F, &fn2));
+    double fn = std::sqrt(fn2);
+    const double macheps = sizeof(Real) == 4 ? 1.1920929e-7 : 2.220446049250313e-16;
+    const double eps = std::sqrt(macheps) * std::sqrt(double(n));
+    const double eta = 0.1;            // GMRES relative tolerance (forcing term)
+    std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), gv(m + 1, 0.0), y(m, 0.0);
+    int it = 0;
+    for (; it < max_newton && !(r < tol) && fn > 0.0; ++it) {
+        // GMRES(m) on J d = -F from d = 0
+        NK_CUDA(vk.axpby(-1.0 / fn, F, 0.0, Vk(0)));
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = fn;
+        int jm = 0;
+        for (int j = 0; j < m; ++j) {
+            // w = J v_j
+            NK_CUDA(vk.step(rho, Vk(j), eps, V, rt));
+            TRY(evalG(rt, gt, nullptr));
+            NK_CUDA(vk.jv(rt, gt, F, V, eps, Vk(j + 1)));
+            for (int i = 0; i <= j; ++i) {      // modified Gram-Schmidt
+                double h = 0.0;
+                TRY(dot(Vk(j + 1), Vk(i), &h));
+                H[size_t(i) * m + j] = h;
+                NK_CUDA(vk.axpby(-h, Vk(i), 1.0, Vk(j + 1)));
+            }
+            double hn2 = 0.0;
+            TRY(dot(Vk(j + 1), Vk(j + 1), &hn2));
+            const double hn = std::sqrt(hn2);
+            H[size_t(j + 1) * m + j] = hn;
+            if (hn > 0.0) NK_CUDA(vk.axpby(1.0 / hn, Vk(j + 1), 0.0, Vk(j + 1)));
+            for (int i = 0; i < j; ++i) {       // previous rotations on column j
+                const double a = H[size_t(i) * m + j], b = H[size_t(i + 1) * m + j];
+                H[size_t(i) * m + j] = cs[i] * a + sn[i] * b;
+                H[size_t(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[size_t(j) * m + j], b = H[size_t(j + 1) * m + j];
+            const double rr = std::hypot(a, b);
+            cs[j] = rr > 0.0 ? a / rr : 1.0;
+            sn[j] = rr > 0.0 ? b / rr : 0.0;
+            H[size_t(j) * m + j] = rr;
+            H[size_t(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            jm = j + 1;
+            if (std::fabs(gv[j + 1]) <= eta * fn || hn == 0.0) break;
+        }
+        for (int i = jm - 1; i >= 0; --i) {     // back substitution
+            double t = gv[i];
+            for (int k = i + 1; k < jm; ++k) t -= H[size_t(i) * m + k] * y[k];
+            y[i] = H[size_t(i) * m + i] != 0.0 ? t / H[size_t(i) * m + i] : 0.0;
+        }
+        NK_CUDA(vk.axpby(y[0], Vk(0), 0.0, d));
+        for (int i = 1; i < jm; ++i) NK_CUDA(vk.axpby(y[i], Vk(i), 1.0, d));
+        // backtracking on |F|: u <- u + lam d
+        double lam = 1.0, rnew = r, ftn = fn;
+        bool accepted = false;
+        for (int t = 0; t < 8 && !accepted; ++t, lam *= 0.5) {
+            NK_CUDA(vk.step(rho, d, lam, V, rt));
+            dft_status st = evalG(rt, gt, &rnew);
+            if (st == DFT_EN3BOUND || st == DFT_ENONFINITE) continue;     // too long a step
+            if (st != DFT_OK) return st;
+            NK_CUDA(vk.residual(rt, gt, V, Ft));
+            double f2 = 0.0;
+            TRY(dot(Ft, Ft, &f2));
+            ftn = std::sqrt(f2);
+            if (ftn <= (1.0 - 1e-4 * lam) * fn) accepted = true;
+        }
+        if (!accepted) break;
+        NK_CUDA(cudaMemcpyAsync(rho, rt, sizeof(Real) * n, cudaMemcpyDeviceToDevice, p->stream));
+        std::swap(g, gt);
+        std::swap(F, Ft);
+        fn = ftn;
+        r = rnew;
+    }
+#undef NK_CUDA
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(p, DFT_ECUDA, "Newton-Krylov: synchronize");
+    if (iters_out) *iters_out = it;
+    if (gevals_out) *gevals_out = gevals;
+    if (resid_out) *resid_out = r;
+    if (!(r < tol)) return fail(p, DFT_ENOCONV, "Newton-Krylov: tol not reached");
+    return DFT_OK;
+}
+}  // namespace
+
+namespace {
+// --------------------------------------------------------------------------------------
 // x-pass autotuner: rows per block of the three x passes that stream every iteration
 // (xfwd, xphi, xupdate), timed on the plan's own data and cached per grid, species count
 // and precision for the life of the process.
@@ -1100,6 +1249,20 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
 dft_status dft_picard_step(dft_plan* p, void* rho, const void* V, double alpha, double* resid_out, double* alpha_out) {
     TRY(dft_iter_begin(p, rho, V));
     return dft_iter_step(p, rho, V, alpha, resid_out, alpha_out);
+}
+
+dft_status dft_solve_newton(dft_plan* p, void* rho, const void* V, double tol, int max_newton, int krylov_dim,
+                            int* newton_out, int* gevals_out, double* resid_out) {
+    TRY(check_plan(p));
+    if (!rho || !V) return fail(p, DFT_EINVAL, "NULL field pointer");
+    if (max_newton < 0 || krylov_dim < 1 || krylov_dim > 200) return fail(p, DFT_EINVAL, "bad Newton-Krylov sizes");
+    p->iter_ready = false;
+    release_iter_graph(p);
+    if (is_fp64(p))
+        return newton_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V), tol, max_newton,
+                                krylov_dim, newton_out, gevals_out, resid_out);
+    return newton_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V), tol, max_newton, krylov_dim,
+                           newton_out, gevals_out, resid_out);
 }
 
 dft_status dft_solve(dft_plan* p, void* rho, const void* V, double alpha, double tol, int max_it, int* iters_out,
