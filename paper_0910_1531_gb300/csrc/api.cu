@@ -77,6 +77,8 @@ struct dft_plan {
     std::string err;
     void* ktab = nullptr;           // |k| tables of the compile-time z passes (cubic boxes)
     cudaStream_t cap = nullptr;     // capture stream of the one-iteration graph (dft_iter_run)
+    cudaStream_t side = nullptr;    // copy stream of dft_picard_step_host
+    cudaEvent_t v_ready = nullptr;  // V staged (dft_picard_step_host)
     cudaGraph_t igraph = nullptr;
     cudaGraphExec_t iexec = nullptr;
     const void* graph_rho = nullptr;
@@ -370,11 +372,14 @@ dft_status reset_status(dft_plan* p) {
         if (_s != DFT_OK) return _s;  \
     } while (0)
 
-template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const Real* V) {
+// v_ready (optional): an event the second half (the first use of V) waits for
+template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const Real* V, cudaEvent_t v_ready = nullptr) {
     using O = Ops<Real>;
     TRY(reset_status(p));
     TRY(O::first_half(p, rho, p->slotA, 0));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
+    if (v_ready && cudaStreamWaitEvent(p->stream, v_ready, 0) != cudaSuccess)
+        return fail(p, DFT_ECUDA, "stream wait");
     TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, static_cast<Real*>(p->gbuf)));
     TRY(finalize(p, FIN_F0 | FIN_N3CUR, (int)p->blocks_x(p->LRupd), (int)p->blocks_x(p->LRphi), -1.0));
     p->iter_ready = true;
@@ -1059,6 +1064,8 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->red_canon);
     release_iter_graph(p);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->v_ready) cudaEventDestroy(p->v_ready);
+    if (p->side) cudaStreamDestroy(p->side);
     cudaFree(p->ctl);
     if (p->ctl_host) cudaFreeHost(p->ctl_host);
     for (cudaEvent_t ev : p->evpool) cudaEventDestroy(ev);
@@ -1293,16 +1300,35 @@ dft_status dft_picard_step_host(dft_plan* p, void* rho_host, const void* V_host,
             return fail(p, DFT_ENOMEM, "staging buffers");
         }
     }
+    if (!p->side && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(p, DFT_ECUDA, "side stream creation failed");
+    if (!p->v_ready && cudaEventCreateWithFlags(&p->v_ready, cudaEventDisableTiming) != cudaSuccess)
+        return fail(p, DFT_ECUDA, "event creation failed");
+    // rho in on the plan's stream; V in on a side stream, awaited only by the first pass that
+    // reads it (the first half of G runs meanwhile)
     cudaError_t e = cudaMemcpyAsync(p->stage_rho, rho_host, bytes, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->stage_V, V_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->v_ready, p->stream);       // V may be overwritten only now
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->v_ready, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->stage_V, V_host, bytes, cudaMemcpyHostToDevice, p->side);
+    if (e == cudaSuccess) e = cudaEventRecord(p->v_ready, p->side);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
-    double r = 0, a = 0;
-    TRY(dft_picard_step(p, p->stage_rho, p->stage_V, alpha, &r, &a));
-    e = cudaMemcpyAsync(rho_host, p->stage_rho, bytes, cudaMemcpyDeviceToHost, p->stream);
+    if (is_fp64(p)) TRY(iter_begin_t<double>(p, static_cast<double*>(p->stage_rho), static_cast<const double*>(p->stage_V), p->v_ready));
+    else TRY(iter_begin_t<float>(p, static_cast<float*>(p->stage_rho), static_cast<const float*>(p->stage_V), p->v_ready));
+    p->iter_ready = true;
+    p->iter_rho = p->stage_rho;
+    p->iter_V = p->stage_V;
+    // the step as a replay of the cached one-iteration graph, then the control block and rho
+    // out with one synchronisation
+    TRY(dft_iter_run(p, p->stage_rho, p->stage_V, 1, alpha, nullptr));
+    e = cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rho_host, p->stage_rho, bytes, cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
-    if (resid_out) *resid_out = r;
-    if (alpha_out) *alpha_out = a;
+    if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
+    if (p->ctl_host->status & DEV_NONFINITE) return fail(p, DFT_ENONFINITE, "non-finite density or residual met");
+    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
+    if (resid_out) *resid_out = p->ctl_host->resid_prev;
+    if (alpha_out) *alpha_out = p->ctl_host->alpha;
     return DFT_OK;
 }
 

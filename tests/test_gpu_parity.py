@@ -214,6 +214,11 @@ def test_host_buffer_step_matches_device_step():
     r2, a2 = plan.picard_step_host(rho_h, V_h, -1.0)
     assert r1 == r2 and a1 == a2
     assert torch.equal(rho_h, rho_d.cpu())
+    # a second call (staged inputs overwritten, the step replayed from the cached graph)
+    r1, a1 = plan.picard_step(rho_d, to_dev(w.V, plan), -1.0)
+    r2, a2 = plan.picard_step_host(rho_h, V_h, -1.0)
+    assert r1 == r2 and a1 == a2
+    assert torch.equal(rho_h, rho_d.cpu())
 
 
 def test_profile_counts_launches():
