@@ -37,9 +37,8 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 # profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, command in
 # profiles/launches_obstacles128_fp32.md); valid while the kernel sources hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "061caf355d5c6b82",
-    "per_launch": {"xfwd": 25352789, "yfft": 61256907, "zconv_fwd": 76225963, "xinv": 8710400,
-                   "finalize": 36629, "xphi": 213681920, "zconv_bwd": 137440427, "xupdate": 103318613},
+    "digest": "5f4198b75fc9eda4",
+    "per_launch": {"xfwd": 25349803, "yfft": 61266891, "zconv_fwd": 76109312, "xinv": 8711253, "finalize": 29333, "xphi": 213765035, "zconv_bwd": 137481387, "xupdate": 102687431},
 }
 
 
