@@ -303,6 +303,55 @@ def run_batch(args):
     return 0
 
 
+def cufft_comparator(plan, w, rho, V, reps, stream):
+    """Timed comparison only (never on the product path): the 3D real transforms that a
+    cuFFT-based evaluation of G(rho) performs at the least -- S forward, ten inverse (weighted
+    densities), ten forward (Phi derivatives), S inverse (c1) -- batched through torch.fft,
+    which calls cuFFT, with no pointwise work at all; against one whole G evaluation of the
+    library (dft_picard_map) on the same inputs."""
+    import torch
+    S, shape = w.nspecies, tuple(w.shape)
+    dims = (1, 2, 3)
+    real_s = rho.view((S,) + shape)
+    cdt = torch.complex64 if rho.dtype == torch.float32 else torch.complex128
+    half = shape[:2] + (shape[2] // 2 + 1,)
+    spec_s = torch.empty((S,) + half, dtype=cdt, device=rho.device)
+    spec_10 = torch.zeros((10,) + half, dtype=cdt, device=rho.device)
+    real_10 = torch.empty((10,) + shape, dtype=rho.dtype, device=rho.device)
+    out_s = torch.empty((S,) + shape, dtype=rho.dtype, device=rho.device)
+
+    def transforms():
+        torch.fft.rfftn(real_s, dim=dims, out=spec_s)
+        torch.fft.irfftn(spec_10, s=shape, dim=dims, out=real_10)
+        torch.fft.rfftn(real_10, dim=dims, out=spec_10)
+        torch.fft.irfftn(spec_s, s=shape, dim=dims, out=out_s)
+
+    g_out = plan.empty(S)
+
+    def ours():
+        plan.picard_map(rho, V, out=g_out, resid=False)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_fft, t_ours = timed(transforms), timed(ours)
+    del spec_s, spec_10, real_10, out_s, g_out
+    return {"transforms_per_G": 2 * S + 20, "cufft_transforms_ms_per_G": t_fft, "ours_ms_per_G": t_ours,
+            "ratio_cufft_over_ours": t_fft / t_ours if t_ours > 0 else None, "reps": reps,
+            "note": "torch.fft (cuFFT) batched 3D R2C/C2R transforms only, no pointwise work: a lower bound "
+                    "for a cuFFT-based G; ours = dft_picard_map, the whole G (transforms, weights, Phi, "
+                    "Poisson, Delta C, exp update, residual)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -374,6 +423,8 @@ def run_ours(args):
     prof = {k: plan.profile_read(k) for k in KERNELS}
     plan.profile_enable(False)
     resid_after, alpha_after = plan.iter_step(rho, V, alpha, sync=True)
+    # cuFFT transforms of one G against the library's whole G (comparison only)
+    cufft = None if args.no_cufft else cufft_comparator(plan, w, rho, V, max(10, min(args.steps, 100)), stream)
 
     # time to tolerance from the initial density (chunks of graph replays, residual read
     # between chunks)
@@ -460,7 +511,7 @@ def run_ours(args):
                            "l2": f"no flush: working set {working_set/1e6:.0f} MB > L2 129 MB",
                            "resid_after": resid_after},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "kernels": kernels}
+                "cpu_baseline": cpu, "kernels": kernels, "cufft_comparator": cufft}
         print(json.dumps(line))
     plan.close()
     if world > 1:
@@ -479,6 +530,7 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--alpha", type=float, default=None,

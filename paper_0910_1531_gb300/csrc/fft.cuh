@@ -331,3 +331,87 @@ __device__ __forceinline__ C* ct_fft_grouped(C* a, C* b, int groups, const C* tw
     ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, 0>(a, b, groups, tw);
     return a;
 }
+
+// ------------------------------------------------------------------------------------
+// In-place grouped column transforms (same layouts, SRC_DENSE / DST_DENSE meaning and twiddle
+// table as ct_fft_grouped).  Each thread takes one butterfly of a stage, holds its R inputs in
+// registers across a barrier and then writes its outputs over the same tile, so that no scratch
+// tiles are needed; the groups are taken in chunks of NT / (T N / R) per pass of the threads
+// (chunks touch disjoint groups, so one barrier per chunk orders its reads before its writes).
+// The caller syncs before the call; the last stage is NOT followed by a barrier, so the caller
+// syncs (after any proxy fence its TMA stores need) before reading the result.
+// ------------------------------------------------------------------------------------
+// barrier among the first `count` threads of the CTA (a multiple of 32), named barrier 1
+__device__ __forceinline__ void bar_sync_first(int count) {
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, bool END_SYNC, typename C>
+__device__ __forceinline__ void ct_stage_grouped_ip(C* buf, int groups, const C* __restrict__ tw) {
+    constexpr int M = N / R;
+    constexpr int TWSTEP = N / (NS * R);
+    constexpr int PERG = M * T;
+    static_assert(PERG <= NT, "the butterflies of one group fit the threads of a pass");
+    constexpr int GCH = NT / PERG;
+    // the thread index read through a volatile move: the compiler would otherwise hoist every
+    // stage's butterfly offsets (loop invariants of a persistent kernel's tile loop) and keep
+    // them all live across the loop
+    int tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    const int gl = tid / PERG;
+    const int rem = tid - gl * PERG;
+    const int t = rem % T, j = rem / T;
+    const int k = j % NS;
+    const int base = (j / NS) * (NS * R) + k;
+    for (int g0 = 0; g0 < groups; g0 += GCH) {
+        const int ng = groups - g0 < GCH ? groups - g0 : GCH;
+        // the warps that hold this chunk's butterflies take part (named barrier among them);
+        // their idle lanes transform a copy of the chunk's first group and do not store it
+        const int nthr = (ng * PERG + 31) & ~31;
+        if (tid < nthr) {
+            const bool act = gl < ng;
+            const int off = (g0 + (act ? gl : 0)) * GSTR + t;
+            C v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = j + r * M;
+                v[r] = buf[(SD ? e * T : ct_gpos(e, T)) + off];
+            }
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[k * r * TWSTEP];
+                    if (INV) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            dft_small<R, INV>(v);
+            bar_sync_first(nthr);
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int e = base + r * NS;
+                    buf[(DD ? e * T : ct_gpos(e, T)) + off] = v[r];
+                }
+            }
+        }
+    }
+    if constexpr (END_SYNC) __syncthreads();
+}
+
+template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, typename C>
+__device__ __forceinline__ void ct_stages_grouped_ip(C* a, int groups, const C* tw) {
+    if constexpr (S < ct_nstages(N)) {
+        constexpr int R = ct_radix_at(N, S);
+        constexpr int NS = ct_ns_at(N, S);
+        constexpr bool last = (S + 1 == ct_nstages(N));
+        ct_stage_grouped_ip<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT, !last>(a, groups, tw);
+        ct_stages_grouped_ip<N, INV, T, GSTR, SD, DD, NT, S + 1>(a, groups, tw);
+    }
+}
+
+// Transform `groups` tiles held in a, in place; the caller syncs before and after.
+template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads, typename C>
+__device__ __forceinline__ void ct_fft_grouped_ip(C* a, int groups, const C* tw) {
+    ct_stages_grouped_ip<N, INV, T, GSTR, SD, DD, NT, 0>(a, groups, tw);
+}

@@ -745,6 +745,12 @@ __global__ void k_ktab(SpeciesDesc<Real> sp, double kf, int m2max, Real* tab_w, 
 }
 
 __device__ __forceinline__ int signed_index(int j, int n) { return (2 * j <= n) ? j : j - n; }
+// m^2 = mx^2 + my^2 + mz^2 of a cubic box's mode (the |k| table index) from kx index kxi >= 0,
+// signed y index my and z index kzi
+__device__ __forceinline__ int kmode2(int kxi, int my, int kzi, int nz) {
+    const int mz = signed_index(kzi, nz);
+    return kxi * kxi + my * my + mz * mz;
+}
 
 // First-half z pass (same contract as k_zconv_fwd): S species spectra in, the ten weighted
 // densities (z inverse, 1/N applied) and the bulk-fluid/Poisson spectra out.  Per-species loops
@@ -1018,8 +1024,8 @@ template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zf
     return ((2 * size_t(S) + 2 * DFT_NSPEC) * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
 }
 
-template <typename Real, int NZ, int TZ, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const __grid_constant__ CUtensorMap map_in,
+template <typename Real, int NZ, int TZ, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constant__ CUtensorMap map_in,
                                                                          const __grid_constant__ CUtensorMap map_n,
                                                                          GridDesc g, SpeciesDesc<Real> sp, Real kfx,
                                                                          Real kfy, Real kfz, int want_psi,
@@ -1202,82 +1208,106 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_fwd_tma(const _
 
 // ------------------------------------------------------------------------------------
 // Second-half z pass with TMA tiles (same contract as k_zconv_bwd), persistent: CTA b handles
-// tiles b, b + gridDim.x, ...  Two shared-memory stages, each holding one tile's ten Phi'
-// components and its bulk-fluid/Poisson spectra, are filled by TMA loads (one
-// cp.async.bulk.tensor per component, completing on the stage's mbarrier) while the previous
-// tile is transformed; the ncomp_out results leave through TMA stores.  A tensor map views a
-// half-spectrum array as (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements, E =
-// sizeof(complex) / 8; a component tile is the box (TZ * E, 1, NZ) at plane c * nz.  Columns
-// past nxh read as zero and are not written.  A wait that runs out sets DEV_TIMEOUT and the
-// CTA stops after draining the loads it has in flight.
-// Shared memory: stage 0 | stage 1 (each ten padded groups, then the dense ES tiles) |
-// W (ten padded groups) | twiddles | two mbarriers.
+// tiles b, b + gridDim.x, ...  Two shared-memory stages, each holding one tile's nine Phi'
+// spectra, are filled by TMA loads (one cp.async.bulk.tensor per component, completing on the
+// stage's mbarrier) while the previous tile is transformed; the tile's bulk-fluid/Poisson
+// spectra arrive in one single-buffered area (third mbarrier), loaded while the previous tile's
+// inverse and this tile's forward transform run.  The ncomp_out results are written over the
+// first groups of the transformed tile and leave through TMA stores.  At length 256 both
+// transforms run in place (ct_fft_grouped_ip), which keeps the CTA within half an SM's shared
+// memory (two CTAs per SM instead of one); shorter lengths, where two CTAs fit anyway,
+// alternate with a scratch area W (one barrier per stage instead of two).  A tensor map views a half-spectrum array as (x: nxh * E, y: ny,
+// plane: nz * ncomp) 8-byte elements, E = sizeof(complex) / 8; a component tile is the box
+// (TZ * E, 1, NZ) at plane c * nz.  Columns past nxh read as zero and are not written.  A
+// wait that runs out sets DEV_TIMEOUT and the CTA stops after draining the loads it has in
+// flight.
+// Shared memory: stage 0 | stage 1 (nine padded groups each) | W (nine padded groups, below
+// length 256) | ES (nes dense tiles) | twiddles | three mbarriers.
 // ------------------------------------------------------------------------------------
+__host__ __device__ constexpr bool zbwd_in_place(int nz) { return nz >= 256; }
+
 template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zbwd_tma_smem(int nes) {
     using C = typename Cplx<Real>::type;
     constexpr size_t GS = size_t(ct_gstride(NZ, TZ, int(sizeof(C))));
-    return (2 * (DFT_NSPEC * GS + size_t(nes) * TZ * NZ) + DFT_NSPEC * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
+    constexpr size_t groups = (zbwd_in_place(NZ) ? 2 : 3) * size_t(DFT_NSPEC);
+    return (groups * GS + size_t(nes) * TZ * NZ + NZ) * sizeof(C) + 3 * sizeof(uint64_t) + 128;
 }
 
-template <typename Real, int NZ, int TZ, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const __grid_constant__ CUtensorMap map_phi,
-                                                         const __grid_constant__ CUtensorMap map_esA,
-                                                         const __grid_constant__ CUtensorMap map_esB, GridDesc g,
-                                                         SpeciesDesc<Real> sp, Real kfx, Real kfy, Real kfz, int flags,
-                                                         int ncomp_out, int has_esB, const Ctl* __restrict__ ctl,
-                                                         typename Cplx<Real>::type* es_mat, int ntiles_x, int ntiles,
-                                                         int* __restrict__ status,
-                                                         const typename Cplx<Real>::type* __restrict__ twz) {
+template <typename Real, int NZ, int TZ, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constant__ CUtensorMap map_phi,
+                                                            const __grid_constant__ CUtensorMap map_esA,
+                                                            const __grid_constant__ CUtensorMap map_esB, GridDesc g,
+                                                            SpeciesDesc<Real> sp, Real kfx, Real kfy, Real kfz,
+                                                            int flags, int ncomp_out, int has_esB,
+                                                            const Ctl* __restrict__ ctl,
+                                                            typename Cplx<Real>::type* es_mat, int ntiles_x,
+                                                            int ntiles, int* __restrict__ status,
+                                                            const typename Cplx<Real>::type* __restrict__ twz) {
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
     constexpr int PER = (TILE + NT - 1) / NT;
+    constexpr bool PF = PER == 1;
     constexpr int EMAX = DFT_MAXS + 1;
     constexpr uint32_t BOX = uint32_t(TILE * sizeof(C));
     static_assert(NZ > 0 && NZ <= 256 && (TZ * sizeof(C)) % 16 == 0 && BOX % 128 == 0, "z TMA tile");
     extern __shared__ unsigned char smem_raw[];
     const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
     const int nes = es_on ? ncomp_out * (has_esB ? 2 : 1) : 0;
-    const int stage_elems = DFT_NSPEC * GS + nes * TILE;
+    constexpr int stage_elems = DFT_NSPEC * GS;
+    constexpr bool IP = zbwd_in_place(NZ);
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
     C* const stage0 = reinterpret_cast<C*>(base);
-    C* W = stage0 + 2 * stage_elems;
-    C* tw = W + DFT_NSPEC * GS;
+    C* const W = stage0 + 2 * stage_elems;
+    C* const es_t = W + (IP ? 0 : stage_elems);
+    C* tw = es_t + nes * TILE;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
-    const uint32_t tile_bytes = uint32_t((hs ? DFT_NSPEC : 0) + nes) * BOX;
     const int S = sp.S, ny = g.ny, nxh = g.nxh;
     const long long zstride = (long long)ny * g.pxh;
 
-    auto issue = [&](int tile, int s) {
+    auto issue_phi = [&](int tile, int s) {
         C* st = stage0 + s * stage_elems;
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
-        tma::mbar_expect_tx(&bar[s], tile_bytes);
-        if (hs)
-            for (int c = 0; c < DFT_NSPEC; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
-        if (es_on) {
+        tma::mbar_expect_tx(&bar[s], uint32_t(DFT_NSPEC) * BOX);
+        for (int c = 0; c < DFT_NSPEC; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
+    };
+    auto issue_es = [&](int tile) {
+        const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
+        tma::mbar_expect_tx(&bar[2], uint32_t(nes) * BOX);
+        for (int c = 0; c < ncomp_out; ++c) tma::load_3d(es_t + c * TILE, &map_esA, x, y, c * NZ, &bar[2]);
+        if (has_esB)
             for (int c = 0; c < ncomp_out; ++c)
-                tma::load_3d(st + DFT_NSPEC * GS + c * TILE, &map_esA, x, y, c * NZ, &bar[s]);
-            if (has_esB)
-                for (int c = 0; c < ncomp_out; ++c)
-                    tma::load_3d(st + DFT_NSPEC * GS + (ncomp_out + c) * TILE, &map_esB, x, y, c * NZ, &bar[s]);
-        }
+                tma::load_3d(es_t + (ncomp_out + c) * TILE, &map_esB, x, y, c * NZ, &bar[2]);
     };
     if (threadIdx.x == 0) {
-        tma::mbar_init(&bar[0], 1);
-        tma::mbar_init(&bar[1], 1);
+        for (int b = 0; b < 3; ++b) tma::mbar_init(&bar[b], 1);
         tma::fence_mbar_init();
     }
     for (int i = threadIdx.x; i < NZ; i += NT) tw[i] = twz[i];
     __syncthreads();
-    // loads issued / consumed per stage, packed as (stage 1 << 16) | stage 0; meaningful in thread 0
-    int issued = 0, consumed = 0;
+    // Phi' loads issued / consumed per stage, packed as (stage 1 << 16) | stage 0, and ES loads
+    // issued / consumed; meaningful in thread 0
+    int issued = 0, consumed = 0, es_issued = 0, es_consumed = 0;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
-            const int tile = blockIdx.x + s * gridDim.x;
-            if (tile < ntiles) { issue(tile, s); issued += 1 << (16 * s); }
-        }
+        if (hs)
+            for (int s = 0; s < 2; ++s) {
+                const int tile = blockIdx.x + s * gridDim.x;
+                if (tile < ntiles) { issue_phi(tile, s); issued += 1 << (16 * s); }
+            }
+        if (es_on && blockIdx.x < ntiles) { issue_es(blockIdx.x); ++es_issued; }
     }
+    // on a wait that ran out: record it, let the copies in flight land, stop
+    auto drain = [&]() {
+        if (threadIdx.x == 0) {
+            atomicOr(status, DEV_TIMEOUT);
+            for (int s = 0; s < 2; ++s) {
+                const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
+                if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
+            }
+            if (es_issued > es_consumed) tma::mbar_wait(&bar[2], (es_issued - 1) & 1);
+        }
+    };
     const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
     const Real fourpi = Real(4.0 * CUDART_PI);
     const bool tab = sp.tab_w != nullptr;
@@ -1286,44 +1316,30 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
         const int cur = it & 1;
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
-        // table records of this thread's points, in flight while the tile arrives
-        Real wr[PER][DFT_TAB_W];
-        if (hs && tab) {
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const int idx = threadIdx.x + i * NT;
-                const int kzi = idx / TZ, kxi = kx0 + idx % TZ;
-                int m2 = 0;
-                if (((TILE % NT == 0) || idx < TILE) && kxi < nxh) {
-                    const int mz = signed_index(kzi, g.nz);
-                    m2 = kxi * kxi + my * my + mz * mz;
-                }
-                load_record(wr[i], sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
-            }
+        // with one point per thread, its table record is in flight while the tile arrives;
+        // with more, each point's record is loaded where it is used
+        Real wr[DFT_TAB_W];
+        if (PF && hs && tab) {
+            const int idx = threadIdx.x;
+            const int kxi = kx0 + idx % TZ;
+            const int m2 = (((TILE % NT == 0) || idx < TILE) && kxi < nxh) ? kmode2(kxi, my, idx / TZ, g.nz) : 0;
+            load_record(wr, sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
         }
-        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
-        // the previous tile's TMA stores have finished reading shared memory (W is written next)
-        if (threadIdx.x == 0) tma::wait_read_all();
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(status, DEV_TIMEOUT);
-                for (int s = 0; s < 2; ++s) {
-                    const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
-                    if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
-                }
-            }
-            break;
-        }
-        consumed += 1 << (16 * cur);
-        C* st = stage0 + cur * stage_elems;
-        const C* es_t = st + DFT_NSPEC * GS;
+        C* const st = stage0 + cur * stage_elems;
         C* X = st;
-        C* Y = W;
         if (hs) {
-            X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NSPEC, tw);
-            Y = (X == st) ? W : st;
+            const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+            if (__syncthreads_or(!ok)) { drain(); break; }
+            if (threadIdx.x == 0) consumed += 1 << (16 * cur);
+            if constexpr (IP) ct_fft_grouped_ip<NZ, false, TZ, GS, true, false, NT>(X, DFT_NSPEC, tw);
+            else X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NSPEC, tw);
         }
-#pragma unroll
+        // the ES tiles of this tile (loaded since the previous tile's pointwise phase); the
+        // barrier also ends the forward transform
+        const bool ok_es = es_on ? tma::mbar_wait(&bar[2], it & 1) : true;
+        if (__syncthreads_or(!ok_es)) { drain(); break; }
+        if (threadIdx.x == 0 && es_on) ++es_consumed;
+#pragma unroll 1
         for (int i = 0; i < PER; ++i) {
             const int idx = threadIdx.x + i * NT;
             if ((TILE % NT != 0) && idx >= TILE) break;
@@ -1347,6 +1363,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
                     if (s < ncomp_out) es_mat[(long long)s * g.nc + o] = out[s];
             }
             if (hs) {
+                if (!PF && tab)
+                    load_record(wr, sp.tab_w + (long long)(kxi < nxh ? kmode2(kxi, my, kzi, g.nz) : 0) * sp.tab_ws,
+                                2 * S);
                 const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
                 C asum[5];
                 bwd_sums<Real>(X, GS, pos, p, asum);
@@ -1356,7 +1375,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
                     if (s >= S) break;
                     Real w0, j3;
                     const Real Rs = sp.R[s];
-                    if (tab) { w0 = wr[i][2 * s]; j3 = wr[i][2 * s + 1]; }
+                    if (tab) { w0 = wr[2 * s]; j3 = wr[2 * s + 1]; }
                     else fmt_weights<Real>(p.kmag, Rs, &w0, &j3);
                     C mu = cscale(a0, w0);
                     mu = cadd(mu, cscale(a1, Rs * w0));
@@ -1366,24 +1385,30 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_zconv_bwd_tma(const _
                     out[s] = cmake<C>(out[s].x - mu.x, out[s].y - mu.y);
                 }
             }
+            // over the first groups at this thread's own position (read above, by this thread only)
 #pragma unroll
             for (int s = 0; s < EMAX; ++s)
-                if (s < ncomp_out) Y[s * GS + pos] = cscale(out[s], sp.inv_n);
+                if (s < ncomp_out) X[s * GS + pos] = cscale(out[s], sp.inv_n);
         }
         __syncthreads();
-        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(Y, X, ncomp_out, tw);
+        // the ES area is free: load the next tile's while this one is finished
+        if (threadIdx.x == 0 && es_on) {
+            const int next = tile + gridDim.x;
+            if (next < ntiles) { issue_es(next); ++es_issued; }
+        }
+        C* Q = X;
+        if constexpr (IP) ct_fft_grouped_ip<NZ, true, TZ, GS, false, true, NT>(X, ncomp_out, tw);
+        else Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(X, X == st ? W : st, ncomp_out, tw);
         tma::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int s = 0; s < ncomp_out; ++s) tma::store_3d(&map_phi, kx0 * E, kyi, s * NZ, Q + s * GS);
             tma::commit();
-            // the stage may be refilled at once unless the stores read from it; otherwise their
-            // shared-memory reads are awaited before the next tile writes W
-            if (Q == st) tma::wait_read_all();
+            // the stores read the stage or W: let them finish reading before either is written
+            tma::wait_read_all();
             const int next = tile + 2 * gridDim.x;
-            if (next < ntiles) { issue(next, cur); issued += 1 << (16 * cur); }
+            if (hs && next < ntiles) { issue_phi(next, cur); issued += 1 << (16 * cur); }
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0) tma::wait_all();
 }

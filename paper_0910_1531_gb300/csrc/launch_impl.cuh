@@ -177,10 +177,12 @@ cudaError_t LaunchZ<Real, N>::init() {
         if ((r = set_max_smem(dftk::k_zconv_fwd_g<Real, N, TZ, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_bwd_g<Real, N, TZ>)) != cudaSuccess) e = r;
         constexpr int TB = dft_tile_zb<Real>(N), TF = dft_tile_zf<Real>(N);
+        constexpr int NB = dft_zbwd_threads<Real>(N), MBB = dft_zbwd_minb<Real>(N);
+        constexpr int NF = dft_zfwd_threads<Real>(N), MBF = dft_zfwd_minb<Real>(N);
         if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0)
-            if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
+            if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, NB, MBB>)) != cudaSuccess) e = r;
         if constexpr ((TF * sizeof(typename Cplx<Real>::type)) % 16 == 0)
-            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, dft_zbwd_threads<Real>(N)>)) != cudaSuccess) e = r;
+            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, NF, MBF>)) != cudaSuccess) e = r;
     } else {
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
@@ -207,7 +209,7 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
         const size_t sm = dftk::zfwd_tma_smem<Real, N, TB>(sp.S);
         if (!red_energy && status && sm <= size_t(optin)) {
             // TMA path (the grand-potential sums keep the one-tile-per-CTA kernel below)
-            constexpr int NT = dft_zbwd_threads<Real>(N);
+            constexpr int NT = dft_zfwd_threads<Real>(N), MB = dft_zfwd_minb<Real>(N);
             constexpr int E = int(sizeof(C) / 8);
             CUtensorMap map_in, map_n;
             auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
@@ -221,10 +223,10 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
             const int ntx = (int)ceil_div(g.nxh, TB);
             const int ntiles = ntx * g.ny;
             int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_fwd_tma<Real, N, TB, NT>, NT, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB>, NT, sm);
             if (occ < 1) occ = 1;
             const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-            dftk::k_zconv_fwd_tma<Real, N, TB, NT><<<grid, NT, sm, st>>>(map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
+            dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB><<<grid, NT, sm, st>>>(map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
                                                                          slot_es, ntx, ntiles, status, tw);
             return cudaSuccess;
         }
@@ -268,8 +270,8 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
     }
     if constexpr (kTma) {
         if (dftk::zbwd_tma_smem<Real, N, TB>(nes) <= size_t(optin)) {
-            // TMA path: persistent CTAs, two TMA-filled stages (ten Phi' tiles + the ES tiles each)
-            constexpr int NT = dft_zbwd_threads<Real>(N);
+            // TMA path: persistent CTAs, two TMA-filled stages of nine Phi' tiles, one area of ES tiles
+            constexpr int NT = dft_zbwd_threads<Real>(N), MB = dft_zbwd_minb<Real>(N);
             constexpr int E = int(sizeof(C) / 8);
             CUtensorMap map_phi, map_esA, map_esB;
             auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
@@ -291,12 +293,12 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             }
             int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_bwd_tma<Real, N, TB, NT>, NT, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, NT, sm);
             if (occ < 1) occ = 1;
             const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
             // the status word of the device control block records a TMA wait that ran out
             int* status = const_cast<int*>(&ctl->status);
-            dftk::k_zconv_bwd_tma<Real, N, TB, NT><<<grid, NT, sm, st>>>(
+            dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB><<<grid, NT, sm, st>>>(
                 map_phi, map_esA, map_esB, g, sp, kfx, kfy, kfz, flags, ncomp_out, esB ? 1 : 0, ctl, es_mat, ntx, ntiles,
                 status, tw);
             return cudaSuccess;

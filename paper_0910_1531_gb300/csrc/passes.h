@@ -37,14 +37,13 @@ template <typename Real> __host__ __device__ constexpr int dft_tile_z(int n) {
 }
 
 // Persistent TMA z passes: half the grouped width (at least 16 bytes of a row, the TMA
-// minimum); 256 threads (two CTAs per SM) up to length 128, 512 at 256 where the two stages
-// leave room for one CTA per SM; DFT_ZBWD_THREADS (build flag) overrides the thread count.
+// minimum).
 template <typename Real> __host__ __device__ constexpr int dft_tile_zb(int n) {
     const int t = dft_tile_z<Real>(n) / 2, tmin = sizeof(Real) == 4 ? 2 : 1;
     return t > tmin ? t : tmin;
 }
 // Tile width of the persistent TMA first-half z pass: the second half's (DFT_ZFWD_WIDE: the
-// grouped width, two CTAs per SM still fitting at length 128 with three species).
+// grouped width).
 template <typename Real> __host__ __device__ constexpr int dft_tile_zf(int n) {
 #ifdef DFT_ZFWD_WIDE
     return dft_tile_z<Real>(n);
@@ -53,11 +52,39 @@ template <typename Real> __host__ __device__ constexpr int dft_tile_zf(int n) {
 #endif
 }
 
+// Threads of the persistent TMA z passes and the resident CTAs per SM their register budget
+// is sized for.  First half: 256 threads, two CTAs per SM, up to length 128; 512 threads, one
+// CTA, at 256.  Second half: 256 threads, three CTAs per SM (FP32; two in FP64, whose
+// butterflies need twice the registers), up to 128; 288 threads (nine warps: one pass of the
+// threads covers the radix-16 butterflies of the nine Phi' groups of a two-column tile), two
+// CTAs per SM, at 256 (its shared memory allows no more).  DFT_ZFWD_THREADS / DFT_ZFWD_MINB / DFT_ZBWD_THREADS / DFT_ZBWD_MINB (build
+// flags) override.
+template <typename Real> __host__ __device__ constexpr int dft_zfwd_threads(int n) {
+#ifdef DFT_ZFWD_THREADS
+    return DFT_ZFWD_THREADS;
+#else
+    return n >= 256 ? 512 : 256;
+#endif
+}
+template <typename Real> __host__ __device__ constexpr int dft_zfwd_minb(int n) {
+#ifdef DFT_ZFWD_MINB
+    return DFT_ZFWD_MINB;
+#else
+    return dft_zfwd_threads<Real>(n) <= 256 ? 2 : 1;
+#endif
+}
 template <typename Real> __host__ __device__ constexpr int dft_zbwd_threads(int n) {
 #ifdef DFT_ZBWD_THREADS
     return DFT_ZBWD_THREADS;
 #else
-    return n >= 256 ? 512 : 256;
+    return n >= 256 ? 288 : 256;
+#endif
+}
+template <typename Real> __host__ __device__ constexpr int dft_zbwd_minb(int n) {
+#ifdef DFT_ZBWD_MINB
+    return DFT_ZBWD_MINB;
+#else
+    return (n < 256 && sizeof(Real) == 4) ? 3 : 2;
 #endif
 }
 
