@@ -34,6 +34,7 @@
 namespace dftk {
 
 constexpr int kThreads = 256;
+constexpr int kFinThreads = 1024;   // the one-block line-search bookkeeping kernel
 
 // Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
 #ifndef DFT_XUPD_KP
@@ -2166,16 +2167,35 @@ __device__ __forceinline__ void set_weights(Ctl* c, double a) {
     c->wA = 1.0 - a; c->wB = a; c->w0 = 1.0 - a; c->w1 = a;
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
-                                                       const float* __restrict__ red_max, int nmax, int op,
-                                                       double inv_count, double alpha_fixed, double n3_bound,
-                                                       double alpha_floor) {
+__global__ void __launch_bounds__(kFinThreads) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
+                                                          const float* __restrict__ red_max, int nmax, int op,
+                                                          double inv_count, double alpha_fixed, double n3_bound,
+                                                          double alpha_floor) {
     __shared__ double scratch_d[32];
     __shared__ float scratch_f[32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nsum; i += blockDim.x) s += red_sum[i];
-    float m = -CUDART_INF_F;
-    for (int i = threadIdx.x; i < nmax; i += blockDim.x) m = fmaxf(m, red_max[i]);
+    // four independent partial results per thread, so that a thread's loads are all in flight
+    // at once (the partial sums are L2-resident: the kernel is a few load latencies long)
+    constexpr int B = kFinThreads;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * B < nsum; i += 4 * B) {
+        s0 += red_sum[i];
+        s1 += red_sum[i + B];
+        s2 += red_sum[i + 2 * B];
+        s3 += red_sum[i + 3 * B];
+    }
+    for (; i < nsum; i += B) s0 += red_sum[i];
+    const double s = (s0 + s1) + (s2 + s3);
+    float m0 = -CUDART_INF_F, m1 = -CUDART_INF_F, m2 = -CUDART_INF_F, m3 = -CUDART_INF_F;
+    i = threadIdx.x;
+    for (; i + 3 * B < nmax; i += 4 * B) {
+        m0 = fmaxf(m0, red_max[i]);
+        m1 = fmaxf(m1, red_max[i + B]);
+        m2 = fmaxf(m2, red_max[i + 2 * B]);
+        m3 = fmaxf(m3, red_max[i + 3 * B]);
+    }
+    for (; i < nmax; i += B) m0 = fmaxf(m0, red_max[i]);
+    const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
     const double tot = block_sum(s, scratch_d);
     const float mx = block_max(m, scratch_f);
     if (threadIdx.x != 0) return;
