@@ -43,16 +43,23 @@ NCU_TRAFFIC = {
 
 
 def workload(args):
-    """The bench workload: 3-species obstacles (128^3 by default), or the pore/slab geometry
-    with eight confined half-charged O (fixed number; 256^3, h = 0.05 nm by default)."""
+    """The bench workload: 3-species obstacles (128^3 by default), the pore/slab geometry with
+    eight confined half-charged O (fixed number; 256^3, h = 0.05 nm by default), or the paper's
+    ionic hard-wall calculation (21 x 21 x 161, 1 M univalent salt)."""
     from paper_0910_1531_gb300 import workloads
     if args.workload == "pore256":
         return workloads.pore_slab_4species(n=args.n or 256, h=0.05)
+    if args.workload == "wall161":
+        return workloads.hard_wall_ionic()
     n = args.n or 128
     return workloads.obstacles_3species(n=n, h=0.05 * 128 / n, seed=1)
 
 
 def workload_config(w):
+    if w.name.startswith("hard_wall"):
+        return {"geometry": "hard uncharged wall at z = 0 in a periodic 2 x 2 x 6 nm cell",
+                "h_nm_xyz": list(w.h),
+                "paper_time_to_solution": "1.5 min (Sec. Results, the authors' 2009 cluster; tolerance not stated)"}
     if w.n_fixed is not None:
         return {"geometry": "hard slab |z - L/2| < 1 nm with a 0.5 nm-radius pore along z",
                 "n_fixed": list(map(float, w.n_fixed)),
@@ -376,7 +383,12 @@ def run_ours(args):
     alpha = args.alpha if args.alpha is not None else (0.05 if args.workload == "pore256" else -1.0)
     if args.converge_tol is None:
         # the pore's FP32 floor of the weighted residual is ~3e-5 (FP64 reaches 1e-6)
-        args.converge_tol = (1e-4 if args.precision == "fp32" else 1e-6) if args.workload == "pore256" else 0.0
+        if args.workload == "pore256":
+            args.converge_tol = 1e-4 if args.precision == "fp32" else 1e-6
+        elif args.workload == "wall161":
+            args.converge_tol = 1e-5 if args.precision == "fp32" else 1e-8
+        else:
+            args.converge_tol = 0.0
     if args.solver is None:
         args.solver = "newton" if args.workload == "pore256" else "picard"
     # x-pass rows per block timed on this workload (cached per shape inside the library)
@@ -508,7 +520,9 @@ def run_ours(args):
                            "ms_per_step_launched": ms_prof / args.steps,
                            "x_rows_per_block": x_lines,
                            "parallelism": f"replicas x{world}",
-                           "l2": f"no flush: working set {working_set/1e6:.0f} MB > L2 129 MB",
+                           "l2": (f"no flush: working set {working_set/1e6:.0f} MB > L2 129 MB" if working_set > L2_BYTES
+                                  else f"no flush: working set {working_set/1e6:.0f} MB fits the 129 MB L2 "
+                                       "(L2-resident; the time-to-tolerance line is the comparison)"),
                            "resid_after": resid_after},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "kernels": kernels, "cufft_comparator": cufft}
@@ -531,7 +545,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
-    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64"])
+    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161"])
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--alpha", type=float, default=None,
                     help="fixed Picard mixing (default: line search; 0.05 for pore256, where the line search stalls)")

@@ -101,23 +101,6 @@ dft_status fail(dft_plan* p, dft_status code, const std::string& msg) {
     return code;
 }
 
-bool radix_plan(int n, AxisPlan* out) {
-    out->n = n;
-    out->nstages = 0;
-    int m = n;
-    while (m % 3 == 0) { out->radix[out->nstages++] = 3; m /= 3; }
-    while (m >= 16 && m % 16 == 0) { out->radix[out->nstages++] = 16; m /= 16; }
-    if (m == 2 || m == 4 || m == 8) { out->radix[out->nstages++] = m; m = 1; }
-    return m == 1 && out->nstages <= DFT_MAXSTAGES && out->nstages > 0;
-}
-
-bool valid_n(int n) {
-    if (n < 4 || n > 512) return false;
-    int m = n;
-    while (m % 2 == 0) m /= 2;
-    while (m % 3 == 0) m /= 3;
-    return m == 1;
-}
 
 // Shared-memory budget of a pass's row block (bytes); a positive environment value overrides it.
 size_t env_budget(const char* name, size_t dflt) {
@@ -878,8 +861,8 @@ const char* dft_last_error(const dft_plan* plan) {
 dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** out) {
     if (!prm || !out) return fail(nullptr, DFT_EINVAL, "NULL params or out");
     *out = nullptr;
-    if (!valid_n(prm->nx) || !valid_n(prm->ny) || !valid_n(prm->nz))
-        return fail(nullptr, DFT_EINVAL, "grid sizes must be 2^a 3^b with 4 <= n <= 512");
+    if (!dft_valid_length(prm->nx) || !dft_valid_length(prm->ny) || !dft_valid_length(prm->nz))
+        return fail(nullptr, DFT_EINVAL, "grid sizes must be 4 <= n <= 512 with prime factors <= 31");
     if (!(prm->hx > 0 && prm->hy > 0 && prm->hz > 0)) return fail(nullptr, DFT_EINVAL, "grid spacing must be > 0");
     if (prm->nspecies < 1 || prm->nspecies > DFT_MAX_SPECIES) return fail(nullptr, DFT_EINVAL, "nspecies out of range");
     if (!prm->radius_nm || !prm->valence || !prm->bulk_molar) return fail(nullptr, DFT_EINVAL, "NULL species array");
@@ -932,7 +915,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->kf[0] = two_pi / (g.nx * g.hx);
     p->kf[1] = two_pi / (g.ny * g.hy);
     p->kf[2] = two_pi / (g.nz * g.hz);
-    if (!radix_plan(g.nx, &p->ax) || !radix_plan(g.ny, &p->ay) || !radix_plan(g.nz, &p->az)) {
+    if (!dft_radix_plan(g.nx, &p->ax) || !dft_radix_plan(g.ny, &p->ay) || !dft_radix_plan(g.nz, &p->az)) {
         delete p;
         return fail(nullptr, DFT_EINVAL, "no radix plan for the grid sizes");
     }
@@ -943,6 +926,15 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->rsize = f64 ? sizeof(double) : sizeof(float);
     p->Ty = f64 ? Passes<double>::tile_y(g.ny, 100 * 1024) : Passes<float>::tile_y(g.ny, 100 * 1024);
     p->Tz = f64 ? Passes<double>::tile_z(g.nz, 112 * 1024) : Passes<float>::tile_z(g.nz, 112 * 1024);
+    {   // run-time lengths: narrower column tiles while a column pass would have fewer than two
+        // CTAs per SM (small grids)
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || sms < 1) sms = 1;
+        if (!dft_is_ct_size(g.ny))
+            while (p->Ty > 1 && ceil_div(g.nxh, p->Ty) * g.nz < 2LL * sms) p->Ty /= 2;
+        if (!dft_is_ct_size(g.nz))
+            while (p->Tz > 1 && ceil_div(g.nxh, p->Tz) * g.ny < 2LL * sms) p->Tz /= 2;
+    }
     p->LX = pick_lines(g.nx, p->csize, 1, env_budget("DFT_XFWD_SMEM", 48 * 1024), 32);
     p->LRphi = pick_lines(g.nx, p->csize, 5, env_budget("DFT_XPHI_SMEM", 32 * 1024), 16);
     p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, env_budget("DFT_XUPD_SMEM", 48 * 1024), 16);

@@ -32,12 +32,43 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmake<C>(-a.y, a.x); }
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
 
-// Radix decomposition of one axis length: n = prod radix[s]; radices in {2,3,4,8,16}.
+// Radix decomposition of one axis length: n = prod radix[s]; radices 2, 3, 4, 8, 16 and the
+// odd primes 5..DFT_MAX_PRIME (run-time transforms only; see dft_radix_plan).
 struct AxisPlan {
     int n;
     int nstages;
     int radix[DFT_MAXSTAGES];
 };
+
+// Largest prime factor an axis length may have.  Factors 5..31 take a direct odd-radix stage
+// (the R-point DFT by its definition) in the run-time transforms.
+#define DFT_MAX_PRIME 31
+
+// Radix plan of an axis length: the 3s, then the other odd primes up to DFT_MAX_PRIME, then
+// 16s and one of 2 / 4 / 8.  False if n has a larger prime factor or needs more than
+// DFT_MAXSTAGES stages.
+inline bool dft_radix_plan(int n, AxisPlan* out) {
+    out->n = n;
+    out->nstages = 0;
+    int m = n;
+    auto push = [&](int r) {
+        if (out->nstages >= DFT_MAXSTAGES) return false;
+        out->radix[out->nstages++] = r;
+        return true;
+    };
+    while (m % 3 == 0) { if (!push(3)) return false; m /= 3; }
+    for (int p = 5; p <= DFT_MAX_PRIME; p += 2)
+        while (m % p == 0) { if (!push(p)) return false; m /= p; }
+    while (m >= 16 && m % 16 == 0) { if (!push(16)) return false; m /= 16; }
+    if (m == 2 || m == 4 || m == 8) { if (!push(m)) return false; m = 1; }
+    return m == 1 && out->nstages > 0;
+}
+
+// Axis lengths a plan accepts: 4 <= n <= 512 with a radix plan.
+inline bool dft_valid_length(int n) {
+    AxisPlan p;
+    return n >= 4 && n <= 512 && dft_radix_plan(n, &p);
+}
 
 // Grid of one state point.  Real fields: [c][nz][ny][nx]; half spectra after the
 // x transform: [c][nz][ny][pxh], of which kx < nxh = nx/2 + 1 are used; the row pitch

@@ -133,6 +133,40 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
     }
 }
 
+// Stage of an odd prime radix R without a dedicated butterfly (5 <= R <= DFT_MAX_PRIME): the
+// R-point DFT by its definition, out_q = sum_r v_r W_R^(r q), W_R = exp(-+2 pi i / R).  The stage
+// twiddle of v_r and W_R^(r q) are both powers of exp(-+2 pi i / n), so each term takes one
+// table entry, tw[(k r n/(Ns R) + (r q mod R) n/R) mod n].  R^2 terms per butterfly, one output
+// per thread.
+template <bool INV, typename C>
+__device__ __forceinline__ void stockham_stage_odd(const C* __restrict__ src, C* __restrict__ dst, int n, int ns,
+                                                   int R, int lines, int es, int ls, const C* __restrict__ tw) {
+    const int m = n / R;
+    const int twstep = n / (ns * R);
+    const int total = m * lines * R;
+    // one output q of one butterfly per task (R times the tasks of a butterfly per thread)
+    for (int task = threadIdx.x; task < total; task += blockDim.x) {
+        const int q = task % R;
+        const int bt = task / R;
+        const int line = bt % lines;
+        const int j = bt / lines;
+        const int k = j % ns;
+        const int base = (j / ns) * ns * R + k;
+        C acc = cmake<C>(0, 0);
+        int rq = 0;   // r q mod R
+        for (int r = 0; r < R; ++r) {
+            int e = k * r * twstep + rq * m;
+            if (e >= n) e -= n;
+            C w = tw[e];
+            if (INV) w.y = -w.y;
+            acc = cadd(acc, cmul(src[(j + r * m) * es + line * ls], w));
+            rq += q;
+            if (rq >= R) rq -= R;
+        }
+        dst[(base + q * ns) * es + line * ls] = acc;
+    }
+}
+
 // Transform all lines held in `a` (b is scratch of the same size).  The caller must
 // __syncthreads() before the call (data in a visible).  Returns the buffer holding
 // the result; all threads see it on return.
@@ -146,7 +180,8 @@ __device__ C* smem_fft(C* a, C* b, const AxisPlan& p, int lines, int es, int ls,
             case 3: stockham_stage<3, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
             case 4: stockham_stage<4, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
             case 8: stockham_stage<8, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
-            default: stockham_stage<16, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            case 16: stockham_stage<16, INV>(a, b, p.n, ns, lines, es, ls, tw); break;
+            default: stockham_stage_odd<INV>(a, b, p.n, ns, R, lines, es, ls, tw); break;
         }
         __syncthreads();
         C* t = a; a = b; b = t;

@@ -67,23 +67,6 @@ __global__ void k_twiddles(float2* tw, int n) {
     }
 }
 
-bool radix_plan_na(int n, AxisPlan* out) {
-    out->n = n;
-    out->nstages = 0;
-    int m = n;
-    while (m % 3 == 0) { out->radix[out->nstages++] = 3; m /= 3; }
-    while (m >= 16 && m % 16 == 0) { out->radix[out->nstages++] = 16; m /= 16; }
-    if (m == 2 || m == 4 || m == 8) { out->radix[out->nstages++] = m; m = 1; }
-    return m == 1 && out->nstages > 0 && out->nstages <= DFT_MAXSTAGES;
-}
-
-bool valid_n_na(int n) {
-    if (n < 4 || n > 512) return false;
-    int m = n;
-    while (m % 2 == 0) m /= 2;
-    while (m % 3 == 0) m /= 3;
-    return m == 1;
-}
 
 int lines_for(int nx, int per_unit, size_t budget, int cap) {
     const long long avail = (long long)(budget / sizeof(float2)) - nx;
@@ -109,8 +92,8 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
 #define FAIL(code, msg) return fail_na(errbuf, errbuf_len, code, msg)
     if (!prm || !rho || !n_out) FAIL(DFT_EINVAL, "NULL argument");
     if (prm->precision != DFT_FP32_STAB) FAIL(DFT_EINVAL, "only DFT_FP32_STAB is supported");
-    if (!valid_n_na(prm->nx) || !valid_n_na(prm->ny) || !valid_n_na(prm->nz))
-        FAIL(DFT_EINVAL, "grid sizes must be 2^a 3^b with 4 <= n <= 512");
+    if (!dft_valid_length(prm->nx) || !dft_valid_length(prm->ny) || !dft_valid_length(prm->nz))
+        FAIL(DFT_EINVAL, "grid sizes must be 4 <= n <= 512 with prime factors <= 31");
     if (!(prm->hx > 0 && prm->hy > 0 && prm->hz > 0)) FAIL(DFT_EINVAL, "grid spacing must be > 0");
     const int S = prm->nspecies;
     if (S < 1 || S > DFT_MAX_SPECIES || !prm->radius_nm) FAIL(DFT_EINVAL, "bad species");
@@ -125,7 +108,7 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     g.nc = (long long)g.nz * g.ny * g.pxh;
     g.hx = prm->hx; g.hy = prm->hy; g.hz = prm->hz;
     AxisPlan ax, ay, az;
-    if (!radix_plan_na(g.nx, &ax) || !radix_plan_na(g.ny, &ay) || !radix_plan_na(g.nz, &az))
+    if (!dft_radix_plan(g.nx, &ax) || !dft_radix_plan(g.ny, &ay) || !dft_radix_plan(g.nz, &az))
         FAIL(DFT_EINVAL, "no radix plan for the grid sizes");
 
     // scratch layout (float2 elements): status word | twiddles x, y, z | S spectra | 10 weighted

@@ -168,6 +168,28 @@ def pore_slab_4species(n=256, h=0.05, slab_half=1.0, pore_radius=0.5, pore_half=
                     notes={"slab_half_nm": slab_half, "pore_radius_nm": pore_radius, "pore_half_nm": pore_half})
 
 
+def hard_wall_ionic(nxy=21, nz=161, lxy=2.0, lz=6.0, molar=1.0, tol=1e-8, max_it=2000):
+    """Univalent salt at a hard, uncharged wall (Sec. "Results", the representative ionic
+    calculation): cation R 0.1 nm, anion R 0.2125 nm, `molar` each, in a periodic
+    lxy x lxy x lz nm cell on an nxy x nxy x nz grid (h_d = L_d / N_d) with a zero-thickness wall
+    in the plane z = 0.  The cell is periodic along z, so the wall bounds the fluid from both
+    sides: species i is excluded where the minimum-image distance to the plane is < R_i.
+    """
+    names = ["cation(0.1)", "anion(0.2125)"]
+    radius = np.array([0.1, 0.2125])
+    z = np.array([1.0, -1.0])
+    shape = (nz, nxy, nxy)
+    hh = (lxy / nxy, lxy / nxy, lz / nz)
+    zc, _, _ = grid_coordinates(shape, hh)
+    dist = np.abs(_min_image(zc, lz))
+    V = np.zeros((2,) + shape, dtype=np.float64)
+    for i in range(2):
+        V[i][np.broadcast_to(dist < radius[i], shape)] = np.inf
+    return Workload(name=f"hard_wall_ionic_{nxy}x{nxy}x{nz}", shape=shape, h=hh, species=names, radius=radius,
+                    z=z, bulk_molar=np.array([molar, molar]), V=V, mixing=None, max_it=max_it, tol=tol,
+                    notes={"cell_nm": [lxy, lxy, lz], "wall": "z = 0 plane, hard, uncharged"})
+
+
 def gaussian_random_field(shape, h, corr_len, std, seed):
     """Zero-mean periodic Gaussian field with covariance ~ exp(-r^2 / (2 l^2)), scaled to `std`."""
     rng = np.random.default_rng(seed)

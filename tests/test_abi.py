@@ -51,7 +51,7 @@ def _params(nx=16, ny=16, nz=16, radius=(0.095, 0.181), z=(1.0, -1.0), molar=(0.
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(nx=20), -1),                     # 20 = 4 * 5: not 2^a 3^b
+    (dict(nx=74), -1),                     # 74 = 2 * 37: prime factor above 31
     (dict(nx=1024), -1),                   # above 512
     (dict(nx=2), -1),                      # below 4
     (dict(radius=(0.0, 0.181)), -1),       # R <= 0

@@ -73,6 +73,8 @@ CASES = [
     ((48, 48, 48), 0.1, 3),
     ((4, 6, 64), 0.05, 5),         # thin grid, five species
     ((6, 4, 12), 0.1, 1),          # single uncharged species (Gamma = 0)
+    ((35, 21, 10), (0.1, 0.09, 0.11), 2),   # odd radices 5 and 7 (z 5*7, y 3*7, x 5*2)
+    ((23, 22, 14), 0.08, 3),       # radix 23 (z), 11 (y), 7 (x)
 ]
 
 
