@@ -1,7 +1,8 @@
 """Bath (bulk) thermodynamics, App. A (test infrastructure only).
 
 * Percus-Yevick / scaled-particle hard-sphere bath chemical potential
-  (eq. muHSBath) and pressure (eq. HSPressure), with sigma_i = 2 R_i.
+  (eq. muHSBath) and pressure (eq. HSPressure), with sigma_i = 2 R_i; for the White Bear
+  functional (an alternative Phi_HS, see fmt.py) the uniform limit of that functional instead.
 * MSA screening parameter Gamma from the implicit equation eq. Gamma, with the
   auxiliary eta and Omega printed beneath it, and the electrostatic bath
   chemical potential mu^{ES,bath} printed last in App. A.
@@ -114,11 +115,31 @@ class Bath:
         return self.mu_hs + self.mu_es
 
 
-def make_bath(rho, radius, z, lb):
+def hs_bath_fmt(rho, radius, kind):
+    """(beta mu^HS_i, beta P^HS) of a uniform fluid under the FMT form `kind` (fmt.KINDS): with
+    n_alpha = sum_j rho_j w_hat_j^alpha(0) (the fundamental measures 1, R, 4 pi R^2, 4 pi R^3/3)
+    and n_V = 0, beta mu_i = sum_alpha dPhi/dn_alpha w_hat_i^alpha(0) and beta P = n0 + sum_alpha
+    n_alpha dPhi/dn_alpha - Phi.  For rslt and rosenfeld this is App. A's Percus-Yevick bath."""
+    from . import fmt
+    rho = np.asarray(rho, dtype=np.float64)
+    R = np.asarray(radius, dtype=np.float64)
+    w = [np.ones_like(R), R, 4.0 * math.pi * R ** 2, 4.0 * math.pi * R ** 3 / 3.0]
+    n = [float(np.sum(rho * wa)) for wa in w]
+    zero = [0.0, 0.0, 0.0]
+    d = fmt.phi_derivatives(n[0], n[1], n[2], n[3], zero, zero, kind)[:4]
+    mu = sum(float(d[a]) * w[a] for a in range(4))
+    beta_p = n[0] + sum(n[a] * float(d[a]) for a in range(4)) - float(fmt.phi(n[0], n[1], n[2], n[3], zero, zero, kind))
+    return mu, beta_p
+
+
+def make_bath(rho, radius, z, lb, functional="rslt"):
     rho = np.asarray(rho, dtype=np.float64)
     radius = np.asarray(radius, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
-    mu_hs, beta_p = hs_bath(rho, radius)
+    if functional == "white_bear":
+        mu_hs, beta_p = hs_bath_fmt(rho, radius, functional)
+    else:
+        mu_hs, beta_p = hs_bath(rho, radius)
     gamma = msa_gamma(rho, radius, z, lb)
     mu_es = msa_mu(rho, radius, z, lb, gamma)
     lam = radius + (0.5 / gamma if gamma > 0.0 else np.inf)

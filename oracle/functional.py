@@ -73,7 +73,8 @@ class Problem:
     bulk_molar in mol/L.
     """
 
-    def __init__(self, shape, h, radius, z, bulk_molar, temperature_K=298.15, eps_r=78.5, n_fixed=None):
+    def __init__(self, shape, h, radius, z, bulk_molar, temperature_K=298.15, eps_r=78.5, n_fixed=None,
+                 functional="rslt"):
         self.shape = tuple(int(s) for s in shape)
         if np.isscalar(h):
             h = (h, h, h)
@@ -83,7 +84,11 @@ class Problem:
         self.nspecies = len(self.radius)
         self.lb = bjerrum_length_nm(temperature_K, eps_r)
         rho_b = np.array([molar_to_per_nm3(c) for c in bulk_molar], dtype=np.float64)
-        self.bath = make_bath(rho_b, self.radius, self.z, self.lb)
+        # hard-sphere free-energy density: eq. Phi ("rslt") or another form of fmt.KINDS
+        if functional not in fmt.KINDS:
+            raise ValueError(f"unknown functional {functional!r}")
+        self.functional = functional
+        self.bath = make_bath(rho_b, self.radius, self.z, self.lb, functional)
         self.npoints = self.shape[0] * self.shape[1] * self.shape[2]
         self.dv = self.h[0] * self.h[1] * self.h[2]
         # Fixed-number (canonical) species: n_fixed[i] > 0 particles in the box, not in the bath
@@ -121,14 +126,14 @@ def weighted_densities(prob, rho):
     return np.real(fourier.idft3(np.stack(acc)))
 
 
-def phi_derivative_fields(n):
+def phi_derivative_fields(n, kind="rslt"):
     """The ten dPhi/dn_alpha fields for weighted densities n (10, Nz, Ny, Nx)."""
-    d0, d1, d2, d3, dV1, dV2 = fmt.phi_derivatives(n[0], n[1], n[2], n[3], n[4:7], n[7:10])
+    d0, d1, d2, d3, dV1, dV2 = fmt.phi_derivatives(n[0], n[1], n[2], n[3], n[4:7], n[7:10], kind)
     return np.stack([d0, d1, d2, d3] + list(dV1) + list(dV2))
 
 
-def phi_field(n):
-    return fmt.phi(n[0], n[1], n[2], n[3], n[4:7], n[7:10])
+def phi_field(n, kind="rslt"):
+    return fmt.phi(n[0], n[1], n[2], n[3], n[4:7], n[7:10], kind)
 
 
 def mu_hs(prob, dphi):
@@ -174,7 +179,7 @@ def mu_sc(prob, rho):
 def c1_hs(prob, rho):
     """-beta mu_HS_i(x): the hard-sphere one-body direct correlation."""
     n = weighted_densities(prob, rho)
-    return -mu_hs(prob, phi_derivative_fields(n))
+    return -mu_hs(prob, phi_derivative_fields(n, prob.functional))
 
 
 def c1_es(prob, rho):
@@ -186,7 +191,7 @@ def c1_es(prob, rho):
 def excess_mu(prob, rho):
     """beta mu_ex_i(x) = beta (mu_HS + mu_SC + z e phi) (eq. excessChemicalPotential)."""
     n = weighted_densities(prob, rho)
-    return (mu_hs(prob, phi_derivative_fields(n)) + mu_sc(prob, rho)
+    return (mu_hs(prob, phi_derivative_fields(n, prob.functional)) + mu_sc(prob, rho)
             + prob.z[:, None, None, None] * psi(prob, rho)[None])
 
 
@@ -228,7 +233,7 @@ def grand_potential(prob, rho, V):
         ideal = np.where(rho > 0.0, rho * (np.log(rho / rb) - 1.0), 0.0)
         ext = np.where(acc, rho * (V - prob.bath.mu_ex[:, None, None, None]), 0.0)
     n = weighted_densities(prob, rho)
-    f_hs = np.sum(phi_field(n))
+    f_hs = np.sum(phi_field(n, prob.functional))
     q = np.tensordot(prob.z, rho, axes=(0, 0))
     f_mf = 0.5 * np.sum(q * psi(prob, rho))
     drho = rho - rb
@@ -253,7 +258,8 @@ def grad_omega_v(prob, rho):
     return prob.dv * rho
 
 
-def grad_omega_bulk(shape, h, radius, z, bulk_molar, rho, V, temperature_K=298.15, eps_r=78.5, rel=1e-3):
+def grad_omega_bulk(shape, h, radius, z, bulk_molar, rho, V, temperature_K=298.15, eps_r=78.5, rel=1e-3,
+                    functional="rslt"):
     """dOmega/drho_bath_k / kT (kT nm^3) at fixed rho and V, by its definition: central differences
     of Omega over the bath density with steps rel*c_k and rel*c_k/2, Richardson-extrapolated.  The
     bath (mu_ex_bath, mu_ES_bath, Gamma) and the bulk-fluid kernel are recomputed at every
@@ -267,8 +273,10 @@ def grad_omega_bulk(shape, h, radius, z, bulk_molar, rho, V, temperature_K=298.1
             cp, cm = c.copy(), c.copy()
             cp[k] += step
             cm[k] = max(c[k] - step, 0.0)
-            op = grand_potential(Problem(shape, h, radius, z, cp, temperature_K, eps_r), rho, V)
-            om = grand_potential(Problem(shape, h, radius, z, cm, temperature_K, eps_r), rho, V)
+            op = grand_potential(Problem(shape, h, radius, z, cp, temperature_K, eps_r, functional=functional),
+                                 rho, V)
+            om = grand_potential(Problem(shape, h, radius, z, cm, temperature_K, eps_r, functional=functional),
+                                 rho, V)
             est.append((op - om) / (cp[k] - cm[k]))
         out[k] = (4.0 * est[1] - est[0]) / 3.0 / molar_to_per_nm3(1.0)
     return out

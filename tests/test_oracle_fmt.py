@@ -83,3 +83,97 @@ def test_uniform_limit_is_percus_yevick(rho, R):
     assert np.allclose(mu, mu_py, rtol=1e-13)
     p = np.sum(rho) + np.sum(np.asarray(rho) * mu) - fmt.phi(n0, n1, n2, n3, zero, zero)
     assert p == pytest.approx(p_py, rel=1e-13)
+
+
+# ---- the other hard-sphere forms (Rosenfeld 1989, White Bear 2002) ----------------------------
+
+@pytest.mark.parametrize("kind", ["rosenfeld", "white_bear"])
+def test_other_forms_derivatives_match_central_differences(kind):
+    rng = np.random.default_rng(6)
+    state = _random_state(rng)
+    state[3] = np.concatenate([rng.uniform(1e-4, 0.05, 10), rng.uniform(0.05, 0.85, 30)])   # both WB branches
+    v = _flat(state)
+    d = fmt.phi_derivatives(*_unflat(v), kind=kind)
+    dflat = np.concatenate([[d[0], d[1], d[2], d[3]], d[4], d[5]])
+    for a in range(10):
+        eps = 3e-4 * np.maximum(np.abs(v[a]), 0.1)
+        if a == 3:
+            eps = np.minimum(eps, 0.2 * v[3])
+
+        def at(t):
+            w = v.copy()
+            w[a] = w[a] + t * eps
+            return fmt.phi(*_unflat(w), kind=kind)
+        fd = (-at(2) + 8 * at(1) - 8 * at(-1) + at(-2)) / (12 * eps)
+        assert np.allclose(dflat[a], fd, rtol=1e-7, atol=1e-8), (kind, a)
+
+
+def test_rosenfeld_form_equals_eq_phi_without_vectors_and_white_bear_tends_to_it():
+    # With n_V = 0 the original Rosenfeld form is eq. Phi; White Bear's f(n3) -> 1/(24 pi) as n3 -> 0.
+    rng = np.random.default_rng(7)
+    n0, n1, n2, n3, _, _ = _random_state(rng)
+    zero = [0.0, 0.0, 0.0]
+    assert np.allclose(fmt.phi(n0, n1, n2, n3, zero, zero, kind="rosenfeld"), fmt.phi(n0, n1, n2, n3, zero, zero),
+                       rtol=1e-14)
+    f, _ = fmt._tensor_f(np.array([1e-9]), "white_bear")
+    assert f[0] == pytest.approx(1.0 / (24.0 * math.pi), rel=1e-8)
+
+
+def test_white_bear_series_matches_closed_form():
+    # Below n3 = 0.5 g(n3) = (n3 + D^2 ln D)/n3^2 is summed as a series; compare with the closed form
+    # where the closed form keeps its digits (n3 >= 0.05) and with high-precision values at small n3.
+    n3 = np.linspace(0.05, 0.499, 50)
+    g, dg = fmt._wb_g(n3)
+    d = 1.0 - n3
+    ln_d = np.log(d)
+    num = n3 + d * d * ln_d
+    assert np.allclose(g, num / n3 ** 2, rtol=1e-12)
+    assert np.allclose(dg, (n3 - 2 * d * ln_d) / n3 ** 2 - 2 * num / n3 ** 3, rtol=1e-9)
+    import decimal
+    decimal.getcontext().prec = 60
+    for t in ("1e-6", "0.001", "0.02"):
+        x = decimal.Decimal(t)
+        dd = 1 - x
+        exact = (x + dd * dd * dd.ln()) / (x * x)
+        assert float(fmt._wb_g(np.array([float(x)]))[0][0]) == pytest.approx(float(exact), rel=1e-14)
+
+
+@pytest.mark.parametrize("eta", [1e-5, 0.1, 0.25, 0.4])
+def test_white_bear_uniform_limit_is_carnahan_starling(eta):
+    # One component: beta mu_ex = (8 eta - 9 eta^2 + 3 eta^3)/(1 - eta)^3 and
+    # beta P / rho = (1 + eta + eta^2 - eta^3)/(1 - eta)^3 (Carnahan-Starling).
+    from oracle.bulk import hs_bath_fmt
+    R = 0.1
+    rho = eta / (4.0 / 3.0 * math.pi * R ** 3)
+    mu, p = hs_bath_fmt([rho], [R], "white_bear")
+    e = eta
+    assert mu[0] == pytest.approx((8 * e - 9 * e ** 2 + 3 * e ** 3) / (1 - e) ** 3, rel=1e-12, abs=1e-15)
+    assert p == pytest.approx(rho * (1 + e + e ** 2 - e ** 3) / (1 - e) ** 3, rel=1e-12)
+
+
+@pytest.mark.parametrize("rho,R", [
+    ([0.602, 0.602], [0.1, 0.2125]),
+    ([3.0, 1.0, 0.5], [0.1, 0.15, 0.2]),
+])
+def test_white_bear_uniform_mixture_pressure_is_bmcsl(rho, R):
+    # Mixture: beta P = (6/pi) [xi0/D + 3 xi1 xi2/D^2 + (3 - xi3) xi2^3/D^3] (BMCSL), xi_n = (pi/6)
+    # sum rho sigma^n; the chemical potentials obey Gibbs-Duhem with it (dP = sum rho_i dmu_i).
+    from oracle.bulk import hs_bath_fmt
+    rho, R = np.asarray(rho), np.asarray(R)
+    sig = 2 * R
+    xi = [math.pi / 6 * np.sum(rho * sig ** n) for n in range(4)]
+    D = 1 - xi[3]
+    p_bmcsl = 6 / math.pi * (xi[0] / D + 3 * xi[1] * xi[2] / D ** 2 + (3 - xi[3]) * xi[2] ** 3 / D ** 3)
+    mu, p = hs_bath_fmt(rho, R, "white_bear")
+    assert p == pytest.approx(p_bmcsl, rel=1e-12)
+    for k in range(len(rho)):
+        h = 1e-5 * rho[k]
+        rp, rm = rho.copy(), rho.copy()
+        rp[k] += h
+        rm[k] -= h
+        mp, pp = hs_bath_fmt(rp, R, "white_bear")
+        mm, pm = hs_bath_fmt(rm, R, "white_bear")
+        # ideal part: d(sum rho)/drho_k = 1 plus sum_i rho_i dmu_ex_i/drho_k
+        lhs = (pp - pm) / (2 * h)
+        rhs = 1.0 + np.sum(rho * (mp - mm) / (2 * h))
+        assert lhs == pytest.approx(rhs, rel=1e-7)
