@@ -52,9 +52,18 @@ typedef enum {
 
 enum { DFT_FP32_STAB = 0, DFT_FP64 = 1 };
 enum { DFT_MAX_SPECIES = 5 };
+/* Hard-sphere free-energy density Phi_HS (dft_params.functional).  The paper uses the
+ * antisymmetrised Rosenfeld form, eq. Phi (DFT_PHI_RSLT, the default, with the |nV2| <= n2
+ * bound of Sec. "Numerical Stability"), and notes that the other Phi_HS it cites leave the
+ * numerical scheme unchanged: DFT_PHI_ROSENFELD (original 1989 form, last term
+ * (n2^3 - 3 n2 nV2.nV2) / (24 pi (1 - n3)^2)) and DFT_PHI_WHITE_BEAR (2002 form, last term
+ * (n2^3 - 3 n2 nV2.nV2) (n3 + (1 - n3)^2 ln(1 - n3)) / (36 pi n3^2 (1 - n3)^2)).  The bath
+ * mu^HS and P are App. A's Percus-Yevick values for the first two and the uniform limit of the
+ * White Bear form (Carnahan-Starling / BMCSL) for the third. */
+enum { DFT_PHI_RSLT = 0, DFT_PHI_ROSENFELD = 1, DFT_PHI_WHITE_BEAR = 2 };
 
 typedef struct {
-    int nx, ny, nz;                 /* grid points per axis; each 2^a 3^b, 4 <= n <= 512 */
+    int nx, ny, nz;                 /* grid points per axis, 4 <= n <= 512, prime factors <= 31 */
     double hx, hy, hz;              /* spacing (nm); periodic box L_d = n_d h_d */
     int nspecies;                   /* 1 .. DFT_MAX_SPECIES */
     const double* radius_nm;        /* [nspecies] hard-sphere radii R_i > 0 */
@@ -70,16 +79,18 @@ typedef struct {
      * of eq. rhoEquation); its residual weight is its mean density n_fixed[i] / (N h^3).
      * dft_grad rejects plans with such species (DFT_EINVAL). */
     const double* n_fixed;
+    int functional;                 /* DFT_PHI_RSLT (0, eq. Phi), DFT_PHI_ROSENFELD or DFT_PHI_WHITE_BEAR */
 } dft_params;
 
 /*
  * Create a plan: checks the parameters, computes the bath thermodynamics of
- * App. A (Percus-Yevick mu^HS and P, MSA Gamma, eta, Omega and mu^ES; Gamma
- * by Newton's method as in App. A), builds the FFT plans of each axis and
- * allocates scratch on the current CUDA device.
+ * App. A (Percus-Yevick mu^HS and P -- or the White Bear uniform limit, see
+ * DFT_PHI_WHITE_BEAR --, MSA Gamma, eta, Omega and mu^ES; Gamma by Newton's
+ * method as in App. A), builds the FFT plans of each axis and allocates scratch
+ * on the current CUDA device.
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * Rejects (DFT_EINVAL) sizes outside the supported set, R <= 0, negative
- * concentrations, a bath packing fraction >= 0.9; rejects a bath with
+ * concentrations, a bath packing fraction >= 0.9, an unknown functional; rejects a bath with
  * |sum z_i c_i| > 1e-12 sum |z_i| c_i (DFT_ENONNEUTRAL).
  * On success *out owns device memory until dft_plan_destroy.
  */

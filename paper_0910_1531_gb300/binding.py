@@ -41,7 +41,11 @@ class DftParams(ctypes.Structure):
                 ("bulk_molar", ctypes.POINTER(ctypes.c_double)),
                 ("temperature_K", ctypes.c_double), ("eps_r", ctypes.c_double),
                 ("precision", ctypes.c_int),
-                ("n_fixed", ctypes.POINTER(ctypes.c_double))]
+                ("n_fixed", ctypes.POINTER(ctypes.c_double)),
+                ("functional", ctypes.c_int)]
+
+# dft_params.functional: the hard-sphere free-energy density (include/gb300dft.h, DFT_PHI_*)
+FUNCTIONALS = {"rslt": 0, "rosenfeld": 1, "white_bear": 2}
 
 
 _P = ctypes.c_void_p
@@ -110,7 +114,7 @@ class Plan:
     """One state point: grid, species and bath; owns the library plan and its scratch."""
 
     def __init__(self, shape, h, radius, valence, bulk_molar, temperature_K=298.15, eps_r=78.5,
-                 precision="fp32", stream=None, device=None, n_fixed=None):
+                 precision="fp32", stream=None, device=None, n_fixed=None, functional="rslt"):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -132,7 +136,8 @@ class Plan:
         prm = DftParams(nx, ny, nz, self.h[0], self.h[1], self.h[2], self.nspecies,
                         pd(self._arrays[0]), pd(self._arrays[1]), pd(self._arrays[2]),
                         float(temperature_K), float(eps_r), self.precision,
-                        pd(self._arrays[3]) if n_fixed is not None else None)
+                        pd(self._arrays[3]) if n_fixed is not None else None,
+                        FUNCTIONALS[functional] if isinstance(functional, str) else int(functional))
         with torch.cuda.device(self.device):
             if stream is None:
                 stream = torch.cuda.current_stream(self.device)

@@ -472,8 +472,8 @@ bool bath_derivatives(dft_plan* p, BathDerivs* d, std::string* err) {
             cm[k] = c - hh;
             if (cm[k] < 0.0) cm[k] = 0.0;
             const double span = cp[k] - cm[k];
-            if (!compute_bath(S, p->R.data(), p->z.data(), cp.data(), p->T, p->eps_r, &bp, err) ||
-                !compute_bath(S, p->R.data(), p->z.data(), cm.data(), p->T, p->eps_r, &bm, err))
+            if (!compute_bath(S, p->R.data(), p->z.data(), cp.data(), p->T, p->eps_r, &bp, err, p->g.phi) ||
+                !compute_bath(S, p->R.data(), p->z.data(), cm.data(), p->T, p->eps_r, &bm, err, p->g.phi))
                 return false;
             for (int i = 0; i < S; ++i) {
                 dex[lev][i] = ((bp.mu_hs[i] + bp.mu_es[i]) - (bm.mu_hs[i] + bm.mu_es[i])) / span;
@@ -899,12 +899,19 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         }
     p->T = prm->temperature_K;
     p->eps_r = prm->eps_r;
+    if (prm->functional != DFT_PHI_RSLT && prm->functional != DFT_PHI_ROSENFELD &&
+        prm->functional != DFT_PHI_WHITE_BEAR) {
+        delete p;
+        return fail(nullptr, DFT_EINVAL, "unknown functional");
+    }
     std::string err;
-    if (!compute_bath(S, p->R.data(), p->z.data(), p->molar.data(), p->T, p->eps_r, &p->bath, &err)) {
+    if (!compute_bath(S, p->R.data(), p->z.data(), p->molar.data(), p->T, p->eps_r, &p->bath, &err,
+                      prm->functional)) {
         delete p;
         return fail(nullptr, DFT_EINVAL, err);
     }
     GridDesc& g = p->g;
+    g.phi = prm->functional;
     g.nx = prm->nx; g.ny = prm->ny; g.nz = prm->nz;
     g.nxh = g.nx / 2 + 1;
     g.pxh = (g.nxh + 1) & ~1;

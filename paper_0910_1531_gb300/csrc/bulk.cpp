@@ -4,6 +4,8 @@
 // The paper's "epsilon" is read as eps0 eps_r throughout, so e^2/(kT eps) = 4 pi lambda_B.
 #include "bulk.h"
 
+#include "gb300dft.h"
+
 #include <cmath>
 
 namespace {
@@ -45,8 +47,48 @@ struct Msa {
 };
 }  // namespace
 
+// White Bear uniform fluid: Phi = -n0 ln D + n1 n2 / D + n2^3 g(n3) / (36 pi D^2), D = 1 - n3,
+// g = (n3 + D^2 ln D) / n3^2 (power series of ln D below n3 = 1/2, where the closed form
+// cancels).  beta mu_i = sum_alpha dPhi/dn_alpha w_i^alpha(0) with the fundamental measures
+// w_i(0) = (1, R_i, 4 pi R_i^2, 4 pi R_i^3 / 3); beta P = n0 + sum_alpha n_alpha dPhi/dn_alpha - Phi.
+static void white_bear_bath(int S, const double* rho, const double* radius, double* mu, double* beta_p) {
+    double n[4] = {0, 0, 0, 0};
+    for (int j = 0; j < S; ++j) {
+        const double R = radius[j];
+        n[0] += rho[j];
+        n[1] += rho[j] * R;
+        n[2] += rho[j] * 4.0 * kPi * R * R;
+        n[3] += rho[j] * 4.0 * kPi * R * R * R / 3.0;
+    }
+    const double D = 1.0 - n[3], lnD = std::log(D);
+    double g, dg;
+    if (n[3] < 0.5) {
+        double sg = 0.0, sd = 0.0;
+        for (int k = 60; k >= 3; --k) {
+            sg = sg * n[3] + 2.0 / (double(k) * (k - 1) * (k - 2));
+            sd = sd * n[3] + 2.0 / (double(k) * (k - 1));
+        }
+        g = 1.5 - n[3] * sg;
+        dg = -sd;
+    } else {
+        const double num = n[3] + D * D * lnD;
+        g = num / (n[3] * n[3]);
+        dg = (n[3] - 2.0 * D * lnD) / (n[3] * n[3]) - 2.0 * num / (n[3] * n[3] * n[3]);
+    }
+    const double f = g / (36.0 * kPi * D * D);
+    const double df = (dg * D + 2.0 * g) / (36.0 * kPi * D * D * D);
+    const double phi = -n[0] * lnD + n[1] * n[2] / D + n[2] * n[2] * n[2] * f;
+    const double d[4] = {-lnD, n[2] / D, n[1] / D + 3.0 * n[2] * n[2] * f,
+                         n[0] / D + n[1] * n[2] / (D * D) + n[2] * n[2] * n[2] * df};
+    for (int i = 0; i < S; ++i) {
+        const double R = radius[i];
+        mu[i] = d[0] + d[1] * R + d[2] * 4.0 * kPi * R * R + d[3] * 4.0 * kPi * R * R * R / 3.0;
+    }
+    *beta_p = n[0] + n[0] * d[0] + n[1] * d[1] + n[2] * d[2] + n[3] * d[3] - phi;
+}
+
 bool compute_bath(int S, const double* radius, const double* z, const double* molar, double T, double eps_r,
-                  BathState* out, std::string* err) {
+                  BathState* out, std::string* err, int functional) {
     out->rho.assign(S, 0.0);
     out->mu_hs.assign(S, 0.0);
     out->mu_es.assign(S, 0.0);
@@ -69,6 +111,7 @@ bool compute_bath(int S, const double* radius, const double* z, const double* mo
         out->mu_hs[i] = -std::log(delta) + (3.0 * xi[2] * s + 3.0 * xi[1] * s * s) / delta
                         + 9.0 * xi[2] * xi[2] * s * s / (2.0 * delta * delta) + kPi * out->beta_p * s * s * s / 6.0;
     }
+    if (functional == DFT_PHI_WHITE_BEAR) white_bear_bath(S, out->rho.data(), radius, out->mu_hs.data(), &out->beta_p);
     // MSA Gamma (eq. Gamma) by Newton on F with a numerical derivative, kept in [lo, hi]
     double k2 = 0.0;
     for (int j = 0; j < S; ++j) k2 += 4.0 * kPi * out->lb * out->rho[j] * z[j] * z[j];

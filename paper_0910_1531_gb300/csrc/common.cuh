@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gb300dft.h"
+
 #define DFT_MAXS 5          // species (the back-convolution keeps 5 k-space accumulators)
 #define DFT_MAXSTAGES 8     // radix stages per axis
 #define DFT_NCOMP 10        // n0 n1 n2 n3 nV1(xyz) nV2(xyz)
@@ -79,6 +81,7 @@ struct GridDesc {
     long long n;     // nx * ny * nz
     long long nc;    // nz * ny * pxh (elements per half-spectrum component)
     double hx, hy, hz;
+    int phi;         // hard-sphere free-energy density of the state point (DFT_PHI_*; 0 = eq. Phi)
 };
 
 // Species constants in the kernels' precision (host fills them in double, then converts).

@@ -1420,22 +1420,60 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
 // formed in FP64 where n3 >= 0.5, i.e. where n3 approaches 1; below, 1 - n3 is exact in the
 // working precision and log1p / the reciprocal are within 2 ulp.  Returns false if n3 >= 1.
 // ------------------------------------------------------------------------------------
-// Phi itself (eq. Phi), in FP64, for the grand potential; same clamp as the derivatives.
-template <typename Real> __device__ __forceinline__ double phi_value(const Real* n) {
+// White Bear g(n3) = (n3 + D^2 ln D) / n3^2 and g'(n3), D = 1 - n3 (the other forms' last term
+// is (n2^3 - 3 n2 nV2.nV2) f(n3), f = g / (36 pi D^2) for White Bear).  Below n3 = 1/2 the closed
+// form cancels, so the power series of ln D is summed: g = 3/2 - sum_{k>=3} 2 n3^(k-2) /
+// (k (k-1) (k-2)), g' = -sum_{k>=3} 2 n3^(k-3) / (k (k-1)), to k = 24 (FP32) / 52 (FP64), where
+// the truncation is below the working precision; from 1/2 up the closed form in FP64 with
+// lnD_hi = ln D.
+template <typename Real>
+__device__ __forceinline__ void wb_g(Real n3, double lnD_hi, Real* g, Real* dg) {
+    if (n3 < Real(0.5)) {
+        constexpr int K = sizeof(Real) == 4 ? 24 : 52;
+        Real sg = Real(0), sd = Real(0);
+#pragma unroll
+        for (int k = K; k >= 3; --k) {
+            sg = sg * n3 + Real(2.0 / (double(k) * double(k - 1) * double(k - 2)));
+            sd = sd * n3 + Real(2.0 / (double(k) * double(k - 1)));
+        }
+        *g = Real(1.5) - n3 * sg;
+        *dg = -sd;
+    } else {
+        const double u = double(n3), d = 1.0 - u, num = u + d * d * lnD_hi;
+        *g = Real(num / (u * u));
+        *dg = Real((u - 2.0 * d * lnD_hi) / (u * u) - 2.0 * num / (u * u * u));
+    }
+}
+
+// Phi itself (eq. Phi, or the form `kind`), in FP64, for the grand potential; same clamp as the
+// derivatives.
+template <typename Real> __device__ __forceinline__ double phi_value(const Real* n, int kind) {
     const double n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     const double D = 1.0 - n3;
     const double q = double(n[7]) * n[7] + double(n[8]) * n[8] + double(n[9]) * n[9];
+    const double dot = double(n[4]) * n[7] + double(n[5]) * n[8] + double(n[6]) * n[9];
+    const double base = -n0 * log(D) + (n1 * n2 - dot) / D;
+    if (kind == DFT_PHI_ROSENFELD) return base + (n2 * n2 * n2 - 3.0 * n2 * q) / (24.0 * CUDART_PI * D * D);
+    if (kind == DFT_PHI_WHITE_BEAR) {
+        double g, dg;
+        wb_g<double>(n3, log(D), &g, &dg);
+        return base + (n2 * n2 * n2 - 3.0 * n2 * q) * g / (36.0 * CUDART_PI * D * D);
+    }
     double xi = (n2 > 1e-30) ? q / (n2 * n2) : 1.0;
     xi = xi < 0.0 ? 0.0 : (xi > 1.0 ? 1.0 : xi);
     const double om = 1.0 - xi;
-    const double dot = double(n[4]) * n[7] + double(n[5]) * n[8] + double(n[6]) * n[9];
-    return -n0 * log(D) + (n1 * n2 - dot) / D + n2 * n2 * n2 * om * om * om / (24.0 * CUDART_PI * D * D);
+    return base + n2 * n2 * n2 * om * om * om / (24.0 * CUDART_PI * D * D);
 }
 
-template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n) {
+// The derivatives of eq. Phi (kind DFT_PHI_RSLT) or of the other forms, whose last term
+// T f(n3), T = n2^3 - 3 n2 nV2.nV2, gives dPhi/dn2 += 3 (n2^2 - nV2.nV2) f, dPhi/dn3 += T f',
+// dPhi/dnV2 += -6 n2 f nV2 (no clamp); f = 1/(24 pi D^2) (Rosenfeld) or g/(36 pi D^2) (White
+// Bear, f' = (g' D + 2 g)/(36 pi D^3)).
+template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n, int kind) {
     const Real n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     const Real v1x = n[4], v1y = n[5], v1z = n[6], v2x = n[7], v2y = n[8], v2z = n[9];
     Real lnD, fiD;
+    double lnD_hi = 0.0;
     bool ok = true;
     if (n3 < Real(0.5)) {
         lnD = log1p(-n3);
@@ -1443,24 +1481,45 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
     } else {
         const double D = 1.0 - double(n3);
         ok = D > 0.0;
-        lnD = Real(log(D));
+        lnD_hi = log(D);
+        lnD = Real(lnD_hi);
         fiD = Real(1.0 / D);
     }
     const Real fiD2 = fiD * fiD, fiD3 = fiD2 * fiD;
     const Real q = v2x * v2x + v2y * v2y + v2z * v2z;
-    Real xi = (n2 > Real(1e-30)) ? q / (n2 * n2) : Real(1);
-    xi = xi < Real(0) ? Real(0) : (xi > Real(1) ? Real(1) : xi);
-    const Real om = Real(1) - xi;
     const Real dot = v1x * v2x + v1y * v2y + v1z * v2z;
     const Real pi = Real(CUDART_PI);
     n[0] = -lnD;
     n[1] = n2 * fiD;
-    n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 / (Real(8) * pi);
-    n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 / (Real(12) * pi);
-    const Real cv = n2 * om * om * fiD2 / (Real(4) * pi);
     n[4] = -v2x * fiD;
     n[5] = -v2y * fiD;
     n[6] = -v2z * fiD;
+    if (kind != DFT_PHI_RSLT) {
+        Real f, df;
+        if (kind == DFT_PHI_ROSENFELD) {
+            f = fiD2 / (Real(24) * pi);
+            df = fiD3 / (Real(12) * pi);
+        } else {
+            Real g, dg;
+            wb_g<Real>(n3, lnD_hi, &g, &dg);
+            f = g * fiD2 / (Real(36) * pi);
+            df = (dg * fiD2 + Real(2) * g * fiD3) / (Real(36) * pi);
+        }
+        const Real T = n2 * n2 * n2 - Real(3) * n2 * q;
+        const Real c6 = Real(6) * n2 * f;
+        n[2] = n1 * fiD + Real(3) * (n2 * n2 - q) * f;
+        n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + T * df;
+        n[7] = -v1x * fiD - c6 * v2x;
+        n[8] = -v1y * fiD - c6 * v2y;
+        n[9] = -v1z * fiD - c6 * v2z;
+        return ok;
+    }
+    Real xi = (n2 > Real(1e-30)) ? q / (n2 * n2) : Real(1);
+    xi = xi < Real(0) ? Real(0) : (xi > Real(1) ? Real(1) : xi);
+    const Real om = Real(1) - xi;
+    n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 / (Real(8) * pi);
+    n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 / (Real(12) * pi);
+    const Real cv = n2 * om * om * fiD2 / (Real(4) * pi);
     n[7] = -v1x * fiD - cv * v2x;
     n[8] = -v1y * fiD - cv * v2y;
     n[9] = -v1z * fiD - cv * v2z;
@@ -1725,8 +1784,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
             n[7] = v2.y; n[4] = v3.x; n[6] = v3.y; n[8] = v4.x; n[9] = v4.y;
         }
         if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
-        if (red_phi && row0 + r < nrows) phi_acc += phi_value<Real>(n);
-        const bool ok = phi_derivatives<Real>(n);
+        if (red_phi && row0 + r < nrows) phi_acc += phi_value<Real>(n, g.phi);
+        const bool ok = phi_derivatives<Real>(n, g.phi);
         if (!ok && row0 + r < nrows) bad = true;
         base[0] = cmake<C>(n[0], n[1]);
         base[pitch] = cmake<C>(n[2], n[5]);

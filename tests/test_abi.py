@@ -41,12 +41,12 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(binding.SIGNATURES)
 
 
-def _params(nx=16, ny=16, nz=16, radius=(0.095, 0.181), z=(1.0, -1.0), molar=(0.1, 0.1), precision=0):
+def _params(nx=16, ny=16, nz=16, radius=(0.095, 0.181), z=(1.0, -1.0), molar=(0.1, 0.1), precision=0, functional=0):
     from paper_0910_1531_gb300.binding import DftParams
     arrs = [np.array(radius, dtype=np.float64), np.array(z, dtype=np.float64), np.array(molar, dtype=np.float64)]
     pd = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     prm = DftParams(nx, ny, nz, 0.1, 0.1, 0.1, len(radius), pd(arrs[0]), pd(arrs[1]), pd(arrs[2]), 298.15, 78.5,
-                    precision)
+                    precision, None, functional)
     return prm, arrs
 
 
@@ -59,6 +59,7 @@ def _params(nx=16, ny=16, nz=16, radius=(0.095, 0.181), z=(1.0, -1.0), molar=(0.
     (dict(molar=(0.1, 0.2)), -2),          # not electroneutral
     (dict(molar=(60.0, 60.0)), -1),        # bath packing fraction >= 0.9
     (dict(precision=7), -1),
+    (dict(functional=3), -1),              # unknown hard-sphere form
 ])
 def test_plan_create_rejects_invalid_parameters(lib, kw, code):
     prm, keep = _params(**kw)
