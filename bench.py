@@ -51,11 +51,17 @@ def workload(args):
         return workloads.pore_slab_4species(n=args.n or 256, h=0.05)
     if args.workload == "wall161":
         return workloads.hard_wall_ionic()
+    if args.workload == "hswall":
+        return workloads.hard_wall_hs(args.eta)
     n = args.n or 128
     return workloads.obstacles_3species(n=n, h=0.05 * 128 / n, seed=1)
 
 
 def workload_config(w):
+    if w.name.startswith("hard_sphere_wall"):
+        return {"geometry": "hard spheres R 0.1 nm at a hard wall at z = 0, periodic 0.2 x 0.2 x 3.2 nm",
+                "eta": w.notes["eta"], "h_nm_xyz": list(w.h),
+                "paper_time_to_solution": "< 1.5 h on a laptop at liquid densities (Sec. Hard sphere fluids)"}
     if w.name.startswith("hard_wall"):
         return {"geometry": "hard uncharged wall at z = 0 in a periodic 2 x 2 x 6 nm cell",
                 "h_nm_xyz": list(w.h),
@@ -387,10 +393,13 @@ def run_ours(args):
             args.converge_tol = 1e-4 if args.precision == "fp32" else 1e-6
         elif args.workload == "wall161":
             args.converge_tol = 1e-5 if args.precision == "fp32" else 1e-8
+        elif args.workload == "hswall":
+            # FP32 floor of the weighted residual at eta = 0.4: ~1.1e-6
+            args.converge_tol = 2e-6 if args.precision == "fp32" else 1e-10
         else:
             args.converge_tol = 0.0
     if args.solver is None:
-        args.solver = "newton" if args.workload == "pore256" else "picard"
+        args.solver = "newton" if args.workload in ("pore256", "hswall") else "picard"
     # x-pass rows per block timed on this workload (cached per shape inside the library)
     x_lines = plan.autotune(rho, V)
     plan.iter_begin(rho, V)
@@ -545,7 +554,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
-    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161"])
+    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161", "hswall"])
+    ap.add_argument("--eta", type=float, default=0.4, help="bath packing fraction of --workload hswall")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--alpha", type=float, default=None,
                     help="fixed Picard mixing (default: line search; 0.05 for pore256, where the line search stalls)")

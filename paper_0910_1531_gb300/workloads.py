@@ -190,6 +190,27 @@ def hard_wall_ionic(nxy=21, nz=161, lxy=2.0, lz=6.0, molar=1.0, tol=1e-8, max_it
                     notes={"cell_nm": [lxy, lxy, lz], "wall": "z = 0 plane, hard, uncharged"})
 
 
+def hard_wall_hs(eta, nz=512, nxy=4, hz=0.00625, hxy=0.05, radius=0.1, tol=1e-10, max_it=5000):
+    """Hard spheres of radius `radius` at bath packing fraction `eta` against a hard wall (Sec.
+    "Hard sphere fluids": R 0.1 nm, packing fractions 1e-5 ... 0.4, voxels 0.05 x 0.05 x 0.00625
+    nm, the effectively one-dimensional problem computed in full 3D).  The paper gives no domain
+    size; here nxy x nxy x nz voxels, periodic, with a zero-thickness wall in the plane z = 0 seen
+    from both sides (excluded where the minimum-image distance to the plane is < R).  The contact
+    density is rho at z = R (grid index R / hz when that is an integer)."""
+    rho = eta / (4.0 / 3.0 * np.pi * radius ** 3)
+    shape = (nz, nxy, nxy)
+    hh = (hxy, hxy, hz)
+    zc, _, _ = grid_coordinates(shape, hh)
+    lz = nz * hz
+    dist = np.abs(_min_image(zc, lz))
+    V = np.zeros((1,) + shape, dtype=np.float64)
+    V[0][np.broadcast_to(dist < radius, shape)] = np.inf
+    return Workload(name=f"hard_sphere_wall_eta{eta:g}_{nxy}x{nxy}x{nz}", shape=shape, h=hh, species=["HS(0.1)"],
+                    radius=np.array([radius]), z=np.array([0.0]), bulk_molar=np.array([rho / 0.602214076]), V=V,
+                    mixing=None, max_it=max_it, tol=tol,
+                    notes={"eta": eta, "contact_index": radius / hz, "wall": "z = 0 plane, hard"})
+
+
 def gaussian_random_field(shape, h, corr_len, std, seed):
     """Zero-mean periodic Gaussian field with covariance ~ exp(-r^2 / (2 l^2)), scaled to `std`."""
     rng = np.random.default_rng(seed)

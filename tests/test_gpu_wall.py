@@ -108,3 +108,44 @@ def test_wall_fp32_converges_to_fp64_solution(wall, wall_fp64_solution):
     acc = ~np.isinf(w.V)
     for s in range(2):
         assert relerr(got[s][acc[s]], ref[s][acc[s]]) < 1e-4
+
+
+# ---- hard spheres at a hard wall (Sec. "Hard sphere fluids", eq. sumRule) ----------------------
+
+def _solve_fp64(w, tol=1e-10):
+    from paper_0910_1531_gb300 import binding
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp64")
+    beta_p = plan.bulk()["beta_p"]
+    rho = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=torch.float64, device="cuda")
+    V = torch.tensor(w.V, dtype=torch.float64, device="cuda")
+    it, r, ok = plan.solve(rho, V, tol=tol, max_it=3000)
+    if not ok:
+        _, _, r, ok = plan.solve_newton(rho, V, tol, max_newton=100, krylov_dim=40)
+    plan.close()
+    assert ok, r
+    return rho.cpu().numpy(), beta_p
+
+
+@pytest.mark.parametrize("eta", [0.1, 0.3])
+def test_hard_sphere_wall_contact_sum_rule(eta):
+    # the contact density converges to beta P at first order in h_z; two Richardson steps leave
+    # the sum rule satisfied to 1e-4
+    devs = []
+    for nz, hz in ((128, 0.0125), (256, 0.00625), (512, 0.003125)):
+        w = workloads.hard_wall_hs(eta, nz=nz, hz=hz)
+        rho, beta_p = _solve_fp64(w)
+        assert np.max(np.ptp(rho, axis=(2, 3))) < 1e-12 * np.max(rho)
+        devs.append(rho[0, int(round(0.1 / hz)), 0, 0] / beta_p - 1.0)
+    e1, e2, e3 = devs
+    assert 1.9 < e1 / e2 < 2.1 and 1.9 < e2 / e3 < 2.1
+    assert abs((4 * (2 * e3 - e2) - (2 * e2 - e1)) / 3) < 1e-4
+
+
+def test_hard_sphere_wall_solution_matches_oracle():
+    w = workloads.hard_wall_hs(0.2, nz=128, hz=0.0125)
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+    ref, it, r = P.solve(prob, w.initial_rho_nm3(prob.bath.rho), w.V, tol=1e-11, max_it=300)
+    assert r < 1e-11
+    got, _ = _solve_fp64(w, tol=1e-11)
+    acc = ~np.isinf(w.V)
+    assert relerr(got[acc], ref[acc]) < 1e-9

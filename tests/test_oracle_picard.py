@@ -126,3 +126,25 @@ def test_canonical_iteration_conserves_number_and_converges():
     assert r < 1e-6
     # the weight of the residual is the species' mean density
     assert prob.rho_ref[3] == pytest.approx(8.0 / (prob.npoints * prob.dv))
+
+
+def test_hard_wall_contact_sum_rule_under_refinement():
+    # Sec. "Hard sphere fluids", eq. sumRule: at a hard wall the contact density of a hard-sphere
+    # fluid equals the bath pressure, beta P = rho(R).  On the grid the contact value converges to
+    # it at first order in h_z (the deviation halves with h_z); two Richardson steps (first- then
+    # second-order) remove the discretisation error.  eta = 0.1, R = 0.1 nm, a 1.6 nm periodic
+    # slit at h_z = 0.0125, 0.00625, 0.003125 nm.
+    devs = []
+    for nz, hz in ((128, 0.0125), (256, 0.00625), (512, 0.003125)):
+        w = workloads.hard_wall_hs(0.1, nz=nz, nxy=2, hz=hz)
+        prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar)
+        rho0 = w.initial_rho_nm3(prob.bath.rho)
+        rho, it, r = picard.solve(prob, rho0, w.V, tol=1e-11, max_it=200)
+        assert r < 1e-11
+        assert np.max(np.ptp(rho, axis=(2, 3))) < 1e-12 * np.max(rho)
+        devs.append(rho[0, int(round(0.1 / hz)), 0, 0] / prob.bath.beta_p - 1.0)
+    e1, e2, e3 = devs
+    assert 1.9 < e1 / e2 < 2.1 and 1.9 < e2 / e3 < 2.1
+    r1a, r1b = 2 * e2 - e1, 2 * e3 - e2
+    assert abs((4 * r1b - r1a) / 3) < 1e-4
+    assert abs(e2) > 0.01   # the unextrapolated value is off by about 1 %: the pin is the limit
