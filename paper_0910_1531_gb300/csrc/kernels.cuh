@@ -1087,22 +1087,16 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
         // table records of this thread's points, in flight while the tile arrives
-        Real wr[PER][DFT_TAB_W];
-        Real kr[PER][DFT_TAB_K];
-        if (tab) {
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const int idx = threadIdx.x + i * NT;
-                const int kzi = idx / TZ, kxi = kx0 + idx % TZ;
-                int m2 = 0;
-                if (((TILE % NT == 0) || idx < TILE) && kxi < nxh) {
-                    const int mz = signed_index(kzi, g.nz);
-                    m2 = kxi * kxi + my * my + mz * mz;
-                }
-                load_record(wr[i], sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
-                load_record(kr[i], sp.tab_k + (long long)m2 * sp.tab_ks, Pn);
-            }
-        }
+        // (the first point's; a thread's later points load theirs at the top of their iteration)
+        Real wr[DFT_TAB_W];
+        Real kr[DFT_TAB_K];
+        auto load_tab = [&](int idx) {
+            const int kxi = kx0 + idx % TZ;
+            const int m2 = (((TILE % NT == 0) || idx < TILE) && kxi < nxh) ? kmode2(kxi, my, idx / TZ, g.nz) : 0;
+            load_record(wr, sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
+            load_record(kr, sp.tab_k + (long long)m2 * sp.tab_ks, Pn);
+        };
+        if (tab) load_tab(threadIdx.x);
         const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
         // the previous tile's TMA stores have finished reading shared memory
         if (threadIdx.x == 0) tma::wait_read_all();
@@ -1119,10 +1113,11 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
         consumed += 1 << (16 * cur);
         C* st = stage0 + cur * stage_elems;
         C* X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, Vb, S, tw);
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < PER; ++i) {
             const int idx = threadIdx.x + i * NT;
             if ((TILE % NT != 0) && idx >= TILE) break;
+            if (tab && i > 0) load_tab(idx);
             const int kzi = idx / TZ, t = idx % TZ;
             const int pos = ct_gpos(kzi, TZ) + t;
             const int kxi = kx0 + t;
@@ -1139,7 +1134,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
             for (int s = 0; s < DFT_MAXS; ++s) {
                 if (s >= S) break;
                 Real w0, j3;
-                if (tab) { w0 = wr[i][2 * s]; j3 = wr[i][2 * s + 1]; }
+                if (tab) { w0 = wr[2 * s]; j3 = wr[2 * s + 1]; }
                 else fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
                 const Real Rs = sp.R[s];
                 acc[0] = cadd(acc[0], cscale(v[s], w0));
@@ -1166,7 +1161,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                         if (j >= S) continue;
                         Real K;
                         if (tab) {
-                            K = kr[i][dft_pair(i2, j)];
+                            K = kr[dft_pair(i2, j)];
                             if (!p.zero) K -= sp.pois[i2][j] * inv_lap;
                         } else {
                             K = es_kernel<Real>(sp, i2, j, p, inv_lap, nullptr);
@@ -1249,7 +1244,6 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
     constexpr int PER = (TILE + NT - 1) / NT;
-    constexpr bool PF = PER == 1;
     constexpr int EMAX = DFT_MAXS + 1;
     constexpr uint32_t BOX = uint32_t(TILE * sizeof(C));
     static_assert(NZ > 0 && NZ <= 256 && (TZ * sizeof(C)) % 16 == 0 && BOX % 128 == 0, "z TMA tile");
@@ -1317,10 +1311,10 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
         const int cur = it & 1;
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
-        // with one point per thread, its table record is in flight while the tile arrives;
-        // with more, each point's record is loaded where it is used
+        // the first point's table record is in flight while the tile arrives; a thread's later
+        // points load theirs where they are used
         Real wr[DFT_TAB_W];
-        if (PF && hs && tab) {
+        if (hs && tab) {
             const int idx = threadIdx.x;
             const int kxi = kx0 + idx % TZ;
             const int m2 = (((TILE % NT == 0) || idx < TILE) && kxi < nxh) ? kmode2(kxi, my, idx / TZ, g.nz) : 0;
@@ -1364,7 +1358,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
                     if (s < ncomp_out) es_mat[(long long)s * g.nc + o] = out[s];
             }
             if (hs) {
-                if (!PF && tab)
+                if (i > 0 && tab)
                     load_record(wr, sp.tab_w + (long long)(kxi < nxh ? kmode2(kxi, my, kzi, g.nz) : 0) * sp.tab_ws,
                                 2 * S);
                 const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
