@@ -140,8 +140,13 @@ template struct Passes<double>;
 
 cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
                      int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor) {
-    dftk::k_finalize<<<1, dftk::kFinThreads, 0, st>>>(ctl, red_sum, nsum, red_max, nmax, op, inv_count, alpha_fixed,
-                                                  n3_bound, alpha_floor);
+    if (nsum + nmax > 8 * dftk::kFinThreadsSmall)
+        dftk::k_finalize<dftk::kFinThreads><<<1, dftk::kFinThreads, 0, st>>>(ctl, red_sum, nsum, red_max, nmax, op,
+                                                                           inv_count, alpha_fixed, n3_bound,
+                                                                           alpha_floor);
+    else
+        dftk::k_finalize<dftk::kFinThreadsSmall><<<1, dftk::kFinThreadsSmall, 0, st>>>(
+            ctl, red_sum, nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
     return cudaSuccess;
 }
 

@@ -34,7 +34,9 @@
 namespace dftk {
 
 constexpr int kThreads = 256;
-constexpr int kFinThreads = 1024;   // the one-block line-search bookkeeping kernel
+// the one-block line-search bookkeeping kernel: 1024 threads for many partial results, 256 for
+// few (small grids, where its latency is all that counts)
+constexpr int kFinThreads = 1024, kFinThreadsSmall = 256;
 
 // Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
 #ifndef DFT_XUPD_KP
@@ -2220,7 +2222,8 @@ __device__ __forceinline__ void set_weights(Ctl* c, double a) {
     c->wA = 1.0 - a; c->wB = a; c->w0 = 1.0 - a; c->w1 = a;
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
+template <int B>
+__global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
                                                           const float* __restrict__ red_max, int nmax, int op,
                                                           double inv_count, double alpha_fixed, double n3_bound,
                                                           double alpha_floor) {
@@ -2228,7 +2231,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(Ctl* ctl, const double
     __shared__ float scratch_f[32];
     // four independent partial results per thread, so that a thread's loads are all in flight
     // at once (the partial sums are L2-resident: the kernel is a few load latencies long)
-    constexpr int B = kFinThreads;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = threadIdx.x;
     for (; i + 3 * B < nsum; i += 4 * B) {
