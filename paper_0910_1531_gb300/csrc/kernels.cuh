@@ -38,10 +38,6 @@ constexpr int kThreads = 256;
 // few (small grids, where its latency is all that counts)
 constexpr int kFinThreads = 1024, kFinThreadsSmall = 256;
 
-// Points per thread whose loads k_xupdate issues together (build flag DFT_XUPD_KP).
-#ifndef DFT_XUPD_KP
-#define DFT_XUPD_KP 1
-#endif
 
 template <typename Real> __device__ __forceinline__ void sc(Real x, Real* s, Real* c);
 template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { sincosf(x, s, c); }
@@ -2015,7 +2011,7 @@ __global__ void __launch_bounds__(kThreads) k_canon_scale(Ctl* ctl, SpeciesDesc<
 // rho_out may alias rho0 and g_out may alias rho1 (each point is read before it is written).
 // ------------------------------------------------------------------------------------
 template <typename Real, int NX>
-__global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR,
+__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR,
                                                       const Ctl* __restrict__ ctl,
                                                       const typename Cplx<Real>::type* __restrict__ cspec,
                                                       const Real* rho0, const Real* rho1,
@@ -2035,8 +2031,29 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec, A);
+    // rho0, rho1 and V of a thread's point: loaded one point ahead of its use; rho_out / g_out
+    // may alias rho0 / rho1, but a point's values are read before that point is written and the
+    // points are distinct
+    const int total = LR * nx;
+    Real r0[DFT_MAXS], r1[DFT_MAXS], vv[DFT_MAXS];
+    auto load_point = [&](int idx, Real* a0, Real* a1, Real* av) {
+        const long long row = row0 + idx / nx;
+        const bool live = idx < total && row < nrows;
+        const long long pt = row0 * nx + idx;
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            a0[s] = a1[s] = av[s] = Real(0);
+            if (s < S && live) {
+                const long long o = (long long)s * g.n + pt;
+                a0[s] = rho0[o];
+                a1[s] = rho1 ? rho1[o] : Real(0);
+                av[s] = V[o];
+            }
+        }
+    };
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
+    load_point(threadIdx.x, r0, r1, vv);
     const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
     // G_i = pref_i exp(mu0_i - V_i + c_i): the bath (rho_b, beta mu_HS,b), or for a
     // fixed-number species the normalisation of this evaluation and no bath constant
@@ -2051,33 +2068,11 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
     // double-single (FP32) or FP64 across threads, FP64 across blocks
     Real acc = Real(0), comp = Real(0);
     bool bad = false;
-    // KP points per thread at a time: every load of the KP points is issued before the first
-    // store (rho_out / g_out may alias rho0 / rho1; the points are distinct)
-    constexpr int KP = DFT_XUPD_KP;
-    const int total = LR * nx;
-    for (int base = threadIdx.x; base < total; base += KP * kThreads) {
-        Real r0[KP][DFT_MAXS], r1[KP][DFT_MAXS], vv[KP][DFT_MAXS];
-#pragma unroll
-        for (int q = 0; q < KP; ++q) {
-            const int idx = base + q * kThreads;
-            const long long row = row0 + idx / nx;
-            const bool live = idx < total && row < nrows;
-            const long long pt = row0 * nx + idx;
-#pragma unroll
-            for (int s = 0; s < DFT_MAXS; ++s) {
-                if (s < S && live) {
-                    const long long o = (long long)s * g.n + pt;
-                    r0[q][s] = rho0[o];
-                    r1[q][s] = rho1 ? rho1[o] : Real(0);
-                    vv[q][s] = V[o];
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < KP; ++q) {
-            const int idx = base + q * kThreads;
-            const int r = idx / nx, x = idx - (idx / nx) * nx;
-            if (idx >= total || row0 + r >= nrows) continue;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+        Real n0[DFT_MAXS], n1[DFT_MAXS], nv[DFT_MAXS];
+        load_point(idx + kThreads, n0, n1, nv);
+        const int r = idx / nx, x = idx - (idx / nx) * nx;
+        if (row0 + r < nrows) {
             const long long pt = row0 * nx + idx;
 #pragma unroll
             for (int s = 0; s < DFT_MAXS; ++s) {
@@ -2085,8 +2080,8 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
                 const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
                 const Real c = (s & 1) ? pr.y : pr.x;
                 const long long o = (long long)s * g.n + pt;
-                const Real rho = w0 * r0[q][s] + w1 * r1[q][s];
-                const Real v = vv[q][s];
+                const Real rho = w0 * r0[s] + w1 * r1[s];
+                const Real v = vv[s];
                 Real gval;
                 if (isinf(v) && v > Real(0)) gval = Real(0);
                 else gval = pref[s] * exp(mu0[s] - v + c);
@@ -2099,6 +2094,12 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(GridDesc g, AxisPlan px, S
                 if (rho_out) rho_out[o] = rho;
                 if (g_out) g_out[o] = gval;
             }
+        }
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            r0[s] = n0[s];
+            r1[s] = n1[s];
+            vv[s] = nv[s];
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);
