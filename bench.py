@@ -37,8 +37,8 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 # profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, command in
 # profiles/launches_obstacles128_fp32.md); valid while the kernel sources hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "5f4198b75fc9eda4",
-    "per_launch": {"xfwd": 25349803, "yfft": 61266891, "zconv_fwd": 76109312, "xinv": 8711253, "finalize": 29333, "xphi": 213765035, "zconv_bwd": 137481387, "xupdate": 102687431},
+    "digest": "32892e80e8744ac7",
+    "per_launch": {"xfwd": 25349205, "yfft": 61268736, "zconv_fwd": 76148565, "xinv": 8710144, "finalize": 46400, "xphi": 214007040, "zconv_bwd": 137009237, "xupdate": 103295147},
 }
 
 
