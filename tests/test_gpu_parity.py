@@ -75,6 +75,9 @@ CASES = [
     ((6, 4, 12), 0.1, 1),          # single uncharged species (Gamma = 0)
     ((35, 21, 10), (0.1, 0.09, 0.11), 2),   # odd radices 5 and 7 (z 5*7, y 3*7, x 5*2)
     ((23, 22, 14), 0.08, 3),       # radix 23 (z), 11 (y), 7 (x)
+    ((6, 4, 512), 0.05, 2),        # the longest axis accepted, on each pass: x 512
+    ((4, 512, 6), 0.05, 2),        # y 512
+    ((512, 6, 4), 0.05, 2),        # z 512
 ]
 
 
