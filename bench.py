@@ -109,6 +109,21 @@ def blas_threads():
     return os.cpu_count()
 
 
+def cpu_model():
+    """The host CPU's model name (best effort; Arm hosts report no model name, then the part)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            info = fh.read()
+        for key in ("model name", "Model", "CPU part"):
+            for ln in info.splitlines():
+                if ln.startswith(key):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling while kernels run."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -233,7 +248,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
                        "oracle": "plain FP64 numpy, explicit per-axis DFT matrices (no FFT library)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "nproc": os.cpu_count(),
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -508,7 +524,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, tg, twd, tit = oracle_sample(w)
-        cpu = {"value": 1.0 / tit, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+        cpu = {"value": 1.0 / tit, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(),
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"one oracle G(rho) ({tg:.2f} s) + one weighted-density evaluation ({twd:.2f} s) on the "
                          f"same {w.shape[0]}^3 workload on the host cores; iteration = 3 G + 2 WD"}
 
