@@ -765,7 +765,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
-    constexpr int P = DFT_MAXS * (DFT_MAXS + 1) / 2;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
     const int ny = g.ny, nxh = g.nxh, S = sp.S;
@@ -1037,7 +1036,6 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
     constexpr int PER = (TILE + NT - 1) / NT;
-    constexpr int P = DFT_MAXS * (DFT_MAXS + 1) / 2;
     constexpr uint32_t BOX = uint32_t(TILE * sizeof(C));
     static_assert(NZ > 0 && NZ <= 256 && (TZ * sizeof(C)) % 16 == 0 && BOX % 128 == 0, "z TMA tile");
     extern __shared__ unsigned char smem_raw[];
@@ -1621,6 +1619,29 @@ __device__ __forceinline__ void load_species_rows(const GridDesc& g, int rows, l
     }
 }
 
+// One component's half rows of `rows` grid rows, two grid rows per complex line (rows 2l and
+// 2l + 1 of the block in line l; a missing partner row reads as zero).
+template <typename Real, int NX>
+__device__ __forceinline__ void load_row_pairs(const GridDesc& g, int rows, long long row0, long long nrows,
+                                               const typename Cplx<Real>::type* __restrict__ spec,
+                                               typename Cplx<Real>::type* dst) {
+    using C = typename Cplx<Real>::type;
+    const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
+    const bool even = (nx % 2) == 0;
+    const int lines = (rows + 1) / 2;
+    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
+        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const int ra = 2 * l, rb = 2 * l + 1;
+        C a = cmake<C>(Real(0), Real(0)), b = a;
+        if (row0 + ra < nrows) a = spec[(row0 + ra) * g.pxh + k];
+        if (rb < rows && row0 + rb < nrows) b = spec[(row0 + rb) * g.pxh + k];
+        const bool edge = k == 0 || (even && 2 * k == nx);
+        if (edge) { a.y = Real(0); b.y = Real(0); }
+        dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+        if (!edge) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+    }
+}
+
 // The ten weighted-density rows of `rows` grid rows as five complex lines each (wd_comp
 // arrangement), built from the nine kept spectra mixed as wA * A + wB * B (B optional), with
 // n_V1x = i k_x m and n_V2x = i k_x n3 (zero on the Nyquist index); mat_out (optional) receives
@@ -2183,8 +2204,10 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
     const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
+    // one component without outputs (the maximum only): two grid rows per complex line
+    const bool rows2 = ncomp == 1 && !wd && !out && !out_last;
     const int lpr = (ncomp + 1) / 2;
-    const int lines = lpr * LR;
+    const int lines = rows2 ? (LR + 1) / 2 : lpr * LR;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
     C* B = A + lines * pitch;
@@ -2192,6 +2215,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     if (wd) load_wd_rows<Real, NX>(g, LR, row0, nrows, spec, nullptr, Real(1), Real(0), nullptr, kfx, A);
+    else if (rows2) load_row_pairs<Real, NX>(g, LR, row0, nrows, spec, A);
     else load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
@@ -2200,6 +2224,11 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
         const int r = idx / nx, x = idx - (idx / nx) * nx;
         const long long row = row0 + r;
         if (row >= nrows) continue;
+        if (rows2) {
+            const C pr = R[(r / 2) * pitch + xo<NX>(x)];
+            mx = fmaxf(mx, float(((r & 1) ? pr.y : pr.x) + off.v[0]));
+            continue;
+        }
         for (int c = 0; c < ncomp; ++c) {
             const int l = wd ? wd_line(c) : c / 2, j = wd ? wd_slot(c) : (c & 1);
             const C pr = R[(r * lpr + l) * pitch + xo<NX>(x)];

@@ -73,8 +73,10 @@ cudaError_t LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const Axi
                             const C* spec, Real* out, Real* out_last, const Offsets<Real>& off, int cmax,
                             float* red_max, int wd, Real kfx, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    const int lpr = (ncomp + 1) / 2;
-    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
+    // one component and no outputs: the kernel pairs grid rows in its lines
+    const bool rows2 = ncomp == 1 && !wd && !out && !out_last;
+    const int lines = rows2 ? (LR + 1) / 2 : (ncomp + 1) / 2 * LR;
+    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lines), st>>>(
         g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, wd, kfx, tw);
     return cudaSuccess;
 }
