@@ -37,8 +37,8 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 # profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, command in
 # profiles/launches_obstacles128_fp32.md); valid while the kernel sources hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "32892e80e8744ac7",
-    "per_launch": {"xfwd": 25349205, "yfft": 61268736, "zconv_fwd": 76148565, "xinv": 8710144, "finalize": 46400, "xphi": 214007040, "zconv_bwd": 137009237, "xupdate": 103295147},
+    "digest": "007b2a81faf7b87b",
+    "per_launch": {"xfwd": 25332224, "yfft": 61262432, "zconv_fwd": 75963819, "xinv": 8708011, "finalize": 43264, "xphi": 213977401, "zconv_bwd": 136580324, "xupdate": 102697415},
 }
 
 
@@ -114,10 +114,16 @@ def cpu_model():
     try:
         with open("/proc/cpuinfo") as fh:
             info = fh.read()
-        for key in ("model name", "Model", "CPU part"):
+        for key in ("model name", "Model"):
             for ln in info.splitlines():
                 if ln.startswith(key):
                     return ln.split(":", 1)[1].strip()
+        # Arm: the implementer and part numbers (0x41 / 0xd4f: Arm Neoverse V2, as in Grace)
+        parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+        for ln in info.splitlines():
+            if ln.startswith("CPU part"):
+                code = ln.split(":", 1)[1].strip()
+                return parts.get(code, "Arm CPU part " + code)
     except Exception:
         pass
     import platform
