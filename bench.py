@@ -29,16 +29,21 @@ METRIC = "Picard iterations/s and FFT-conv HBM GB/s at 128³–256³ (FP32 vs FP
 UNIT = "Picard iterations/s"
 L2_BYTES = 129e6
 FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic peak: 152 SMs x 4 FP64 flop per clock (two FMAs) x 2.07 GHz (the part's
+# nominal 1.25 TFLOP/s dense FP64)
+FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
 
-# DRAM traffic per launch (bytes) of the kernels measured by ncu on this workload, keyed by
-# kernel name, with the source digest of csrc/ at capture time; None until captured.
-# DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of three
-# profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, command in
-# profiles/launches_obstacles128_fp32.md); valid while the kernel sources hash to `digest`.
+# DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of the
+# profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum; commands in
+# profiles/launches_obstacles128_fp32.md and profiles/launches_obstacles256_fp32.md), per
+# workload and precision; valid while the kernel sources hash to `digest`.
 NCU_TRAFFIC = {
     "digest": "007b2a81faf7b87b",
-    "per_launch": {"xfwd": 25332224, "yfft": 61262432, "zconv_fwd": 75963819, "xinv": 8708011, "finalize": 43264, "xphi": 213977401, "zconv_bwd": 136580324, "xupdate": 102697415},
+    "captures": {
+        "3species_16obstacles_128^3/fp32": {"xfwd": 25332224, "yfft": 61262432, "zconv_fwd": 75963819, "xinv": 8708011, "finalize": 43264, "xphi": 213977401, "zconv_bwd": 136580324, "xupdate": 102697415},
+        "3species_16obstacles_256^3/fp32": {"xfwd": 359503616, "yfft": 758558208, "zconv_fwd": 1004156800, "xinv": 68238208, "finalize": 106688, "xphi": 2018111189, "zconv_bwd": 1273750784, "xupdate": 926792789},
+    },
 }
 
 
@@ -502,10 +507,25 @@ def run_ours(args):
     achieved = by / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
     traffic = None
     if NCU_TRAFFIC and NCU_TRAFFIC.get("digest") == csrc_digest():
-        traffic = NCU_TRAFFIC["per_launch"].get(dom)
+        traffic = NCU_TRAFFIC["captures"].get(f"{w.name}/{args.precision}", {}).get(dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": by / max(n_l, 1), "ms_per_launch": t_ms / max(n_l, 1)}
+    if args.precision == "fp64" and dom == "xphi":
+        # the plain-FP64 form runs on the FP64 pipe (1/64 of the FP32 rate on this part): its
+        # roofline is arithmetic.  Algorithmic flops of the x pass: ten real rows per grid row,
+        # i.e. five complex nx-point transforms each way, at 5 nx log2(nx) flops each (the
+        # pointwise Phi' and mixing work is not counted: a lower bound of the achieved rate)
+        nz_, ny_, nx_ = w.shape
+        flops = 2 * 5 * ny_ * nz_ * 5.0 * nx_ * math.log2(nx_)
+        t_launch = t_ms * 1e-3 / max(n_l, 1)
+        achieved_tf = flops / t_launch / 1e12 if t_launch > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_TFLOPS, "traffic": None, "kernel": dom,
+                    "peak_source": "nominal FP64: 152 SMs x 4 FP64 flop/clock x 2.07 GHz (not measured)",
+                    "flop_model": "5 nx log2(nx) per complex x transform, 10 per grid row",
+                    "flops_per_launch": flops, "ms_per_launch": t_ms / max(n_l, 1),
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
     total_kernel_ms = sum(prof[k][1] for k in KERNELS)
     kernels = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 4),
                    "share": round(prof[k][1] / total_kernel_ms, 4) if total_kernel_ms else None,
