@@ -26,7 +26,7 @@ def test_separable_equals_bruteforce():
     assert np.allclose(fourier.idft3(f) * f.size, fourier.dft3_bruteforce(f, +1), atol=1e-11)
 
 
-@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 6, 9), (3, 16, 10)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 6, 9), (3, 16, 10), (161, 21, 21), (35, 22, 23)])
 def test_dft_matches_library_fft(shape):
     rng = np.random.default_rng(1)
     f = rng.standard_normal((2,) + shape)
