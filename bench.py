@@ -2,11 +2,12 @@
 """Benchmark of the FFT/Picard classical-DFT hot path on GB300.
 
 A step is one Picard iteration with the quadratic line search (three residual
-evaluations sharing one weighted-density pass) on the 128^3,
-three-species workload with 16 seeded hard obstacles, inputs resident in HBM.
-Prints one JSON line.  Usage:
+evaluations sharing one weighted-density pass: the weighted densities are linear
+in rho) on the 128^3, three-species workload with 16 seeded hard obstacles,
+inputs resident in HBM.  Prints one JSON line.  Usage:
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl reference]
+                  [--n 256] [--workload obstacles128|pore256|batch64|wall161|hswall]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path does not shard; no collective on the data path); the value is the
@@ -35,9 +36,10 @@ FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
 
 # DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of the
-# profiled iterations (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum; commands in
-# profiles/launches_obstacles128_fp32.md and profiles/launches_obstacles256_fp32.md), per
-# workload and precision; valid while the kernel sources hash to `digest`.
+# profiled iterations (ncu --nvtx --nvtx-include 'profiled_steps/' --metrics
+# gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none on
+# this script with --no-cpu-baseline --no-cufft --steps 3 (2 at 256^3) --warmup 3 --e2e-steps 1),
+# per workload and precision; valid while the kernel sources hash to `digest`.
 NCU_TRAFFIC = {
     "digest": "007b2a81faf7b87b",
     "captures": {
