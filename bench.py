@@ -7,7 +7,7 @@ in rho) on the 128^3, three-species workload with 16 seeded hard obstacles,
 inputs resident in HBM.  Prints one JSON line.  Usage:
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl reference]
-                  [--n 256] [--workload obstacles128|pore256|batch64|wall161|hswall]
+                  [--n 256] [--workload obstacles128|pore256|batch64|wall161|hswall|sphere32|grad64]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path does not shard; no collective on the data path); the value is the
@@ -60,6 +60,8 @@ def workload(args):
         return workloads.hard_wall_ionic()
     if args.workload == "hswall":
         return workloads.hard_wall_hs(args.eta)
+    if args.workload == "sphere32":
+        return workloads.centred_sphere(n=args.n or 32, h=0.1, molar=0.1, sphere_radius=0.5)
     n = args.n or 128
     return workloads.obstacles_3species(n=n, h=0.05 * 128 / n, seed=1)
 
@@ -73,6 +75,8 @@ def workload_config(w):
         return {"geometry": "hard uncharged wall at z = 0 in a periodic 2 x 2 x 6 nm cell",
                 "h_nm_xyz": list(w.h),
                 "paper_time_to_solution": "1.5 min (Sec. Results, the authors' 2009 cluster; tolerance not stated)"}
+    if w.name.startswith("nacl_sphere"):
+        return {"geometry": "one neutral hard sphere R 0.5 nm at the box centre", "mixing": 0.1}
     if w.n_fixed is not None:
         return {"geometry": "hard slab |z - L/2| < 1 nm with a 0.5 nm-radius pore along z",
                 "n_fixed": list(map(float, w.n_fixed)),
@@ -345,6 +349,73 @@ def run_batch(args):
     return 0
 
 
+def run_grad(args):
+    """Secondary line for the differentiated form: NaCl 0.5 M in a smooth seeded external field
+    (64^3, h 0.1 nm, correlation length 0.5 nm, std 1 kT); a step is one evaluation of Omega and
+    its gradients with respect to rho, V and the bath concentrations through dft_grad (host
+    scalars read back every step); value = gradient evaluations/s, with Picard iterations/s of
+    the same plan beside it."""
+    import numpy as np
+    import torch
+    from paper_0910_1531_gb300 import binding, build, workloads
+
+    world, rank, local = dist_setup()
+    build.build()
+    torch.cuda.set_device(local)
+    w = workloads.smooth_field_nacl(n=args.n or 64, h=0.1, molar=0.5, seed=2)
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=args.precision)
+    dt = plan.dtype
+    rho = torch.tensor(workloads.random_density(w.shape, 2, plan.bulk()["rho"], 0.3, seed=9), dtype=dt, device="cuda")
+    V = torch.tensor(w.V, dtype=dt, device="cuda")
+    for _ in range(args.warmup):
+        plan.grad(rho, V)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        om, _, _, _ = plan.grad(rho, V)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    value = job_throughput(args.steps, world, ms)
+    # Picard iterations/s of the same plan (graph replays), for comparison
+    rho_p = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=dt, device="cuda")
+    plan.iter_begin(rho_p, V)
+    plan.iter_run(rho_p, V, args.warmup, -1.0, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.iter_run(rho_p, V, args.steps, -1.0, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    picard = args.steps / (e0.elapsed_time(e1) * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value,
+                "unit": "gradient evaluations/s (Omega, dOmega/drho, dOmega/dV, dOmega/dbath)", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
+                           "bulk_molar": list(map(float, w.bulk_molar)),
+                           "field": "seeded Gaussian random field, correlation length 0.5 nm, std 1 kT, sign by charge",
+                           "step": "dft_grad: Omega and its gradients (host scalars read back every step)",
+                           "omega": om, "picard_iterations_per_s_same_plan": picard},
+                "clocks": clocks}
+        print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def cufft_comparator(plan, w, rho, V, reps, stream):
     """Timed comparison only (never on the product path): the 3D real transforms that a
     cuFFT-based evaluation of G(rho) performs at the least -- S forward, ten inverse (weighted
@@ -415,7 +486,7 @@ def run_ours(args):
     working_set = (2 * (10 + S + 1) + 10) * nc * 2 * elem + 3 * S * N * elem
 
     # line search (alpha < 0) unless a fixed mixing is asked for or the workload needs one
-    alpha = args.alpha if args.alpha is not None else (0.05 if args.workload == "pore256" else -1.0)
+    alpha = args.alpha if args.alpha is not None else {"pore256": 0.05, "sphere32": 0.1}.get(args.workload, -1.0)
     if args.converge_tol is None:
         # the pore's FP32 floor of the weighted residual is ~3e-5 (FP64 reaches 1e-6)
         if args.workload == "pore256":
@@ -599,7 +670,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
-    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161", "hswall"])
+    ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161", "hswall", "sphere32",
+                                                                   "grad64"])
     ap.add_argument("--eta", type=float, default=0.4, help="bath packing fraction of --workload hswall")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--alpha", type=float, default=None,
@@ -616,6 +688,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "grad64":
+        return run_grad(args)
     return run_ours(args)
 
 
