@@ -82,6 +82,8 @@ CASES = [
     ((6, 4, 512), 0.05, 2),        # the longest axis accepted, on each pass: x 512
     ((4, 512, 6), 0.05, 2),        # y 512
     ((512, 6, 4), 0.05, 2),        # z 512
+    ((256, 8, 12), 0.05, 3),       # compile-time z 256: the persistent z passes of the 256^3 workloads
+    ((256, 6, 8), (0.1, 0.1, 0.03), 5),   # z 256 with five species (the largest ES tile set)
 ]
 
 
@@ -265,3 +267,38 @@ def test_autotune_keeps_results(precision):
     assert plan2.autotune(rd, Vd, reps=2) == lines
     plan.close()
     plan2.close()
+
+
+@pytest.mark.parametrize("workload", ["obstacles256", "pore256"])
+def test_full_size_256_axis_permutation_and_shift(workload):
+    # The 256^3 configurations in the launch configuration the benchmark times, checked through
+    # properties that hold at any size: the discrete operator of a cubic box with equal spacings
+    # commutes with exchanging the x and z axes (the x pass and the z pass then compute each
+    # other's share of the same G) and with a circular shift of the grid.
+    from paper_0910_1531_gb300 import binding
+    if workload == "obstacles256":
+        w = workloads.obstacles_3species(n=256, h=0.025, seed=1)
+        plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32")
+    else:
+        w = workloads.pore_slab_4species(n=256, h=0.05)
+        plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32", n_fixed=w.n_fixed)
+    S = w.nspecies
+    base = w.initial_rho_nm3(plan.bulk()["rho"])
+    ref_rho = np.where(base > 0, base, 0.0)
+    pert = workloads.random_density((64, 64, 64), S, np.ones(S), 0.2, seed=17)
+    rho = np.where(np.isinf(w.V), 0.0, ref_rho * np.tile(pert, (1, 4, 4, 4)))
+    # G = pref exp(mu0 - V + c): FP32 rounding of c turns into a relative error of G of about
+    # |c| ulps; in the pore the bound species reach |c| ~ 10 (Ca2+ enriched ~1e4 fold)
+    tol = 1e-5 if workload == "obstacles256" else 1e-4
+    g0, r0 = plan.picard_map(to_dev(rho, plan), to_dev(w.V, plan))
+    g0 = g0.cpu().numpy()
+    assert np.all(np.isfinite(g0)) and np.all(g0[np.isinf(w.V)] == 0.0)
+    t = lambda a: np.ascontiguousarray(np.swapaxes(a, 1, 3))
+    g1, r1 = plan.picard_map(to_dev(t(rho), plan), to_dev(t(w.V), plan))
+    assert relerr(g1.cpu().numpy(), t(g0)) < tol
+    assert r1 == pytest.approx(r0, rel=tol)
+    sh = lambda a: np.ascontiguousarray(np.roll(a, (37, -91, 128), axis=(1, 2, 3)))
+    g2, r2 = plan.picard_map(to_dev(sh(rho), plan), to_dev(sh(w.V), plan))
+    assert relerr(g2.cpu().numpy(), sh(g0)) < tol
+    assert r2 == pytest.approx(r0, rel=tol)
+    plan.close()
