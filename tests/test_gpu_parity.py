@@ -84,6 +84,8 @@ CASES = [
     ((512, 6, 4), 0.05, 2),        # z 512
     ((256, 8, 12), 0.05, 3),       # compile-time z 256: the persistent z passes of the 256^3 workloads
     ((256, 6, 8), (0.1, 0.1, 0.03), 5),   # z 256 with five species (the largest ES tile set)
+    ((64, 32, 48), 0.08, 2),       # compile-time z 64, y 32 (TMA), x 48
+    ((12, 8, 256), 0.05, 2),       # compile-time x 256
 ]
 
 
