@@ -74,3 +74,15 @@ def test_null_arguments(lib):
     assert lib.dft_plan_create(None, None, None) == -1
     assert lib.dft_plan_destroy(None) == 0
     assert lib.dft_weighted_densities(None, None, None) == -1
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(21, 21, 161), (35, 22, 23), (10, 58, 124), (512, 4, 6)])
+def test_plan_create_accepts_prime_factors_up_to_31(lib, nx, ny, nz):
+    # lengths with the odd primes 5..31 (direct odd-radix stages) and up to 512 pass validation;
+    # without a GPU the call then fails at the device set-up, never with DFT_EINVAL
+    prm, keep = _params(nx=nx, ny=ny, nz=nz)
+    handle = ctypes.c_void_p()
+    st = lib.dft_plan_create(ctypes.byref(prm), None, ctypes.byref(handle))
+    if handle.value:
+        lib.dft_plan_destroy(handle)
+    assert st != -1, lib.dft_last_error(None)
