@@ -8,11 +8,13 @@
 //     k_yfft     y forward
 //     k_zconv_fwd  z forward, the analytic weights of App. B (n_hat_alpha), the
 //                bulk-fluid kernel (eq. CplusPsiHat) and the Poisson symbol
-//                (eq. potentialSolution) applied in k space, z inverse of the ten n
-//     k_yfft     y inverse of the ten n
+//                (eq. potentialSolution) applied in k space, z inverse of the nine
+//                weighted-density spectra (the x derivatives are formed in k_xphi)
+//     k_yfft     y inverse of the nine spectra
 //   second half (weighted densities -> c1 -> G)
-//     k_xphi     x C2R of the ten n, dPhi/dn_alpha of eq. Phi (|nV2| <= n2 bound,
-//                FP64 log(1-n3) and 1/(1-n3)^m), x R2C of the ten derivatives
+//     k_xphi     x C2R to the ten n, dPhi/dn_alpha of eq. Phi (|nV2| <= n2 bound,
+//                FP64 log(1-n3) and 1/(1-n3)^m; or another hard-sphere form), x R2C back
+//                to nine spectra
 //     k_yfft     y forward
 //     k_zconv_bwd  z forward, adjoint weights (eq. muHS), + bulk-fluid/Poisson spectra,
 //                z inverse of the S one-body correlations
