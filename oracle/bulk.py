@@ -17,7 +17,11 @@ argument beyond continuity and a sign change.
 Parity: pinned (tests/test_oracle_bulk.py) by the textbook single-component
 Percus-Yevick compressibility pressure and chemical potential, the closed-form
 restricted-primitive-model Gamma, the Debye-Hueckel limit, and (in
-tests/test_oracle_fmt.py) by the bulk limit of the FMT functional eq. Phi.
+tests/test_oracle_fmt.py) by the bulk limit of the FMT functional eq. Phi.  The
+size-asymmetric MSA branch (eta != 0: eta, Omega, the eta terms of eq. Gamma and of
+mu^ES) is pinned by the MSA free energy of the unrestricted primitive model (Blum's
+internal energy plus Gamma^3 / (3 pi)), which App. A does not print: Gamma must be its
+stationary point and mu^ES its density derivative, on baths with eta up to O(0.1).
 """
 
 import math
