@@ -86,21 +86,39 @@ def workload_config(w):
 
 
 def csrc_digest():
-    """Digest of the kernel sources with comments and layout removed (a comment edit leaves the
-    compiled kernels, and so their recorded traffic, unchanged)."""
+    """Digest of what decides the compiled kernels -- the kernel sources and the build script
+    (its nvcc flags and instantiation list) -- with comments and layout removed (a comment edit
+    leaves the compiled kernels, and so their recorded traffic, unchanged)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_0910_1531_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), encoding="utf-8", errors="replace") as fh:
+    pkg = os.path.join(ROOT, "paper_0910_1531_gb300")
+    d = os.path.join(pkg, "csrc")
+    files = [(f, os.path.join(d, f), "c") for f in sorted(os.listdir(d))]
+    build_py = os.path.join(pkg, "build.py")
+    if os.path.exists(build_py):
+        files.append(("build.py", build_py, "py"))
+    for f, path, kind in files:
+        with open(path, encoding="utf-8", errors="replace") as fh:
             text = fh.read()
-        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-        text = re.sub(r"//[^\n]*", " ", text)
+        if kind == "c":
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+        else:
+            text = re.sub(r'"""(.*?)"""', " ", text, flags=re.S)
+            text = re.sub(r"#[^\n]*", " ", text)
         text = " ".join(text.split())
         h.update(f.encode())
         h.update(text.encode())
     return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name, precision, kernel):
+    """DRAM bytes per launch of `kernel` from the recorded ncu capture of this workload and
+    precision, or None when there is none or the kernels changed since it was taken."""
+    if not NCU_TRAFFIC or NCU_TRAFFIC.get("digest") != csrc_digest():
+        return None
+    return NCU_TRAFFIC["captures"].get(f"{workload_name}/{precision}", {}).get(kernel)
 
 
 def measured_peaks():
@@ -595,9 +613,7 @@ def run_ours(args):
     dom = max((k for k in KERNELS if k != "finalize"), key=lambda k: prof[k][1])
     n_l, t_ms, by = prof[dom]
     achieved = by / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
-    traffic = None
-    if NCU_TRAFFIC and NCU_TRAFFIC.get("digest") == csrc_digest():
-        traffic = NCU_TRAFFIC["captures"].get(f"{w.name}/{args.precision}", {}).get(dom)
+    traffic = recorded_traffic(w.name, args.precision, dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": by / max(n_l, 1), "ms_per_launch": t_ms / max(n_l, 1)}

@@ -190,6 +190,13 @@ dft_status dft_solve_newton(dft_plan* plan, void* rho_inout, const void* V, doub
  * kept state (no re-evaluation of G(rho)).  rho_inout and V must be the same
  * buffers, unmodified by the caller, between begin and the steps.
  * resid_out/alpha_out: as dft_picard_step; NULL skips the synchronisation.
+ * DFT_FP32_STAB plans carry the iterate in extended precision: rho_inout holds
+ * its float value and the plan a float low part (its rounding error, zero at
+ * dft_iter_begin), the mixing rho0 + alpha (G - rho0) adds into the pair
+ * without rounding steps below half an ulp away, and the residual is that of
+ * the pair.  rho_inout alone is the pair rounded to float.  The same holds within dft_solve,
+ * dft_iter_run, dft_picard_step and dft_picard_step_host (each call starts
+ * from a zero low part).
  */
 dft_status dft_iter_begin(dft_plan* plan, void* rho_inout, const void* V);
 dft_status dft_iter_step(dft_plan* plan, void* rho_inout, const void* V, double alpha_or_neg,
@@ -275,6 +282,20 @@ dft_status dft_batch_begin(dft_batch* batch, void* const* rho, const void* const
 dft_status dft_batch_iterate(dft_batch* batch, int iters, double alpha_or_neg, double* resid_out);
 
 /*
+ * Bound of the bounded device-side waits (failure detection; no counterpart in the paper).
+ * The y passes move their column tiles by TMA and wait for each tile on an mbarrier; a wait
+ * gives up after `polls` polls (default DFT_WAIT_POLLS_DEFAULT), the CTA then drains the copies
+ * it still has in flight (those waits keep the default bound, so no copy outlives the CTA),
+ * records the timeout in the plan's device status word and stops, and the call that queued the
+ * work returns DFT_ETIMEOUT (the context stays usable; results of that call are undefined).
+ * polls = 0 makes every such wait give up at once, which is how the timeout path is exercised
+ * without a fault or a hang.  Applies to the plan's later calls (a cached iteration graph is
+ * dropped and recaptured).  polls < 0: DFT_EINVAL.
+ */
+#define DFT_WAIT_POLLS_DEFAULT (1LL << 24)
+dft_status dft_set_wait_polls(dft_plan* plan, long long polls);
+
+/*
  * Per-kernel timing with CUDA events recorded on the plan's stream around
  * each launch.  enable != 0 starts collection (and clears totals).
  * dft_profile_read returns, for the kernel kind named by `name`, the number
@@ -299,7 +320,9 @@ dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, dou
  * of its scratch (twiddles, spectra, weighted densities) lives in one file-scope
  * device array of DFT_NOALLOC_SCRATCH_BYTES that every GPU loading this part of
  * the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * allocating library routine.  Under lazy module loading (CUDA_MODULE_LOADING=LAZY)
+ * the first call on a device loads the module and so reserves the array there; a
+ * caller that needs a fixed footprint makes that first call at initialisation.
  *
  * params: as for dft_plan_create; precision must be DFT_FP32_STAB; only the
  *   grid and the radii are used (the weighted densities need no bath).
@@ -311,10 +334,16 @@ dft_status dft_profile_read(dft_plan* plan, const char* name, int* launches, dou
  *   bytes needed (64^3 fits with up to 5 species; 96^3 does not).
  * Set-up: the first call on each device looks up the device address of the
  *   scratch array (and sets the kernels' shared-memory limits) with that device
- *   current; make that first call before any CUDA stream capture.
+ *   current and keeps it for the life of the process; make that first call before
+ *   any CUDA stream capture.  A cudaDeviceReset invalidates it: do not use this entry
+ *   point on a device after resetting it in the same process.
+ * Completion: the call clears the scratch's status word (where a bounded wait of the
+ *   TMA passes records that it gave up), queues the work and reads the status word
+ *   back, so it returns only when n_out is complete (it synchronises cuda_stream);
+ *   DFT_ETIMEOUT if a wait gave up (n_out is then incomplete).
  * Sharing: every call on a device uses the same array and leaves its contents
- *   behind; each call writes every scratch element before reading it, so nothing
- *   needs clearing, but calls whose work overlaps on the GPU (different streams,
+ *   behind; each call clears the status word and writes every other scratch element
+ *   before reading it, but calls whose work overlaps on the GPU (different streams,
  *   or host threads without ordering) race on the array and corrupt each other.
  *   Order the calls (one stream, or events) to keep them apart.
  */

@@ -23,6 +23,8 @@ DFT_FP64 = 1
 STATUS = {0: "DFT_OK", -1: "DFT_EINVAL", -2: "DFT_ENONNEUTRAL", -3: "DFT_ENOMEM", -4: "DFT_ECUDA",
           -5: "DFT_EN3BOUND", -6: "DFT_ENONFINITE", -7: "DFT_ENOCONV", -8: "DFT_ETIMEOUT"}
 
+WAIT_POLLS_DEFAULT = 1 << 24   # DFT_WAIT_POLLS_DEFAULT
+
 KERNEL_NAMES = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
 
 
@@ -78,6 +80,7 @@ SIGNATURES = {
     "dft_batch_last_error": (ctypes.c_char_p, [_P]),
     "dft_batch_begin": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "dft_batch_iterate": (_I, [_P, _I, _D, _PD]),
+    "dft_set_wait_polls": (_I, [_P, ctypes.c_longlong]),
     "dft_profile_enable": (_I, [_P, _I]),
     "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
@@ -285,6 +288,10 @@ class Plan:
         self._check(self.lib.dft_picard_step_host(self.handle, hp(rho_host), hp(V_host), float(alpha),
                                                   ctypes.byref(r), ctypes.byref(a)))
         return r.value, a.value
+
+    def set_wait_polls(self, polls=None):
+        """Bound of the y passes' TMA tile waits (None: the default); 0 makes them give up at once."""
+        self._check(self.lib.dft_set_wait_polls(self.handle, WAIT_POLLS_DEFAULT if polls is None else int(polls)))
 
     def profile_enable(self, enable=True):
         self._check(self.lib.dft_profile_enable(self.handle, 1 if enable else 0))

@@ -57,6 +57,7 @@ struct dft_plan {
     void* slotA = nullptr;
     void* slotB = nullptr;
     void* gbuf = nullptr;
+    void* rho_lo = nullptr;         // FP32 plans: low part of the extended iterate of dft_iter_*
     void* stage_rho = nullptr;
     void* stage_V = nullptr;
     double* red_sum = nullptr;
@@ -89,6 +90,7 @@ struct dft_plan {
     bool iter_ready = false;
     const void* iter_rho = nullptr;
     const void* iter_V = nullptr;
+    long long wait_polls = DFT_WAIT_POLLS;   // bound of the y passes' TMA tile waits
 
     long long blocks_x(int LR) const { return ceil_div((long long)g.ny * g.nz, LR); }
 };
@@ -271,16 +273,17 @@ template <typename Real> struct Ops {
                                  double* red_energy = nullptr) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1), p->wait_polls));
         LAUNCH(p, K_ZFWD, (p->S + DFT_NSPEC + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
                                        T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 1), p->wait_polls));
         return DFT_OK;
     }
 
     // weighted densities mixed from slot A (and slot B) -> G at rho = w0 rho0 + w1 rho1
+    // rho_lo (FP32 iterations, else nullptr): low part of the extended iterate rho0 + rho_lo
     static dft_status second_half(dft_plan* p, bool use_B, bool materialise, const Real* rho0, const Real* rho1,
-                                  const Real* V, Real* rho_out, Real* g_out) {
+                                  const Real* V, Real* rho_out, Real* g_out, Real* rho_lo = nullptr) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         C* A = slot_n(p->slotA);
         C* B = use_B ? slot_n(p->slotB) : nullptr;
@@ -289,11 +292,11 @@ template <typename Real> struct Ops {
         LAUNCH(p, K_XPHI, ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0)) * DFT_NSPEC * CB(p),
                P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, B, materialise ? A : nullptr, T1(p),
                                   p->red_max, &p->ctl->status, nullptr, kf(p, 0), tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, T1(p), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, T1(p), &p->ctl->status, tw(p, 1), p->wait_polls));
         LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S * ((use_B ? 2 : 1) + 1 + (materialise ? 1 : 0))) * CB(p),
                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
                                        p->ctl, T1(p), esA, esB, materialise ? esA : nullptr, tw(p, 2)));
-        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1), p->wait_polls));
         if (p->ncanon > 0) {
             // fixed-number species: the sum of their Boltzmann factors first (its reciprocal
             // scales G in the update pass)
@@ -302,9 +305,10 @@ template <typename Real> struct Ops {
             LAUNCH(p, K_FIN, p->blocks_x(p->LRupd) * DFT_MAXS * 8.0,
                    P::canon_scale(p->stream, p->ctl, sp, p->red_canon, (int)p->blocks_x(p->LRupd)));
         }
-        LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0))),
+        LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0) +
+                                            (rho_lo ? (rho_out ? 2 : 1) : 0))),
                P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
-                                     g_out, p->red_sum, &p->ctl->status, tw(p, 0)));
+                                     g_out, rho_lo, p->red_sum, &p->ctl->status, tw(p, 0)));
         return DFT_OK;
     }
 
@@ -337,9 +341,10 @@ dft_status read_ctl(dft_plan* p) {
     cudaError_t e = cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("reading control block: ") + cudaGetErrorString(e));
+    // a timeout first: the passes after it ran on unfinished spectra
+    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
     if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
     if (p->ctl_host->status & DEV_NONFINITE) return fail(p, DFT_ENONFINITE, "non-finite density or residual met");
-    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
     return DFT_OK;
 }
 
@@ -359,6 +364,9 @@ dft_status reset_status(dft_plan* p) {
 template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const Real* V, cudaEvent_t v_ready = nullptr) {
     using O = Ops<Real>;
     TRY(reset_status(p));
+    // the extended iterate starts as the caller's rho with a zero low part
+    if (p->rho_lo && cudaMemsetAsync(p->rho_lo, 0, size_t(p->S) * p->g.n * sizeof(Real), p->stream) != cudaSuccess)
+        return fail(p, DFT_ECUDA, "memset of the iterate's low part");
     TRY(O::first_half(p, rho, p->slotA, 0));
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     if (v_ready && cudaStreamWaitEvent(p->stream, v_ready, 0) != cudaSuccess)
@@ -380,13 +388,14 @@ template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Re
     TRY(O::xinv(p, 1, O::slot_n(p->slotB) + 3 * p->g.nc, nullptr, nullptr, nullptr, 0, p->red_max, &nb));
     TRY(finalize(p, FIN_AMAX, 0, nb, alpha));
     const int nsum = (int)p->blocks_x(p->LRupd);
+    Real* lo = static_cast<Real*>(p->rho_lo);
     if (alpha < 0.0) {
-        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr));
+        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr, lo));
         TRY(finalize(p, FIN_F1, nsum, 0, alpha));
-        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr));
+        TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr, lo));
         TRY(finalize(p, FIN_F2_CHOOSE, nsum, 0, alpha));
     }
-    TRY(O::second_half(p, true, true, rho, g, V, rho, g));
+    TRY(O::second_half(p, true, true, rho, g, V, rho, g, lo));
     TRY(finalize(p, FIN_ACCEPT, nsum, (int)p->blocks_x(p->LRphi), alpha));
     (void)sizeof(C);
     return DFT_OK;
@@ -411,10 +420,10 @@ template <typename Real> dft_status c1_hs_t(dft_plan* p, const Real* rho, Real* 
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     LAUNCH(p, K_XPHI, 2.0 * DFT_NSPEC * CB(p), P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, O::slot_n(p->slotA), nullptr, nullptr,
                               O::T1(p), p->red_max, &p->ctl->status, nullptr, O::kf(p, 0), O::tw(p, 0)));
-    LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p), &p->ctl->status, O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p), &p->ctl->status, O::tw(p, 1), p->wait_polls));
     LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S) * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 1, p->S,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), &p->ctl->status, O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, O::T1(p), &p->ctl->status, O::tw(p, 1), p->wait_polls));
     TRY(O::xinv(p, p->S, O::T1(p), c1, nullptr, nullptr, -1, nullptr, nullptr));
     return DFT_OK;
 }
@@ -429,7 +438,7 @@ template <typename Real> dft_status c1_es_t(dft_plan* p, const Real* rho, Real* 
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     LAUNCH(p, K_ZBWD, 2.0 * nout * CB(p), P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 2, nout,
                                    p->ctl, O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
-    LAUNCH(p, K_YFFT, 2.0 * (nout) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), &p->ctl->status, O::tw(p, 1)));
+    LAUNCH(p, K_YFFT, 2.0 * (nout) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, nout, O::T1(p), &p->ctl->status, O::tw(p, 1), p->wait_polls));
     double offs[DFT_NCOMP + 2] = {0};
     for (int s = 0; s < p->S; ++s) offs[s] = -p->bath.mu_es[s];
     TRY(O::xinv(p, nout, O::T1(p), c1, psi, offs, -1, nullptr, nullptr));
@@ -538,12 +547,12 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
                                                         nullptr, nullptr, O::T1(p), p->red_max, &p->ctl->status,
                                                         r_phi, O::kf(p, 0), O::tw(p, 0)));
     LAUNCH(p, K_YFFT, 2.0 * DFT_NSPEC * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p),
-                                                        &p->ctl->status, O::tw(p, 1)));
+                                                        &p->ctl->status, O::tw(p, 1), p->wait_polls));
     LAUNCH(p, K_ZBWD, (DFT_NSPEC + 2 * S) * CB(p),
            P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 3, S, p->ctl,
                         O::T1(p), O::slot_es(p, p->slotA), nullptr, nullptr, O::tw(p, 2)));
     LAUNCH(p, K_YFFT, 2.0 * S * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, S, O::T1(p), &p->ctl->status,
-                                                O::tw(p, 1)));
+                                                O::tw(p, 1), p->wait_polls));
     LAUNCH(p, K_XUPD, S * (CB(p) + RB(p) * (2 + (d_rho ? 1 : 0) + (d_V ? 1 : 0))),
            P::xgrad(p->stream, p->g, p->ax, sp, p->LRupd, Real(dv), O::T1(p), rho, V, d_rho, d_V, r_g, O::tw(p, 0)));
     std::vector<double> h(need);
@@ -551,8 +560,8 @@ dft_status grad_t(dft_plan* p, const Real* rho, const Real* V, double* omega_out
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("reading gradient sums: ") + cudaGetErrorString(e));
-    if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
     if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
+    if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
     double energy = 0.0, qgam = 0.0, phisum = 0.0, ideal = 0.0;
     std::vector<double> Ni(S, 0.0);
     for (long long b = 0; b < n_zk; ++b) { energy += h[2 * b]; qgam += h[2 * b + 1]; }
@@ -820,7 +829,7 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
         }
         if (P::smem_x(p->g.nx, lpr_upd * L) <= size_t(optin)) {
             const float ms = time_it([&] {
-                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, p->red_sum,
+                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, nullptr, p->red_sum,
                            &p->ctl->status, O::tw(p, 0));
             });
             if (ms < best_ms[2]) { best_ms[2] = ms; best[2] = L; }
@@ -975,11 +984,14 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         {&p->slotA, slot_comps * g.nc * p->csize, "slot A"},
         {&p->slotB, slot_comps * g.nc * p->csize, "slot B"},
         {&p->gbuf, size_t(S) * g.n * p->rsize, "G buffer"},
+        // FP32 iterations carry the iterate as the caller's field plus this low part
+        {f64 ? nullptr : &p->rho_lo, size_t(S) * g.n * p->rsize, "iterate low part"},
         {(void**)&p->red_sum, nred * sizeof(double), "reduction sums"},
         {(void**)&p->red_max, nred * sizeof(float), "reduction maxima"},
         {(void**)&p->ctl, sizeof(Ctl), "control block"},
     };
     for (auto& a : allocs) {
+        if (!a.ptr) continue;
         if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             dft_plan_destroy(p);
@@ -1054,6 +1066,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->slotA);
     cudaFree(p->slotB);
     cudaFree(p->gbuf);
+    cudaFree(p->rho_lo);
     cudaFree(p->stage_rho);
     cudaFree(p->stage_V);
     cudaFree(p->red_sum);
@@ -1323,9 +1336,10 @@ dft_status dft_picard_step_host(dft_plan* p, void* rho_host, const void* V_host,
     if (e == cudaSuccess) e = cudaMemcpyAsync(rho_host, p->stage_rho, bytes, cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+    // a timeout first: the passes after it ran on unfinished spectra
+    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
     if (p->ctl_host->status & DEV_N3BOUND) return fail(p, DFT_EN3BOUND, "local packing fraction n3 >= 1 met");
     if (p->ctl_host->status & DEV_NONFINITE) return fail(p, DFT_ENONFINITE, "non-finite density or residual met");
-    if (p->ctl_host->status & DEV_TIMEOUT) return fail(p, DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up");
     if (resid_out) *resid_out = p->ctl_host->resid_prev;
     if (alpha_out) *alpha_out = p->ctl_host->alpha;
     return DFT_OK;
@@ -1496,6 +1510,15 @@ dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, doubl
             resid_out[i] = b->plans[i]->ctl_host->resid;
         }
     }
+    return DFT_OK;
+}
+
+dft_status dft_set_wait_polls(dft_plan* p, long long polls) {
+    TRY(check_plan(p));
+    if (polls < 0) return fail(p, DFT_EINVAL, "polls must be >= 0");
+    // a captured iteration holds the old bound in its kernel parameters
+    release_iter_graph(p);
+    p->wait_polls = polls;
     return DFT_OK;
 }
 

@@ -15,6 +15,8 @@
 // the x pass that takes the spectra to real space (and the divergence terms of the back
 // convolution in the x pass that leaves it), so the y and z passes carry nine components.
 #define DFT_NSPEC 9
+// Polls of a TMA tile wait before it gives up (the plans' default; dft_set_wait_polls)
+#define DFT_WAIT_POLLS (1LL << 24)
 
 template <typename Real> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };

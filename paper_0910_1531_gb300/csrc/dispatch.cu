@@ -89,8 +89,8 @@ cudaError_t Passes<Real>::xfwd(cudaStream_t st, const GridDesc& g, const AxisPla
 
 template <typename Real>
 cudaError_t Passes<Real>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
-                               C* data, int* status, const C* tw) {
-    DFT_SWITCH_Y(g.ny, yfft(st, inv, g, py, T, ncomp, data, status, tw))
+                               C* data, int* status, const C* tw, long long polls) {
+    DFT_SWITCH_Y(g.ny, yfft(st, inv, g, py, T, ncomp, data, status, tw, polls))
 }
 
 template <typename Real>
@@ -117,8 +117,10 @@ cudaError_t Passes<Real>::zconv_bwd(cudaStream_t st, const GridDesc& g, const Ax
 template <typename Real>
 cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                            const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                           Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw) {
-    DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw))
+                           Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                           const C* tw) {
+    DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, status,
+                               tw))
 }
 
 template <typename Real>

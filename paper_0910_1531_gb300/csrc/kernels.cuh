@@ -339,7 +339,8 @@ template <typename Real, int NY, int TY> __host__ __device__ constexpr size_t yf
 template <typename Real, bool INV, int NY, int TY>
 __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ CUtensorMap map, int ntiles_x,
                                                        int ntiles, int* __restrict__ status,
-                                                       const typename Cplx<Real>::type* __restrict__ twy) {
+                                                       const typename Cplx<Real>::type* __restrict__ twy,
+                                                       long long polls) {
     static_assert(NY > 0 && NY <= 256 && TY > 0, "compile-time TMA y pass");
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int cur = it & 1;
         C* st = stage0 + cur * TILE;
-        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1, polls);
         // an odd stage count leaves the result in X, which the first stage writes next
         if (NST % 2 == 1 && threadIdx.x == 0) tma::wait_read_all();
         if (__syncthreads_or(!ok)) {
@@ -1532,6 +1533,23 @@ __host__ __device__ constexpr int wd_slot(int c) { return (c == 1 || c == 5 || c
 
 // Load the Hermitian half rows of two components (mixed wA * A + wB * B) as Z = a + i b over the
 // full length nx (Z[nx-k] = conj(a_k) + i conj(b_k)).  Optionally stores the mixed half rows.
+// Items in flight per thread in the update pass's pointwise phase (build flag).
+#ifndef DFT_XUPD_BATCH
+#define DFT_XUPD_BATCH 1
+#endif
+
+// 16 bytes of consecutive real values (four floats or two doubles), for 16-byte loads and stores.
+template <typename Real> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ float4 ld16(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ double2 ld16(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void st16(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st16(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+__device__ __forceinline__ float& vel(float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
+__device__ __forceinline__ double& vel(double2& v, int e) { return e == 0 ? v.x : v.y; }
+template <typename V> __device__ __forceinline__ V vzero() { V v; memset(&v, 0, sizeof(V)); return v; }
+
 // Loads are issued in batches of kBatch elements per thread before any store, so that several
 // are in flight at once.
 template <typename Real, int NX>
@@ -2039,7 +2057,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                                                       const typename Cplx<Real>::type* __restrict__ cspec,
                                                       const Real* rho0, const Real* rho1,
                                                       const Real* __restrict__ V, Real* rho_out, Real* g_out,
-                                                      double* __restrict__ red_sum, int* __restrict__ status,
+                                                      Real* rho_lo, double* __restrict__ red_sum,
+                                                      int* __restrict__ status,
                                                       const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -2054,75 +2073,146 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec, A);
-    // rho0, rho1 and V of a thread's point: loaded one point ahead of its use; rho_out / g_out
-    // may alias rho0 / rho1, but a point's values are read before that point is written and the
-    // points are distinct
     const int total = LR * nx;
-    Real r0[DFT_MAXS], r1[DFT_MAXS], vv[DFT_MAXS];
-    auto load_point = [&](int idx, Real* a0, Real* a1, Real* av) {
-        const long long row = row0 + idx / nx;
-        const bool live = idx < total && row < nrows;
-        const long long pt = row0 * nx + idx;
-#pragma unroll
-        for (int s = 0; s < DFT_MAXS; ++s) {
-            a0[s] = a1[s] = av[s] = Real(0);
-            if (s < S && live) {
-                const long long o = (long long)s * g.n + pt;
-                a0[s] = rho0[o];
-                a1[s] = rho1 ? rho1[o] : Real(0);
-                av[s] = V[o];
-            }
-        }
-    };
-    __syncthreads();
-    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
-    load_point(threadIdx.x, r0, r1, vv);
-    const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
     // G_i = pref_i exp(mu0_i - V_i + c_i): the bath (rho_b, beta mu_HS,b), or for a
     // fixed-number species the normalisation of this evaluation and no bath constant
-    Real pref[DFT_MAXS], mu0[DFT_MAXS];
-#pragma unroll
-    for (int s = 0; s < DFT_MAXS; ++s) {
+    __shared__ Real s_pref[DFT_MAXS], s_mu0[DFT_MAXS], s_irb[DFT_MAXS];
+    if (threadIdx.x < DFT_MAXS) {
+        const int s = threadIdx.x;
         const bool cn = s < S && sp.canon[s];
-        pref[s] = cn ? Real(ctl->canon_scale[s]) : sp.rho_b[s];
-        mu0[s] = cn ? Real(0) : sp.mu_hs_b[s];
+        s_pref[s] = cn ? Real(ctl->canon_scale[s]) : sp.rho_b[s];
+        s_mu0[s] = cn ? Real(0) : sp.mu_hs_b[s];
+        s_irb[s] = sp.inv_rho_b[s];
     }
+    __syncthreads();
+    C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
+    const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
     // per-thread partial sum in the working precision with Kahan compensation, then
     // double-single (FP32) or FP64 across threads, FP64 across blocks
     Real acc = Real(0), comp = Real(0);
     bool bad = false;
-    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
-        Real n0[DFT_MAXS], n1[DFT_MAXS], nv[DFT_MAXS];
-        load_point(idx + kThreads, n0, n1, nv);
-        const int r = idx / nx, x = idx - (idx / nx) * nx;
-        if (row0 + r < nrows) {
+    // one point of species s: new iterate (and its low part), G, squared weighted residual
+    auto point = [&](int s, Real c, Real r0, Real r1, Real v, Real l0, Real& rho, Real& lo, Real& gval) {
+        lo = Real(0);
+        if (rho_lo) {
+            // extended iterate rho0 = r0 + l0 (a value and its rounding error):
+            // rho = rho0 + w1 (rho1 - rho0) formed so that steps below half an ulp of rho0
+            // accumulate in the low part instead of rounding away (w0 = 1 - w1), then split
+            // again into rho + lo by an error-free sum (Knuth's TwoSum)
+            const Real t = l0 + w1 * ((r1 - r0) - l0);
+            rho = r0 + t;
+            const Real bv = rho - r0;
+            lo = (r0 - (rho - bv)) + (t - bv);
+        } else {
+            rho = w0 * r0 + w1 * r1;
+        }
+        if (isinf(v) && v > Real(0)) gval = Real(0);
+        else gval = s_pref[s] * exp(s_mu0[s] - v + c);
+        if (!isfinite(gval) || !isfinite(rho)) bad = true;
+        const Real d = ((rho - gval) + lo) * s_irb[s];
+        const Real y = d * d - comp;
+        const Real t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    };
+    // rho_out / g_out / rho_lo may alias rho0 / rho1 / the low part read: every value is read
+    // before the same thread writes that element, and the threads' elements are distinct
+    if constexpr (NX > 0) {
+        // compile-time lengths: items (species, group of VW consecutive points of a row),
+        // KB items per thread with their 16-byte loads of rho0, rho1, V (and the low part)
+        // issued before any is used, results stored 16 bytes at a time
+        using V16 = typename Vec16<Real>::type;
+        constexpr int VW = Vec16<Real>::n;
+        constexpr int KB = DFT_XUPD_BATCH;
+        static_assert(NX % VW == 0, "row length a multiple of the vector width");
+        const int groups = total / VW;
+        const int items = S * groups;
+        for (int base = threadIdx.x; base < items; base += KB * kThreads) {
+            V16 a0[KB], a1[KB], av[KB], al[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int it = base + j * kThreads;
+                const int s = it / groups, gi = it - (it / groups) * groups;
+                const bool live = it < items && row0 + (gi * VW) / NX < nrows;
+                const long long o = (long long)s * g.n + row0 * NX + (long long)gi * VW;
+                a0[j] = a1[j] = av[j] = al[j] = vzero<V16>();
+                if (live) {
+                    a0[j] = ld16(rho0 + o);
+                    if (rho1) a1[j] = ld16(rho1 + o);
+                    av[j] = ld16(V + o);
+                    if (rho_lo) al[j] = ld16(rho_lo + o);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int it = base + j * kThreads;
+                const int s = it / groups, gi = it - (it / groups) * groups;
+                const int idx = gi * VW, r = idx / NX, x = idx - (idx / NX) * NX;
+                if (!(it < items && row0 + r < nrows)) continue;
+                const long long o = (long long)s * g.n + row0 * NX + idx;
+                const C* Rl = R + (r * lpr + s / 2) * pitch;
+                V16 orho, og, olo;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const C pc = Rl[xo<NX>(x + e)];
+                    point(s, (s & 1) ? pc.y : pc.x, vel(a0[j], e), vel(a1[j], e), vel(av[j], e), vel(al[j], e),
+                          vel(orho, e), vel(olo, e), vel(og, e));
+                }
+                if (rho_out) {
+                    st16(rho_out + o, orho);
+                    if (rho_lo) st16(rho_lo + o, olo);
+                }
+                if (g_out) st16(g_out + o, og);
+            }
+        }
+    } else {
+        // run-time lengths: one point per thread at a time, its rho0, rho1, V (and low part)
+        // loaded one point ahead of their use
+        Real r0[DFT_MAXS], r1[DFT_MAXS], vv[DFT_MAXS], rl[DFT_MAXS];
+        auto load_point = [&](int idx, Real* a0, Real* a1, Real* av, Real* al) {
+            const long long row = row0 + idx / nx;
+            const bool live = idx < total && row < nrows;
             const long long pt = row0 * nx + idx;
 #pragma unroll
             for (int s = 0; s < DFT_MAXS; ++s) {
-                if (s >= S) continue;
-                const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
-                const Real c = (s & 1) ? pr.y : pr.x;
-                const long long o = (long long)s * g.n + pt;
-                const Real rho = w0 * r0[s] + w1 * r1[s];
-                const Real v = vv[s];
-                Real gval;
-                if (isinf(v) && v > Real(0)) gval = Real(0);
-                else gval = pref[s] * exp(mu0[s] - v + c);
-                if (!isfinite(gval) || !isfinite(rho)) bad = true;
-                const Real e = (rho - gval) * sp.inv_rho_b[s];
-                const Real y = e * e - comp;
-                const Real t = acc + y;
-                comp = (t - acc) - y;
-                acc = t;
-                if (rho_out) rho_out[o] = rho;
-                if (g_out) g_out[o] = gval;
+                a0[s] = a1[s] = av[s] = al[s] = Real(0);
+                if (s < S && live) {
+                    const long long o = (long long)s * g.n + pt;
+                    a0[s] = rho0[o];
+                    a1[s] = rho1 ? rho1[o] : Real(0);
+                    av[s] = V[o];
+                    if (rho_lo) al[s] = rho_lo[o];
+                }
             }
-        }
+        };
+        load_point(threadIdx.x, r0, r1, vv, rl);
+        for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+            Real n0[DFT_MAXS], n1[DFT_MAXS], nv[DFT_MAXS], nl[DFT_MAXS];
+            load_point(idx + kThreads, n0, n1, nv, nl);
+            const int r = idx / nx, x = idx - (idx / nx) * nx;
+            if (row0 + r < nrows) {
+                const long long pt = row0 * nx + idx;
 #pragma unroll
-        for (int s = 0; s < DFT_MAXS; ++s) {
-            r0[s] = n0[s];
-            r1[s] = n1[s];
-            vv[s] = nv[s];
+                for (int s = 0; s < DFT_MAXS; ++s) {
+                    if (s >= S) continue;
+                    const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
+                    const long long o = (long long)s * g.n + pt;
+                    Real rho, lo, gval;
+                    point(s, (s & 1) ? pr.y : pr.x, r0[s], r1[s], vv[s], rl[s], rho, lo, gval);
+                    if (rho_out) {
+                        rho_out[o] = rho;
+                        if (rho_lo) rho_lo[o] = lo;
+                    }
+                    if (g_out) g_out[o] = gval;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                r0[s] = n0[s];
+                r1[s] = n1[s];
+                vv[s] = nv[s];
+                rl[s] = nl[s];
+            }
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);

@@ -59,12 +59,12 @@ cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const Axi
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                                int LR, const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1,
-                               const Real* V, Real* rho_out, Real* g_out, double* red_sum, int* status,
-                               const C* tw) {
+                               const Real* V, Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum,
+                               int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
     dftk::k_xupdate<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
-        g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, red_sum, status, tw);
+        g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, status, tw);
     return cudaSuccess;
 }
 
@@ -130,7 +130,7 @@ cudaError_t LaunchY<Real, N>::init() {
 
 template <typename Real, int N>
 cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp,
-                                   C* data, int* status, const C* tw) {
+                                   C* data, int* status, const C* tw, long long polls) {
     if constexpr (N > 0) {
         // TMA path: persistent CTAs, two TMA-filled stages + one FFT scratch tile + twiddles + 2 mbarriers
         constexpr int TY = dft_tile_y<Real>(N);
@@ -155,8 +155,8 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
             if (occ < 1) occ = 1;
         }
         const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-        if (inv) dftk::k_yfft_tma<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw);
-        else dftk::k_yfft_tma<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw);
+        if (inv) dftk::k_yfft_tma<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw, polls);
+        else dftk::k_yfft_tma<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw, polls);
         return cudaSuccess;
     } else {
         dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.nz, (unsigned)ncomp);
@@ -164,6 +164,7 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
         if (inv) dftk::k_yfft<Real, true, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
         else dftk::k_yfft<Real, false, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
         (void)status;
+        (void)polls;
         return cudaSuccess;
     }
 }

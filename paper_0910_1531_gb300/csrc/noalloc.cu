@@ -9,8 +9,10 @@
 // file-scope device array instead of memory obtained from cudaMalloc.
 //
 // The array is part of the library image: every GPU on which this part of the library
-// is loaded holds it (kNoAllocScratchBytes) until the process exits, whether or not
-// the entry point is ever called.
+// is loaded holds it (kNoAllocScratchBytes) until the process exits.  Under lazy module
+// loading (CUDA_MODULE_LOADING=LAZY, the default of recent CUDA runtimes) the module, and
+// with it the array, is loaded on a device by the first call there; callers who need a
+// fixed footprint make one call at initialisation.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -35,7 +37,9 @@ float2* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // One-time set-up per device, with that device current: look up the device address of
 // the scratch array and allow the kernels their full shared memory.  Returns nullptr
-// (and an error text) on failure.
+// (and an error text) on failure.  The result is kept for the life of the process: a
+// cudaDeviceReset of that device invalidates it, so the entry point must not be used on a
+// device after a reset within the same process.
 float2* device_scratch(int dev, std::string* err) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (dev < 0 || dev >= kMaxDevices) {
@@ -147,11 +151,13 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
     const int LX = lines_for(g.nx, 1, 48 * 1024, 32);
     const int LR = lines_for(g.nx, DFT_NCOMP / 2, 48 * 1024, 16);
 
-    // Every scratch element the pipeline reads is first written by this call, so nothing
-    // needs clearing; the twiddles are rewritten every call (the previous call may have
-    // used other grid sizes).
-    // the status word records a bounded wait that gave up inside the y pass (never expected)
+    // The status word, where a bounded TMA wait of the y or z passes records that it gave up,
+    // keeps the previous call's value: it is cleared here and read back at the end.  Every
+    // other scratch element the pipeline reads is first written by this call; the twiddles
+    // are rewritten every call (the previous call may have used other grid sizes).
     int* status = reinterpret_cast<int*>(base + o_status);
+    e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e != cudaSuccess) FAIL(DFT_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     k_twiddles<<<4, 256, 0, st>>>(base + o_twx, g.nx);
     k_twiddles<<<4, 256, 0, st>>>(base + o_twy, g.ny);
     k_twiddles<<<4, 256, 0, st>>>(base + o_twz, g.nz);
@@ -168,6 +174,14 @@ dft_status dft_weighted_densities_noalloc(const dft_params* prm, void* cuda_stre
                                 nullptr, 1, kfx, base + o_twx);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) FAIL(DFT_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    // the status word, read back once the work is done (a pageable copy into a local: no
+    // allocation); this makes the call synchronous with respect to `st`
+    int dev_status = 0;
+    e = cudaMemcpyAsync(&dev_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) FAIL(DFT_ECUDA, std::string("status read-back: ") + cudaGetErrorString(e));
+    if (dev_status & DEV_TIMEOUT)
+        FAIL(DFT_ETIMEOUT, "a bounded wait on an asynchronous copy gave up; n_out is incomplete");
     if (errbuf && errbuf_len > 0) errbuf[0] = '\0';
     return DFT_OK;
 #undef FAIL

@@ -99,7 +99,8 @@ struct LaunchX {
                      const C* tw);
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                        Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
+                        Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                        const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
                      Real kfx, const C* tw);
@@ -115,7 +116,7 @@ struct LaunchY {
     using C = typename Cplx<Real>::type;
     static cudaError_t init();
     static cudaError_t yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
-                     int* status, const C* tw);
+                     int* status, const C* tw, long long polls);
 };
 
 template <typename Real, int N>
@@ -143,8 +144,9 @@ struct Passes {
 
     static cudaError_t xfwd(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int ncomp, int lx, const Real* in,
                      C* out, const C* tw);
+    // polls: bound of each TMA tile wait (DFT_WAIT_POLLS; the drains after a give-up keep it)
     static cudaError_t yfft(cudaStream_t st, bool inv, const GridDesc& g, const AxisPlan& py, int T, int ncomp, C* data,
-                     int* status, const C* tw);
+                     int* status, const C* tw, long long polls = DFT_WAIT_POLLS);
     static cudaError_t zconv_fwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int want_psi, const C* in, C* slot_n, C* slot_es,
                           double* red_energy, const C* tw, int* status);
@@ -154,9 +156,12 @@ struct Passes {
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
+    // rho_lo (or nullptr): low part of an extended iterate rho0 + rho_lo, read
+    // with rho0 and, when rho_out is written, replaced by the low part of the new iterate
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                        Real* rho_out, Real* g_out, double* red_sum, int* status, const C* tw);
+                        Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                        const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
                      Real kfx, const C* tw);

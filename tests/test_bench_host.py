@@ -24,11 +24,29 @@ def test_digest_ignores_comments_and_layout_but_not_code(tmp_path, monkeypatch):
     assert bench.csrc_digest() != d0
 
 
-def test_recorded_traffic_matches_the_current_kernels():
-    assert bench.NCU_TRAFFIC["digest"] == bench.csrc_digest()
+def test_digest_covers_the_build_flags(tmp_path, monkeypatch):
+    pkg = tmp_path / "paper_0910_1531_gb300"
+    (pkg / "csrc").mkdir(parents=True)
+    (pkg / "csrc" / "k.cuh").write_text("int f(int a) { return a + 1; }\n")
+    (pkg / "build.py").write_text('"""doc"""\nFLAGS = ["-O3"]  # flags\n')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.csrc_digest()
+    (pkg / "build.py").write_text('"""other doc"""\nFLAGS = ["-O3"]   # other comment\n')
+    assert bench.csrc_digest() == d0
+    (pkg / "build.py").write_text('"""doc"""\nFLAGS = ["-O2"]\n')
+    assert bench.csrc_digest() != d0
+
+
+def test_recorded_traffic_is_well_formed_and_dropped_once_stale(monkeypatch):
     for key, per in bench.NCU_TRAFFIC["captures"].items():
         assert set(per) == set(bench.KERNELS), key
         assert all(v >= 0 for v in per.values())
+    key = next(iter(bench.NCU_TRAFFIC["captures"]))
+    name, prec = key.rsplit("/", 1)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "digest", bench.csrc_digest())
+    assert bench.recorded_traffic(name, prec, "xphi") == bench.NCU_TRAFFIC["captures"][key]["xphi"]
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "digest", "0" * 16)
+    assert bench.recorded_traffic(name, prec, "xphi") is None
 
 
 def test_fp64_peak_from_unit_counts():

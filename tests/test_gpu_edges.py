@@ -5,7 +5,8 @@ record a flag, the call returns the status, and the next call on the same plan w
 * a species excluded from every voxel: its G is 0 everywhere, the others match the oracle;
 * a bath at packing fraction 0.6: the pointwise terms take the FP64 branch (n3 >= 0.5) and the
   uniform bath stays a fixed point;
-* n3 >= 1 somewhere: DFT_EN3BOUND; an infinite Boltzmann factor: DFT_ENONFINITE.
+* n3 >= 1 somewhere: DFT_EN3BOUND; an infinite Boltzmann factor: DFT_ENONFINITE;
+* TMA tile waits bounded at 0 polls (each gives up at once): DFT_ETIMEOUT.
 """
 import numpy as np
 import pytest
@@ -107,4 +108,26 @@ def test_n3_bound_and_nonfinite_are_reported_and_the_plan_recovers():
     assert e.value.status == -6                  # DFT_ENONFINITE
     g, r = plan.picard_map(_dev(good, plan), _dev(V, plan))
     assert relerr(g.cpu().numpy(), good) < 1e-5 and r < 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_bounded_wait_gives_up_and_the_plan_recovers(precision):
+    # A y length with a compile-time TMA pass (32): with a bound of 0 polls every tile wait gives
+    # up at once, each CTA drains the copies it has in flight (full bound) and stops, and the
+    # call reports DFT_ETIMEOUT; with the default bound back, the same plan's next G and step
+    # match the oracle.
+    from paper_0910_1531_gb300.binding import DftError
+    shape, h = (12, 32, 18), (0.1, 0.09, 0.11)
+    prob = F.Problem(shape, h, *SPECIES)
+    rho = workloads.random_density(shape, 2, prob.bath.rho, 0.3, seed=37)
+    V = np.zeros_like(rho)
+    plan = _plan(precision, shape=shape, h=h)
+    plan.set_wait_polls(0)
+    with pytest.raises(DftError) as e:
+        plan.picard_map(_dev(rho, plan), _dev(V, plan))
+    assert e.value.status == -8                  # DFT_ETIMEOUT
+    plan.set_wait_polls(None)
+    g, _ = plan.picard_map(_dev(rho, plan), _dev(V, plan))
+    assert relerr(g.cpu().numpy(), F.picard_map(prob, rho, V)) < TOL[precision]
     plan.close()

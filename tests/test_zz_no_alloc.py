@@ -5,9 +5,10 @@ memory for its own pool, code that must not trigger an allocation's implicit dev
 synchronisation, users who need a fixed device footprint); for them
 dft_weighted_densities_noalloc keeps its scratch in a fixed device array inside the
 library.  This file checks, through the C ABI, that two calls in a row (and a third on
-another grid) give the same weighted densities as dft_weighted_densities, and that a
-grid too large for the fixed scratch is refused with a clear message.  It runs last so
-that a failure here cannot hide the other tests; it passes alone or after them.
+another grid) give the same weighted densities as dft_weighted_densities, that the
+largest documented case (64^3, five species) does too, that they match the FP64 oracle,
+and that a grid too large for the fixed scratch is refused with a clear message.  It runs
+last so that a failure here cannot hide the other tests; it passes alone or after them.
 """
 import ctypes
 
@@ -24,6 +25,12 @@ TOL = 1e-5   # the FP32 weighted-density tolerance of tests/test_gpu_parity.py
 RADIUS = [0.095, 0.181]
 VALENCE = [1.0, -1.0]
 MOLAR = [0.5, 0.5]
+# five species (radii nm, valences, molar), electroneutral
+RADIUS5 = [0.095, 0.099, 0.181, 0.14, 0.12]
+VALENCE5 = [1.0, 2.0, -1.0, -0.5, 0.0]
+MOLAR5 = [0.1, 0.01, 0.1, 0.04, 0.3]
+# the weighted densities alpha as index lists into the ten components (a vector is one field)
+FIELDS = [[0], [1], [2], [3], [4, 5, 6], [7, 8, 9]]
 
 
 @pytest.fixture(scope="module")
@@ -33,10 +40,10 @@ def lib():
     return binding.load_library()
 
 
-def _params(shape, h, radius):
+def _params(shape, h, radius, valence=VALENCE, molar=MOLAR):
     from paper_0910_1531_gb300.binding import DftParams
-    keep = [np.array(radius, dtype=np.float64), np.array(VALENCE[:len(radius)], dtype=np.float64),
-            np.array(MOLAR[:len(radius)], dtype=np.float64)]
+    keep = [np.array(radius, dtype=np.float64), np.array(valence[:len(radius)], dtype=np.float64),
+            np.array(molar[:len(radius)], dtype=np.float64)]
     pd = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     nz, ny, nx = shape
     prm = DftParams(nx, ny, nz, h, h, h, len(radius), pd(keep[0]), pd(keep[1]), pd(keep[2]), 298.15, 78.5, 0)
@@ -79,5 +86,57 @@ def test_rejects_a_grid_beyond_the_fixed_scratch(lib):
     rho = torch.zeros((2,) + shape, dtype=torch.float32, device="cuda")
     out = torch.zeros((10,) + shape, dtype=torch.float32, device="cuda")
     st, msg = _noalloc(lib, prm, rho, out)
+    assert st == -1
+    assert "bytes of scratch" in msg
+
+
+def test_largest_documented_case_matches_plan_entry_point(lib):
+    # 64^3 with five species: (2 S + 10) half spectra of 64 x 64 x 34 points, 22.3 MB of the 24 MiB
+    from paper_0910_1531_gb300 import binding
+    shape, h = (64, 64, 64), 0.1
+    rho_np = workloads.random_density(shape, 5, [0.06, 0.006, 0.06, 0.024, 0.18], 0.4, 5)
+    rho = torch.tensor(rho_np, dtype=torch.float32, device="cuda")
+    plan = binding.Plan(shape, h, RADIUS5, VALENCE5, MOLAR5, precision="fp32")
+    expect = plan.weighted_densities(rho).cpu().numpy()
+    plan.close()
+    prm, keep = _params(shape, h, RADIUS5, VALENCE5, MOLAR5)
+    for _ in range(2):
+        out = torch.full((10,) + shape, float("nan"), dtype=torch.float32, device="cuda")
+        st, msg = _noalloc(lib, prm, rho, out)
+        assert st == 0, msg
+        got = out.cpu().numpy()
+        for a in range(10):
+            assert _relerr(got[a], expect[a]) < TOL, a
+
+
+def test_matches_the_oracle(lib):
+    # the FP64 oracle's weighted densities (eq. nDef by eq. conv), per field alpha
+    from oracle import functional as F
+    shape, h = (24, 32, 20), (0.08, 0.1, 0.09)
+    prob = F.Problem(shape, h, RADIUS, VALENCE, MOLAR)
+    rho_np = workloads.random_density(shape, 2, prob.bath.rho, 0.4, 11)
+    expect = F.weighted_densities(prob, rho_np)
+    rho = torch.tensor(rho_np, dtype=torch.float32, device="cuda")
+    prm, keep = _params(shape, h[0], RADIUS)
+    prm.hx, prm.hy, prm.hz = h
+    out = torch.full((10,) + shape, float("nan"), dtype=torch.float32, device="cuda")
+    st, msg = _noalloc(lib, prm, rho, out)
+    assert st == 0, msg
+    got = out.cpu().numpy()
+    for idx in FIELDS:
+        assert _relerr(got[idx], expect[idx]) < TOL, idx
+
+
+def test_limit_is_the_scratch_size(lib):
+    # 72^3 (half spectra of 72 x 72 x 38 points): (2 S + 10) spectra fit in 24 MiB for two
+    # species (22.1 MB) and not for three (25.2 MB)
+    shape = (72, 72, 72)
+    rho = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+    out = torch.zeros((10,) + shape, dtype=torch.float32, device="cuda")
+    prm, keep = _params(shape, 0.05, RADIUS)
+    st, msg = _noalloc(lib, prm, rho, out)
+    assert st == 0, msg
+    prm3, keep3 = _params(shape, 0.05, RADIUS5[:3], VALENCE5[:3], [0.1, 0.01, 0.12])
+    st, msg = _noalloc(lib, prm3, rho, out)
     assert st == -1
     assert "bytes of scratch" in msg
