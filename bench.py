@@ -250,21 +250,24 @@ def job_throughput(units_per_rank, world, ms_max):
 # ----------------------------------------------------------------------------------------
 # CPU oracle sample (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------------------
-def oracle_sample(w, prob=None):
-    """Time one G evaluation and one weighted-density evaluation of the oracle on the full
-    workload; a line-search iteration of the oracle costs 3 G + 2 weighted densities."""
-    import numpy as np
+def oracle_iteration(prob, rho, V, g, alpha_prev):
+    """One whole line-search Picard iteration of the oracle from rho (with g = G(rho) known): the
+    step (two sampled G evaluations and two n3 maxima) and G of the new iterate, as
+    oracle.picard.solve does it.  Returns (rho_new, g_new, alpha, seconds)."""
     from oracle import functional as F
-    if prob is None:
-        prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar, n_fixed=w.n_fixed)
-    rho = w.initial_rho_nm3(prob.bath.rho)
+    from oracle import picard as P
     t0 = time.perf_counter()
-    F.picard_map(prob, rho, w.V)
-    t1 = time.perf_counter()
-    F.weighted_densities(prob, rho)
-    t2 = time.perf_counter()
-    t_it = 3 * (t1 - t0) + 2 * (t2 - t1)
-    return prob, t1 - t0, t2 - t1, t_it
+    rho_new, info = P.picard_step(prob, rho, V, g0=g, alpha_prev=alpha_prev)
+    g_new = F.picard_map(prob, rho_new, V)
+    return rho_new, g_new, info["alpha"], time.perf_counter() - t0
+
+
+def oracle_start(w):
+    """The oracle's problem, the initial density and its G (untimed set-up of the oracle runs)."""
+    from oracle import functional as F
+    prob = F.Problem(w.shape, w.h, w.radius, w.z, w.bulk_molar, n_fixed=w.n_fixed)
+    rho = w.initial_rho_nm3(prob.bath.rho)
+    return prob, rho, F.picard_map(prob, rho, w.V)
 
 
 def run_reference(args):
@@ -272,28 +275,26 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = workload(args)
-    # time-boxed: one sample (one G and one weighted-density evaluation of the full workload)
-    # takes seconds at 128^3, so the warm-up is one sample and the timed steps stop once the
-    # samples so far have used REFERENCE_BUDGET_S (at least one is always timed)
-    prob = None
+    # time-boxed: one oracle iteration takes seconds (about 12 s at 128^3 on 16 Grace cores), so
+    # the warm-up is one iteration and the timed iterations stop once REFERENCE_BUDGET_S is used
+    # (at least one is always timed); steps reports the iterations actually timed
+    prob, rho, g = oracle_start(w)
+    alpha = None
     for _ in range(min(args.warmup, 1)):
-        prob, *_ = oracle_sample(w, prob)
-    t_its, t_g, t_wd = [], [], []
-    t_start = time.perf_counter()
+        rho, g, alpha, _ = oracle_iteration(prob, rho, w.V, g, alpha)
+    t_its = []
     for _ in range(args.steps):
-        prob, tg, twd, tit = oracle_sample(w, prob)
-        t_its.append(tit)
-        t_g.append(tg)
-        t_wd.append(twd)
-        if time.perf_counter() - t_start > REFERENCE_BUDGET_S:
+        rho, g, alpha, t = oracle_iteration(prob, rho, w.V, g, alpha)
+        t_its.append(t)
+        if sum(t_its) > REFERENCE_BUDGET_S:
             break
     mean_it = sum(t_its) / len(t_its)
     value = 1.0 / mean_it
     cores = blas_threads()
-    sample = (f"per step one oracle G(rho) ({sum(t_g)/len(t_g):.2f} s) and one weighted-density evaluation "
-              f"({sum(t_wd)/len(t_wd):.2f} s) on the full {w.shape[0]}^3 workload; iteration time = 3 G + 2 WD; "
-              f"{len(t_its)} of {args.steps} requested steps timed (budget {REFERENCE_BUDGET_S:.0f} s), "
-              f"{min(args.warmup, 1)} warm-up sample")
+    sample = (f"{len(t_its)} whole oracle line-search iterations (step with two sampled G and two n3 maxima, "
+              f"then G of the new iterate; {mean_it:.2f} s each) on the full {w.shape[0]}^3 workload from "
+              f"the bath density after {min(args.warmup, 1)} untimed one; {args.steps} requested, time-boxed "
+              f"to {REFERENCE_BUDGET_S:.0f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(t_its),
             "steps_requested": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_it * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -310,16 +311,14 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------
-def run_batch(args):
-    """Secondary line: 64 seeded NaCl state points on ragged grids {32,48,64,96}^3, each with a
-    centred hard sphere, advanced together by CUDA-graph replays; value = state-iterations/s."""
+def batch_measure(args, world, steps, warmup):
+    """64 seeded NaCl state points on ragged grids {32,48,64,96}^3, each with a centred hard sphere,
+    advanced together by CUDA-graph replays (dft_batch_iterate); returns (state-iterations/s of
+    the job, record)."""
     import numpy as np
     import torch
-    from paper_0910_1531_gb300 import binding, build, workloads
+    from paper_0910_1531_gb300 import binding, workloads
 
-    world, rank, local = dist_setup()
-    build.build()
-    torch.cuda.set_device(local)
     ws = workloads.batch_state_points(count=args.batch_count, seed=4)
     dt = torch.float64 if args.precision == "fp64" else torch.float32
     specs = [dict(shape=w.shape, h=w.h, radius=w.radius, valence=w.z, bulk_molar=w.bulk_molar) for w in ws]
@@ -339,48 +338,62 @@ def run_batch(args):
         Vs.append(V)
     batch = binding.Batch(specs, precision=args.precision)
     batch.begin(rhos, Vs)
-    batch.iterate(args.warmup, -1.0, resid=False)
+    batch.iterate(warmup, -1.0, resid=False)
     torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    batch.iterate(steps, -1.0, resid=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    resid = batch.iterate(1, -1.0, resid=True)
+    batch.close()
+    n_states = len(ws)
+    value = job_throughput(n_states * steps, world, ms)
+    peak, peak_kind = measured_peaks()
+    achieved = byte_per_it * steps / (ms * 1e-3) / 1e9
+    sizes = {}
+    for w in ws:
+        sizes[str(w.shape[0])] = sizes.get(str(w.shape[0]), 0) + 1
+    rec = {"value": value, "unit": "state Picard iterations/s", "steps": steps, "ms_per_step": ms / steps,
+           "config": {"workload": f"batch of {n_states} NaCl state points, ragged grids", "grids": sizes,
+                      "h_nm": 0.1, "c_molar": "log-uniform 0.01-1", "sphere_R_nm": "uniform 0.3-1.0", "seed": 4,
+                      "step": "one line-search Picard iteration of every state (one CUDA-graph launch)",
+                      "max_resid_after": float(np.max(resid))},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "kernel": "whole batched iteration", "peak_source": f"{peak_kind} hbm_gbs",
+                        "algorithmic_bytes_per_step": byte_per_it}}
+    return value, rec
+
+
+def run_batch(args):
+    """Secondary line: the batched form alone (64 ragged state points); value =
+    state-iterations/s."""
+    import torch
+    from paper_0910_1531_gb300 import build
+
+    world, rank, local = dist_setup()
+    build.build()
+    torch.cuda.set_device(local)
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
     sampler = ClockSampler(uuid)
-    stream = torch.cuda.current_stream()
-    barrier(world)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    batch.iterate(args.steps, -1.0, resid=False)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    value, rec = batch_measure(args, world, args.steps, args.warmup)
     clocks = sampler.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    resid = batch.iterate(1, -1.0, resid=True)
-    n_states = len(ws)
-    value = job_throughput(n_states * args.steps, world, ms)
-    peak, peak_kind = measured_peaks()
-    achieved = byte_per_it * args.steps / (ms * 1e-3) / 1e9
-    sizes = {}
-    for w in ws:
-        sizes[str(w.shape[0])] = sizes.get(str(w.shape[0]), 0) + 1
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "state Picard iterations/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        line = {"metric": METRIC, "value": value, "unit": rec["unit"], "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-                "config": {"workload": f"batch of {n_states} NaCl state points, ragged grids", "grids": sizes,
-                           "h_nm": 0.1, "c_molar": "log-uniform 0.01-1", "sphere_R_nm": "uniform 0.3-1.0",
-                           "step": "one line-search Picard iteration of every state (one CUDA-graph launch)",
-                           "l2": "no flush: inputs and scratch of 64 states exceed L2",
-                           "max_resid_after": float(np.max(resid))},
-                "clocks": clocks,
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "whole batched iteration",
-                             "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_step": byte_per_it}}
+                "config": dict(rec["config"], l2="no flush: inputs and scratch of 64 states exceed L2"),
+                "clocks": clocks, "roofline": rec["roofline"]}
         print(json.dumps(line))
-    batch.close()
     return 0
 
 
@@ -500,6 +513,177 @@ def cufft_comparator(plan, w, rho, V, reps, stream):
                     "Poisson, Delta C, exp update, residual)"}
 
 
+def graph_iterations_ms(plan, rho, V, alpha, steps, warmup, stream, world):
+    """Device time (ms, CUDA events on the stream, max over ranks) of `steps` Picard iterations
+    queued as replays of the plan's one-iteration CUDA graph, after `warmup` untimed ones."""
+    import torch
+    plan.iter_begin(rho, V)
+    plan.iter_run(rho, V, warmup, alpha, sync=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.iter_run(rho, V, steps, alpha, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(ev0.elapsed_time(ev1), world)
+
+
+def profile_iterations(plan, rho, V, alpha, steps, stream):
+    """The same iterations launched one by one with the library's CUDA events around every kernel
+    (inside the NVTX range the ncu commands of profiles/ filter on): per kernel kind (launches,
+    ms, algorithmic bytes), and the wall of the range in ms."""
+    import torch
+    plan.profile_enable(True)
+    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    torch.cuda.nvtx.range_push("profiled_steps")     # ncu --nvtx-include "profiled_steps/"
+    for _ in range(steps):
+        plan.iter_step(rho, V, alpha, sync=False)
+    torch.cuda.nvtx.range_pop()
+    ep1.record(stream)
+    torch.cuda.synchronize()
+    prof = {k: plan.profile_read(k) for k in KERNELS}
+    plan.profile_enable(False)
+    return prof, ep0.elapsed_time(ep1)
+
+
+def kernel_table(prof, peak):
+    total = sum(prof[k][1] for k in KERNELS)
+    out = {}
+    for k in KERNELS:
+        n, ms, by = prof[k]
+        gbps = by / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[k] = {"launches": n, "ms": round(ms, 4), "share": round(ms / total, 4) if total else None,
+                  "GBps": round(gbps, 1) if gbps else None, "frac": round(gbps / peak, 3) if gbps else None}
+    return out
+
+
+def dominant_roofline(prof, w, precision):
+    """Roofline of the kernel with the largest share of device time: algorithmic bytes per launch
+    over its live event time against the measured HBM copy bandwidth (FP32), or its transform
+    flops against the FP64 arithmetic peak (the plain-FP64 form is FP64-pipe bound)."""
+    peak, peak_kind = measured_peaks()
+    dom = max((k for k in KERNELS if k != "finalize"), key=lambda k: prof[k][1])
+    n_l, t_ms, by = prof[dom]
+    achieved = by / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(w.name, precision, dom), "kernel": dom,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": by / max(n_l, 1), "ms_per_launch": t_ms / max(n_l, 1)}
+    if precision == "fp64" and dom == "xphi":
+        # the plain-FP64 form runs on the FP64 pipe (1/64 of the FP32 rate on this part): its
+        # roofline is arithmetic.  Algorithmic flops of the x pass: ten real rows per grid row,
+        # i.e. five complex nx-point transforms each way, at 5 nx log2(nx) flops each (the
+        # pointwise Phi' and mixing work is not counted: a lower bound of the achieved rate)
+        nz_, ny_, nx_ = w.shape
+        flops = 2 * 5 * ny_ * nz_ * 5.0 * nx_ * math.log2(nx_)
+        t_launch = t_ms * 1e-3 / max(n_l, 1)
+        achieved_tf = flops / t_launch / 1e12 if t_launch > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_TFLOPS, "traffic": None, "kernel": dom,
+                    "peak_source": "nominal FP64: 152 SMs x 4 FP64 flop/clock x 2.07 GHz (not measured)",
+                    "flop_model": "5 nx log2(nx) per complex x transform, 10 per grid row",
+                    "flops_per_launch": flops, "ms_per_launch": t_ms / max(n_l, 1),
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
+    return roofline
+
+
+def picard_to_tolerance(plan, rho0, V, alpha, tol, max_it, chunk=10):
+    """Wall time from the initial density to r < tol by line-search (or fixed-mixing) Picard
+    iterations as graph replays, the residual read every `chunk` iterations."""
+    import torch
+    rho = torch.tensor(rho0, dtype=plan.dtype, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.iter_begin(rho, V)
+    it, r = 0, float("inf")
+    while it < max_it:
+        r = plan.iter_run(rho, V, chunk, alpha)
+        it += chunk
+        if r < tol:
+            break
+    t = time.perf_counter() - t0
+    return {"solver": "picard" + (" (line search)" if alpha < 0 else f" (fixed mixing {alpha})"), "tol": tol,
+            "iterations": it, "resid": r, "seconds": t, "converged": bool(r < tol), "checked_every": chunk}
+
+
+def newton_to_tolerance(plan, rho, V, tol, max_newton=100):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its, gevals, r, ok = plan.solve_newton(rho, V, tol, max_newton=max_newton, krylov_dim=30)
+    return {"solver": "newton-krylov (dft_solve_newton)", "tol": tol, "newton_steps": its, "g_evaluations": gevals,
+            "resid": r, "seconds": time.perf_counter() - t0, "converged": bool(ok)}
+
+
+def fp64_record(args, w, stream, world):
+    """The plain-FP64 form on the same workload: iterations/s, its arithmetic roofline and the
+    time to the configuration's tolerance."""
+    import torch
+    from paper_0910_1531_gb300 import binding
+    plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp64", n_fixed=w.n_fixed)
+    rho0 = w.initial_rho_nm3(plan.bulk()["rho"])
+    rho = torch.tensor(rho0, dtype=torch.float64, device="cuda")
+    V = torch.tensor(w.V, dtype=torch.float64, device="cuda")
+    steps = max(10, min(args.steps, 50))
+    plan.autotune(rho, V)
+    ms = graph_iterations_ms(plan, rho, V, -1.0, steps, args.warmup, stream, world)
+    prof, _ = profile_iterations(plan, rho, V, -1.0, steps, stream)
+    peak, _ = measured_peaks()
+    rec = {"value": job_throughput(steps, world, ms), "unit": UNIT, "dtype": "f64", "steps": steps,
+           "ms_per_step": ms / steps, "roofline": dominant_roofline(prof, w, "fp64"),
+           "kernels": kernel_table(prof, peak),
+           "convergence": picard_to_tolerance(plan, rho0, V, -1.0, 1e-8, 400)}
+    plan.close()
+    return rec
+
+
+def large_record(args, stream, world):
+    """The large configuration: 256^3 pore/slab, four species with eight confined fixed-number O.
+    FP32 iterations/s (fixed mixing 0.05: the line search stalls at the pore's charge), the
+    per-kernel HBM fractions, and the time to r < 1e-6: by the FP32+FP64-stability form (FP32
+    Newton-Krylov to 1e-4, then FP64 Newton-Krylov from that iterate: the FP32 map's rounding
+    noise, amplified by the 1/rho_bath weight of the 0.001 M Ca2+ enriched ~10^4 in the pore,
+    floors its weighted residual near 1e-5) against the plain-FP64 form from the bath."""
+    import torch
+    from paper_0910_1531_gb300 import binding, workloads
+    w = workloads.pore_slab_4species(n=256, h=0.05)
+    alpha = 0.05
+    p32 = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32", n_fixed=w.n_fixed)
+    rho0 = w.initial_rho_nm3(p32.bulk()["rho"])
+    rho = torch.tensor(rho0, dtype=torch.float32, device="cuda")
+    V32 = torch.tensor(w.V, dtype=torch.float32, device="cuda")
+    steps = max(10, min(args.steps, 50))
+    x_lines = p32.autotune(rho, V32)
+    ms = graph_iterations_ms(p32, rho, V32, alpha, steps, args.warmup, stream, world)
+    prof, _ = profile_iterations(p32, rho, V32, alpha, steps, stream)
+    peak, _ = measured_peaks()
+    # time to 1e-6: FP32 Newton to 1e-4, then FP64 Newton from there
+    r32 = torch.tensor(rho0, dtype=torch.float32, device="cuda")
+    phase32 = newton_to_tolerance(p32, r32, V32, 1e-4)
+    p32.close()
+    del V32, rho
+    p64 = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp64", n_fixed=w.n_fixed)
+    V64 = torch.tensor(w.V, dtype=torch.float64, device="cuda")
+    r64 = r32.double()
+    del r32
+    phase64 = newton_to_tolerance(p64, r64, V64, 1e-6)
+    only64 = newton_to_tolerance(p64, torch.tensor(rho0, dtype=torch.float64, device="cuda"), V64, 1e-6)
+    p64.close()
+    return {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
+            "bulk_molar": list(map(float, w.bulk_molar)), **workload_config(w),
+            "value": job_throughput(steps, world, ms), "unit": UNIT, "dtype": "f32", "steps": steps,
+            "ms_per_step": ms / steps, "step": f"one Picard iteration with fixed mixing {alpha} (graph replay)",
+            "x_rows_per_block": x_lines, "roofline": dominant_roofline(prof, w, "fp32"),
+            "kernels": kernel_table(prof, peak),
+            "convergence": {"tol": 1e-6, "seconds": phase32["seconds"] + phase64["seconds"],
+                            "converged": phase64["converged"], "resid": phase64["resid"],
+                            "fp32_phase": phase32, "fp64_phase": phase64,
+                            "fp64_only": only64}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -518,125 +702,62 @@ def run_ours(args):
     S, N = w.nspecies, int(np.prod(w.shape))
     elem = 8 if args.precision == "fp64" else 4
     nc = w.shape[0] * w.shape[1] * (w.shape[2] // 2 + 1)
-    working_set = (2 * (10 + S + 1) + 10) * nc * 2 * elem + 3 * S * N * elem
+    working_set = (2 * (10 + S + 1) + 10) * nc * 2 * elem + 4 * S * N * elem
+    default = args.workload == "obstacles128" and args.n is None
 
     # line search (alpha < 0) unless a fixed mixing is asked for or the workload needs one
     alpha = args.alpha if args.alpha is not None else {"pore256": 0.05, "sphere32": 0.1}.get(args.workload, -1.0)
     if args.converge_tol is None:
-        # the pore's FP32 floor of the weighted residual is ~3e-5 (FP64 reaches 1e-6)
         if args.workload == "pore256":
+            # the pore's FP32 floor of the weighted residual is ~1e-5 (the large record below
+            # reaches 1e-6 by finishing in FP64)
             args.converge_tol = 1e-4 if args.precision == "fp32" else 1e-6
         elif args.workload == "wall161":
             args.converge_tol = 1e-5 if args.precision == "fp32" else 1e-8
         elif args.workload == "hswall":
             # FP32 floor of the weighted residual at eta = 0.4: ~1.1e-6
             args.converge_tol = 2e-6 if args.precision == "fp32" else 1e-10
+        elif args.workload == "obstacles128":
+            args.converge_tol = 1e-8      # the precision configuration's tolerance
         else:
             args.converge_tol = 0.0
     if args.solver is None:
         args.solver = "newton" if args.workload in ("pore256", "hswall") else "picard"
     # x-pass rows per block timed on this workload (cached per shape inside the library)
     x_lines = plan.autotune(rho, V)
-    plan.iter_begin(rho, V)
-    # warm-up through the same call as the timed region (captures the one-iteration graph)
-    plan.iter_run(rho, V, args.warmup, alpha, sync=False)
-    torch.cuda.synchronize()
 
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
-    sampler = ClockSampler(uuid)
-    # warm the sampler window with a few untimed iterations
-    plan.iter_run(rho, V, max(1, args.warmup), alpha, sync=False)
     stream = torch.cuda.current_stream()
-    barrier(world)
-    torch.cuda.synchronize()
+    # warm the sampler window with a few untimed iterations
+    plan.iter_begin(rho, V)
+    plan.iter_run(rho, V, args.warmup, alpha, sync=False)
+    sampler = ClockSampler(uuid)
+    plan.iter_run(rho, V, max(1, args.warmup), alpha, sync=False)
     # timed region: K iterations as replays of the plan's one-iteration CUDA graph
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    plan.iter_run(rho, V, args.steps, alpha, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    ms_max = graph_iterations_ms(plan, rho, V, alpha, args.steps, args.warmup, stream, world)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(ms, world)
     value = job_throughput(args.steps, world, ms_max)
-    # per-kernel table: the same K iterations launched one by one with CUDA events around
-    # every kernel (untimed for the headline)
-    plan.profile_enable(True)
-    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ep0.record(stream)
-    torch.cuda.nvtx.range_push("profiled_steps")     # ncu --nvtx-include "profiled_steps/"
-    for _ in range(args.steps):
-        plan.iter_step(rho, V, alpha, sync=False)
-    torch.cuda.nvtx.range_pop()
-    ep1.record(stream)
-    torch.cuda.synchronize()
-    ms_prof = ep0.elapsed_time(ep1)
-    prof = {k: plan.profile_read(k) for k in KERNELS}
-    plan.profile_enable(False)
-    resid_after, alpha_after = plan.iter_step(rho, V, alpha, sync=True)
+    # per-kernel table: the same K iterations launched one by one (untimed for the headline)
+    prof, ms_prof = profile_iterations(plan, rho, V, alpha, args.steps, stream)
+    resid_after, _ = plan.iter_step(rho, V, alpha, sync=True)
     # cuFFT transforms of one G against the library's whole G (comparison only)
     cufft = None if args.no_cufft else cufft_comparator(plan, w, rho, V, max(10, min(args.steps, 100)), stream)
 
-    # time to tolerance from the initial density (chunks of graph replays, residual read
-    # between chunks)
+    # time to tolerance from the initial density
     convergence = None
     if args.converge_tol > 0:
-        rho_c = torch.tensor(rho0, dtype=dt, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         if args.solver == "newton":
-            its, gevals, r_c, ok = plan.solve_newton(rho_c, V, args.converge_tol, max_newton=100, krylov_dim=30)
-            t_c = time.perf_counter() - t0
-            convergence = {"solver": "newton-krylov (dft_solve_newton)", "tol": args.converge_tol,
-                           "newton_steps": its, "g_evaluations": gevals, "resid": r_c, "seconds": t_c,
-                           "converged": bool(ok)}
+            convergence = newton_to_tolerance(plan, torch.tensor(rho0, dtype=dt, device="cuda"), V, args.converge_tol)
         else:
-            plan.iter_begin(rho_c, V)
-            it_c, r_c = 0, float("inf")
-            while it_c < args.converge_max:
-                r_c = plan.iter_run(rho_c, V, 50, alpha)
-                it_c += 50
-                if r_c < args.converge_tol:
-                    break
-            t_c = time.perf_counter() - t0
-            convergence = {"solver": "picard", "tol": args.converge_tol, "iterations": it_c, "resid": r_c,
-                           "seconds": t_c, "converged": bool(r_c < args.converge_tol), "checked_every": 50}
-        del rho_c
+            convergence = picard_to_tolerance(plan, rho0, V, alpha, args.converge_tol, args.converge_max)
 
-    # roofline of the dominant kernel (largest share of device time in the timed region)
-    peak, peak_kind = measured_peaks()
-    dom = max((k for k in KERNELS if k != "finalize"), key=lambda k: prof[k][1])
-    n_l, t_ms, by = prof[dom]
-    achieved = by / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
-    traffic = recorded_traffic(w.name, args.precision, dom)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": by / max(n_l, 1), "ms_per_launch": t_ms / max(n_l, 1)}
-    if args.precision == "fp64" and dom == "xphi":
-        # the plain-FP64 form runs on the FP64 pipe (1/64 of the FP32 rate on this part): its
-        # roofline is arithmetic.  Algorithmic flops of the x pass: ten real rows per grid row,
-        # i.e. five complex nx-point transforms each way, at 5 nx log2(nx) flops each (the
-        # pointwise Phi' and mixing work is not counted: a lower bound of the achieved rate)
-        nz_, ny_, nx_ = w.shape
-        flops = 2 * 5 * ny_ * nz_ * 5.0 * nx_ * math.log2(nx_)
-        t_launch = t_ms * 1e-3 / max(n_l, 1)
-        achieved_tf = flops / t_launch / 1e12 if t_launch > 0 else 0.0
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_TFLOPS, "traffic": None, "kernel": dom,
-                    "peak_source": "nominal FP64: 152 SMs x 4 FP64 flop/clock x 2.07 GHz (not measured)",
-                    "flop_model": "5 nx log2(nx) per complex x transform, 10 per grid row",
-                    "flops_per_launch": flops, "ms_per_launch": t_ms / max(n_l, 1),
-                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
-    total_kernel_ms = sum(prof[k][1] for k in KERNELS)
-    kernels = {k: {"launches": prof[k][0], "ms": round(prof[k][1], 4),
-                   "share": round(prof[k][1] / total_kernel_ms, 4) if total_kernel_ms else None,
-                   "GBps": round(prof[k][2] / (prof[k][1] * 1e-3) / 1e9, 1) if prof[k][1] > 0 else None}
-               for k in KERNELS}
+    peak, _ = measured_peaks()
+    roofline = dominant_roofline(prof, w, args.precision)
+    kernels = kernel_table(prof, peak)
     launches = sum(prof[k][0] for k in KERNELS)
 
     # end to end: public host-buffer entry point, pinned buffers, copies inside the timed region
@@ -650,16 +771,30 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t0
     t_e2e = max_over_ranks(t_e2e, world)
     e2e = {"value": args.e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * S * N * elem,
-           "d2h_bytes_per_step": S * N * elem,
-           "note": "dft_picard_step_host: H2D rho+V, G(rho) and one line-search iteration, D2H rho"}
+           "d2h_bytes_per_step": S * N * elem, "calls": args.e2e_steps,
+           "note": "dft_picard_step_host: H2D rho+V, G(rho) and one line-search iteration, D2H rho "
+                   "(host wall time over the calls)"}
+    plan.close()
+    del rho, V
+
+    # the rest of the metric on the same GPU: the plain-FP64 form of this workload, the large
+    # 256^3 configuration and the batched form (default run only)
+    extra = {}
+    if default and args.precision == "fp32" and not args.no_extra:
+        extra["fp64"] = fp64_record(args, w, stream, world)
+        extra["large"] = large_record(args, stream, world)
+        bv, brec = batch_measure(args, world, max(10, min(args.steps, 50)), args.warmup)
+        extra["batch"] = brec
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, tg, twd, tit = oracle_sample(w)
-        cpu = {"value": 1.0 / tit, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(),
+        prob, rho_o, g_o = oracle_start(w)
+        _, _, _, t_it = oracle_iteration(prob, rho_o, w.V, g_o, None)
+        cpu = {"value": 1.0 / t_it, "unit": UNIT, "cores": blas_threads(), "nproc": os.cpu_count(),
                "cpu_model": cpu_model(), "kind": "oracle",
-               "sample": f"one oracle G(rho) ({tg:.2f} s) + one weighted-density evaluation ({twd:.2f} s) on the "
-                         f"same {w.shape[0]}^3 workload on the host cores; iteration = 3 G + 2 WD"}
+               "sample": f"one whole oracle line-search iteration ({t_it:.2f} s: step with two sampled G and two "
+                         f"n3 maxima, then G of the new iterate) on the same {w.shape[0]}^3 workload from the "
+                         f"bath density, on the host cores"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -669,7 +804,8 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": w.name, "grid": list(w.shape), "h_nm": w.h[0], "species": list(w.species),
                            "bulk_molar": list(map(float, w.bulk_molar)), **workload_config(w),
-                           "precision": "FP32 fields, FP64 log(1-n3)/(1-n3)^-m, residual and line-search sums"
+                           "precision": "FP32 fields (iterate carried with a float low part), FP64 "
+                                        "log(1-n3)/(1-n3)^-m, residual and line-search sums"
                            if args.precision == "fp32" else "all FP64",
                            "step": ("one Picard iteration with quadratic line search" if alpha < 0 else
                                     f"one Picard iteration with fixed mixing {alpha}")
@@ -683,9 +819,8 @@ def run_ours(args):
                                        "(L2-resident; the time-to-tolerance line is the comparison)"),
                            "resid_after": resid_after},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "kernels": kernels, "cufft_comparator": cufft}
+                "cpu_baseline": cpu, "kernels": kernels, "cufft_comparator": cufft, **extra}
         print(json.dumps(line))
-    plan.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -700,8 +835,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the FP64, 256^3 pore and batched-form records of the default run")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     ap.add_argument("--workload", default="obstacles128", choices=["obstacles128", "pore256", "batch64", "wall161", "hswall", "sphere32",
                                                                    "grad64"])
