@@ -61,10 +61,12 @@ struct dft_plan {
     void* stage_rho = nullptr;
     void* stage_V = nullptr;
     double* red_sum = nullptr;
+    double* red_sum2 = nullptr;     // the second line-search sample's partial sums (paired samples)
     float* red_max = nullptr;
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;
     int Ty = 1, Tz = 1, LX = 1, LRphi = 1, LRupd = 1;
+    int LRphi2 = 1, LRupd2 = 1;     // rows per block of the paired-sample x passes
     int LRn3 = 0;                   // rows per block of the n3-maximum x pass (0: from the budget)
     SpeciesDesc<float> spf{};
     SpeciesDesc<double> spd{};
@@ -312,6 +314,37 @@ template <typename Real> struct Ops {
         return DFT_OK;
     }
 
+    // The two line-search samples rho0 + a_m (rho1 - rho0), a_1 = alpha_s / 2, a_2 = alpha_s (weights
+    // in ctl[1], ctl[2], set by FIN_AMAX), evaluated together: one Phi' x pass for both mixtures of
+    // the slots (one read of slots A and B), one y pass over the 18 Phi' spectra, the two z passes,
+    // the two S-component y passes, and one update pass reading rho0, rho1, V (and the low part)
+    // once for both residual sums (red_sum, red_sum2).  Nothing is written to rho or G.
+    static dft_status second_half_pair(dft_plan* p, const Real* rho0, const Real* rho1, const Real* V, Real* rho_lo) {
+        const SpeciesDesc<Real>& sp = species<Real>(p);
+        C* A = slot_n(p->slotA);
+        C* B = slot_n(p->slotB);
+        C* esA = slot_es(p, p->slotA);
+        C* esB = slot_es(p, p->slotB);
+        C* T2 = T1(p) + (long long)DFT_NSPEC * p->g.nc;   // the second sample's spectra
+        LAUNCH(p, K_XPHI, 4.0 * DFT_NSPEC * CB(p),
+               P::xphi2(p->stream, p->g, p->ax, p->LRphi2, p->ctl, A, B, T1(p), &p->ctl->status, kf(p, 0), tw(p, 0)));
+        LAUNCH(p, K_YFFT, 2.0 * (2 * DFT_NSPEC) * CB(p),
+               P::yfft(p->stream, false, p->g, p->ay, p->Ty, 2 * DFT_NSPEC, T1(p), &p->ctl->status, tw(p, 1),
+                       p->wait_polls));
+        for (int m = 0; m < 2; ++m) {
+            C* phi = m == 0 ? T1(p) : T2;
+            LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S * 3) * CB(p),
+                   P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S, p->ctl + 1 + m,
+                                phi, esA, esB, nullptr, tw(p, 2)));
+            LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p),
+                   P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, phi, &p->ctl->status, tw(p, 1), p->wait_polls));
+        }
+        LAUNCH(p, K_XUPD, 2.0 * p->S * CB(p) + p->S * RB(p) * (3 + (rho_lo ? 1 : 0)),
+               P::xupdate2(p->stream, p->g, p->ax, sp, p->LRupd2, p->ctl, T1(p), T2, rho0, rho1, V, rho_lo,
+                           p->red_sum, p->red_sum2, &p->ctl->status, tw(p, 0)));
+        return DFT_OK;
+    }
+
     static dft_status xinv(dft_plan* p, int ncomp, const C* spec, Real* out, Real* out_last, const double* offs,
                            int cmax, float* red_max, int* blocks_out) {
         const int lpr = (ncomp + 1) / 2;
@@ -330,10 +363,11 @@ template <typename Real> struct Ops {
     }
 };
 
-dft_status finalize(dft_plan* p, int op, int nsum, int nmax, double alpha_fixed) {
+dft_status finalize(dft_plan* p, int op, int nsum, int nmax, double alpha_fixed, bool pair = false) {
     const double inv_count = 1.0 / (double(p->S) * double(p->g.n));
-    LAUNCH(p, K_FIN, nsum * 8.0 + nmax * 4.0, launch_finalize(p->stream, p->ctl, p->red_sum, nsum, p->red_max, nmax, op, inv_count,
-                                     alpha_fixed, kN3Bound, kAlphaFloor));
+    LAUNCH(p, K_FIN, (pair ? 2 : 1) * nsum * 8.0 + nmax * 4.0,
+           launch_finalize(p->stream, p->ctl, p->red_sum, pair ? p->red_sum2 : nullptr, nsum, p->red_max, nmax, op,
+                           inv_count, alpha_fixed, kN3Bound, kAlphaFloor));
     return DFT_OK;
 }
 
@@ -349,7 +383,9 @@ dft_status read_ctl(dft_plan* p) {
 }
 
 dft_status reset_status(dft_plan* p) {
-    cudaError_t e = cudaMemsetAsync(&p->ctl->status, 0, sizeof(int), p->stream);
+    // the iteration's status word and those of the two samples' blocks
+    cudaError_t e = cudaSuccess;
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m) e = cudaMemsetAsync(&p->ctl[m].status, 0, sizeof(int), p->stream);
     if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
     return DFT_OK;
 }
@@ -389,7 +425,13 @@ template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Re
     TRY(finalize(p, FIN_AMAX, 0, nb, alpha));
     const int nsum = (int)p->blocks_x(p->LRupd);
     Real* lo = static_cast<Real*>(p->rho_lo);
-    if (alpha < 0.0) {
+    if (alpha < 0.0 && p->ncanon == 0) {
+        // both samples in one paired evaluation (their points are known before either is
+        // evaluated); fixed-number species need the normalisation of each sample first, so
+        // those plans take the samples one after the other
+        TRY(O::second_half_pair(p, rho, g, V, lo));
+        TRY(finalize(p, FIN_F12_CHOOSE, (int)p->blocks_x(p->LRupd2), 0, alpha, true));
+    } else if (alpha < 0.0) {
         TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr, lo));
         TRY(finalize(p, FIN_F1, nsum, 0, alpha));
         TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr, lo));
@@ -765,7 +807,7 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 4>> g_tune_cache;
+std::map<TuneKey, std::array<int, 6>> g_tune_cache;
 
 template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, const Real* V, int reps) {
     using O = Ops<Real>;
@@ -799,8 +841,8 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
         return ms;
     };
     const int lpr_upd = (p->S + 1) / 2;
-    int best[4] = {p->LX, p->LRphi, p->LRupd, p->LRn3};
-    float best_ms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    int best[6] = {p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2};
+    float best_ms[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     const C* A = O::slot_n(p->slotA);
     Offsets<Real> off0;
     for (int c = 0; c < DFT_NCOMP + 2; ++c) off0.v[c] = Real(0);
@@ -834,6 +876,20 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
             });
             if (ms < best_ms[2]) { best_ms[2] = ms; best[2] = L; }
         }
+        // the paired-sample passes (weights of ctl[1], ctl[2]: zero at create, any values time alike)
+        if (P::smem_x(p->g.nx, 10 * L) <= size_t(optin)) {
+            const float ms = time_it([&] {
+                P::xphi2(p->stream, p->g, p->ax, L, p->ctl, A, A, O::T1(p), &p->ctl->status, O::kf(p, 0), O::tw(p, 0));
+            });
+            if (ms < best_ms[4]) { best_ms[4] = ms; best[4] = L; }
+        }
+        if (P::smem_x(p->g.nx, 2 * lpr_upd * L) <= size_t(optin)) {
+            const float ms = time_it([&] {
+                P::xupdate2(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), O::T1(p), rho, rho, V, nullptr,
+                            p->red_sum, p->red_sum2, &p->ctl->status, O::tw(p, 0));
+            });
+            if (ms < best_ms[5]) { best_ms[5] = ms; best[5] = L; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -845,6 +901,8 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     p->LRphi = best[1];
     p->LRupd = best[2];
     p->LRn3 = best[3];
+    p->LRphi2 = best[4];
+    p->LRupd2 = best[5];
     return DFT_OK;
 }
 }  // namespace
@@ -954,6 +1012,8 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     p->LX = pick_lines(g.nx, p->csize, 1, env_budget("DFT_XFWD_SMEM", 48 * 1024), 32);
     p->LRphi = pick_lines(g.nx, p->csize, 5, env_budget("DFT_XPHI_SMEM", 32 * 1024), 16);
     p->LRupd = pick_lines(g.nx, p->csize, (S + 1) / 2, env_budget("DFT_XUPD_SMEM", 48 * 1024), 16);
+    p->LRphi2 = pick_lines(g.nx, p->csize, 10, env_budget("DFT_XPHI_SMEM", 32 * 1024), 16);
+    p->LRupd2 = pick_lines(g.nx, p->csize, 2 * ((S + 1) / 2), env_budget("DFT_XUPD_SMEM", 48 * 1024), 16);
     if (f64) fill_species<double>(p);
     else fill_species<float>(p);
 
@@ -980,15 +1040,18 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     const size_t slot_comps = DFT_NSPEC + S + 1;
     const size_t nred = size_t(g.ny) * g.nz + 1;
     struct { void** ptr; size_t bytes; const char* what; } allocs[] = {
-        {&p->T1, size_t(DFT_NCOMP) * g.nc * p->csize, "work spectra"},
+        // the weighted-density rows (ten) or the two line-search samples' Phi' spectra (2 x nine)
+        {&p->T1, size_t(2 * DFT_NSPEC > DFT_NCOMP ? 2 * DFT_NSPEC : DFT_NCOMP) * g.nc * p->csize, "work spectra"},
         {&p->slotA, slot_comps * g.nc * p->csize, "slot A"},
         {&p->slotB, slot_comps * g.nc * p->csize, "slot B"},
         {&p->gbuf, size_t(S) * g.n * p->rsize, "G buffer"},
         // FP32 iterations carry the iterate as the caller's field plus this low part
         {f64 ? nullptr : &p->rho_lo, size_t(S) * g.n * p->rsize, "iterate low part"},
         {(void**)&p->red_sum, nred * sizeof(double), "reduction sums"},
+        {(void**)&p->red_sum2, nred * sizeof(double), "second sample's reduction sums"},
         {(void**)&p->red_max, nred * sizeof(float), "reduction maxima"},
-        {(void**)&p->ctl, sizeof(Ctl), "control block"},
+        // the iteration's control block and the two line-search samples' weights
+        {(void**)&p->ctl, 3 * sizeof(Ctl), "control blocks"},
     };
     for (auto& a : allocs) {
         if (!a.ptr) continue;
@@ -998,7 +1061,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
             return fail(nullptr, DFT_ENOMEM, std::string("cudaMalloc failed: ") + a.what);
         }
     }
-    cudaMemset(p->ctl, 0, sizeof(Ctl));
+    cudaMemset(p->ctl, 0, 3 * sizeof(Ctl));
     if (p->ncanon > 0 &&
         cudaMalloc(&p->red_canon, (size_t(g.ny) * g.nz + 1) * DFT_MAXS * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -1070,6 +1133,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->stage_rho);
     cudaFree(p->stage_V);
     cudaFree(p->red_sum);
+    cudaFree(p->red_sum2);
     cudaFree(p->red_max);
     cudaFree(p->grad_red);
     cudaFree(p->ktab);
@@ -1245,6 +1309,8 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
             p->LRphi = it->second[1];
             p->LRupd = it->second[2];
             p->LRn3 = it->second[3];
+            p->LRphi2 = it->second[4];
+            p->LRupd2 = it->second[5];
             cached = true;
         }
     }
@@ -1252,7 +1318,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         if (is_fp64(p)) TRY(autotune_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), reps));
         else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd, p->LRn3};
+        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2};
     }
     // the iteration state and its graph depend on the block counts
     p->iter_ready = false;

@@ -169,5 +169,6 @@ enum {
     FIN_F1 = 8,             // f1 = sum; weights for the second sample
     FIN_F2_CHOOSE = 16,     // f2 = sum; alpha from the parabola; weights for the accepted point
     FIN_ACCEPT = 32,        // f0 = f3 = sum; n3max_cur = max; resid; iter++
-    FIN_IDENTITY = 64       // weights (1, 0) for a plain G evaluation
+    FIN_IDENTITY = 64,      // weights (1, 0) for a plain G evaluation
+    FIN_F12_CHOOSE = 128    // f1 = sum, f2 = second sum (paired samples); alpha; weights for the accepted point
 };

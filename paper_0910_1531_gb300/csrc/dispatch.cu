@@ -124,6 +124,21 @@ cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const Axis
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::xphi2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl, const C* A,
+                                const C* B, C* phi, int* status, Real kfx, const C* tw) {
+    DFT_SWITCH_X(g.nx, xphi2(st, g, px, LR, ctl, A, B, phi, status, kfx, tw))
+}
+
+template <typename Real>
+cudaError_t Passes<Real>::xupdate2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                                   int LR, const Ctl* ctl, const C* cspec, const C* cspec2, const Real* rho0,
+                                   const Real* rho1, const Real* V, Real* rho_lo, double* red_sum, double* red_sum2,
+                                   int* status, const C* tw) {
+    DFT_SWITCH_X(g.nx, xupdate2(st, g, px, sp, LR, ctl, cspec, cspec2, rho0, rho1, V, rho_lo, red_sum, red_sum2,
+                                status, tw))
+}
+
+template <typename Real>
 cudaError_t Passes<Real>::xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                         Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
                         Real kfx, const C* tw) {
@@ -140,15 +155,16 @@ cudaError_t Passes<Real>::xgrad(cudaStream_t st, const GridDesc& g, const AxisPl
 template struct Passes<float>;
 template struct Passes<double>;
 
-cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
-                     int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor) {
-    if (nsum + nmax > 8 * dftk::kFinThreadsSmall)
-        dftk::k_finalize<dftk::kFinThreads><<<1, dftk::kFinThreads, 0, st>>>(ctl, red_sum, nsum, red_max, nmax, op,
-                                                                           inv_count, alpha_fixed, n3_bound,
-                                                                           alpha_floor);
+cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, const double* red_sum2, int nsum,
+                            const float* red_max, int nmax, int op, double inv_count, double alpha_fixed,
+                            double n3_bound, double alpha_floor) {
+    if ((red_sum2 ? 2 : 1) * nsum + nmax > 8 * dftk::kFinThreadsSmall)
+        dftk::k_finalize<dftk::kFinThreads><<<1, dftk::kFinThreads, 0, st>>>(ctl, red_sum, red_sum2, nsum, red_max,
+                                                                           nmax, op, inv_count, alpha_fixed,
+                                                                           n3_bound, alpha_floor);
     else
         dftk::k_finalize<dftk::kFinThreadsSmall><<<1, dftk::kFinThreadsSmall, 0, st>>>(
-            ctl, red_sum, nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
+            ctl, red_sum, red_sum2, nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
     return cudaSuccess;
 }
 

@@ -1666,12 +1666,13 @@ __device__ __forceinline__ void load_row_pairs(const GridDesc& g, int rows, long
 // arrangement), built from the nine kept spectra mixed as wA * A + wB * B (B optional), with
 // n_V1x = i k_x m and n_V2x = i k_x n3 (zero on the Nyquist index); mat_out (optional) receives
 // the nine mixed spectra.  One thread handles all lines of one (row, k): the index arithmetic is
-// shared and its eighteen loads are in flight together.
-template <typename Real, int NX>
+// shared and its eighteen loads are in flight together.  NM mixtures (weights wA[a], wB[a]) of
+// the same loads: mixture a of row r goes to lines (r NM + a) 5 .. + 4.
+template <typename Real, int NX, int NM = 1>
 __device__ __forceinline__ void load_wd_rows(const GridDesc& g, int rows, long long row0, long long nrows,
                                              const typename Cplx<Real>::type* A,
-                                             const typename Cplx<Real>::type* Bm, Real wA, Real wB,
-                                             typename Cplx<Real>::type* mat_out, Real kfx,
+                                             const typename Cplx<Real>::type* Bm, const Real* wA,
+                                             const Real* wB, typename Cplx<Real>::type* mat_out, Real kfx,
                                              typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
@@ -1694,22 +1695,27 @@ __device__ __forceinline__ void load_wd_rows(const GridDesc& g, int rows, long l
         const bool nyq = even && 2 * k == nx;
         const Real kx = Real(k) * kfx;
 #pragma unroll
-        for (int c = 0; c < DFT_NSPEC; ++c) {
-            v[c] = cadd(cscale(v[c], wA), cscale(vb[c], wB));
-            if (edge) v[c].y = Real(0);
-            if (mat_out && live) mat_out[(long long)c * g.nc + o] = v[c];
-        }
-        const C zero = cmake<C>(Real(0), Real(0));
-        const C dm = nyq ? zero : cmake<C>(-kx * v[4].y, kx * v[4].x);     // i k_x m
-        const C dn3 = nyq ? zero : cmake<C>(-kx * v[3].y, kx * v[3].x);    // i k_x n3
-        // line l holds (a, b) = (wd_comp(l, 0), wd_comp(l, 1))
-        const C la[5] = {v[0], v[2], v[3], dm, v[7]};
-        const C lb[5] = {v[1], v[5], dn3, v[6], v[8]};
+        for (int m = 0; m < NM; ++m) {
+            C u[DFT_NSPEC];
 #pragma unroll
-        for (int l = 0; l < 5; ++l) {
-            const C a = la[l], b = lb[l];
-            dst[(r * 5 + l) * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
-            if (!edge) dst[(r * 5 + l) * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            for (int c = 0; c < DFT_NSPEC; ++c) {
+                u[c] = cadd(cscale(v[c], wA[m]), cscale(vb[c], wB[m]));
+                if (edge) u[c].y = Real(0);
+                if (NM == 1 && mat_out && live) mat_out[(long long)c * g.nc + o] = u[c];
+            }
+            const C zero = cmake<C>(Real(0), Real(0));
+            const C dm = nyq ? zero : cmake<C>(-kx * u[4].y, kx * u[4].x);     // i k_x m
+            const C dn3 = nyq ? zero : cmake<C>(-kx * u[3].y, kx * u[3].x);    // i k_x n3
+            // line l holds (a, b) = (wd_comp(l, 0), wd_comp(l, 1))
+            const C la[5] = {u[0], u[2], u[3], dm, u[7]};
+            const C lb[5] = {u[1], u[5], dn3, u[6], u[8]};
+            const int l0 = (r * NM + m) * 5;
+#pragma unroll
+            for (int l = 0; l < 5; ++l) {
+                const C a = la[l], b = lb[l];
+                dst[(l0 + l) * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+                if (!edge) dst[(l0 + l) * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            }
         }
     }
 }
@@ -1740,22 +1746,25 @@ __device__ __forceinline__ void store_pair_rows(const GridDesc& g, int lines, in
 // Phi_0..Phi_2, B3 = Phi_3 - i k_x Phi_V2x, B4 = -i k_x Phi_V1x, Phi_V1y, Phi_V1z, Phi_V2y,
 // Phi_V2z (the -i k_x terms dropped on the Nyquist index).  Each line maps to its own outputs:
 // line 2 holds Phi_3 and Phi_V2x, line 3 Phi_V1x and Phi_V1z.
-template <typename Real, int NX>
+// NM mixtures: those of sub-row r NM + m (lines (r NM + m) 5 ..) go to out + m DFT_NSPEC nc.
+template <typename Real, int NX, int NM = 1>
 __device__ __forceinline__ void store_phi_spectra(const GridDesc& g, int rows, long long row0, long long nrows,
                                                   Real kfx, const typename Cplx<Real>::type* R,
-                                                  typename Cplx<Real>::type* out) {
+                                                  typename Cplx<Real>::type* out0) {
     using C = typename Cplx<Real>::type;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
-    for (int idx = threadIdx.x; idx < rows * nxh; idx += blockDim.x) {
-        const int r = idx / nxh, k = idx - (idx / nxh) * nxh;
+    for (int idx = threadIdx.x; idx < rows * NM * nxh; idx += blockDim.x) {
+        const int rr = idx / nxh, k = idx - (idx / nxh) * nxh;
+        const int r = rr / NM;
         const long long row = row0 + r;
         if (row >= nrows) continue;
+        C* out = out0 + (long long)(rr - r * NM) * DFT_NSPEC * g.nc;
         C a[5], b[5];
 #pragma unroll
         for (int l = 0; l < 5; ++l) {
-            const C zk = R[(r * 5 + l) * pitch + xo<NX>(k)];
-            const C znk = R[(r * 5 + l) * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
+            const C zk = R[(rr * 5 + l) * pitch + xo<NX>(k)];
+            const C znk = R[(rr * 5 + l) * pitch + xo<NX>(k == 0 ? 0 : nx - k)];
             const C s = cadd(zk, cconj(znk));
             const C d = csub(zk, cconj(znk));
             a[l] = cmake<C>(Real(0.5) * s.x, Real(0.5) * s.y);
@@ -1779,7 +1788,9 @@ __device__ __forceinline__ void store_phi_spectra(const GridDesc& g, int rows, l
 // x pass of the second half's start: n_alpha (mixed from slots A and B) -> real space ->
 // dPhi/dn_alpha -> half spectra.  grid: ceil(ny nz / LR); 5 lines (component pairs) per row.
 // ------------------------------------------------------------------------------------
-template <typename Real, int NX>
+// NM = 2: the two line-search samples at once (weights from ctl[1] and ctl[2]; the same loads
+// of both slots serve both; sample m's nine Phi' spectra go to phi_out + m DFT_NSPEC nc).
+template <typename Real, int NX, int NM = 1>
 __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int LR, const Ctl* __restrict__ ctl,
                                                    const typename Cplx<Real>::type* slotA,
                                                    const typename Cplx<Real>::type* slotB,
@@ -1794,22 +1805,29 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     __shared__ double scratch_d[32];
     double phi_acc = 0.0;   // sum of Phi(n) over the block's points (grand potential only)
     const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
-    const int lines = 5 * LR;
+    const int lines = 5 * NM * LR;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
     C* B = A + lines * pitch;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
-    load_wd_rows<Real, NX>(g, LR, row0, nrows, slotA, slotB, wA, wB, mat_out, kfx, A);
+    Real wA[NM], wB[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
+        wA[m] = Real(cw->wA);
+        wB[m] = Real(cw->wB);
+    }
+    load_wd_rows<Real, NX, NM>(g, LR, row0, nrows, slotA, slotB, wA, wB, mat_out, kfx, A);
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
     float mx = -CUDART_INF_F;
     bool bad = false;
-    for (int idx = threadIdx.x; idx < LR * nx; idx += blockDim.x) {
-        const int r = idx / nx, x = idx - (idx / nx) * nx;
-        C* base = R + (r * 5) * pitch + xo<NX>(x);
+    for (int idx = threadIdx.x; idx < LR * NM * nx; idx += blockDim.x) {
+        const int rr = idx / nx, x = idx - (idx / nx) * nx;
+        const int r = rr / NM;
+        C* base = R + (rr * 5) * pitch + xo<NX>(x);
         Real n[DFT_NCOMP];
         {   // lines (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z): see wd_comp
             const C v0 = base[0], v1 = base[pitch], v2 = base[2 * pitch], v3 = base[3 * pitch], v4 = base[4 * pitch];
@@ -1830,9 +1848,9 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
     __syncthreads();
     C* other = (R == A) ? B : A;
     C* F = any_fft<NX, false, false, 0>(R, other, px, lines, 1, pitch, tw);
-    store_phi_spectra<Real, NX>(g, LR, row0, nrows, kfx, F, phi_out);
+    store_phi_spectra<Real, NX, NM>(g, LR, row0, nrows, kfx, F, phi_out);
     const float bm = block_max(mx, scratch_f);
-    if (threadIdx.x == 0) red_max[blockIdx.x] = bm;
+    if (threadIdx.x == 0 && red_max) red_max[blockIdx.x] = bm;
     if (red_phi) {
         const double bp = block_sum(phi_acc, scratch_d);
         if (threadIdx.x == 0) red_phi[blockIdx.x] = bp;
@@ -2051,21 +2069,25 @@ __global__ void __launch_bounds__(kThreads) k_canon_scale(Ctl* ctl, SpeciesDesc<
 // accumulated in FP64.  grid: ceil(ny nz / LR); ceil(S/2) lines per row.
 // rho_out may alias rho0 and g_out may alias rho1 (each point is read before it is written).
 // ------------------------------------------------------------------------------------
-template <typename Real, int NX>
+// NM = 2: the two line-search samples at once -- the c spectra of sample m at cspec (m = 0) and
+// cspec2 (m = 1), weights from ctl[1 + m], rho0, rho1, V (and the low part) read once for both;
+// the residual sums of sample m go to red_sum / red_sum2; nothing is written to rho or G.
+template <typename Real, int NX, int NM = 1>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate(GridDesc g, AxisPlan px, SpeciesDesc<Real> sp, int LR,
                                                       const Ctl* __restrict__ ctl,
                                                       const typename Cplx<Real>::type* __restrict__ cspec,
+                                                      const typename Cplx<Real>::type* __restrict__ cspec2,
                                                       const Real* rho0, const Real* rho1,
                                                       const Real* __restrict__ V, Real* rho_out, Real* g_out,
                                                       Real* rho_lo, double* __restrict__ red_sum,
-                                                      int* __restrict__ status,
+                                                      double* __restrict__ red_sum2, int* __restrict__ status,
                                                       const typename Cplx<Real>::type* __restrict__ twx) {
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
     const int nx = NX > 0 ? NX : g.nx, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1, S = sp.S;
     const int lpr = (S + 1) / 2;
-    const int lines = lpr * LR;
+    const int lines = NM * lpr * LR;
     C* tw = align_ptr<C>(smem_raw);
     C* A = tw + nx;
     C* B = A + lines * pitch;
@@ -2073,6 +2095,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
     load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec, A);
+    if constexpr (NM == 2) load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec2, A + lpr * LR * pitch);
     const int total = LR * nx;
     // G_i = pref_i exp(mu0_i - V_i + c_i): the bath (rho_b, beta mu_HS,b), or for a
     // fixed-number species the normalisation of this evaluation and no bath constant
@@ -2086,34 +2109,43 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
     }
     __syncthreads();
     C* R = any_fft<NX, true, false, 0>(A, B, px, lines, 1, pitch, tw);
-    const Real w0 = Real(ctl->w0), w1 = Real(ctl->w1);
-    // per-thread partial sum in the working precision with Kahan compensation, then
+    Real w0[NM], w1[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
+        w0[m] = Real(cw->w0);
+        w1[m] = Real(cw->w1);
+    }
+    // per-thread partial sums in the working precision with Kahan compensation, then
     // double-single (FP32) or FP64 across threads, FP64 across blocks
-    Real acc = Real(0), comp = Real(0);
+    Real acc[NM], comp[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = comp[m] = Real(0);
     bool bad = false;
-    // one point of species s: new iterate (and its low part), G, squared weighted residual
-    auto point = [&](int s, Real c, Real r0, Real r1, Real v, Real l0, Real& rho, Real& lo, Real& gval) {
+    // one point of species s under mixture m: new iterate (and its low part), G, squared
+    // weighted residual
+    auto point = [&](int m, int s, Real c, Real r0, Real r1, Real v, Real l0, Real& rho, Real& lo, Real& gval) {
         lo = Real(0);
         if (rho_lo) {
             // extended iterate rho0 = r0 + l0 (a value and its rounding error):
             // rho = rho0 + w1 (rho1 - rho0) formed so that steps below half an ulp of rho0
             // accumulate in the low part instead of rounding away (w0 = 1 - w1), then split
             // again into rho + lo by an error-free sum (Knuth's TwoSum)
-            const Real t = l0 + w1 * ((r1 - r0) - l0);
+            const Real t = l0 + w1[m] * ((r1 - r0) - l0);
             rho = r0 + t;
             const Real bv = rho - r0;
             lo = (r0 - (rho - bv)) + (t - bv);
         } else {
-            rho = w0 * r0 + w1 * r1;
+            rho = w0[m] * r0 + w1[m] * r1;
         }
         if (isinf(v) && v > Real(0)) gval = Real(0);
         else gval = s_pref[s] * exp(s_mu0[s] - v + c);
         if (!isfinite(gval) || !isfinite(rho)) bad = true;
         const Real d = ((rho - gval) + lo) * s_irb[s];
-        const Real y = d * d - comp;
-        const Real t = acc + y;
-        comp = (t - acc) - y;
-        acc = t;
+        const Real y = d * d - comp[m];
+        const Real t = acc[m] + y;
+        comp[m] = (t - acc[m]) - y;
+        acc[m] = t;
     };
     // rho_out / g_out / rho_lo may alias rho0 / rho1 / the low part read: every value is read
     // before the same thread writes that element, and the threads' elements are distinct
@@ -2150,19 +2182,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                 const int idx = gi * VW, r = idx / NX, x = idx - (idx / NX) * NX;
                 if (!(it < items && row0 + r < nrows)) continue;
                 const long long o = (long long)s * g.n + row0 * NX + idx;
-                const C* Rl = R + (r * lpr + s / 2) * pitch;
-                V16 orho, og, olo;
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const C pc = Rl[xo<NX>(x + e)];
-                    point(s, (s & 1) ? pc.y : pc.x, vel(a0[j], e), vel(a1[j], e), vel(av[j], e), vel(al[j], e),
-                          vel(orho, e), vel(olo, e), vel(og, e));
+                for (int m = 0; m < NM; ++m) {
+                    const C* Rl = R + (m * lpr * LR + r * lpr + s / 2) * pitch;
+                    V16 orho, og, olo;
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const C pc = Rl[xo<NX>(x + e)];
+                        point(m, s, (s & 1) ? pc.y : pc.x, vel(a0[j], e), vel(a1[j], e), vel(av[j], e),
+                              vel(al[j], e), vel(orho, e), vel(olo, e), vel(og, e));
+                    }
+                    if (NM == 1 && rho_out) {
+                        st16(rho_out + o, orho);
+                        if (rho_lo) st16(rho_lo + o, olo);
+                    }
+                    if (NM == 1 && g_out) st16(g_out + o, og);
                 }
-                if (rho_out) {
-                    st16(rho_out + o, orho);
-                    if (rho_lo) st16(rho_lo + o, olo);
-                }
-                if (g_out) st16(g_out + o, og);
             }
         }
     } else {
@@ -2195,15 +2230,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
 #pragma unroll
                 for (int s = 0; s < DFT_MAXS; ++s) {
                     if (s >= S) continue;
-                    const C pr = R[(r * lpr + s / 2) * pitch + xo<NX>(x)];
                     const long long o = (long long)s * g.n + pt;
-                    Real rho, lo, gval;
-                    point(s, (s & 1) ? pr.y : pr.x, r0[s], r1[s], vv[s], rl[s], rho, lo, gval);
-                    if (rho_out) {
-                        rho_out[o] = rho;
-                        if (rho_lo) rho_lo[o] = lo;
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        const C pr = R[(m * lpr * LR + r * lpr + s / 2) * pitch + xo<NX>(x)];
+                        Real rho, lo, gval;
+                        point(m, s, (s & 1) ? pr.y : pr.x, r0[s], r1[s], vv[s], rl[s], rho, lo, gval);
+                        if (NM == 1 && rho_out) {
+                            rho_out[o] = rho;
+                            if (rho_lo) rho_lo[o] = lo;
+                        }
+                        if (NM == 1 && g_out) g_out[o] = gval;
                     }
-                    if (g_out) g_out[o] = gval;
                 }
             }
 #pragma unroll
@@ -2216,10 +2254,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);
-    double bs;
-    if constexpr (sizeof(Real) == 4) bs = block_sum_ds(acc, -comp, scratch_d);
-    else bs = block_sum(double(acc) - double(comp), scratch_d);
-    if (threadIdx.x == 0) red_sum[blockIdx.x] = bs;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        double bs;
+        if constexpr (sizeof(Real) == 4) bs = block_sum_ds(acc[m], -comp[m], scratch_d);
+        else bs = block_sum(double(acc[m]) - double(comp[m]), scratch_d);
+        if (threadIdx.x == 0) (m == 0 ? red_sum : red_sum2)[blockIdx.x] = bs;
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -2306,7 +2347,8 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    if (wd) load_wd_rows<Real, NX>(g, LR, row0, nrows, spec, nullptr, Real(1), Real(0), nullptr, kfx, A);
+    const Real one = Real(1), zero = Real(0);
+    if (wd) load_wd_rows<Real, NX>(g, LR, row0, nrows, spec, nullptr, &one, &zero, nullptr, kfx, A);
     else if (rows2) load_row_pairs<Real, NX>(g, LR, row0, nrows, spec, A);
     else load_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, ncomp, spec, nullptr, Real(1), Real(0), nullptr, A);
     __syncthreads();
@@ -2344,13 +2386,10 @@ __device__ __forceinline__ void set_weights(Ctl* c, double a) {
     c->wA = 1.0 - a; c->wB = a; c->w0 = 1.0 - a; c->w1 = a;
 }
 
+// ctl points at three control blocks: the iteration's, then the weights of the two line-search
+// samples (ctl[1], ctl[2]: wA, wB, w0, w1 only), which FIN_AMAX sets for the paired evaluation.
 template <int B>
-__global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restrict__ red_sum, int nsum,
-                                                          const float* __restrict__ red_max, int nmax, int op,
-                                                          double inv_count, double alpha_fixed, double n3_bound,
-                                                          double alpha_floor) {
-    __shared__ double scratch_d[32];
-    __shared__ float scratch_f[32];
+__device__ __forceinline__ double partial_sum(const double* __restrict__ red_sum, int nsum) {
     // four independent partial results per thread, so that a thread's loads are all in flight
     // at once (the partial sums are L2-resident: the kernel is a few load latencies long)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -2362,9 +2401,21 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
         s3 += red_sum[i + 3 * B];
     }
     for (; i < nsum; i += B) s0 += red_sum[i];
-    const double s = (s0 + s1) + (s2 + s3);
+    return (s0 + s1) + (s2 + s3);
+}
+
+template <int B>
+__global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restrict__ red_sum,
+                                                          const double* __restrict__ red_sum2, int nsum,
+                                                          const float* __restrict__ red_max, int nmax, int op,
+                                                          double inv_count, double alpha_fixed, double n3_bound,
+                                                          double alpha_floor) {
+    __shared__ double scratch_d[32];
+    __shared__ float scratch_f[32];
+    const double s = partial_sum<B>(red_sum, nsum);
+    const double s_2 = red_sum2 ? partial_sum<B>(red_sum2, nsum) : 0.0;
     float m0 = -CUDART_INF_F, m1 = -CUDART_INF_F, m2 = -CUDART_INF_F, m3 = -CUDART_INF_F;
-    i = threadIdx.x;
+    int i = threadIdx.x;
     for (; i + 3 * B < nmax; i += 4 * B) {
         m0 = fmaxf(m0, red_max[i]);
         m1 = fmaxf(m1, red_max[i + B]);
@@ -2374,6 +2425,7 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
     for (; i < nmax; i += B) m0 = fmaxf(m0, red_max[i]);
     const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
     const double tot = block_sum(s, scratch_d);
+    const double tot2 = red_sum2 ? block_sum(s_2, scratch_d) : 0.0;
     const float mx = block_max(m, scratch_f);
     if (threadIdx.x != 0) return;
     Ctl* c = ctl;
@@ -2404,7 +2456,10 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
             const double as = fmin(am, 2.0 * c->alpha);
             c->alpha_s = as;
             c->sample_alpha[0] = 0.5 * as;
+            c->sample_alpha[1] = as;
             set_weights(c, 0.5 * as);
+            set_weights(c + 1, 0.5 * as);
+            set_weights(c + 2, as);
         }
     }
     if (op & FIN_F1) {
@@ -2412,10 +2467,18 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
         c->sample_alpha[1] = c->alpha_s;
         set_weights(c, c->alpha_s);
     }
-    if (op & FIN_F2_CHOOSE) {
-        c->f[2] = f;
+    if (op & (FIN_F2_CHOOSE | FIN_F12_CHOOSE)) {
+        // FIN_F12_CHOOSE: both samples' sums at once (f1 in red_sum, f2 in red_sum2); the z
+        // passes of the samples recorded their status in the samples' blocks
+        if (op & FIN_F12_CHOOSE) {
+            c->f[1] = f;
+            c->status |= c[1].status | c[2].status;
+            c[1].status = 0;
+            c[2].status = 0;
+        }
+        c->f[2] = (op & FIN_F12_CHOOSE) ? tot2 * inv_count : f;
         const double am = c->alpha_s, a = 0.5 * am;
-        const double f0 = c->f[0], f1 = c->f[1], f2 = f;
+        const double f0 = c->f[0], f1 = c->f[1], f2 = c->f[2];
         const double c2 = (f0 - 2.0 * f1 + f2) / (2.0 * a * a);
         const double c1 = (-3.0 * f0 + 4.0 * f1 - f2) / (2.0 * a);
         double al;

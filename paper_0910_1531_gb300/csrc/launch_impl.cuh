@@ -29,8 +29,10 @@ template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::init() {
     cudaError_t e = cudaSuccess, r;
     if ((r = set_max_smem(dftk::k_xfwd<Real, N>)) != cudaSuccess) e = r;
-    if ((r = set_max_smem(dftk::k_xphi<Real, N>)) != cudaSuccess) e = r;
-    if ((r = set_max_smem(dftk::k_xupdate<Real, N>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xphi<Real, N, 1>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xphi<Real, N, 2>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xupdate<Real, N, 1>)) != cudaSuccess) e = r;
+    if ((r = set_max_smem(dftk::k_xupdate<Real, N, 2>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xcanon<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xinv<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xgrad<Real, N>)) != cudaSuccess) e = r;
@@ -51,8 +53,17 @@ cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const Axi
                             const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi,
                             Real kfx, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    dftk::k_xphi<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
+    dftk::k_xphi<Real, N, 1><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
                                                                                     red_max, status, red_phi, kfx, tw);
+    return cudaSuccess;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchX<Real, N>::xphi2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
+                                    const C* A, const C* B, C* phi, int* status, Real kfx, const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    dftk::k_xphi<Real, N, 2><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 10 * LR), st>>>(
+        g, px, LR, ctl, A, B, nullptr, phi, nullptr, status, nullptr, kfx, tw);
     return cudaSuccess;
 }
 
@@ -63,8 +74,20 @@ cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const 
                                int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
-    dftk::k_xupdate<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
-        g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, status, tw);
+    dftk::k_xupdate<Real, N, 1><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
+        g, px, sp, LR, ctl, cspec, nullptr, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, nullptr, status, tw);
+    return cudaSuccess;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchX<Real, N>::xupdate2(cudaStream_t st, const GridDesc& g, const AxisPlan& px,
+                                       const SpeciesDesc<Real>& sp, int LR, const Ctl* ctl, const C* cspec,
+                                       const C* cspec2, const Real* rho0, const Real* rho1, const Real* V,
+                                       Real* rho_lo, double* red_sum, double* red_sum2, int* status, const C* tw) {
+    const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
+    const int lpr = (sp.S + 1) / 2;
+    dftk::k_xupdate<Real, N, 2><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 2 * lpr * LR), st>>>(
+        g, px, sp, LR, ctl, cspec, cspec2, rho0, rho1, V, nullptr, nullptr, rho_lo, red_sum, red_sum2, status, tw);
     return cudaSuccess;
 }
 

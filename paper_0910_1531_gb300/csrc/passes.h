@@ -101,6 +101,16 @@ struct LaunchX {
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
                         const C* tw);
+    // the two line-search samples in one pass each (weights from ctl[1] and ctl[2]): Phi' of
+    // both mixtures of the slots (sample m's nine spectra at phi + m DFT_NSPEC nc), and the
+    // update pass's residual sums of both (c spectra at cspec / cspec2, sums into red_sum /
+    // red_sum2; nothing written to rho or G)
+    static cudaError_t xphi2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
+                             const C* A, const C* B, C* phi, int* status, Real kfx, const C* tw);
+    static cudaError_t xupdate2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                                int LR, const Ctl* ctl, const C* cspec, const C* cspec2, const Real* rho0,
+                                const Real* rho1, const Real* V, Real* rho_lo, double* red_sum, double* red_sum2,
+                                int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
                      Real kfx, const C* tw);
@@ -162,6 +172,16 @@ struct Passes {
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                         Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
                         const C* tw);
+    // the two line-search samples in one pass each (weights from ctl[1] and ctl[2]): Phi' of
+    // both mixtures of the slots (sample m's nine spectra at phi + m DFT_NSPEC nc), and the
+    // update pass's residual sums of both (c spectra at cspec / cspec2, sums into red_sum /
+    // red_sum2; nothing written to rho or G)
+    static cudaError_t xphi2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
+                             const C* A, const C* B, C* phi, int* status, Real kfx, const C* tw);
+    static cudaError_t xupdate2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
+                                int LR, const Ctl* ctl, const C* cspec, const C* cspec2, const Real* rho0,
+                                const Real* rho1, const Real* V, Real* rho_lo, double* red_sum, double* red_sum2,
+                                int* status, const C* tw);
     static cudaError_t xinv(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, int ncomp, const C* spec,
                      Real* out, Real* out_last, const Offsets<Real>& off, int cmax, float* red_max, int wd,
                      Real kfx, const C* tw);
@@ -179,7 +199,10 @@ struct Passes {
     static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
 };
 
-cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, int nsum, const float* red_max, int nmax,
-                     int op, double inv_count, double alpha_fixed, double n3_bound, double alpha_floor);
+// ctl: the plan's three control blocks (iteration, sample 1 weights, sample 2 weights);
+// red_sum2 (or nullptr): the second sample's partial sums for FIN_F12_CHOOSE
+cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, const double* red_sum2, int nsum,
+                            const float* red_max, int nmax, int op, double inv_count, double alpha_fixed,
+                            double n3_bound, double alpha_floor);
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
