@@ -203,13 +203,17 @@ dft_status dft_iter_step(dft_plan* plan, void* rho_inout, const void* V, double 
                          double* resid_out, double* alpha_out);
 
 /*
- * `iters` consecutive dft_iter_step iterations (same arithmetic, same order) queued as
- * replays of a CUDA graph of one iteration, captured on the first call for these
- * (rho_inout, V, alpha_or_neg) and kept in the plan until they change, dft_iter_begin is
- * called or the plan is destroyed.  Requires a preceding dft_iter_begin on the same
- * buffers.  resid_out (may be NULL; NULL skips the synchronisation) receives r of rho
- * after the last iteration.  While kernel profiling is enabled the iterations are
- * launched one by one instead (the per-kernel events are not captured).
+ * `iters` consecutive dft_iter_step iterations (same arithmetic, same order) queued as ONE
+ * launch of a CUDA graph whose body -- one iteration, captured on the first call for these
+ * (rho_inout, V, alpha_or_neg) -- repeats on the device `iters` times (a conditional WHILE
+ * graph node counting down a device-side counter), so the host takes no part between
+ * iterations; a runtime without conditional graph nodes gets `iters` replays of a graph of
+ * one iteration instead.  The graph is kept in the plan until those arguments change,
+ * dft_iter_begin or dft_autotune is called or the plan is destroyed.  Requires a preceding
+ * dft_iter_begin on the same buffers.  resid_out (may be NULL; NULL skips the
+ * synchronisation) receives r of rho after the last iteration.  While kernel profiling is
+ * enabled the iterations are launched one by one instead (the per-kernel events are not
+ * captured).
  */
 dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iters, double alpha_or_neg,
                         double* resid_out);
@@ -267,9 +271,11 @@ dft_status dft_picard_step_host(dft_plan* plan, void* rho_host, const void* V_ho
  * takes per-state DEVICE pointers rho[i] ([S_i][N_i], updated in place) and V[i]
  * and evaluates G for every state.  dft_batch_iterate then advances every state
  * by `iters` Picard iterations (alpha_or_neg as in dft_picard_step); one
- * iteration of all states is captured once into a CUDA graph (fork/join across
- * the state streams) and replayed, so the states run concurrently and the host
- * does one graph launch per iteration.  resid_out ([count], may be NULL)
+ * iteration of all states is captured once into the body of an on-device loop (a
+ * CUDA graph with a conditional WHILE node; fork/join across the state streams
+ * inside the body), so one graph launch runs all `iters` iterations of all states,
+ * the states concurrently (a runtime without conditional graph nodes gets one
+ * graph launch per iteration instead).  resid_out ([count], may be NULL)
  * receives each state's r after the last iteration (synchronises).
  * cuda_stream: stream the batch orders its work after (NULL: an internal one).
  * The rho and V pointers must stay valid and unmoved between begin and iterate.

@@ -87,6 +87,7 @@ struct dft_plan {
     const void* graph_rho = nullptr;
     const void* graph_V = nullptr;
     double graph_alpha = 0.0;
+    bool iloop = false;             // the cached graph is the on-device loop (else one iteration)
     double* grad_red = nullptr;     // partial sums of dft_grad (allocated on first use)
     size_t grad_red_len = 0;
     bool iter_ready = false;
@@ -913,6 +914,59 @@ void release_iter_graph(dft_plan* p) {
     if (p->igraph) cudaGraphDestroy(p->igraph);
     p->iexec = nullptr;
     p->igraph = nullptr;
+    p->iloop = false;
+}
+
+// On-device iteration loop: a graph whose only node is a conditional WHILE node; its body is one
+// iteration followed by k_loop_tail, which counts the iterations left (set by k_loop_set before
+// each launch) and clears the condition after the last, so one graph launch runs all of them
+// without returning to the host.
+__global__ void k_loop_set(int* left, int n) { *left = n; }
+__global__ void k_loop_tail(cudaGraphConditionalHandle h, int* left) {
+    const int n = *left - 1;
+    *left = n;
+    cudaGraphSetConditional(h, n > 0 ? 1u : 0u);
+}
+
+// Build the loop graph: `body` queues one iteration on `st` (a capture stream) and returns a
+// status.  On success *graph holds the loop; a runtime without conditional nodes returns an
+// error and the caller replays a one-iteration graph instead.
+template <typename F>
+cudaError_t build_loop_graph(cudaStream_t st, int* left, cudaGraph_t* graph, dft_status* body_status, F&& body) {
+    *graph = nullptr;
+    *body_status = DFT_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return e;
+    }
+    *body_status = body();
+    k_loop_tail<<<1, 1, 0, st>>>(h, left);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(st, &captured);
+    if (e == cudaSuccess && *body_status != DFT_OK) e = cudaErrorUnknown;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return e;
+    }
+    *graph = g;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -1256,23 +1310,38 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
             if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
                 return fail(p, DFT_ECUDA, "capture stream creation failed");
             cudaStream_t user = p->stream;
+            auto one_iteration = [&]() -> dft_status {
+                return is_fp64(p)
+                    ? iter_step_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V), alpha)
+                    : iter_step_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V), alpha);
+            };
+            // the on-device loop first; a runtime without conditional graph nodes falls back to
+            // replays of a one-iteration graph
             p->stream = p->cap;
-            cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) {
-                p->stream = user;
-                return fail(p, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-            }
-            dft_status st = is_fp64(p)
-                ? iter_step_t<double>(p, static_cast<double*>(rho), static_cast<const double*>(V), alpha)
-                : iter_step_t<float>(p, static_cast<float*>(rho), static_cast<const float*>(V), alpha);
             cudaGraph_t g = nullptr;
-            e = cudaStreamEndCapture(p->cap, &g);
+            dft_status st = DFT_OK;
+            cudaError_t e = build_loop_graph(p->cap, &p->ctl->loop_left, &g, &st, one_iteration);
             p->stream = user;
-            if (st != DFT_OK) {
-                if (g) cudaGraphDestroy(g);
-                return st;
+            if (st != DFT_OK) return st;
+            if (e == cudaSuccess) {
+                p->iloop = true;
+            } else {
+                p->stream = p->cap;
+                e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) {
+                    p->stream = user;
+                    return fail(p, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+                }
+                st = one_iteration();
+                e = cudaStreamEndCapture(p->cap, &g);
+                p->stream = user;
+                if (st != DFT_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return st;
+                }
+                if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+                p->iloop = false;
             }
-            if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
             p->igraph = g;
             e = cudaGraphInstantiate(&p->iexec, p->igraph, 0);
             if (e != cudaSuccess) {
@@ -1283,9 +1352,16 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
             p->graph_V = V;
             p->graph_alpha = alpha;
         }
-        for (int it = 0; it < iters; ++it) {
-            cudaError_t e = cudaGraphLaunch(p->iexec, p->stream);
+        if (p->iloop && iters > 0) {
+            k_loop_set<<<1, 1, 0, p->stream>>>(&p->ctl->loop_left, iters);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGraphLaunch(p->iexec, p->stream);
             if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        } else {
+            for (int it = 0; it < iters; ++it) {
+                cudaError_t e = cudaGraphLaunch(p->iexec, p->stream);
+                if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            }
         }
     }
     if (resid_out) {
@@ -1439,6 +1515,7 @@ struct dft_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double graph_alpha = 0.0;
+    bool loop = false;              // the graph is the on-device loop over iterations
     std::vector<void*> rho;
     std::vector<const void*> V;
     bool begun = false;
@@ -1457,6 +1534,7 @@ void batch_release_graph(dft_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
+    b->loop = false;
 }
 }  // namespace
 
@@ -1535,26 +1613,39 @@ dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, doubl
     if (!b || !b->begun) return bfail(b, DFT_EINVAL, "dft_batch_iterate needs a preceding dft_batch_begin");
     if (iters < 0) return bfail(b, DFT_EINVAL, "negative iteration count");
     if (b->exec && b->graph_alpha != alpha_or_neg) batch_release_graph(b);
+    int* left = &b->plans[0]->ctl->loop_left;   // the loop's counter (in the first state's block)
     if (!b->exec) {
-        // capture one iteration of every state: fork from the main stream, join back
-        cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-        cudaEventRecord(b->fork, b->main);
-        dft_status st = DFT_OK;
-        for (size_t i = 0; i < b->plans.size() && st == DFT_OK; ++i) {
-            cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-            st = dft_iter_step(b->plans[i], b->rho[i], b->V[i], alpha_or_neg, nullptr, nullptr);
-            if (st != DFT_OK) b->err = "state " + std::to_string(i) + ": " + b->plans[i]->err;
-            cudaEventRecord(b->joins[i], b->streams[i]);
-            cudaStreamWaitEvent(b->main, b->joins[i], 0);
-        }
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(b->main, &g);
-        if (st != DFT_OK) {
-            if (g) cudaGraphDestroy(g);
+        // one iteration of every state: fork from the main stream, join back
+        auto one_iteration = [&]() -> dft_status {
+            cudaEventRecord(b->fork, b->main);
+            dft_status st = DFT_OK;
+            for (size_t i = 0; i < b->plans.size() && st == DFT_OK; ++i) {
+                cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+                st = dft_iter_step(b->plans[i], b->rho[i], b->V[i], alpha_or_neg, nullptr, nullptr);
+                if (st != DFT_OK) b->err = "state " + std::to_string(i) + ": " + b->plans[i]->err;
+                cudaEventRecord(b->joins[i], b->streams[i]);
+                cudaStreamWaitEvent(b->main, b->joins[i], 0);
+            }
             return st;
+        };
+        // all iterations of all states in one graph launch (an on-device loop over the
+        // captured iteration); a runtime without conditional graph nodes replays a graph of one
+        cudaGraph_t g = nullptr;
+        dft_status st = DFT_OK;
+        cudaError_t e = build_loop_graph(b->main, left, &g, &st, one_iteration);
+        if (st != DFT_OK) return st;
+        b->loop = e == cudaSuccess;
+        if (!b->loop) {
+            e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+            st = one_iteration();
+            e = cudaStreamEndCapture(b->main, &g);
+            if (st != DFT_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
         }
-        if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
         b->graph = g;
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);
         if (e != cudaSuccess) {
@@ -1563,9 +1654,16 @@ dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, doubl
         }
         b->graph_alpha = alpha_or_neg;
     }
-    for (int it = 0; it < iters; ++it) {
-        cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+    if (b->loop && iters > 0) {
+        k_loop_set<<<1, 1, 0, b->main>>>(left, iters);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->main);
         if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+            if (e != cudaSuccess) return bfail(b, DFT_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        }
     }
     if (resid_out) {
         cudaError_t e = cudaStreamSynchronize(b->main);

@@ -151,6 +151,7 @@ struct Ctl {
     double sample_alpha[2];
     int status;             // dft_status bits raised on the device (see DEV_* below)
     int iter;
+    int loop_left;          // iterations left in an on-device loop of dft_iter_run / dft_batch_iterate
     // fixed-number species: G_i = canon_scale[i] exp(-V_i + c_i), canon_scale = N_i / (h^3 sum e)
     double canon_scale[DFT_MAXS];
 };

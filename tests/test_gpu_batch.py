@@ -74,8 +74,9 @@ def test_batch_state_with_steep_residual_converges():
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("alpha", [-1.0, 0.1])
 def test_iter_run_graph_matches_iter_step(precision, alpha):
-    # dft_iter_run replays a captured graph of one iteration: the iterate must equal, bit for
-    # bit, the same number of dft_iter_step calls (same kernels in the same order)
+    # dft_iter_run runs a captured iteration in an on-device loop (one graph launch per call,
+    # the count kept on the device): the iterate must equal, bit for bit, the same number of
+    # dft_iter_step calls (same kernels in the same order), over two calls of 2 and 3
     from paper_0910_1531_gb300 import binding
     w = workloads.centred_sphere(n=32, h=0.1, molar=0.5, sphere_radius=0.5, mixing=None)
     dt = torch.float64 if precision == "fp64" else torch.float32
