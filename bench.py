@@ -633,11 +633,12 @@ def fp64_record(args, w, stream, world):
     V = torch.tensor(w.V, dtype=torch.float64, device="cuda")
     steps = max(10, min(args.steps, 50))
     plan.autotune(rho, V)
+    tuning = plan.tuning()
     ms = graph_iterations_ms(plan, rho, V, -1.0, steps, args.warmup, stream, world)
     prof, _ = profile_iterations(plan, rho, V, -1.0, steps, stream)
     peak, _ = measured_peaks()
     rec = {"value": job_throughput(steps, world, ms), "unit": UNIT, "dtype": "f64", "steps": steps,
-           "ms_per_step": ms / steps, "roofline": dominant_roofline(prof, w, "fp64"),
+           "ms_per_step": ms / steps, "autotuned": tuning, "roofline": dominant_roofline(prof, w, "fp64"),
            "kernels": kernel_table(prof, peak),
            "convergence": picard_to_tolerance(plan, rho0, V, -1.0, 1e-8, 400)}
     plan.close()
@@ -661,6 +662,7 @@ def large_record(args, stream, world):
     V32 = torch.tensor(w.V, dtype=torch.float32, device="cuda")
     steps = max(10, min(args.steps, 50))
     x_lines = p32.autotune(rho, V32)
+    tuning = p32.tuning()
     ms = graph_iterations_ms(p32, rho, V32, alpha, steps, args.warmup, stream, world)
     prof, _ = profile_iterations(p32, rho, V32, alpha, steps, stream)
     peak, _ = measured_peaks()
@@ -680,7 +682,7 @@ def large_record(args, stream, world):
             "bulk_molar": list(map(float, w.bulk_molar)), **workload_config(w),
             "value": job_throughput(steps, world, ms), "unit": UNIT, "dtype": "f32", "steps": steps,
             "ms_per_step": ms / steps, "step": f"one Picard iteration with fixed mixing {alpha} (graph replay)",
-            "x_rows_per_block": x_lines, "roofline": dominant_roofline(prof, w, "fp32"),
+            "x_rows_per_block": x_lines, "autotuned": tuning, "roofline": dominant_roofline(prof, w, "fp32"),
             "kernels": kernel_table(prof, peak),
             "convergence": {"tol": 1e-6, "seconds": phase32["seconds"] + phase64["seconds"],
                             "converged": phase64["converged"], "resid": phase64["resid"],
@@ -727,8 +729,10 @@ def run_ours(args):
             args.converge_tol = 0.0
     if args.solver is None:
         args.solver = "newton" if args.workload in ("pore256", "hswall") else "picard"
-    # x-pass rows per block timed on this workload (cached per shape inside the library)
+    # rows per block and transform variants timed on this workload (cached per shape inside
+    # the library)
     x_lines = plan.autotune(rho, V)
+    tuning = plan.tuning()
 
     uuid = None
     try:
@@ -818,6 +822,7 @@ def run_ours(args):
                            "convergence": convergence,
                            "ms_per_step_launched": ms_prof / args.steps,
                            "x_rows_per_block": x_lines,
+                           "autotuned": tuning,
                            "parallelism": f"replicas x{world}",
                            "l2": (f"no flush: working set {working_set/1e6:.0f} MB > L2 129 MB" if working_set > L2_BYTES
                                   else f"no flush: working set {working_set/1e6:.0f} MB fits the 129 MB L2 "

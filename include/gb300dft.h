@@ -219,16 +219,35 @@ dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iter
                         double* resid_out);
 
 /*
- * Autotuner (no counterpart in the paper): times the rows per block of the x passes that run
- * every iteration (forward x transform of the densities; the Phi' pass; the update pass over
- * candidates 1..16; the n3-maximum pass of the line search over 8..64) on the plan's own data (rho, V: [S][N] device, read only;
- * `reps` timed launches per candidate, < 1 selects 5) and keeps the fastest in the plan.
+ * Autotuner (no counterpart in the paper): on the plan's own data (rho, V: [S][N] device,
+ * read only; `reps` timed launches per candidate, < 1 selects 5) it times and keeps the fastest
+ *  - rows per block of the x passes that run every iteration (forward x transform of the
+ *    densities; the Phi' pass and its paired-sample form; the update pass and its paired form,
+ *    over candidates 1..16; the n3-maximum pass of the line search over 8..64);
+ *  - the x transform: the compile-time kernels (where the length has them) against the
+ *    run-time ones under each candidate radix order (the default plan -- 3s, other odd primes,
+ *    16s, then 2/4/8 --, its reverse, and for powers of two a plan of 8s and one of 4s);
+ *  - the y transform: the persistent TMA pass against the run-time column kernel;
+ *  - the z passes: the persistent TMA passes against the grouped one-tile-per-CTA kernels.
  * Results are cached per (grid, species count, precision) for the life of the process, so
  * later plans of the same shape reuse them without timing.  Invalidates a preceding
- * dft_iter_begin (call it again).  lines_out (may be NULL) receives the first three choices.
- * Runs on the plan's stream and synchronises it.
+ * dft_iter_begin (call it again).  lines_out (may be NULL) receives the first three row
+ * choices; dft_plan_tuning describes all of them.  Runs on the plan's stream and synchronises it.
  */
 dft_status dft_autotune(dft_plan* plan, const void* rho, const void* V, int reps, int lines_out[3]);
+
+/* One line describing the plan's transform variants, radix orders and rows per block (the
+ * defaults until dft_autotune chooses); owned by the plan, valid until its next call.  "" for NULL. */
+const char* dft_plan_tuning(const dft_plan* plan);
+
+/* Pin the transform variants instead of letting dft_autotune choose them (and for tests):
+ * x_variant 0 = the compile-time x kernels (only for lengths that have them), k >= 1 = the
+ * run-time ones under candidate radix order k (in dft_autotune's order; DFT_EINVAL past the
+ * last); y_variant 0 = persistent TMA pass (run-time kernel for lengths without one), 1 =
+ * run-time column kernel; z_variant 0 = persistent TMA passes, 1 = grouped one-tile-per-CTA
+ * kernels (lengths without compile-time kernels run the run-time ones either way).
+ * Invalidates a preceding dft_iter_begin. */
+dft_status dft_set_variants(dft_plan* plan, int x_variant, int y_variant, int z_variant);
 
 /*
  * Grand potential and its gradients (differentiated form).  The paper asserts

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "bulk.h"
+#include "fft.cuh"
 #include "gb300dft.h"
 #include "newton.h"
 #include "passes.h"
@@ -88,6 +89,7 @@ struct dft_plan {
     const void* graph_V = nullptr;
     double graph_alpha = 0.0;
     bool iloop = false;             // the cached graph is the on-device loop (else one iteration)
+    std::string tuning;             // the transform variants and rows per block in use (text)
     double* grad_red = nullptr;     // partial sums of dft_grad (allocated on first use)
     size_t grad_red_len = 0;
     bool iter_ready = false;
@@ -808,7 +810,77 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 6>> g_tune_cache;
+struct TuneResult {
+    std::array<int, 6> lines;       // LX, LRphi, LRupd, LRn3, LRphi2, LRupd2
+    int xrt, yrt, zgrp;             // transform variants (GridDesc)
+    AxisPlan ax;                    // radix order of the x passes
+};
+std::map<TuneKey, TuneResult> g_tune_cache;
+
+// Candidate radix orders of a run-time transform of length n: the default plan (3s, other odd
+// primes, 16s, then 2/4/8), its reverse, and for powers of two one of 8s (then 4 or 2) and one of
+// 4s (then 2).
+std::vector<AxisPlan> radix_orders(int n) {
+    std::vector<AxisPlan> out;
+    AxisPlan d;
+    if (!dft_radix_plan(n, &d)) return out;
+    out.push_back(d);
+    AxisPlan r = d;
+    std::reverse(r.radix, r.radix + r.nstages);
+    auto same = [](const AxisPlan& a, const AxisPlan& b) {
+        if (a.nstages != b.nstages) return false;
+        for (int s = 0; s < a.nstages; ++s)
+            if (a.radix[s] != b.radix[s]) return false;
+        return true;
+    };
+    auto add = [&](const AxisPlan& a) {
+        for (const AxisPlan& o : out)
+            if (same(o, a)) return;
+        out.push_back(a);
+    };
+    add(r);
+    if ((n & (n - 1)) == 0) {
+        for (int big : {8, 4}) {
+            AxisPlan q{n, 0, {}};
+            int m = n;
+            while (m % big == 0 && q.nstages < DFT_MAXSTAGES) { q.radix[q.nstages++] = big; m /= big; }
+            if (m > 1 && q.nstages < DFT_MAXSTAGES) q.radix[q.nstages++] = m;
+            if (m <= 16 && q.nstages <= DFT_MAXSTAGES) add(q);
+        }
+    }
+    return out;
+}
+
+std::string radix_text(const AxisPlan& a) {
+    std::string s;
+    for (int i = 0; i < a.nstages; ++i) s += (i ? "x" : "") + std::to_string(a.radix[i]);
+    return s;
+}
+
+std::string ct_radix_text(int n) {
+    std::string s;
+    for (int i = 0; i < ct_nstages(n); ++i) s += (i ? "x" : "") + std::to_string(ct_radix_at(n, i));
+    return s;
+}
+
+// Text of a plan's transform variants and rows per block (dft_plan_tuning).
+void describe_tuning(dft_plan* p) {
+    const GridDesc& g = p->g;
+    std::string t = "x: ";
+    t += (!g.xrt && dft_is_ct_size(g.nx)) ? "compile-time radix " + ct_radix_text(g.nx)
+                                          : "run-time radix " + radix_text(p->ax);
+    t += "; rows per block xfwd " + std::to_string(p->LX) + ", xphi " + std::to_string(p->LRphi) + ", xupdate " +
+         std::to_string(p->LRupd) + ", n3 max " + std::to_string(p->LRn3) + ", paired xphi " +
+         std::to_string(p->LRphi2) + ", paired xupdate " + std::to_string(p->LRupd2);
+    t += "; y: ";
+    t += (!g.yrt && dft_is_ct_size(g.ny)) ? "TMA persistent, " + std::to_string(p->precision == DFT_FP64 ? 8 : 16) +
+                                                "-column tiles"
+                                          : "run-time column kernel, " + std::to_string(p->Ty) + "-column tiles";
+    t += "; z: ";
+    t += dft_is_ct_size(g.nz) ? (g.zgrp ? std::string("grouped, one tile per CTA") : std::string("TMA persistent"))
+                              : "run-time column kernel, " + std::to_string(p->Tz) + "-column tiles";
+    p->tuning = t;
+}
 
 template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, const Real* V, int reps) {
     using O = Ops<Real>;
@@ -892,18 +964,74 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
             if (ms < best_ms[5]) { best_ms[5] = ms; best[5] = L; }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaError_t e = cudaStreamSynchronize(p->stream);
-    p->prof = prof;
-    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
-    TRY(reset_status(p));
     p->LX = best[0];
     p->LRphi = best[1];
     p->LRupd = best[2];
     p->LRn3 = best[3];
     p->LRphi2 = best[4];
     p->LRupd2 = best[5];
+    // Transform variants, timed on the same data with the rows per block just chosen.
+    // x: the compile-time Phi' pass (where the length has one) against the run-time one under
+    // each candidate radix order.
+    {
+        const AxisPlan ax0 = p->ax;
+        float bms = 1e30f;
+        int bxrt = 1;
+        AxisPlan bax = ax0;
+        auto time_xphi = [&] {
+            return time_it([&] {
+                P::xphi(p->stream, p->g, p->ax, p->LRphi, p->ctl, A, A, nullptr, O::T1(p), p->red_max,
+                        &p->ctl->status, nullptr, O::kf(p, 0), O::tw(p, 0));
+            });
+        };
+        if (dft_is_ct_size(p->g.nx)) {
+            p->g.xrt = 0;
+            bms = time_xphi();
+            bxrt = 0;
+        }
+        for (const AxisPlan& o : radix_orders(p->g.nx)) {
+            if (P::smem_x(p->g.nx, 5 * p->LRphi) > size_t(optin)) break;
+            p->g.xrt = 1;
+            p->ax = o;
+            const float ms = time_xphi();
+            if (ms < bms) { bms = ms; bxrt = 1; bax = o; }
+        }
+        p->g.xrt = bxrt;
+        p->ax = bxrt ? bax : ax0;
+    }
+    // y: the persistent TMA pass against the run-time column kernel (nine components forward)
+    if (dft_is_ct_size(p->g.ny)) {
+        float ms[2];
+        for (int v = 0; v < 2; ++v) {
+            p->g.yrt = v;
+            ms[v] = time_it([&] {
+                P::yfft(p->stream, false, p->g, p->ay, p->Ty, DFT_NSPEC, O::T1(p), &p->ctl->status, O::tw(p, 1),
+                        p->wait_polls);
+            });
+        }
+        p->g.yrt = ms[1] < ms[0] ? 1 : 0;
+    }
+    // z: the persistent TMA passes against the grouped one-tile-per-CTA kernels (both halves)
+    if (dft_is_ct_size(p->g.nz)) {
+        float ms[2];
+        for (int v = 0; v < 2; ++v) {
+            p->g.zgrp = v;
+            ms[v] = time_it([&] {
+                P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 0, O::T1(p),
+                             O::slot_n(p->slotB), O::slot_es(p, p->slotB), nullptr, O::tw(p, 2), &p->ctl->status);
+                P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 3, p->S,
+                             p->ctl, O::T1(p), O::slot_es(p, p->slotA), O::slot_es(p, p->slotB), nullptr,
+                             O::tw(p, 2));
+            });
+        }
+        p->g.zgrp = ms[1] < ms[0] ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    p->prof = prof;
+    if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    TRY(reset_status(p));
     return DFT_OK;
 }
 }  // namespace
@@ -1169,6 +1297,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         dft_plan_destroy(p);
         return fail(nullptr, DFT_ECUDA, std::string("plan setup: ") + cudaGetErrorString(e));
     }
+    describe_tuning(p);
     *out = p;
     return DFT_OK;
 }
@@ -1381,12 +1510,17 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            p->LX = it->second[0];
-            p->LRphi = it->second[1];
-            p->LRupd = it->second[2];
-            p->LRn3 = it->second[3];
-            p->LRphi2 = it->second[4];
-            p->LRupd2 = it->second[5];
+            const TuneResult& t = it->second;
+            p->LX = t.lines[0];
+            p->LRphi = t.lines[1];
+            p->LRupd = t.lines[2];
+            p->LRn3 = t.lines[3];
+            p->LRphi2 = t.lines[4];
+            p->LRupd2 = t.lines[5];
+            p->g.xrt = t.xrt;
+            p->g.yrt = t.yrt;
+            p->g.zgrp = t.zgrp;
+            p->ax = t.ax;
             cached = true;
         }
     }
@@ -1394,11 +1528,13 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         if (is_fp64(p)) TRY(autotune_t<double>(p, static_cast<const double*>(rho), static_cast<const double*>(V), reps));
         else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2};
+        g_tune_cache[key] = TuneResult{{p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2},
+                                       p->g.xrt, p->g.yrt, p->g.zgrp, p->ax};
     }
-    // the iteration state and its graph depend on the block counts
+    // the iteration state and its graph depend on the block counts and variants
     p->iter_ready = false;
     release_iter_graph(p);
+    describe_tuning(p);
     if (lines_out) {
         lines_out[0] = p->LX;
         lines_out[1] = p->LRphi;
@@ -1683,6 +1819,26 @@ dft_status dft_set_wait_polls(dft_plan* p, long long polls) {
     // a captured iteration holds the old bound in its kernel parameters
     release_iter_graph(p);
     p->wait_polls = polls;
+    return DFT_OK;
+}
+
+const char* dft_plan_tuning(const dft_plan* p) { return p ? p->tuning.c_str() : ""; }
+
+dft_status dft_set_variants(dft_plan* p, int x_variant, int y_variant, int z_variant) {
+    TRY(check_plan(p));
+    const std::vector<AxisPlan> orders = radix_orders(p->g.nx);
+    if (x_variant < 0 || x_variant > (int)orders.size() || (x_variant == 0 && !dft_is_ct_size(p->g.nx)))
+        return fail(p, DFT_EINVAL, "x variant out of range for this length");
+    if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 1)
+        return fail(p, DFT_EINVAL, "y and z variants are 0 or 1");
+    p->g.xrt = x_variant > 0 ? 1 : 0;
+    if (x_variant > 0) p->ax = orders[x_variant - 1];
+    else dft_radix_plan(p->g.nx, &p->ax);
+    p->g.yrt = y_variant;
+    p->g.zgrp = z_variant;
+    p->iter_ready = false;
+    release_iter_graph(p);
+    describe_tuning(p);
     return DFT_OK;
 }
 

@@ -84,6 +84,11 @@ struct GridDesc {
     long long nc;    // nz * ny * pxh (elements per half-spectrum component)
     double hx, hy, hz;
     int phi;         // hard-sphere free-energy density of the state point (DFT_PHI_*; 0 = eq. Phi)
+    // transform variants chosen by the autotuner (0 for all: the compile-time passes where a
+    // length has them): x passes by the run-time kernels with the plan's AxisPlan; y passes by
+    // the run-time column kernel; z passes by the one-tile-per-CTA grouped kernels instead of
+    // the persistent TMA ones
+    int xrt, yrt, zgrp;
 };
 
 // Species constants in the kernels' precision (host fills them in double, then converts).

@@ -15,12 +15,12 @@ DFT_CT_SIZES(DFT_DECLARE_EXTERN)
 DFT_DECLARE_EXTERN(0)
 
 #define DFT_CASE(N, L, call) case N: L<Real, N>::call; break;
-#define DFT_SWITCH_X(n, call) switch (n) { \
+#define DFT_SWITCH_X(n, call) if (g.xrt) return LaunchX<Real, 0>::call; switch (n) { \
     case 32: return LaunchX<Real, 32>::call; case 48: return LaunchX<Real, 48>::call; \
     case 64: return LaunchX<Real, 64>::call; case 96: return LaunchX<Real, 96>::call; \
     case 128: return LaunchX<Real, 128>::call; case 256: return LaunchX<Real, 256>::call; \
     default: return LaunchX<Real, 0>::call; }
-#define DFT_SWITCH_Y(n, call) switch (n) { \
+#define DFT_SWITCH_Y(n, call) if (g.yrt) return LaunchY<Real, 0>::call; switch (n) { \
     case 32: return LaunchY<Real, 32>::call; case 48: return LaunchY<Real, 48>::call; \
     case 64: return LaunchY<Real, 64>::call; case 96: return LaunchY<Real, 96>::call; \
     case 128: return LaunchY<Real, 128>::call; case 256: return LaunchY<Real, 256>::call; \

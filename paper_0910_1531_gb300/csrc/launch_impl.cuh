@@ -233,7 +233,7 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         }
         const size_t sm = dftk::zfwd_tma_smem<Real, N, TB>(sp.S);
-        if (!red_energy && status && sm <= size_t(optin)) {
+        if (!red_energy && status && !g.zgrp && sm <= size_t(optin)) {
             // TMA path (the grand-potential sums keep the one-tile-per-CTA kernel below)
             constexpr int NT = dft_zfwd_threads<Real>(N), MB = dft_zfwd_minb<Real>(N);
             constexpr int E = int(sizeof(C) / 8);
@@ -295,7 +295,7 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
     if constexpr (kTma) {
-        if (dftk::zbwd_tma_smem<Real, N, TB>(nes) <= size_t(optin)) {
+        if (!g.zgrp && dftk::zbwd_tma_smem<Real, N, TB>(nes) <= size_t(optin)) {
             // TMA path: persistent CTAs, two TMA-filled stages of nine Phi' tiles, one area of ES tiles
             constexpr int NT = dft_zbwd_threads<Real>(N), MB = dft_zbwd_minb<Real>(N);
             constexpr int E = int(sizeof(C) / 8);
