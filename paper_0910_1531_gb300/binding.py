@@ -82,7 +82,7 @@ SIGNATURES = {
     "dft_batch_iterate": (_I, [_P, _I, _D, _PD]),
     "dft_set_wait_polls": (_I, [_P, ctypes.c_longlong]),
     "dft_plan_tuning": (ctypes.c_char_p, [_P]),
-    "dft_set_variants": (_I, [_P, _I, _I, _I]),
+    "dft_set_variants": (_I, [_P, _I, _I, _I, _I]),
     "dft_profile_enable": (_I, [_P, _I]),
     "dft_profile_read": (_I, [_P, ctypes.c_char_p, _PI, _PD, _PD]),
     "dft_version": (ctypes.c_char_p, []),
@@ -295,9 +295,9 @@ class Plan:
         """The plan's transform variants, radix orders and rows per block, as one line of text."""
         return self.lib.dft_plan_tuning(self.handle).decode()
 
-    def set_variants(self, x=0, y=0, z=0):
+    def set_variants(self, x=0, y=0, z=0, x_persistent=0):
         """Pin the transform variants (see dft_set_variants)."""
-        self._check(self.lib.dft_set_variants(self.handle, int(x), int(y), int(z)))
+        self._check(self.lib.dft_set_variants(self.handle, int(x), int(x_persistent), int(y), int(z)))
 
     def set_wait_polls(self, polls=None):
         """Bound of the y passes' TMA tile waits (None: the default); 0 makes them give up at once."""

@@ -812,7 +812,7 @@ struct TuneKey {
 std::mutex g_tune_mu;
 struct TuneResult {
     std::array<int, 6> lines;       // LX, LRphi, LRupd, LRn3, LRphi2, LRupd2
-    int xrt, yrt, zgrp;             // transform variants (GridDesc)
+    int xrt, xpers, yrt, zgrp;      // transform variants (GridDesc)
     AxisPlan ax;                    // radix order of the x passes
 };
 std::map<TuneKey, TuneResult> g_tune_cache;
@@ -869,6 +869,7 @@ void describe_tuning(dft_plan* p) {
     std::string t = "x: ";
     t += (!g.xrt && dft_is_ct_size(g.nx)) ? "compile-time radix " + ct_radix_text(g.nx)
                                           : "run-time radix " + radix_text(p->ax);
+    if (!g.xrt && dft_is_ct_size(g.nx) && g.xpers) t += ", persistent Phi' passes with bulk-copy prefetch";
     t += "; rows per block xfwd " + std::to_string(p->LX) + ", xphi " + std::to_string(p->LRphi) + ", xupdate " +
          std::to_string(p->LRupd) + ", n3 max " + std::to_string(p->LRn3) + ", paired xphi " +
          std::to_string(p->LRphi2) + ", paired xupdate " + std::to_string(p->LRupd2);
@@ -970,6 +971,30 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     p->LRn3 = best[3];
     p->LRphi2 = best[4];
     p->LRupd2 = best[5];
+    // The persistent Phi' passes (compile-time lengths): their own rows per block, kept if the
+    // single and paired passes together are faster than the per-block kernels.
+    if (dft_is_ct_size(p->g.nx)) {
+        p->g.xpers = 1;
+        int bp[2] = {p->LRphi, p->LRphi2};
+        float bpm[2] = {1e30f, 1e30f};
+        for (int L : cand) {
+            float ms = time_it([&] {
+                P::xphi(p->stream, p->g, p->ax, L, p->ctl, A, A, nullptr, O::T1(p), p->red_max, &p->ctl->status,
+                        nullptr, O::kf(p, 0), O::tw(p, 0));
+            });
+            if (ms < bpm[0]) { bpm[0] = ms; bp[0] = L; }
+            ms = time_it([&] {
+                P::xphi2(p->stream, p->g, p->ax, L, p->ctl, A, A, O::T1(p), &p->ctl->status, O::kf(p, 0), O::tw(p, 0));
+            });
+            if (ms < bpm[1]) { bpm[1] = ms; bp[1] = L; }
+        }
+        if (bpm[0] + bpm[1] < best_ms[1] + best_ms[4]) {
+            p->LRphi = bp[0];
+            p->LRphi2 = bp[1];
+        } else {
+            p->g.xpers = 0;
+        }
+    }
     // Transform variants, timed on the same data with the rows per block just chosen.
     // x: the compile-time Phi' pass (where the length has one) against the run-time one under
     // each candidate radix order.
@@ -1518,6 +1543,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
             p->LRphi2 = t.lines[4];
             p->LRupd2 = t.lines[5];
             p->g.xrt = t.xrt;
+            p->g.xpers = t.xpers;
             p->g.yrt = t.yrt;
             p->g.zgrp = t.zgrp;
             p->ax = t.ax;
@@ -1529,7 +1555,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = TuneResult{{p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2},
-                                       p->g.xrt, p->g.yrt, p->g.zgrp, p->ax};
+                                       p->g.xrt, p->g.xpers, p->g.yrt, p->g.zgrp, p->ax};
     }
     // the iteration state and its graph depend on the block counts and variants
     p->iter_ready = false;
@@ -1824,14 +1850,16 @@ dft_status dft_set_wait_polls(dft_plan* p, long long polls) {
 
 const char* dft_plan_tuning(const dft_plan* p) { return p ? p->tuning.c_str() : ""; }
 
-dft_status dft_set_variants(dft_plan* p, int x_variant, int y_variant, int z_variant) {
+dft_status dft_set_variants(dft_plan* p, int x_variant, int x_persistent, int y_variant, int z_variant) {
     TRY(check_plan(p));
+    if (x_persistent < 0 || x_persistent > 1) return fail(p, DFT_EINVAL, "x_persistent is 0 or 1");
     const std::vector<AxisPlan> orders = radix_orders(p->g.nx);
     if (x_variant < 0 || x_variant > (int)orders.size() || (x_variant == 0 && !dft_is_ct_size(p->g.nx)))
         return fail(p, DFT_EINVAL, "x variant out of range for this length");
     if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 1)
         return fail(p, DFT_EINVAL, "y and z variants are 0 or 1");
     p->g.xrt = x_variant > 0 ? 1 : 0;
+    p->g.xpers = x_persistent;
     if (x_variant > 0) p->ax = orders[x_variant - 1];
     else dft_radix_plan(p->g.nx, &p->ax);
     p->g.yrt = y_variant;

@@ -89,6 +89,7 @@ struct GridDesc {
     // the run-time column kernel; z passes by the one-tile-per-CTA grouped kernels instead of
     // the persistent TMA ones
     int xrt, yrt, zgrp;
+    int xpers;       // the Phi' x passes as the persistent kernel with bulk-copy prefetch
 };
 
 // Species constants in the kernels' precision (host fills them in double, then converts).

@@ -1668,12 +1668,15 @@ __device__ __forceinline__ void load_row_pairs(const GridDesc& g, int rows, long
 // the nine mixed spectra.  One thread handles all lines of one (row, k): the index arithmetic is
 // shared and its eighteen loads are in flight together.  NM mixtures (weights wA[a], wB[a]) of
 // the same loads: mixture a of row r goes to lines (r NM + a) 5 .. + 4.
-template <typename Real, int NX, int NM = 1>
+// STAGED: the spectra come from shared memory instead, component c of the block's rows at
+// stage[c cstride + r pxh + k] (slot B's at components 9..17; Bm only tells that they are there).
+template <typename Real, int NX, int NM = 1, bool STAGED = false>
 __device__ __forceinline__ void load_wd_rows(const GridDesc& g, int rows, long long row0, long long nrows,
                                              const typename Cplx<Real>::type* A,
                                              const typename Cplx<Real>::type* Bm, const Real* wA,
                                              const Real* wB, typename Cplx<Real>::type* mat_out, Real kfx,
-                                             typename Cplx<Real>::type* dst) {
+                                             typename Cplx<Real>::type* dst,
+                                             const typename Cplx<Real>::type* stage = nullptr, int cstride = 0) {
     using C = typename Cplx<Real>::type;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
@@ -1687,8 +1690,13 @@ __device__ __forceinline__ void load_wd_rows(const GridDesc& g, int rows, long l
         for (int c = 0; c < DFT_NSPEC; ++c) {
             v[c] = vb[c] = cmake<C>(Real(0), Real(0));
             if (live) {
-                v[c] = A[(long long)c * g.nc + o];
-                if (Bm) vb[c] = Bm[(long long)c * g.nc + o];
+                if constexpr (STAGED) {
+                    v[c] = stage[c * cstride + r * g.pxh + k];
+                    if (Bm) vb[c] = stage[(DFT_NSPEC + c) * cstride + r * g.pxh + k];
+                } else {
+                    v[c] = A[(long long)c * g.nc + o];
+                    if (Bm) vb[c] = Bm[(long long)c * g.nc + o];
+                }
             }
         }
         const bool edge = k == 0 || (even && 2 * k == nx);
@@ -1855,6 +1863,137 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
         const double bp = block_sum(phi_acc, scratch_d);
         if (threadIdx.x == 0) red_phi[blockIdx.x] = bp;
     }
+}
+
+// ------------------------------------------------------------------------------------
+// Persistent form of k_xphi for compile-time lengths (same contract, same arithmetic per block):
+// CTA b takes the row blocks b, b + gridDim.x, ...  The nine (one slot) or eighteen (two slots)
+// half-spectrum components of a block's LR rows are contiguous in each component, so they
+// arrive by one bulk copy each (cp.async.bulk, completing on the stage's mbarrier) into one of
+// two staging areas, requested two blocks ahead: the transforms and Phi' of one block run
+// while the next blocks' spectra are in flight.  A wait that runs out sets DEV_TIMEOUT and the
+// CTA stops after draining the copies it has in flight.
+// Shared memory: twiddles | stage 0 | stage 1 (nsrc components of LR rows each) | line
+// buffers A, B | two mbarriers.
+// ------------------------------------------------------------------------------------
+template <typename Real, int NX> __host__ __device__ constexpr size_t xphi_tma_smem(int nm, int LR, int nsrc, int pxh) {
+    using C = typename Cplx<Real>::type;
+    return (size_t(NX) + 2 * size_t(nsrc) * LR * pxh + 2 * size_t(5 * nm * LR) * ct_row_pitch(NX)) * sizeof(C) +
+           2 * sizeof(uint64_t) + 256;
+}
+
+template <typename Real, int NX, int NM>
+__global__ void __launch_bounds__(kThreads) k_xphi_tma(GridDesc g, int LR, const Ctl* __restrict__ ctl,
+                                                       const typename Cplx<Real>::type* slotA,
+                                                       const typename Cplx<Real>::type* slotB,
+                                                       typename Cplx<Real>::type* mat_out,
+                                                       typename Cplx<Real>::type* __restrict__ phi_out,
+                                                       float* __restrict__ red_max, int* __restrict__ status,
+                                                       Real kfx, const typename Cplx<Real>::type* __restrict__ twx) {
+    static_assert(NX > 0, "compile-time lengths only");
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float scratch_f[32];
+    constexpr int pitch = ct_row_pitch(NX);
+    const int nsrc = slotB ? 2 * DFT_NSPEC : DFT_NSPEC;
+    const int cstride = LR * g.pxh;                       // elements per staged component
+    const int lines = 5 * NM * LR;
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
+    C* tw = reinterpret_cast<C*>(base);
+    C* stage0 = tw + ((NX + 15) & ~15);                   // 128-byte aligned (NX a multiple of 16)
+    C* A = stage0 + 2 * nsrc * cstride;
+    C* B = A + lines * pitch;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(B + lines * pitch);
+    const long long nrows = (long long)g.ny * g.nz;
+    const int nblk = (int)((nrows + LR - 1) / LR);
+    Real wA[NM], wB[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
+        wA[m] = Real(cw->wA);
+        wB[m] = Real(cw->wB);
+    }
+    auto issue = [&](int blk, int s) {
+        const long long r0 = (long long)blk * LR;
+        const int rows = (int)(nrows - r0 < LR ? nrows - r0 : LR);
+        const uint32_t bytes = uint32_t(rows) * uint32_t(g.pxh) * uint32_t(sizeof(C));
+        C* st = stage0 + s * nsrc * cstride;
+        tma::mbar_expect_tx(&bar[s], bytes * uint32_t(nsrc));
+        for (int c = 0; c < nsrc; ++c) {
+            const C* src = (c < DFT_NSPEC ? slotA + (long long)c * g.nc : slotB + (long long)(c - DFT_NSPEC) * g.nc) +
+                           r0 * g.pxh;
+            tma::bulk_load(st + c * cstride, src, bytes, &bar[s]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = twx[i];
+    __syncthreads();
+    int issued = 0, consumed = 0;   // per stage, packed (stage 1 << 16) | stage 0; thread 0
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            const int blk = blockIdx.x + s * gridDim.x;
+            if (blk < nblk) { issue(blk, s); issued += 1 << (16 * s); }
+        }
+    }
+    bool bad = false;
+    int it = 0;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const long long row0 = (long long)blk * LR;
+        const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, DEV_TIMEOUT);
+                for (int s = 0; s < 2; ++s) {
+                    const int n_is = (issued >> (16 * s)) & 0xffff, n_co = (consumed >> (16 * s)) & 0xffff;
+                    if (n_is > n_co) tma::mbar_wait(&bar[s], (n_is - 1) & 1);
+                }
+            }
+            break;
+        }
+        consumed += 1 << (16 * cur);
+        const C* st = stage0 + cur * nsrc * cstride;
+        load_wd_rows<Real, NX, NM, true>(g, LR, row0, nrows, nullptr, slotB, wA, wB, mat_out, kfx, A, st, cstride);
+        __syncthreads();
+        // the stage is free: request the block after next into it while this one is transformed
+        if (threadIdx.x == 0) {
+            const int next = blk + 2 * gridDim.x;
+            if (next < nblk) { issue(next, cur); issued += 1 << (16 * cur); }
+        }
+        C* R = ct_fft<NX, true, false, 0>(A, B, lines, pitch, tw);
+        float mx = -CUDART_INF_F;
+        for (int idx = threadIdx.x; idx < LR * NM * NX; idx += kThreads) {
+            const int rr = idx / NX, x = idx - (idx / NX) * NX;
+            const int r = rr / NM;
+            C* bp = R + (rr * 5) * pitch + xo<NX>(x);
+            Real n[DFT_NCOMP];
+            {   // lines (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z): see wd_comp
+                const C v0 = bp[0], v1 = bp[pitch], v2 = bp[2 * pitch], v3 = bp[3 * pitch], v4 = bp[4 * pitch];
+                n[0] = v0.x; n[1] = v0.y; n[2] = v1.x; n[5] = v1.y; n[3] = v2.x;
+                n[7] = v2.y; n[4] = v3.x; n[6] = v3.y; n[8] = v4.x; n[9] = v4.y;
+            }
+            if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
+            const bool okp = phi_derivatives<Real>(n, g.phi);
+            if (!okp && row0 + r < nrows) bad = true;
+            bp[0] = cmake<C>(n[0], n[1]);
+            bp[pitch] = cmake<C>(n[2], n[5]);
+            bp[2 * pitch] = cmake<C>(n[3], n[7]);
+            bp[3 * pitch] = cmake<C>(n[4], n[6]);
+            bp[4 * pitch] = cmake<C>(n[8], n[9]);
+        }
+        __syncthreads();
+        C* other = (R == A) ? B : A;
+        C* F = ct_fft<NX, false, false, 0>(R, other, lines, pitch, tw);
+        store_phi_spectra<Real, NX, NM>(g, LR, row0, nrows, kfx, F, phi_out);
+        const float bm = block_max(mx, scratch_f);
+        if (threadIdx.x == 0 && red_max) red_max[blk] = bm;
+        __syncthreads();   // the line buffers are rewritten by the next block
+    }
+    if (bad) atomicOr(status, DEV_N3BOUND);
 }
 
 // ------------------------------------------------------------------------------------

@@ -31,6 +31,10 @@ cudaError_t LaunchX<Real, N>::init() {
     if ((r = set_max_smem(dftk::k_xfwd<Real, N>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xphi<Real, N, 1>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xphi<Real, N, 2>)) != cudaSuccess) e = r;
+    if constexpr (N > 0) {
+        if ((r = set_max_smem(dftk::k_xphi_tma<Real, N, 1>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_xphi_tma<Real, N, 2>)) != cudaSuccess) e = r;
+    }
     if ((r = set_max_smem(dftk::k_xupdate<Real, N, 1>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xupdate<Real, N, 2>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xcanon<Real, N>)) != cudaSuccess) e = r;
@@ -48,10 +52,43 @@ cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const Axi
     return cudaSuccess;
 }
 
+namespace {
+// The persistent Phi' x pass (compile-time lengths, no grand-potential sums): grid = the row
+// blocks, at most the CTAs that fit on the GPU at once.  False if it does not apply.
+template <typename Real, int N, int NM, typename C>
+bool launch_xphi_tma(cudaStream_t st, const GridDesc& g, int LR, const Ctl* ctl, const C* A, const C* B, C* mat,
+                     C* phi, float* red_max, int* status, Real kfx, const C* tw) {
+    if constexpr (N == 0) {
+        return false;
+    } else {
+        const int nsrc = B ? 2 * DFT_NSPEC : DFT_NSPEC;
+        const size_t sm = dftk::xphi_tma_smem<Real, N>(NM, LR, nsrc, g.pxh);
+        static int optin = 0, sms = 0;
+        if (optin == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        if (!g.xpers || !status || sm > size_t(optin)) return false;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_xphi_tma<Real, N, NM>, dftk::kThreads, sm);
+        if (occ < 1) occ = 1;
+        const long long nblk = ceil_div((long long)g.ny * g.nz, LR);
+        const int grid = (int)(nblk < (long long)sms * occ ? nblk : (long long)sms * occ);
+        dftk::k_xphi_tma<Real, N, NM><<<grid, dftk::kThreads, sm, st>>>(g, LR, ctl, A, B, mat, phi, red_max, status,
+                                                                      kfx, tw);
+        return true;
+    }
+}
+}  // namespace
+
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
                             const C* A, const C* B, C* mat, C* phi, float* red_max, int* status, double* red_phi,
                             Real kfx, const C* tw) {
+    if (!red_phi && launch_xphi_tma<Real, N, 1>(st, g, LR, ctl, A, B, mat, phi, red_max, status, kfx, tw))
+        return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     dftk::k_xphi<Real, N, 1><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
                                                                                     red_max, status, red_phi, kfx, tw);
@@ -61,6 +98,9 @@ cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const Axi
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xphi2(cudaStream_t st, const GridDesc& g, const AxisPlan& px, int LR, const Ctl* ctl,
                                     const C* A, const C* B, C* phi, int* status, Real kfx, const C* tw) {
+    if (launch_xphi_tma<Real, N, 2>(st, g, LR, ctl, A, B, static_cast<C*>(nullptr), phi, static_cast<float*>(nullptr),
+                                    status, kfx, tw))
+        return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     dftk::k_xphi<Real, N, 2><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 10 * LR), st>>>(
         g, px, LR, ctl, A, B, nullptr, phi, nullptr, status, nullptr, kfx, tw);

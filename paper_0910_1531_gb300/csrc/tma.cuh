@@ -60,6 +60,14 @@ __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x
         : "memory");
 }
 
+// 1D bulk copy global -> shared of `bytes` (a multiple of 16; both addresses 16-byte aligned);
+// completes `bar`'s transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 3D tiled store shared -> global (elements outside the tensor are not written).
 __device__ __forceinline__ void store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"

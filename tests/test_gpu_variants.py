@@ -1,7 +1,8 @@
 """Every transform variant the autotuner can choose computes the same G as the oracle.
 
-The x passes run either as the compile-time kernels or as the run-time ones under each candidate
-radix order (default, reversed, all-8 and all-4 plans); the y pass as the persistent TMA kernel or
+The x passes run either as the compile-time kernels (the Phi' passes one CTA per row block or
+persistent with bulk-copy prefetch) or as the run-time ones under each candidate radix order
+(default, reversed, all-8 and all-4 plans); the y pass as the persistent TMA kernel or
 the run-time column kernel; the z passes as the persistent TMA kernels or the grouped
 one-tile-per-CTA ones.  Each combination is pinned with dft_set_variants and checked against the
 oracle's G (FP32 1e-5, FP64 1e-10), and one line-search step under a run-time x variant against
@@ -71,25 +72,39 @@ def test_every_variant_matches_oracle(precision, shape):
     xs = _x_variants(plan)
     assert len(xs) >= 3, xs            # compile-time and at least two radix orders
     for x in xs:
-        for y in (0, 1):
-            for z in (0, 1):
-                plan.set_variants(x, y, z)
-                g, _ = plan.picard_map(_dev(rho, plan), _dev(V, plan))
-                assert relerr(g.double().cpu().numpy(), g_ref) < TOL[precision], (x, y, z, plan.tuning())
+        for xp in ((0, 1) if x == 0 else (0,)):
+            for y in (0, 1):
+                for z in (0, 1):
+                    plan.set_variants(x, y, z, x_persistent=xp)
+                    g, _ = plan.picard_map(_dev(rho, plan), _dev(V, plan))
+                    assert relerr(g.double().cpu().numpy(), g_ref) < TOL[precision], (x, xp, y, z, plan.tuning())
     plan.close()
 
 
-def test_line_search_step_under_run_time_variants_fp64():
+@pytest.mark.parametrize("which", ["run-time", "persistent"])
+def test_line_search_steps_under_variants_fp64(which):
+    # three line-search iterations (paired samples, accepted point with its materialised
+    # weighted densities) against the oracle's
     from paper_0910_1531_gb300 import binding
     shape = (32, 64, 128)
     prob, rho, V = _case(shape, (0.05, 0.06, 0.07), seed=43)
-    rho_ref, _ = P.picard_step(prob, rho, V)
+    ref = rho
+    g = F.picard_map(prob, ref, V)
+    a_prev = None
+    for _ in range(3):
+        ref, info = P.picard_step(prob, ref, V, g0=g, alpha_prev=a_prev)
+        a_prev = info["alpha"]
+        g = F.picard_map(prob, ref, V)
     plan = binding.Plan(shape, prob.h, *SPECIES, precision="fp64")
-    xs = _x_variants(plan)
-    plan.set_variants(xs[-1], 1, 1)
-    r = _dev(rho, plan)
-    plan.picard_step(r, _dev(V, plan), -1.0)
-    assert relerr(r.cpu().numpy(), rho_ref) < 1e-10, plan.tuning()
+    if which == "run-time":
+        plan.set_variants(_x_variants(plan)[-1], 1, 1)
+    else:
+        plan.set_variants(0, 0, 0, x_persistent=1)
+    r, Vd = _dev(rho, plan), _dev(V, plan)
+    plan.iter_begin(r, Vd)
+    for _ in range(3):
+        plan.iter_step(r, Vd, -1.0)
+    assert relerr(r.cpu().numpy(), ref) < 1e-10, plan.tuning()
     plan.close()
 
 
