@@ -36,16 +36,19 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
 
-# DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of the
-# profiled iterations (ncu --nvtx --nvtx-include 'profiled_steps/' --metrics
-# gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none on
-# this script with --no-cpu-baseline --no-cufft --steps 3 (2 at 256^3) --warmup 3 --e2e-steps 1),
-# per workload and precision; valid while the kernel sources hash to `digest`.
+# DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of one
+# profiled iteration, from one capture per kernel kind (1-pass metrics):
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       --nvtx --nvtx-include 'profiled_steps/' -k regex:^<kernel>$ -c <launches per iteration> --csv
+#       python bench.py [--workload pore256 --converge-tol 0] --no-extra --no-cpu-baseline --no-cufft
+#       --steps 2 --warmup 3 --e2e-steps 1
+# per workload and precision (the pore's "xupdate" kind includes its fixed-number normalisation
+# pass); valid while the kernel sources and build flags hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "1c8fd09fa52e5a18",
+    "digest": "0c633dfdcf07a740",
     "captures": {
-        "3species_16obstacles_128^3/fp32": {"xfwd": 25332224, "yfft": 61262432, "zconv_fwd": 75963819, "xinv": 8708011, "finalize": 43264, "xphi": 213977401, "zconv_bwd": 136580324, "xupdate": 102697415},
-        "3species_16obstacles_256^3/fp32": {"xfwd": 359503616, "yfft": 758558208, "zconv_fwd": 1004156800, "xinv": 68238208, "finalize": 106688, "xphi": 2018111189, "zconv_bwd": 1273750784, "xupdate": 926792789},
+        "3species_16obstacles_128^3/fp32": {"xfwd": 25350400, "yfft": 78602934, "zconv_fwd": 79972608, "xphi": 261247488, "zconv_bwd": 137554346, "xupdate": 150797952, "xinv": 8713984, "finalize": 75093},
+        "pore_slab_4species_256^3/fp32": {"xfwd": 499722240, "yfft": 875819520, "zconv_fwd": 1155539200, "xphi": 2413544192, "zconv_bwd": 1682457088, "xupdate": 1152287616, "xinv": 68663552, "finalize": 101205},
     },
 }
 
