@@ -250,9 +250,9 @@ def test_profile_counts_launches():
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_autotune_keeps_results(precision):
-    # the x-pass rows per block change only the partition of the rows among blocks: G is
-    # bitwise unchanged, the residual only by the grouping of its partial sums (per-thread
-    # compensated FP32 partials in the FP32 form: a few ulp of FP32)
+    # the autotuner changes the partition of the rows among blocks (G bitwise unchanged) and may
+    # pick other transform kernels (the same arithmetic in another order: G within rounding,
+    # a tenth of the parity tolerance), the residual only by the grouping of its sums
     prob, rho, V = make_case((32, 32, 32), 0.1, 3, seed=11)
     plan = plan_for(prob, precision)
     rd, Vd = to_dev(rho, plan), to_dev(V, plan)
@@ -262,8 +262,8 @@ def test_autotune_keeps_results(precision):
     assert set(lines) == {"xfwd", "xphi", "xupdate"}
     assert all(v in (1, 2, 3, 4, 6, 8, 11, 16) for v in lines.values())
     g1, r1 = plan.picard_map(rd, Vd)
-    assert torch.equal(g0, g1)
-    assert abs(r1 - r0) <= (1e-6 if precision == "fp32" else 1e-12) * abs(r0)
+    assert relerr(g1.cpu().numpy(), g0.cpu().numpy()) < 0.1 * TOL[precision], plan.tuning()
+    assert abs(r1 - r0) <= (1e-6 if precision == "fp32" else 1e-11) * abs(r0)
     # a second plan of the same shape takes the cached choice
     plan2 = plan_for(prob, precision)
     assert plan2.autotune(rd, Vd, reps=2) == lines
