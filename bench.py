@@ -567,7 +567,7 @@ def kernel_table(prof, peak):
     return out
 
 
-def dominant_roofline(prof, w, precision):
+def dominant_roofline(prof, w, precision, steps=None):
     """Roofline of the kernel with the largest share of device time: algorithmic bytes per launch
     over its live event time against the measured HBM copy bandwidth (FP32), or its transform
     flops against the FP64 arithmetic peak (the plain-FP64 form is FP64-pipe bound)."""
@@ -584,14 +584,19 @@ def dominant_roofline(prof, w, precision):
         # roofline is arithmetic.  Algorithmic flops of the x pass: ten real rows per grid row,
         # i.e. five complex nx-point transforms each way, at 5 nx log2(nx) flops each (the
         # pointwise Phi' and mixing work is not counted: a lower bound of the achieved rate)
+        # (a paired-sample launch transforms both samples' rows: twice the flops; of the n_l
+        # launches of `steps` iterations, steps are single and the rest paired)
         nz_, ny_, nx_ = w.shape
         flops = 2 * 5 * ny_ * nz_ * 5.0 * nx_ * math.log2(nx_)
+        paired = max(n_l - steps, 0) if steps else 0
+        flops = flops * (n_l + paired) / max(n_l, 1)     # per launch, averaged
         t_launch = t_ms * 1e-3 / max(n_l, 1)
         achieved_tf = flops / t_launch / 1e12 if t_launch > 0 else 0.0
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tf / FP64_TFLOPS, "traffic": None, "kernel": dom,
                     "peak_source": "nominal FP64: 152 SMs x 4 FP64 flop/clock x 2.07 GHz (not measured)",
-                    "flop_model": "5 nx log2(nx) per complex x transform, 10 per grid row",
+                    "flop_model": "5 nx log2(nx) per complex x transform, 10 per grid row (20 in a "
+                                  "paired-sample launch), averaged over the launches",
                     "flops_per_launch": flops, "ms_per_launch": t_ms / max(n_l, 1),
                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
     return roofline
@@ -641,7 +646,7 @@ def fp64_record(args, w, stream, world):
     prof, _ = profile_iterations(plan, rho, V, -1.0, steps, stream)
     peak, _ = measured_peaks()
     rec = {"value": job_throughput(steps, world, ms), "unit": UNIT, "dtype": "f64", "steps": steps,
-           "ms_per_step": ms / steps, "autotuned": tuning, "roofline": dominant_roofline(prof, w, "fp64"),
+           "ms_per_step": ms / steps, "autotuned": tuning, "roofline": dominant_roofline(prof, w, "fp64", steps),
            "kernels": kernel_table(prof, peak),
            "convergence": picard_to_tolerance(plan, rho0, V, -1.0, 1e-8, 400)}
     plan.close()
@@ -767,7 +772,7 @@ def run_ours(args):
             convergence = picard_to_tolerance(plan, rho0, V, alpha, args.converge_tol, args.converge_max)
 
     peak, _ = measured_peaks()
-    roofline = dominant_roofline(prof, w, args.precision)
+    roofline = dominant_roofline(prof, w, args.precision, args.steps)
     kernels = kernel_table(prof, peak)
     launches = sum(prof[k][0] for k in KERNELS)
 
