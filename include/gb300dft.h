@@ -325,6 +325,20 @@ dft_status dft_batch_iterate(dft_batch* batch, int iters, double alpha_or_neg, d
 dft_status dft_set_wait_polls(dft_plan* plan, long long polls);
 
 /*
+ * Programmatic dependent launch of the plan's passes (no counterpart in the paper; a GPU
+ * scheduling option).  Enabled by default: each pass is launched with CUDA's programmatic
+ * stream serialization attribute, so that its launch overlaps the completion of the previous
+ * kernel in the stream; every pass waits (griddepcontrol.wait) for the kernels before it to
+ * complete before it reads or writes data they touch, so results are the same either way
+ * (bitwise).  enable = 0 launches
+ * the passes in plain stream order.  Per-kernel profiling (dft_profile_enable) launches in
+ * stream order while it is on.  A runtime that cannot capture such launches into the iteration
+ * graph of dft_iter_run / dft_batch_iterate gets the graph in stream order instead.  Applies to
+ * later calls (a cached iteration graph is dropped and recaptured).
+ */
+dft_status dft_set_dependent_launch(dft_plan* plan, int enable);
+
+/*
  * Per-kernel timing with CUDA events recorded on the plan's stream around
  * each launch.  enable != 0 starts collection (and clears totals).
  * dft_profile_read returns, for the kernel kind named by `name`, the number

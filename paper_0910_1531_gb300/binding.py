@@ -81,6 +81,7 @@ SIGNATURES = {
     "dft_batch_begin": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "dft_batch_iterate": (_I, [_P, _I, _D, _PD]),
     "dft_set_wait_polls": (_I, [_P, ctypes.c_longlong]),
+    "dft_set_dependent_launch": (_I, [_P, _I]),
     "dft_plan_tuning": (ctypes.c_char_p, [_P]),
     "dft_set_variants": (_I, [_P, _I, _I, _I, _I]),
     "dft_profile_enable": (_I, [_P, _I]),
@@ -302,6 +303,10 @@ class Plan:
     def set_wait_polls(self, polls=None):
         """Bound of the y passes' TMA tile waits (None: the default); 0 makes them give up at once."""
         self._check(self.lib.dft_set_wait_polls(self.handle, WAIT_POLLS_DEFAULT if polls is None else int(polls)))
+
+    def set_dependent_launch(self, enable=True):
+        """Programmatic dependent launch of the passes (default on; see dft_set_dependent_launch)."""
+        self._check(self.lib.dft_set_dependent_launch(self.handle, 1 if enable else 0))
 
     def profile_enable(self, enable=True):
         self._check(self.lib.dft_profile_enable(self.handle, 1 if enable else 0))

@@ -96,6 +96,7 @@ struct dft_plan {
     const void* iter_rho = nullptr;
     const void* iter_V = nullptr;
     long long wait_polls = DFT_WAIT_POLLS;   // bound of the y passes' TMA tile waits
+    bool pdl_on = true;             // programmatic dependent launch of the passes (off while profiling)
 
     long long blocks_x(int LR) const { return ceil_div((long long)g.ny * g.nz, LR); }
 };
@@ -308,7 +309,7 @@ template <typename Real> struct Ops {
             LAUNCH(p, K_XUPD, p->ncanon * (CB(p) + RB(p)),
                    P::xcanon(p->stream, p->g, p->ax, sp, p->LRupd, T1(p), V, p->red_canon, tw(p, 0)));
             LAUNCH(p, K_FIN, p->blocks_x(p->LRupd) * DFT_MAXS * 8.0,
-                   P::canon_scale(p->stream, p->ctl, sp, p->red_canon, (int)p->blocks_x(p->LRupd)));
+                   P::canon_scale(p->stream, p->ctl, sp, p->red_canon, (int)p->blocks_x(p->LRupd), p->g.pdl));
         }
         LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0) +
                                             (rho_lo ? (rho_out ? 2 : 1) : 0))),
@@ -370,7 +371,7 @@ dft_status finalize(dft_plan* p, int op, int nsum, int nmax, double alpha_fixed,
     const double inv_count = 1.0 / (double(p->S) * double(p->g.n));
     LAUNCH(p, K_FIN, (pair ? 2 : 1) * nsum * 8.0 + nmax * 4.0,
            launch_finalize(p->stream, p->ctl, p->red_sum, pair ? p->red_sum2 : nullptr, nsum, p->red_max, nmax, op,
-                           inv_count, alpha_fixed, kN3Bound, kAlphaFloor));
+                           inv_count, alpha_fixed, kN3Bound, kAlphaFloor, p->g.pdl));
     return DFT_OK;
 }
 
@@ -880,6 +881,7 @@ void describe_tuning(dft_plan* p) {
     t += "; z: ";
     t += dft_is_ct_size(g.nz) ? (g.zgrp ? std::string("grouped, one tile per CTA") : std::string("TMA persistent"))
                               : "run-time column kernel, " + std::to_string(p->Tz) + "-column tiles";
+    t += p->pdl_on ? "; launches: programmatic dependent" : "; launches: stream order";
     p->tuning = t;
 }
 
@@ -1192,6 +1194,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
     g.n = (long long)g.nx * g.ny * g.nz;
     g.nc = (long long)g.nz * g.ny * g.pxh;
     g.hx = prm->hx; g.hy = prm->hy; g.hz = prm->hz;
+    g.pdl = 1;
     const double two_pi = 6.28318530717958647692;
     p->kf[0] = two_pi / (g.nx * g.hx);
     p->kf[1] = two_pi / (g.ny * g.hy);
@@ -1474,9 +1477,19 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
             p->stream = p->cap;
             cudaGraph_t g = nullptr;
             dft_status st = DFT_OK;
+            const int pdl = p->g.pdl;
             cudaError_t e = build_loop_graph(p->cap, &p->ctl->loop_left, &g, &st, one_iteration);
+            if ((e != cudaSuccess || st != DFT_OK) && pdl) {
+                // a runtime that does not capture programmatic edges: the iteration in stream order
+                p->g.pdl = 0;
+                st = DFT_OK;
+                e = build_loop_graph(p->cap, &p->ctl->loop_left, &g, &st, one_iteration);
+            }
             p->stream = user;
-            if (st != DFT_OK) return st;
+            if (st != DFT_OK) {
+                p->g.pdl = pdl;
+                return st;
+            }
             if (e == cudaSuccess) {
                 p->iloop = true;
             } else {
@@ -1484,11 +1497,13 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
                 e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
                 if (e != cudaSuccess) {
                     p->stream = user;
+                    p->g.pdl = pdl;
                     return fail(p, DFT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
                 }
                 st = one_iteration();
                 e = cudaStreamEndCapture(p->cap, &g);
                 p->stream = user;
+                p->g.pdl = pdl;
                 if (st != DFT_OK) {
                     if (g) cudaGraphDestroy(g);
                     return st;
@@ -1496,6 +1511,7 @@ dft_status dft_iter_run(dft_plan* p, void* rho, const void* V, int iters, double
                 if (e != cudaSuccess) return fail(p, DFT_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
                 p->iloop = false;
             }
+            p->g.pdl = pdl;
             p->igraph = g;
             e = cudaGraphInstantiate(&p->iexec, p->igraph, 0);
             if (e != cudaSuccess) {
@@ -1795,6 +1811,19 @@ dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, doubl
         cudaGraph_t g = nullptr;
         dft_status st = DFT_OK;
         cudaError_t e = build_loop_graph(b->main, left, &g, &st, one_iteration);
+        if (e != cudaSuccess || st != DFT_OK) {
+            // a runtime that does not capture programmatic edges: the states' passes in stream order
+            bool any = false;
+            for (dft_plan* q : b->plans) {
+                any = any || q->g.pdl;
+                q->g.pdl = 0;
+                q->pdl_on = false;
+            }
+            if (any) {
+                st = DFT_OK;
+                e = build_loop_graph(b->main, left, &g, &st, one_iteration);
+            }
+        }
         if (st != DFT_OK) return st;
         b->loop = e == cudaSuccess;
         if (!b->loop) {
@@ -1839,6 +1868,16 @@ dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, doubl
     return DFT_OK;
 }
 
+dft_status dft_set_dependent_launch(dft_plan* p, int enable) {
+    TRY(check_plan(p));
+    // a captured iteration holds the launch attributes it was captured with
+    release_iter_graph(p);
+    p->pdl_on = enable != 0;
+    p->g.pdl = (p->pdl_on && !p->prof) ? 1 : 0;
+    describe_tuning(p);
+    return DFT_OK;
+}
+
 dft_status dft_set_wait_polls(dft_plan* p, long long polls) {
     TRY(check_plan(p));
     if (polls < 0) return fail(p, DFT_EINVAL, "polls must be >= 0");
@@ -1879,6 +1918,8 @@ dft_status dft_profile_enable(dft_plan* p, int enable) {
         p->prof_bytes[k] = 0.0;
     }
     p->prof = enable != 0;
+    // per-pass event timing: each pass starts after the previous one has completed
+    p->g.pdl = (p->pdl_on && !p->prof) ? 1 : 0;
     return DFT_OK;
 }
 

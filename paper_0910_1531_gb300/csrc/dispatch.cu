@@ -52,9 +52,8 @@ cudaError_t Passes<Real>::xcanon(cudaStream_t st, const GridDesc& g, const AxisP
 
 template <typename Real>
 cudaError_t Passes<Real>::canon_scale(cudaStream_t st, Ctl* ctl, const SpeciesDesc<Real>& sp, const double* red,
-                                      int nblocks) {
-    dftk::k_canon_scale<Real><<<1, dftk::kThreads, 0, st>>>(ctl, sp, red, nblocks);
-    return cudaSuccess;
+                                      int nblocks, int pdl) {
+    return launch_k(dftk::k_canon_scale<Real>, 1, dftk::kThreads, 0, st, pdl, ctl, sp, red, nblocks);
 }
 
 template <typename Real>
@@ -157,15 +156,12 @@ template struct Passes<double>;
 
 cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, const double* red_sum2, int nsum,
                             const float* red_max, int nmax, int op, double inv_count, double alpha_fixed,
-                            double n3_bound, double alpha_floor) {
+                            double n3_bound, double alpha_floor, int pdl) {
     if ((red_sum2 ? 2 : 1) * nsum + nmax > 8 * dftk::kFinThreadsSmall)
-        dftk::k_finalize<dftk::kFinThreads><<<1, dftk::kFinThreads, 0, st>>>(ctl, red_sum, red_sum2, nsum, red_max,
-                                                                           nmax, op, inv_count, alpha_fixed,
-                                                                           n3_bound, alpha_floor);
-    else
-        dftk::k_finalize<dftk::kFinThreadsSmall><<<1, dftk::kFinThreadsSmall, 0, st>>>(
-            ctl, red_sum, red_sum2, nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
-    return cudaSuccess;
+        return launch_k(dftk::k_finalize<dftk::kFinThreads>, 1, dftk::kFinThreads, 0, st, pdl, ctl, red_sum, red_sum2,
+                        nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
+    return launch_k(dftk::k_finalize<dftk::kFinThreadsSmall>, 1, dftk::kFinThreadsSmall, 0, st, pdl, ctl, red_sum,
+                    red_sum2, nsum, red_max, nmax, op, inv_count, alpha_fixed, n3_bound, alpha_floor);
 }
 
 // ------------------------------------------------------------------------------------

@@ -248,6 +248,8 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GridDesc g, AxisPlan px, int 
                                                    const Real* __restrict__ in,
                                                    typename Cplx<Real>::type* __restrict__ out,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
@@ -301,6 +303,8 @@ template <typename Real, bool INV, int NY, int TY>
 __global__ void __launch_bounds__(kThreads) k_yfft(GridDesc g, AxisPlan py, int Trt,
                                                    typename Cplx<Real>::type* __restrict__ data,
                                                    const typename Cplx<Real>::type* __restrict__ twy) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     const int ny = NY > 0 ? NY : g.ny, nxh = g.nxh, pxh = g.pxh;
@@ -341,6 +345,8 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
                                                        int ntiles, int* __restrict__ status,
                                                        const typename Cplx<Real>::type* __restrict__ twy,
                                                        long long polls) {
+    dep_launch();
+    dep_wait();
     static_assert(NY > 0 && NY <= 256 && TY > 0, "compile-time TMA y pass");
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
@@ -473,6 +479,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
                                                         typename Cplx<Real>::type* __restrict__ slot_es,
                                                         double* __restrict__ red_energy,
                                                         const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
@@ -765,6 +773,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
                                                              typename Cplx<Real>::type* __restrict__ slot_es,
                                                              double* __restrict__ red_energy,
                                                              const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
@@ -909,6 +919,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
                                                              const typename Cplx<Real>::type* esB,
                                                              typename Cplx<Real>::type* es_mat,
                                                              const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     constexpr int TILE = TZ * NZ;
     constexpr int GS = ct_gstride(NZ, TZ, int(sizeof(C)));
@@ -1034,6 +1046,8 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                                                                          int ntiles_x, int ntiles,
                                                                          int* __restrict__ status,
                                                                          const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
     constexpr int TILE = TZ * NZ;
@@ -1238,6 +1252,8 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
                                                             typename Cplx<Real>::type* es_mat, int ntiles_x,
                                                             int ntiles, int* __restrict__ status,
                                                             const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     constexpr int E = int(sizeof(C) / 8);
     constexpr int TILE = TZ * NZ;
@@ -1807,6 +1823,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
                                                    float* __restrict__ red_max, int* __restrict__ status,
                                                    double* __restrict__ red_phi, Real kfx,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
@@ -1890,6 +1908,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi_tma(GridDesc g, int LR, const
                                                        typename Cplx<Real>::type* __restrict__ phi_out,
                                                        float* __restrict__ red_max, int* __restrict__ status,
                                                        Real kfx, const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     static_assert(NX > 0, "compile-time lengths only");
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -2015,6 +2035,8 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
                                                         const typename Cplx<Real>::type* esB,
                                                         typename Cplx<Real>::type* es_mat,
                                                         const typename Cplx<Real>::type* __restrict__ twz) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     const int nz = NZ > 0 ? NZ : g.nz, ny = g.ny, nxh = g.nxh, S = sp.S;
@@ -2114,6 +2136,8 @@ __global__ void __launch_bounds__(kThreads) k_xcanon(GridDesc g, AxisPlan px, Sp
                                                      const typename Cplx<Real>::type* __restrict__ cspec,
                                                      const Real* __restrict__ V, double* __restrict__ red,
                                                      const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
@@ -2187,6 +2211,8 @@ __global__ void __launch_bounds__(kThreads) k_xcanon(GridDesc g, AxisPlan px, Sp
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) k_canon_scale(Ctl* ctl, SpeciesDesc<Real> sp, const double* __restrict__ red,
                                                           int nblocks) {
+    dep_launch();
+    dep_wait();
     __shared__ double scratch_d[32];
     for (int s = 0; s < sp.S; ++s) {
         if (!sp.canon[s]) continue;
@@ -2221,6 +2247,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                                                       Real* rho_lo, double* __restrict__ red_sum,
                                                       double* __restrict__ red_sum2, int* __restrict__ status,
                                                       const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
@@ -2416,6 +2444,8 @@ __global__ void __launch_bounds__(kThreads) k_xgrad(GridDesc g, AxisPlan px, Spe
                                                     Real* __restrict__ grad_rho, Real* __restrict__ grad_V,
                                                     double* __restrict__ red,
                                                     const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double scratch_d[32];
@@ -2472,6 +2502,8 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
                                                    Offsets<Real> off, int cmax,
                                                    float* __restrict__ red_max, int wd, Real kfx,
                                                    const typename Cplx<Real>::type* __restrict__ twx) {
+    dep_launch();
+    dep_wait();
     using C = typename Cplx<Real>::type;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float scratch_f[32];
@@ -2549,6 +2581,8 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
                                                           const float* __restrict__ red_max, int nmax, int op,
                                                           double inv_count, double alpha_fixed, double n3_bound,
                                                           double alpha_floor) {
+    dep_launch();
+    dep_wait();
     __shared__ double scratch_d[32];
     __shared__ float scratch_f[32];
     const double s = partial_sum<B>(red_sum, nsum);

@@ -48,7 +48,7 @@ cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const Axi
                             const Real* in, C* out, const C* tw) {
     const long long rows = (long long)ncomp * g.ny * g.nz;
     const unsigned blocks = (unsigned)ceil_div((rows + 1) / 2, lx);
-    dftk::k_xfwd<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lx), st>>>(g, px, ncomp, lx, in, out, tw);
+    launch_k(dftk::k_xfwd<Real, N>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lx), st, g.pdl, g, px, ncomp, lx, in, out, tw);
     return cudaSuccess;
 }
 
@@ -76,7 +76,7 @@ bool launch_xphi_tma(cudaStream_t st, const GridDesc& g, int LR, const Ctl* ctl,
         if (occ < 1) occ = 1;
         const long long nblk = ceil_div((long long)g.ny * g.nz, LR);
         const int grid = (int)(nblk < (long long)sms * occ ? nblk : (long long)sms * occ);
-        dftk::k_xphi_tma<Real, N, NM><<<grid, dftk::kThreads, sm, st>>>(g, LR, ctl, A, B, mat, phi, red_max, status,
+        launch_k(dftk::k_xphi_tma<Real, N, NM>, grid, dftk::kThreads, sm, st, g.pdl, g, LR, ctl, A, B, mat, phi, red_max, status,
                                                                       kfx, tw);
         return true;
     }
@@ -90,8 +90,8 @@ cudaError_t LaunchX<Real, N>::xphi(cudaStream_t st, const GridDesc& g, const Axi
     if (!red_phi && launch_xphi_tma<Real, N, 1>(st, g, LR, ctl, A, B, mat, phi, red_max, status, kfx, tw))
         return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    dftk::k_xphi<Real, N, 1><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st>>>(g, px, LR, ctl, A, B, mat, phi,
-                                                                                    red_max, status, red_phi, kfx, tw);
+    launch_k(dftk::k_xphi<Real, N, 1>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 5 * LR), st, g.pdl, g, px, LR, ctl,
+             A, B, mat, phi, red_max, status, red_phi, kfx, tw);
     return cudaSuccess;
 }
 
@@ -102,7 +102,7 @@ cudaError_t LaunchX<Real, N>::xphi2(cudaStream_t st, const GridDesc& g, const Ax
                                     status, kfx, tw))
         return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    dftk::k_xphi<Real, N, 2><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 10 * LR), st>>>(
+    launch_k(dftk::k_xphi<Real, N, 2>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 10 * LR), st, g.pdl,
         g, px, LR, ctl, A, B, nullptr, phi, nullptr, status, nullptr, kfx, tw);
     return cudaSuccess;
 }
@@ -114,7 +114,7 @@ cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const 
                                int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
-    dftk::k_xupdate<Real, N, 1><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
+    launch_k(dftk::k_xupdate<Real, N, 1>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st, g.pdl,
         g, px, sp, LR, ctl, cspec, nullptr, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, nullptr, status, tw);
     return cudaSuccess;
 }
@@ -126,7 +126,7 @@ cudaError_t LaunchX<Real, N>::xupdate2(cudaStream_t st, const GridDesc& g, const
                                        Real* rho_lo, double* red_sum, double* red_sum2, int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
-    dftk::k_xupdate<Real, N, 2><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 2 * lpr * LR), st>>>(
+    launch_k(dftk::k_xupdate<Real, N, 2>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 2 * lpr * LR), st, g.pdl,
         g, px, sp, LR, ctl, cspec, cspec2, rho0, rho1, V, nullptr, nullptr, rho_lo, red_sum, red_sum2, status, tw);
     return cudaSuccess;
 }
@@ -139,7 +139,7 @@ cudaError_t LaunchX<Real, N>::xinv(cudaStream_t st, const GridDesc& g, const Axi
     // one component and no outputs: the kernel pairs grid rows in its lines
     const bool rows2 = ncomp == 1 && !wd && !out && !out_last;
     const int lines = rows2 ? (LR + 1) / 2 : (ncomp + 1) / 2 * LR;
-    dftk::k_xinv<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lines), st>>>(
+    launch_k(dftk::k_xinv<Real, N>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lines), st, g.pdl,
         g, px, LR, ncomp, spec, out, out_last, off, cmax, red_max, wd, kfx, tw);
     return cudaSuccess;
 }
@@ -150,7 +150,7 @@ cudaError_t LaunchX<Real, N>::xgrad(cudaStream_t st, const GridDesc& g, const Ax
                                     const Real* V, Real* grad_rho, Real* grad_V, double* red, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
-    dftk::k_xgrad<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st>>>(
+    launch_k(dftk::k_xgrad<Real, N>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st, g.pdl,
         g, px, sp, LR, dv, cspec, rho, V, grad_rho, grad_V, red, tw);
     return cudaSuccess;
 }
@@ -171,7 +171,7 @@ cudaError_t LaunchX<Real, N>::xcanon(cudaStream_t st, const GridDesc& g, const A
     const int nl = canon_lines(sp, lines);
     if (nl == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
-    dftk::k_xcanon<Real, N><<<blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, nl * LR), st>>>(
+    launch_k(dftk::k_xcanon<Real, N>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, nl * LR), st, g.pdl,
         g, px, sp, LR, nl, lines[0], lines[1], lines[2], cspec, V, red, tw);
     return cudaSuccess;
 }
@@ -218,14 +218,14 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
             if (occ < 1) occ = 1;
         }
         const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-        if (inv) dftk::k_yfft_tma<Real, true, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw, polls);
-        else dftk::k_yfft_tma<Real, false, N, TY><<<grid, dftk::kThreads, sm, st>>>(map, ntx, ntiles, status, tw, polls);
+        if (inv) launch_k(dftk::k_yfft_tma<Real, true, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls);
+        else launch_k(dftk::k_yfft_tma<Real, false, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls);
         return cudaSuccess;
     } else {
         dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.nz, (unsigned)ncomp);
         const size_t sm = smem_col_of<C>(g.ny, T, 2);
-        if (inv) dftk::k_yfft<Real, true, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
-        else dftk::k_yfft<Real, false, 0, 0><<<grid, dftk::kThreads, sm, st>>>(g, py, T, data, tw);
+        if (inv) launch_k(dftk::k_yfft<Real, true, 0, 0>, grid, dftk::kThreads, sm, st, g.pdl, g, py, T, data, tw);
+        else launch_k(dftk::k_yfft<Real, false, 0, 0>, grid, dftk::kThreads, sm, st, g.pdl, g, py, T, data, tw);
         (void)status;
         (void)polls;
         return cudaSuccess;
@@ -292,7 +292,7 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB>, NT, sm);
             if (occ < 1) occ = 1;
             const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-            dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB><<<grid, NT, sm, st>>>(map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
+            launch_k(dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB>, grid, NT, sm, st, g.pdl, map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
                                                                          slot_es, ntx, ntiles, status, tw);
             return cudaSuccess;
         }
@@ -301,19 +301,19 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
         const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
         dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
         if (red_energy)
-            dftk::k_zconv_fwd_g<Real, N, TZ, true><<<grid, dftk::kThreads, sm, st>>>(
+            launch_k(dftk::k_zconv_fwd_g<Real, N, TZ, true>, grid, dftk::kThreads, sm, st, g.pdl,
                 g, sp, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
         else
-            dftk::k_zconv_fwd_g<Real, N, TZ, false><<<grid, dftk::kThreads, sm, st>>>(
+            launch_k(dftk::k_zconv_fwd_g<Real, N, TZ, false>, grid, dftk::kThreads, sm, st, g.pdl,
                 g, sp, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, nullptr, tw);
     } else {
         dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.ny);
         const size_t sm = smem_col_of<C>(g.nz, T, 7);
         if (red_energy)
-            dftk::k_zconv_fwd<Real, 0, 0, true><<<grid, dftk::kThreads, sm, st>>>(
+            launch_k(dftk::k_zconv_fwd<Real, 0, 0, true>, grid, dftk::kThreads, sm, st, g.pdl,
                 g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, red_energy, tw);
         else
-            dftk::k_zconv_fwd<Real, 0, 0, false><<<grid, dftk::kThreads, sm, st>>>(
+            launch_k(dftk::k_zconv_fwd<Real, 0, 0, false>, grid, dftk::kThreads, sm, st, g.pdl,
                 g, pz, sp, T, kfx, kfy, kfz, want_psi, in, slot_n, slot_es, nullptr, tw);
     }
     return cudaSuccess;
@@ -364,7 +364,7 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
             const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
             // the status word of the device control block records a TMA wait that ran out
             int* status = const_cast<int*>(&ctl->status);
-            dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB><<<grid, NT, sm, st>>>(
+            launch_k(dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, grid, NT, sm, st, g.pdl,
                 map_phi, map_esA, map_esB, g, sp, kfx, kfy, kfz, flags, ncomp_out, esB ? 1 : 0, ctl, es_mat, ntx, ntiles,
                 status, tw);
             return cudaSuccess;
@@ -373,11 +373,11 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
     if constexpr (N > 0) {
         const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
         dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
-        dftk::k_zconv_bwd_g<Real, N, TZ><<<grid, dftk::kThreads, sm, st>>>(
+        launch_k(dftk::k_zconv_bwd_g<Real, N, TZ>, grid, dftk::kThreads, sm, st, g.pdl,
             g, sp, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
     } else {
         dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.ny);
-        dftk::k_zconv_bwd<Real, 0, 0><<<grid, dftk::kThreads, smem_col_of<C>(g.nz, T, 7), st>>>(
+        launch_k(dftk::k_zconv_bwd<Real, 0, 0>, grid, dftk::kThreads, smem_col_of<C>(g.nz, T, 7), st, g.pdl,
             g, pz, sp, T, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
     }
     return cudaSuccess;

@@ -193,16 +193,17 @@ struct Passes {
     static cudaError_t xcanon(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                               int LR, const C* cspec, const Real* V, double* red, const C* tw);
     static cudaError_t canon_scale(cudaStream_t st, Ctl* ctl, const SpeciesDesc<Real>& sp, const double* red,
-                                   int nblocks);
+                                   int nblocks, int pdl);
     // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
     // number kf of a cubic box
     static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
 };
 
 // ctl: the plan's three control blocks (iteration, sample 1 weights, sample 2 weights);
-// red_sum2 (or nullptr): the second sample's partial sums for FIN_F12_CHOOSE
+// red_sum2 (or nullptr): the second sample's partial sums for FIN_F12_CHOOSE; pdl: launch with
+// programmatic dependent launch (GridDesc::pdl)
 cudaError_t launch_finalize(cudaStream_t st, Ctl* ctl, const double* red_sum, const double* red_sum2, int nsum,
                             const float* red_max, int nmax, int op, double inv_count, double alpha_fixed,
-                            double n3_bound, double alpha_floor);
+                            double n3_bound, double alpha_floor, int pdl);
 
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }

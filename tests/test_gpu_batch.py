@@ -96,3 +96,30 @@ def test_iter_run_graph_matches_iter_step(precision, alpha):
     assert torch.equal(ref, got)
     assert r_ref == r_got and np.isfinite(r_got)
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_dependent_launch_is_bitwise_neutral(precision):
+    # programmatic dependent launch only lets a pass become resident while the previous one
+    # finishes; each pass waits for the kernels before it, so the iterates with and without it
+    # agree bit for bit (eager steps, then the captured on-device loop; the 64^3 obstacle
+    # geometry runs the compile-time persistent TMA passes over many waves)
+    from paper_0910_1531_gb300 import binding
+    w = workloads.obstacles_3species(n=64, h=0.1)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    outs = []
+    for pdl in (False, True):
+        plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=precision)
+        plan.set_dependent_launch(pdl)
+        assert ("programmatic dependent" in plan.tuning()) == pdl, plan.tuning()
+        r = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=dt, device="cuda")
+        V = torch.tensor(w.V, dtype=dt, device="cuda")
+        plan.iter_begin(r, V)
+        for _ in range(2):
+            plan.iter_step(r, V, -1.0, sync=False)
+        resid = plan.iter_run(r, V, 3)
+        torch.cuda.synchronize()
+        outs.append((r, resid))
+        plan.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and np.isfinite(outs[1][1])
