@@ -225,7 +225,8 @@ dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iter
  *    densities; the Phi' pass and its paired-sample form; the update pass and its paired form,
  *    over candidates 1..16; the n3-maximum pass of the line search over 8..64);
  *  - the Phi' x passes: one CTA per row block, or persistent CTAs whose row blocks arrive by
- *    bulk copies two blocks ahead (with their own rows per block);
+ *    bulk copies two blocks ahead, or by per-thread cp.async copies one block ahead (each with
+ *    its own rows per block);
  *  - the x transform: the compile-time kernels (where the length has them) against the
  *    run-time ones under each candidate radix order (the default plan -- 3s, other odd primes,
  *    16s, then 2/4/8 --, its reverse, and for powers of two a plan of 8s and one of 4s);
@@ -246,7 +247,8 @@ const char* dft_plan_tuning(const dft_plan* plan);
  * x_variant 0 = the compile-time x kernels (only for lengths that have them), k >= 1 = the
  * run-time ones under candidate radix order k (in dft_autotune's order; DFT_EINVAL past the
  * last); x_persistent 1 = with the compile-time kernels, the Phi' passes as the persistent
- * kernel whose row blocks arrive by bulk copies two blocks ahead (0 = one CTA per row block);
+ * kernel whose row blocks arrive by bulk copies two blocks ahead, 2 = by per-thread cp.async
+ * copies one block ahead (0 = one CTA per row block);
  * y_variant 0 = persistent TMA pass (run-time kernel for lengths without one), 1 = run-time
  * column kernel; z_variant 0 = persistent TMA passes, 1 = grouped one-tile-per-CTA kernels
  * (lengths without compile-time kernels run the run-time ones either way).  Invalidates a

@@ -80,6 +80,7 @@ struct dft_plan {
     double prof_bytes[K_COUNT] = {0};
     std::string err;
     void* ktab = nullptr;           // |k| tables of the compile-time z passes (cubic boxes)
+    void* laptab = nullptr;         // per-axis Laplacian terms of the Poisson kernel (SpeciesDesc::lap1d)
     cudaStream_t cap = nullptr;     // capture stream of the one-iteration graph (dft_iter_run)
     cudaStream_t side = nullptr;    // copy stream of dft_picard_step_host
     cudaEvent_t v_ready = nullptr;  // V staged (dft_picard_step_host)
@@ -870,7 +871,9 @@ void describe_tuning(dft_plan* p) {
     std::string t = "x: ";
     t += (!g.xrt && dft_is_ct_size(g.nx)) ? "compile-time radix " + ct_radix_text(g.nx)
                                           : "run-time radix " + radix_text(p->ax);
-    if (!g.xrt && dft_is_ct_size(g.nx) && g.xpers) t += ", persistent Phi' passes with bulk-copy prefetch";
+    if (!g.xrt && dft_is_ct_size(g.nx) && g.xpers)
+        t += g.xpers == 2 ? ", persistent Phi' passes with cp.async prefetch"
+                          : ", persistent Phi' passes with bulk-copy prefetch";
     t += "; rows per block xfwd " + std::to_string(p->LX) + ", xphi " + std::to_string(p->LRphi) + ", xupdate " +
          std::to_string(p->LRupd) + ", n3 max " + std::to_string(p->LRn3) + ", paired xphi " +
          std::to_string(p->LRphi2) + ", paired xupdate " + std::to_string(p->LRupd2);
@@ -973,28 +976,40 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     p->LRn3 = best[3];
     p->LRphi2 = best[4];
     p->LRupd2 = best[5];
-    // The persistent Phi' passes (compile-time lengths): their own rows per block, kept if the
-    // single and paired passes together are faster than the per-block kernels.
+    // The persistent Phi' passes (compile-time lengths; bulk copies, then cp.async): their own
+    // rows per block, kept if the single and paired passes together are faster than the
+    // per-block kernels and the other persistent form.
     if (dft_is_ct_size(p->g.nx)) {
-        p->g.xpers = 1;
-        int bp[2] = {p->LRphi, p->LRphi2};
-        float bpm[2] = {1e30f, 1e30f};
-        for (int L : cand) {
-            float ms = time_it([&] {
-                P::xphi(p->stream, p->g, p->ax, L, p->ctl, A, A, nullptr, O::T1(p), p->red_max, &p->ctl->status,
-                        nullptr, O::kf(p, 0), O::tw(p, 0));
-            });
-            if (ms < bpm[0]) { bpm[0] = ms; bp[0] = L; }
-            ms = time_it([&] {
-                P::xphi2(p->stream, p->g, p->ax, L, p->ctl, A, A, O::T1(p), &p->ctl->status, O::kf(p, 0), O::tw(p, 0));
-            });
-            if (ms < bpm[1]) { bpm[1] = ms; bp[1] = L; }
+        float best_sum = best_ms[1] + best_ms[4];
+        int best_pers = 0;
+        int bp_best[2] = {p->LRphi, p->LRphi2};
+        for (int pers = 1; pers <= 2; ++pers) {
+            p->g.xpers = pers;
+            int bp[2] = {p->LRphi, p->LRphi2};
+            float bpm[2] = {1e30f, 1e30f};
+            for (int L : cand) {
+                float ms = time_it([&] {
+                    P::xphi(p->stream, p->g, p->ax, L, p->ctl, A, A, nullptr, O::T1(p), p->red_max, &p->ctl->status,
+                            nullptr, O::kf(p, 0), O::tw(p, 0));
+                });
+                if (ms < bpm[0]) { bpm[0] = ms; bp[0] = L; }
+                ms = time_it([&] {
+                    P::xphi2(p->stream, p->g, p->ax, L, p->ctl, A, A, O::T1(p), &p->ctl->status, O::kf(p, 0),
+                             O::tw(p, 0));
+                });
+                if (ms < bpm[1]) { bpm[1] = ms; bp[1] = L; }
+            }
+            if (bpm[0] + bpm[1] < best_sum) {
+                best_sum = bpm[0] + bpm[1];
+                best_pers = pers;
+                bp_best[0] = bp[0];
+                bp_best[1] = bp[1];
+            }
         }
-        if (bpm[0] + bpm[1] < best_ms[1] + best_ms[4]) {
-            p->LRphi = bp[0];
-            p->LRphi2 = bp[1];
-        } else {
-            p->g.xpers = 0;
+        p->g.xpers = best_pers;
+        if (best_pers) {
+            p->LRphi = bp_best[0];
+            p->LRphi2 = bp_best[1];
         }
     }
     // Transform variants, timed on the same data with the rows per block just chosen.
@@ -1315,6 +1330,29 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
             return fail(nullptr, DFT_ECUDA, std::string("|k| tables: ") + cudaGetErrorString(te));
         }
     }
+    // The Poisson kernel's lap(k) is a sum of one term per axis: tabulated by FFT index once, with
+    // the expression the z passes would evaluate at every point.
+    {
+        const size_t nl = size_t(g.nx) + g.ny + g.nz;
+        if (cudaMalloc(&p->laptab, nl * p->rsize) != cudaSuccess) {
+            cudaGetLastError();
+            dft_plan_destroy(p);
+            return fail(nullptr, DFT_ENOMEM, "cudaMalloc failed: Laplacian table");
+        }
+        cudaError_t te;
+        if (f64) {
+            p->spd.lap1d = static_cast<const double*>(p->laptab);
+            te = Passes<double>::build_laptab(nullptr, g, p->kf[0], p->kf[1], p->kf[2], static_cast<double*>(p->laptab));
+        } else {
+            p->spf.lap1d = static_cast<const float*>(p->laptab);
+            te = Passes<float>::build_laptab(nullptr, g, float(p->kf[0]), float(p->kf[1]), float(p->kf[2]),
+                                             static_cast<float*>(p->laptab));
+        }
+        if (te != cudaSuccess) {
+            dft_plan_destroy(p);
+            return fail(nullptr, DFT_ECUDA, std::string("Laplacian table: ") + cudaGetErrorString(te));
+        }
+    }
     if (cudaMallocHost(&p->ctl_host, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
         dft_plan_destroy(p);
@@ -1348,6 +1386,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->red_max);
     cudaFree(p->grad_red);
     cudaFree(p->ktab);
+    cudaFree(p->laptab);
     cudaFree(p->red_canon);
     release_iter_graph(p);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -1891,7 +1930,7 @@ const char* dft_plan_tuning(const dft_plan* p) { return p ? p->tuning.c_str() : 
 
 dft_status dft_set_variants(dft_plan* p, int x_variant, int x_persistent, int y_variant, int z_variant) {
     TRY(check_plan(p));
-    if (x_persistent < 0 || x_persistent > 1) return fail(p, DFT_EINVAL, "x_persistent is 0 or 1");
+    if (x_persistent < 0 || x_persistent > 2) return fail(p, DFT_EINVAL, "x_persistent is 0, 1 or 2");
     const std::vector<AxisPlan> orders = radix_orders(p->g.nx);
     if (x_variant < 0 || x_variant > (int)orders.size() || (x_variant == 0 && !dft_is_ct_size(p->g.nx)))
         return fail(p, DFT_EINVAL, "x variant out of range for this length");

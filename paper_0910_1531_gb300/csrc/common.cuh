@@ -91,7 +91,7 @@ struct GridDesc {
     // the run-time column kernel; z passes by the one-tile-per-CTA grouped kernels instead of
     // the persistent TMA ones
     int xrt, yrt, zgrp;
-    int xpers;       // the Phi' x passes as the persistent kernel with bulk-copy prefetch
+    int xpers;       // the Phi' x passes as a persistent kernel: 1 bulk-copy prefetch, 2 cp.async prefetch
     int pdl;         // launch the passes with programmatic dependent launch (launch_k)
 };
 
@@ -163,6 +163,9 @@ struct SpeciesDesc {
     const Real* tab_dk;                 // [m2][tab_ks]: d DC_ij_hat / d Gamma, same order
     int tab_m2max;
     int tab_ws, tab_ks;                 // record lengths: 2 S and S (S + 1) / 2 rounded up to 16 bytes
+    // Optional per-axis terms of the discrete Laplacian, sin^2(k_d h_d / 2) / h_d^2 by FFT index:
+    // x indices at 0, y at nx, z at nx + ny (k_laptab); null: the kernels evaluate them per point.
+    const Real* lap1d;
     // fixed-number species (canonical form of eq. rhoEquation): canon[i] != 0, target sum of G_i
     // over the grid N_i / h^3; ncanon of them
     int canon[DFT_MAXS];

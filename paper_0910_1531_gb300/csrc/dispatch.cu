@@ -65,6 +65,13 @@ cudaError_t Passes<Real>::build_ktab(cudaStream_t st, const SpeciesDesc<Real>& s
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::build_laptab(cudaStream_t st, const GridDesc& g, Real kfx, Real kfy, Real kfz, Real* out) {
+    const int n = g.nx + g.ny + g.nz;
+    dftk::k_laptab<Real><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(g, kfx, kfy, kfz, out);
+    return cudaGetLastError();
+}
+
+template <typename Real>
 int Passes<Real>::tile_y(int n, size_t budget) {
     if (dft_is_ct_size(n)) return dft_tile_y<Real>(n);
     for (int T = 16; T >= 1; T /= 2)

@@ -456,12 +456,41 @@ __device__ __forceinline__ Real es_kernel(const SpeciesDesc<Real>& sp, int i, in
     return K;
 }
 
+// One axis's term of lap(k): sin^2(k_d h_d / 2) / h_d^2.
+template <typename Real> __device__ __forceinline__ Real lap_term(Real k, Real h) {
+    const Real s = sin(Real(0.5) * k * h);
+    return s * s / (h * h);
+}
+
 template <typename Real>
 __device__ __forceinline__ Real inverse_laplacian(const KPoint<Real>& p, Real hx, Real hy, Real hz) {
     if (p.zero) return Real(0);
-    const Real sx = sin(Real(0.5) * p.kx * hx), sy = sin(Real(0.5) * p.ky * hy), sz = sin(Real(0.5) * p.kz * hz);
-    const Real lap = Real(4) * (sx * sx / (hx * hx) + sy * sy / (hy * hy) + sz * sz / (hz * hz));
+    const Real lap = Real(4) * (lap_term(p.kx, hx) + lap_term(p.ky, hy) + lap_term(p.kz, hz));
     return Real(1) / lap;
+}
+
+// The same from the plan's per-axis table (sp.lap1d, the lap_term values by FFT index, evaluated
+// by k_laptab with the same expression: equal bit for bit) where it has one.
+template <typename Real>
+__device__ __forceinline__ Real inverse_laplacian(const SpeciesDesc<Real>& sp, const GridDesc& g, const KPoint<Real>& p,
+                                                  int kxi, int kyi, int kzi, Real hx, Real hy, Real hz) {
+    if (!sp.lap1d) return inverse_laplacian<Real>(p, hx, hy, hz);
+    if (p.zero) return Real(0);
+    const Real lap = Real(4) * (__ldg(sp.lap1d + kxi) + __ldg(sp.lap1d + g.nx + kyi) + __ldg(sp.lap1d + g.nx + g.ny + kzi));
+    return Real(1) / lap;
+}
+
+// The per-axis Laplacian terms of a grid: out[i] for x indices i < nx, out[nx + j] for y, out[nx +
+// ny + l] for z (wave numbers kval of the FFT index, as the z passes form them).
+template <typename Real>
+__global__ void k_laptab(GridDesc g, Real kfx, Real kfy, Real kfz, Real* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx + g.ny + g.nz) return;
+    Real v;
+    if (i < g.nx) v = lap_term(kval<Real>(i, g.nx, kfx), Real(g.hx));
+    else if (i < g.nx + g.ny) v = lap_term(kval<Real>(i - g.nx, g.ny, kfy), Real(g.hy));
+    else v = lap_term(kval<Real>(i - g.nx - g.ny, g.nz, kfz), Real(g.hz));
+    out[i] = v;
 }
 
 // ------------------------------------------------------------------------------------
@@ -531,7 +560,7 @@ __global__ void __launch_bounds__(kThreads) k_zconv_fwd(GridDesc g, AxisPlan pz,
             acc[4] = cadd(acc[4], cscale(v[s], R * R * j3));       // w3 / (4 pi R)
         }
         if (kxi < nxh) {
-            const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+            const Real inv_lap = inverse_laplacian<Real>(sp, g, p, kxi, kyi, kzi, hx, hy, hz);
             C dv[DFT_MAXS];
             for (int s = 0; s < S; ++s) {
                 dv[s] = v[s];
@@ -841,7 +870,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_fwd_g(GridDesc g, Species
             acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
         }
         if (live) {
-            const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+            const Real inv_lap = inverse_laplacian<Real>(sp, g, p, kxi, kyi, kzi, hx, hy, hz);
             C dv[DFT_MAXS], es[DFT_MAXS];
 #pragma unroll
             for (int s = 0; s < DFT_MAXS; ++s) {
@@ -1157,7 +1186,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                 acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
             }
             if (live) {
-                const Real inv_lap = inverse_laplacian<Real>(p, hx, hy, hz);
+                const Real inv_lap = inverse_laplacian<Real>(sp, g, p, kxi, kyi, kzi, hx, hy, hz);
                 C dv[DFT_MAXS], es[DFT_MAXS];
 #pragma unroll
                 for (int s = 0; s < DFT_MAXS; ++s) {
@@ -1884,6 +1913,48 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
 }
 
 // ------------------------------------------------------------------------------------
+// The part of the persistent Phi' x passes after the weighted-density lines of a block's LR rows
+// (NM mixtures, the load_wd_rows arrangement) are in A (synced): x C2R, dPhi/dn_alpha at each
+// point (the maximum of n3 over the live rows into *mx, n3 >= 1 met into *bad), x R2C, and the
+// nine Phi' spectra of each mixture out.  The line buffers stay in use until the caller's next
+// barrier.
+// ------------------------------------------------------------------------------------
+template <typename Real, int NX, int NM>
+__device__ __forceinline__ void xphi_rows_ct(const GridDesc& g, int LR, long long row0, long long nrows,
+                                             typename Cplx<Real>::type* A, typename Cplx<Real>::type* B,
+                                             const typename Cplx<Real>::type* tw, Real kfx,
+                                             typename Cplx<Real>::type* __restrict__ phi_out, float* mx,
+                                             bool* bad) {
+    using C = typename Cplx<Real>::type;
+    constexpr int pitch = ct_row_pitch(NX);
+    const int lines = 5 * NM * LR;
+    C* R = ct_fft<NX, true, false, 0>(A, B, lines, pitch, tw);
+    for (int idx = threadIdx.x; idx < LR * NM * NX; idx += kThreads) {
+        const int rr = idx / NX, x = idx - (idx / NX) * NX;
+        const int r = rr / NM;
+        C* bp = R + (rr * 5) * pitch + xo<NX>(x);
+        Real n[DFT_NCOMP];
+        {   // lines (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z): see wd_comp
+            const C v0 = bp[0], v1 = bp[pitch], v2 = bp[2 * pitch], v3 = bp[3 * pitch], v4 = bp[4 * pitch];
+            n[0] = v0.x; n[1] = v0.y; n[2] = v1.x; n[5] = v1.y; n[3] = v2.x;
+            n[7] = v2.y; n[4] = v3.x; n[6] = v3.y; n[8] = v4.x; n[9] = v4.y;
+        }
+        if (row0 + r < nrows) *mx = fmaxf(*mx, float(n[3]));
+        const bool okp = phi_derivatives<Real>(n, g.phi);
+        if (!okp && row0 + r < nrows) *bad = true;
+        bp[0] = cmake<C>(n[0], n[1]);
+        bp[pitch] = cmake<C>(n[2], n[5]);
+        bp[2 * pitch] = cmake<C>(n[3], n[7]);
+        bp[3 * pitch] = cmake<C>(n[4], n[6]);
+        bp[4 * pitch] = cmake<C>(n[8], n[9]);
+    }
+    __syncthreads();
+    C* other = (R == A) ? B : A;
+    C* F = ct_fft<NX, false, false, 0>(R, other, lines, pitch, tw);
+    store_phi_spectra<Real, NX, NM>(g, LR, row0, nrows, kfx, F, phi_out);
+}
+
+// ------------------------------------------------------------------------------------
 // Persistent form of k_xphi for compile-time lengths (same contract, same arithmetic per block):
 // CTA b takes the row blocks b, b + gridDim.x, ...  The nine (one slot) or eighteen (two slots)
 // half-spectrum components of a block's LR rows are contiguous in each component, so they
@@ -1901,7 +1972,7 @@ template <typename Real, int NX> __host__ __device__ constexpr size_t xphi_tma_s
 }
 
 template <typename Real, int NX, int NM>
-__global__ void __launch_bounds__(kThreads) k_xphi_tma(GridDesc g, int LR, const Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 1) k_xphi_tma(GridDesc g, int LR, const Ctl* __restrict__ ctl,
                                                        const typename Cplx<Real>::type* slotA,
                                                        const typename Cplx<Real>::type* slotB,
                                                        typename Cplx<Real>::type* mat_out,
@@ -1984,31 +2055,86 @@ __global__ void __launch_bounds__(kThreads) k_xphi_tma(GridDesc g, int LR, const
             const int next = blk + 2 * gridDim.x;
             if (next < nblk) { issue(next, cur); issued += 1 << (16 * cur); }
         }
-        C* R = ct_fft<NX, true, false, 0>(A, B, lines, pitch, tw);
         float mx = -CUDART_INF_F;
-        for (int idx = threadIdx.x; idx < LR * NM * NX; idx += kThreads) {
-            const int rr = idx / NX, x = idx - (idx / NX) * NX;
-            const int r = rr / NM;
-            C* bp = R + (rr * 5) * pitch + xo<NX>(x);
-            Real n[DFT_NCOMP];
-            {   // lines (n0, n1), (n2, nV1y), (n3, nV2x), (nV1x, nV1z), (nV2y, nV2z): see wd_comp
-                const C v0 = bp[0], v1 = bp[pitch], v2 = bp[2 * pitch], v3 = bp[3 * pitch], v4 = bp[4 * pitch];
-                n[0] = v0.x; n[1] = v0.y; n[2] = v1.x; n[5] = v1.y; n[3] = v2.x;
-                n[7] = v2.y; n[4] = v3.x; n[6] = v3.y; n[8] = v4.x; n[9] = v4.y;
-            }
-            if (row0 + r < nrows) mx = fmaxf(mx, float(n[3]));
-            const bool okp = phi_derivatives<Real>(n, g.phi);
-            if (!okp && row0 + r < nrows) bad = true;
-            bp[0] = cmake<C>(n[0], n[1]);
-            bp[pitch] = cmake<C>(n[2], n[5]);
-            bp[2 * pitch] = cmake<C>(n[3], n[7]);
-            bp[3 * pitch] = cmake<C>(n[4], n[6]);
-            bp[4 * pitch] = cmake<C>(n[8], n[9]);
+        xphi_rows_ct<Real, NX, NM>(g, LR, row0, nrows, A, B, tw, kfx, phi_out, &mx, &bad);
+        const float bm = block_max(mx, scratch_f);
+        if (threadIdx.x == 0 && red_max) red_max[blk] = bm;
+        __syncthreads();   // the line buffers are rewritten by the next block
+    }
+    if (bad) atomicOr(status, DEV_N3BOUND);
+}
+
+// ------------------------------------------------------------------------------------
+// Persistent form of k_xphi with one staging area filled by per-thread 16-byte asynchronous
+// copies (cp.async; same contract, same arithmetic per block): the spectra of a CTA's next row
+// block are requested as soon as the current block's have been turned into lines, and arrive
+// while it is transformed.  Each thread waits for its own copies, then a barrier: no mbarrier,
+// no bound needed.  Shared memory: twiddles | stage (nsrc components of LR rows) | line buffers
+// A, B.  Row blocks of a component are contiguous and start on 16-byte boundaries (pxh even).
+// ------------------------------------------------------------------------------------
+template <typename Real, int NX> __host__ __device__ constexpr size_t xphi_cpa_smem(int nm, int LR, int nsrc, int pxh) {
+    using C = typename Cplx<Real>::type;
+    return (size_t(NX) + size_t(nsrc) * LR * pxh + 2 * size_t(5 * nm * LR) * ct_row_pitch(NX)) * sizeof(C) + 128;
+}
+
+template <typename Real, int NX, int NM>
+__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 1) k_xphi_cpa(GridDesc g, int LR, const Ctl* __restrict__ ctl,
+                                                       const typename Cplx<Real>::type* slotA,
+                                                       const typename Cplx<Real>::type* slotB,
+                                                       typename Cplx<Real>::type* mat_out,
+                                                       typename Cplx<Real>::type* __restrict__ phi_out,
+                                                       float* __restrict__ red_max, int* __restrict__ status,
+                                                       Real kfx, const typename Cplx<Real>::type* __restrict__ twx) {
+    static_assert(NX > 0, "compile-time lengths only");
+    using C = typename Cplx<Real>::type;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float scratch_f[32];
+    const int nsrc = slotB ? 2 * DFT_NSPEC : DFT_NSPEC;
+    const int cstride = LR * g.pxh;                       // elements per staged component
+    const int lines = 5 * NM * LR;
+    constexpr int pitch = ct_row_pitch(NX);
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127);
+    C* tw = reinterpret_cast<C*>(base);
+    C* stage = tw + ((NX + 15) & ~15);                    // 128-byte aligned (NX a multiple of 16)
+    C* A = stage + nsrc * cstride;
+    C* B = A + lines * pitch;
+    const long long nrows = (long long)g.ny * g.nz;
+    const int nblk = (int)((nrows + LR - 1) / LR);
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = twx[i];
+    dep_launch();
+    dep_wait();
+    Real wA[NM], wB[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
+        wA[m] = Real(cw->wA);
+        wB[m] = Real(cw->wB);
+    }
+    // the nsrc components of row block blk, in 16-byte chunks spread over the threads
+    auto issue = [&](int blk) {
+        const long long r0 = (long long)blk * LR;
+        const int rows = (int)(nrows - r0 < LR ? nrows - r0 : LR);
+        const int per = int((long long)rows * g.pxh * sizeof(C) / 16);
+        for (int i = threadIdx.x; i < nsrc * per; i += kThreads) {
+            const int c = i / per, q = i - c * per;
+            const C* src = (c < DFT_NSPEC ? slotA + (long long)c * g.nc : slotB + (long long)(c - DFT_NSPEC) * g.nc) +
+                           r0 * g.pxh;
+            tma::cp16(reinterpret_cast<char*>(stage + c * cstride) + 16 * q, reinterpret_cast<const char*>(src) + 16 * q);
         }
+        tma::cp_commit();
+    };
+    if (blockIdx.x < nblk) issue(blockIdx.x);
+    bool bad = false;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const long long row0 = (long long)blk * LR;
+        tma::cp_wait_all();
         __syncthreads();
-        C* other = (R == A) ? B : A;
-        C* F = ct_fft<NX, false, false, 0>(R, other, lines, pitch, tw);
-        store_phi_spectra<Real, NX, NM>(g, LR, row0, nrows, kfx, F, phi_out);
+        load_wd_rows<Real, NX, NM, true>(g, LR, row0, nrows, nullptr, slotB, wA, wB, mat_out, kfx, A, stage, cstride);
+        __syncthreads();
+        // the stage is free: request the next block into it while this one is transformed
+        if (blk + gridDim.x < nblk) issue(blk + gridDim.x);
+        float mx = -CUDART_INF_F;
+        xphi_rows_ct<Real, NX, NM>(g, LR, row0, nrows, A, B, tw, kfx, phi_out, &mx, &bad);
         const float bm = block_max(mx, scratch_f);
         if (threadIdx.x == 0 && red_max) red_max[blk] = bm;
         __syncthreads();   // the line buffers are rewritten by the next block

@@ -34,6 +34,8 @@ cudaError_t LaunchX<Real, N>::init() {
     if constexpr (N > 0) {
         if ((r = set_max_smem(dftk::k_xphi_tma<Real, N, 1>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_xphi_tma<Real, N, 2>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_xphi_cpa<Real, N, 1>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_xphi_cpa<Real, N, 2>)) != cudaSuccess) e = r;
     }
     if ((r = set_max_smem(dftk::k_xupdate<Real, N, 1>)) != cudaSuccess) e = r;
     if ((r = set_max_smem(dftk::k_xupdate<Real, N, 2>)) != cudaSuccess) e = r;
@@ -53,16 +55,20 @@ cudaError_t LaunchX<Real, N>::xfwd(cudaStream_t st, const GridDesc& g, const Axi
 }
 
 namespace {
-// The persistent Phi' x pass (compile-time lengths, no grand-potential sums): grid = the row
-// blocks, at most the CTAs that fit on the GPU at once.  False if it does not apply.
+// The persistent Phi' x passes (compile-time lengths, no grand-potential sums): g.xpers 1 =
+// bulk copies two blocks ahead, 2 = per-thread cp.async one block ahead; grid = the row blocks,
+// at most the CTAs that fit on the GPU at once.  False if neither applies.
 template <typename Real, int N, int NM, typename C>
 bool launch_xphi_tma(cudaStream_t st, const GridDesc& g, int LR, const Ctl* ctl, const C* A, const C* B, C* mat,
                      C* phi, float* red_max, int* status, Real kfx, const C* tw) {
     if constexpr (N == 0) {
         return false;
     } else {
+        if (!g.xpers || !status) return false;
         const int nsrc = B ? 2 * DFT_NSPEC : DFT_NSPEC;
-        const size_t sm = dftk::xphi_tma_smem<Real, N>(NM, LR, nsrc, g.pxh);
+        const bool cpa = g.xpers == 2;
+        const size_t sm = cpa ? dftk::xphi_cpa_smem<Real, N>(NM, LR, nsrc, g.pxh)
+                              : dftk::xphi_tma_smem<Real, N>(NM, LR, nsrc, g.pxh);
         static int optin = 0, sms = 0;
         if (optin == 0) {
             int dev = 0;
@@ -70,14 +76,19 @@ bool launch_xphi_tma(cudaStream_t st, const GridDesc& g, int LR, const Ctl* ctl,
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         }
-        if (!g.xpers || !status || sm > size_t(optin)) return false;
+        if (sm > size_t(optin)) return false;
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_xphi_tma<Real, N, NM>, dftk::kThreads, sm);
+        if (cpa) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_xphi_cpa<Real, N, NM>, dftk::kThreads, sm);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_xphi_tma<Real, N, NM>, dftk::kThreads, sm);
         if (occ < 1) occ = 1;
         const long long nblk = ceil_div((long long)g.ny * g.nz, LR);
         const int grid = (int)(nblk < (long long)sms * occ ? nblk : (long long)sms * occ);
-        launch_k(dftk::k_xphi_tma<Real, N, NM>, grid, dftk::kThreads, sm, st, g.pdl, g, LR, ctl, A, B, mat, phi, red_max, status,
-                                                                      kfx, tw);
+        if (cpa)
+            launch_k(dftk::k_xphi_cpa<Real, N, NM>, grid, dftk::kThreads, sm, st, g.pdl, g, LR, ctl, A, B, mat, phi,
+                     red_max, status, kfx, tw);
+        else
+            launch_k(dftk::k_xphi_tma<Real, N, NM>, grid, dftk::kThreads, sm, st, g.pdl, g, LR, ctl, A, B, mat, phi,
+                     red_max, status, kfx, tw);
         return true;
     }
 }

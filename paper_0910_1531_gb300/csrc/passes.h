@@ -197,6 +197,8 @@ struct Passes {
     // fill the |k| tables of sp (tab_w, tab_k, tab_dk, tab_m2max set by the caller) for wave
     // number kf of a cubic box
     static cudaError_t build_ktab(cudaStream_t st, const SpeciesDesc<Real>& sp, double kf);
+    // fill out[nx + ny + nz] with the per-axis Laplacian terms of grid g (SpeciesDesc::lap1d)
+    static cudaError_t build_laptab(cudaStream_t st, const GridDesc& g, Real kfx, Real kfy, Real kfz, Real* out);
 };
 
 // ctl: the plan's three control blocks (iteration, sample 1 weights, sample 2 weights);

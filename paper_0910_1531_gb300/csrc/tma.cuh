@@ -68,6 +68,15 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+// Per-thread asynchronous copy of 16 bytes global -> shared (cp.async, cached in L2 only; both
+// addresses 16-byte aligned).  The issuing thread commits its copies as a group and waits for
+// them with cp_wait_all(); like a load, such a copy always completes (no bound needed).
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // 3D tiled store shared -> global (elements outside the tensor are not written).
 __device__ __forceinline__ void store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"

@@ -1,7 +1,7 @@
 """Every transform variant the autotuner can choose computes the same G as the oracle.
 
-The x passes run either as the compile-time kernels (the Phi' passes one CTA per row block or
-persistent with bulk-copy prefetch) or as the run-time ones under each candidate radix order
+The x passes run either as the compile-time kernels (the Phi' passes one CTA per row block, or
+persistent with bulk-copy or cp.async prefetch) or as the run-time ones under each candidate radix order
 (default, reversed, all-8 and all-4 plans); the y pass as the persistent TMA kernel or
 the run-time column kernel; the z passes as the persistent TMA kernels or the grouped
 one-tile-per-CTA ones.  Each combination is pinned with dft_set_variants and checked against the
@@ -81,7 +81,7 @@ def test_every_variant_matches_oracle(precision, shape):
     plan.close()
 
 
-@pytest.mark.parametrize("which", ["run-time", "persistent"])
+@pytest.mark.parametrize("which", ["run-time", "persistent-bulk", "persistent-cp.async"])
 def test_line_search_steps_under_variants_fp64(which):
     # three line-search iterations (paired samples, accepted point with its materialised
     # weighted densities) against the oracle's
@@ -99,7 +99,7 @@ def test_line_search_steps_under_variants_fp64(which):
     if which == "run-time":
         plan.set_variants(_x_variants(plan)[-1], 1, 1)
     else:
-        plan.set_variants(0, 0, 0, x_persistent=1)
+        plan.set_variants(0, 0, 0, x_persistent=1 if which == "persistent-bulk" else 2)
     r, Vd = _dev(rho, plan), _dev(V, plan)
     plan.iter_begin(r, Vd)
     for _ in range(3):
