@@ -321,8 +321,9 @@ template <typename Real> struct Ops {
 
     // The two line-search samples rho0 + a_m (rho1 - rho0), a_1 = alpha_s / 2, a_2 = alpha_s (weights
     // in ctl[1], ctl[2], set by FIN_AMAX), evaluated together: one Phi' x pass for both mixtures of
-    // the slots (one read of slots A and B), one y pass over the 18 Phi' spectra, the two z passes,
-    // the two S-component y passes, and one update pass reading rho0, rho1, V (and the low part)
+    // the slots (one read of slots A and B), one y pass over the 18 Phi' spectra, one z pass for
+    // both (the persistent TMA pass; else one per sample), one y pass over the 2 S correlation
+    // spectra (else one per sample), and one update pass reading rho0, rho1, V (and the low part)
     // once for both residual sums (red_sum, red_sum2).  Nothing is written to rho or G.
     static dft_status second_half_pair(dft_plan* p, const Real* rho0, const Real* rho1, const Real* V, Real* rho_lo) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
@@ -336,16 +337,30 @@ template <typename Real> struct Ops {
         LAUNCH(p, K_YFFT, 2.0 * (2 * DFT_NSPEC) * CB(p),
                P::yfft(p->stream, false, p->g, p->ay, p->Ty, 2 * DFT_NSPEC, T1(p), &p->ctl->status, tw(p, 1),
                        p->wait_polls));
-        for (int m = 0; m < 2; ++m) {
-            C* phi = m == 0 ? T1(p) : T2;
-            LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S * 3) * CB(p),
-                   P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S, p->ctl + 1 + m,
-                                phi, esA, esB, nullptr, tw(p, 2)));
-            LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p),
-                   P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, phi, &p->ctl->status, tw(p, 1), p->wait_polls));
+        C* c2 = T2;   // the second sample's correlation spectra
+        if (P::has_zbwd_pair(p->g, p->S)) {
+            // one z pass for both samples (the ES tiles read once; sample 2's results after sample
+            // 1's, at T1 components S .. 2 S - 1), then one y inverse over the 2 S components
+            LAUNCH(p, K_ZBWD, (2.0 * DFT_NSPEC + 4.0 * p->S) * CB(p),
+                   P::zconv_bwd_pair(p->stream, p->g, sp, kf(p, 0), kf(p, 1), kf(p, 2), p->S, p->ctl + 1, T1(p), esA,
+                                     esB, tw(p, 2)));
+            LAUNCH(p, K_YFFT, 2.0 * (2 * p->S) * CB(p),
+                   P::yfft(p->stream, true, p->g, p->ay, p->Ty, 2 * p->S, T1(p), &p->ctl->status, tw(p, 1),
+                           p->wait_polls));
+            c2 = T1(p) + (long long)p->S * p->g.nc;
+        } else {
+            for (int m = 0; m < 2; ++m) {
+                C* phi = m == 0 ? T1(p) : T2;
+                LAUNCH(p, K_ZBWD, (DFT_NSPEC + p->S * 3) * CB(p),
+                       P::zconv_bwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), 3, p->S,
+                                    p->ctl + 1 + m, phi, esA, esB, nullptr, tw(p, 2)));
+                LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p),
+                       P::yfft(p->stream, true, p->g, p->ay, p->Ty, p->S, phi, &p->ctl->status, tw(p, 1),
+                               p->wait_polls));
+            }
         }
         LAUNCH(p, K_XUPD, 2.0 * p->S * CB(p) + p->S * RB(p) * (3 + (rho_lo ? 1 : 0)),
-               P::xupdate2(p->stream, p->g, p->ax, sp, p->LRupd2, p->ctl, T1(p), T2, rho0, rho1, V, rho_lo,
+               P::xupdate2(p->stream, p->g, p->ax, sp, p->LRupd2, p->ctl, T1(p), c2, rho0, rho1, V, rho_lo,
                            p->red_sum, p->red_sum2, &p->ctl->status, tw(p, 0)));
         return DFT_OK;
     }

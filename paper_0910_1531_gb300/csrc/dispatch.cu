@@ -121,6 +121,18 @@ cudaError_t Passes<Real>::zconv_bwd(cudaStream_t st, const GridDesc& g, const Ax
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::zconv_bwd_pair(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx,
+                                         Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
+                                         const C* esB, const C* tw) {
+    DFT_SWITCH_Z(g.nz, zconv_bwd_pair(st, g, sp, kfx, kfy, kfz, ncomp_out, ctl, phi, esA, esB, tw))
+}
+
+template <typename Real>
+bool Passes<Real>::has_zbwd_pair(const GridDesc& g, int ncomp_out) {
+    DFT_SWITCH_Z(g.nz, has_zbwd_pair(g, ncomp_out))
+}
+
+template <typename Real>
 cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                            const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                            Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,

@@ -1254,11 +1254,16 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
 // first groups of the transformed tile and leave through TMA stores.  At length 256 both
 // transforms run in place (ct_fft_grouped_ip), which keeps the CTA within half an SM's shared
 // memory (two CTAs per SM instead of one); shorter lengths, where two CTAs fit anyway,
-// alternate with a scratch area W (one barrier per stage instead of two).  A tensor map views a half-spectrum array as (x: nxh * E, y: ny,
-// plane: nz * ncomp) 8-byte elements, E = sizeof(complex) / 8; a component tile is the box
-// (TZ * E, 1, NZ) at plane c * nz.  Columns past nxh read as zero and are not written.  A
-// wait that runs out sets DEV_TIMEOUT and the CTA stops after draining the loads it has in
-// flight.
+// alternate with a scratch area W (one barrier per stage instead of two).  A tensor map views a
+// half-spectrum array as (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements, E =
+// sizeof(complex) / 8; a component tile is the box (TZ * E, 1, NZ) at plane c * nz.  Columns
+// past nxh read as zero and are not written.  The results go to map_out (map_phi's array for a
+// single evaluation).  pair: the two line-search samples in one pass, each tile taken for both in
+// turn: sample m's Phi' spectra are components 9 m .. 9 m + 8 of map_phi, its mixing weights
+// ctl[m], its results components m ncomp_out .. of map_out, and the tile's ES spectra serve both.
+// A tile's components are read and written only by the CTA that takes it, loads before stores,
+// so map_out may overlap map_phi.  A wait that runs out sets DEV_TIMEOUT and the CTA stops after
+// draining the loads it has in flight.
 // Shared memory: stage 0 | stage 1 (nine padded groups each) | W (nine padded groups, below
 // length 256) | ES (nes dense tiles) | twiddles | three mbarriers.
 // ------------------------------------------------------------------------------------
@@ -1274,9 +1279,10 @@ template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zb
 template <typename Real, int NZ, int TZ, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constant__ CUtensorMap map_phi,
                                                             const __grid_constant__ CUtensorMap map_esA,
-                                                            const __grid_constant__ CUtensorMap map_esB, GridDesc g,
+                                                            const __grid_constant__ CUtensorMap map_esB,
+                                                            const __grid_constant__ CUtensorMap map_out, GridDesc g,
                                                             SpeciesDesc<Real> sp, Real kfx, Real kfy, Real kfz,
-                                                            int flags, int ncomp_out, int has_esB,
+                                                            int flags, int ncomp_out, int has_esB, int pair,
                                                             const Ctl* __restrict__ ctl,
                                                             typename Cplx<Real>::type* es_mat, int ntiles_x,
                                                             int ntiles, int* __restrict__ status,
@@ -1304,12 +1310,20 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NZ);
     const int S = sp.S, ny = g.ny, nxh = g.nxh;
     const long long zstride = (long long)ny * g.pxh;
+    // Work items: tiles, or (pair) each tile twice, for the two line-search samples in turn
+    // (sample m's nine Phi' spectra at components 9 m .. 9 m + 8 of map_phi, its weights in
+    // ctl[m], its results to components m ncomp_out .. of map_out); the ES tiles of a tile are
+    // loaded once for both.
+    const int shift = pair ? 1 : 0;
+    auto item_tile = [&](int item) { return blockIdx.x + (item >> shift) * gridDim.x; };
 
-    auto issue_phi = [&](int tile, int s) {
+    auto issue_phi = [&](int item, int s) {
         C* st = stage0 + s * stage_elems;
+        const int tile = item_tile(item), m = pair ? (item & 1) : 0;
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
         tma::mbar_expect_tx(&bar[s], uint32_t(DFT_NSPEC) * BOX);
-        for (int c = 0; c < DFT_NSPEC; ++c) tma::load_3d(st + c * GS, &map_phi, x, y, c * NZ, &bar[s]);
+        for (int c = 0; c < DFT_NSPEC; ++c)
+            tma::load_3d(st + c * GS, &map_phi, x, y, (m * DFT_NSPEC + c) * NZ, &bar[s]);
     };
     auto issue_es = [&](int tile) {
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
@@ -1330,10 +1344,8 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
     int issued = 0, consumed = 0, es_issued = 0, es_consumed = 0;
     if (threadIdx.x == 0) {
         if (hs)
-            for (int s = 0; s < 2; ++s) {
-                const int tile = blockIdx.x + s * gridDim.x;
-                if (tile < ntiles) { issue_phi(tile, s); issued += 1 << (16 * s); }
-            }
+            for (int s = 0; s < 2; ++s)
+                if (item_tile(s) < ntiles) { issue_phi(s, s); issued += 1 << (16 * s); }
         if (es_on && blockIdx.x < ntiles) { issue_es(blockIdx.x); ++es_issued; }
     }
     // on a wait that ran out: record it, let the copies in flight land, stop
@@ -1347,11 +1359,15 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
             if (es_issued > es_consumed) tma::mbar_wait(&bar[2], (es_issued - 1) & 1);
         }
     };
-    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
     const Real fourpi = Real(4.0 * CUDART_PI);
     const bool tab = sp.tab_w != nullptr;
-    int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
+        const int tile = item_tile(it);
+        if (tile >= ntiles) break;
+        const int m = pair ? (it & 1) : 0;
+        const int ti = it >> shift;                 // this CTA's tile count so far
+        const bool last_of_tile = !pair || m == 1;
+        const Real wA = Real(ctl[m].wA), wB = Real(ctl[m].wB);
         const int cur = it & 1;
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
@@ -1373,11 +1389,11 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
             if constexpr (IP) ct_fft_grouped_ip<NZ, false, TZ, GS, true, false, NT>(X, DFT_NSPEC, tw);
             else X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NSPEC, tw);
         }
-        // the ES tiles of this tile (loaded since the previous tile's pointwise phase); the
-        // barrier also ends the forward transform
-        const bool ok_es = es_on ? tma::mbar_wait(&bar[2], it & 1) : true;
+        // the ES tiles of this tile (loaded since the previous tile's pointwise phase; a pair's
+        // second item reuses them); the barrier also ends the forward transform
+        const bool ok_es = (es_on && m == 0) ? tma::mbar_wait(&bar[2], ti & 1) : true;
         if (__syncthreads_or(!ok_es)) { drain(); break; }
-        if (threadIdx.x == 0 && es_on) ++es_consumed;
+        if (threadIdx.x == 0 && es_on && m == 0) ++es_consumed;
 #pragma unroll 1
         for (int i = 0; i < PER; ++i) {
             const int idx = threadIdx.x + i * NT;
@@ -1430,8 +1446,9 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
                 if (s < ncomp_out) X[s * GS + pos] = cscale(out[s], sp.inv_n);
         }
         __syncthreads();
-        // the ES area is free: load the next tile's while this one is finished
-        if (threadIdx.x == 0 && es_on) {
+        // the ES area is free after a tile's last item: load the next tile's while this one is
+        // finished
+        if (threadIdx.x == 0 && es_on && last_of_tile) {
             const int next = tile + gridDim.x;
             if (next < ntiles) { issue_es(next); ++es_issued; }
         }
@@ -1441,12 +1458,12 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
         tma::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int s = 0; s < ncomp_out; ++s) tma::store_3d(&map_phi, kx0 * E, kyi, s * NZ, Q + s * GS);
+            for (int s = 0; s < ncomp_out; ++s)
+                tma::store_3d(&map_out, kx0 * E, kyi, (m * ncomp_out + s) * NZ, Q + s * GS);
             tma::commit();
             // the stores read the stage or W: let them finish reading before either is written
             tma::wait_read_all();
-            const int next = tile + 2 * gridDim.x;
-            if (hs && next < ntiles) { issue_phi(next, cur); issued += 1 << (16 * cur); }
+            if (hs && item_tile(it + 2) < ntiles) { issue_phi(it + 2, cur); issued += 1 << (16 * cur); }
         }
     }
     if (threadIdx.x == 0) tma::wait_all();

@@ -330,57 +330,69 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
     return cudaSuccess;
 }
 
+namespace {
+// The persistent TMA second-half z pass: single (pair = 0: nine Phi' spectra at phi, results over
+// its first ncomp_out) or the two line-search samples (pair = 1: eighteen at phi, weights in
+// ctl[0], ctl[1], results at phi components 0 .. 2 ncomp_out - 1).  False if it does not apply
+// (no compile-time length, the grouped variant chosen, or too little shared memory).
+template <typename Real, int N, typename C>
+bool launch_zbwd_tma(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx, Real kfy, Real kfz,
+                     int flags, int ncomp_out, int pair, const Ctl* ctl, C* phi, const C* esA, const C* esB, C* es_mat,
+                     const C* tw) {
+    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
+    constexpr bool kTma = N > 0 && (TB * sizeof(C)) % 16 == 0;
+    if constexpr (!kTma) {
+        return false;
+    } else {
+        const bool es_on = (flags & 2) != 0;
+        const int nes = es_on ? ncomp_out * (esB ? 2 : 1) : 0;
+        static int optin = 0, sms = 0;
+        if (optin == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        const size_t sm = dftk::zbwd_tma_smem<Real, N, TB>(nes);
+        if (g.zgrp || sm > size_t(optin)) return false;
+        // persistent CTAs, two TMA-filled stages of nine Phi' tiles, one area of ES tiles
+        constexpr int NT = dft_zbwd_threads<Real>(N), MB = dft_zbwd_minb<Real>(N);
+        constexpr int E = int(sizeof(C) / 8);
+        CUtensorMap map_phi, map_esA, map_esB, map_out;
+        auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
+            return tma_encode_3d(m, const_cast<C*>(data), (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
+                                 (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
+                                 (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
+        };
+        const int nphi = (pair ? 2 : 1) * DFT_NSPEC;
+        cudaError_t e = encode(&map_phi, phi, nphi);
+        if (e == cudaSuccess) e = encode(&map_esA, es_on ? esA : phi, es_on ? ncomp_out : DFT_NSPEC);
+        if (e == cudaSuccess) e = encode(&map_esB, (es_on && esB) ? esB : phi, (es_on && esB) ? ncomp_out : DFT_NSPEC);
+        if (e == cudaSuccess) e = encode(&map_out, phi, nphi);
+        if (e != cudaSuccess) return false;
+        const int ntx = (int)ceil_div(g.nxh, TB);
+        const int ntiles = ntx * g.ny;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, NT, sm);
+        if (occ < 1) occ = 1;
+        const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
+        // the status word of the device control block records a TMA wait that ran out
+        int* status = const_cast<int*>(&ctl->status);
+        launch_k(dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, grid, NT, sm, st, g.pdl, map_phi, map_esA, map_esB,
+                 map_out, g, sp, kfx, kfy, kfz, flags, ncomp_out, esB ? 1 : 0, pair, ctl, es_mat, ntx, ntiles, status,
+                 tw);
+        return true;
+    }
+}
+}  // namespace
+
 template <typename Real, int N>
 cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp,
                                  int T, Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                                  const C* esA, const C* esB, C* es_mat, const C* tw) {
     constexpr int TZ = N > 0 ? dft_tile_z<Real>(N) : 1;
-    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
-    constexpr bool kTma = N > 0 && (TB * sizeof(C)) % 16 == 0;
-    const bool es_on = (flags & 2) != 0;
-    const int nes = es_on ? ncomp_out * (esB ? 2 : 1) : 0;
-    static int optin = 0;
-    if (optin == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    }
-    if constexpr (kTma) {
-        if (!g.zgrp && dftk::zbwd_tma_smem<Real, N, TB>(nes) <= size_t(optin)) {
-            // TMA path: persistent CTAs, two TMA-filled stages of nine Phi' tiles, one area of ES tiles
-            constexpr int NT = dft_zbwd_threads<Real>(N), MB = dft_zbwd_minb<Real>(N);
-            constexpr int E = int(sizeof(C) / 8);
-            CUtensorMap map_phi, map_esA, map_esB;
-            auto encode = [&](CUtensorMap* m, const C* data, int ncomp) {
-                return tma_encode_3d(m, const_cast<C*>(data), (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
-                                     (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
-                                     (unsigned long long)g.ny * g.pxh * sizeof(C), TB * E, 1, N);
-            };
-            cudaError_t e = encode(&map_phi, phi, DFT_NSPEC);
-            if (e == cudaSuccess) e = encode(&map_esA, es_on ? esA : phi, es_on ? ncomp_out : DFT_NSPEC);
-            if (e == cudaSuccess) e = encode(&map_esB, (es_on && esB) ? esB : phi, (es_on && esB) ? ncomp_out : DFT_NSPEC);
-            if (e != cudaSuccess) return e;
-            const int ntx = (int)ceil_div(g.nxh, TB);
-            const int ntiles = ntx * g.ny;
-            const size_t sm = dftk::zbwd_tma_smem<Real, N, TB>(nes);
-            static int sms = 0;
-            if (sms == 0) {
-                int dev = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            }
-            int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, NT, sm);
-            if (occ < 1) occ = 1;
-            const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-            // the status word of the device control block records a TMA wait that ran out
-            int* status = const_cast<int*>(&ctl->status);
-            launch_k(dftk::k_zconv_bwd_tma<Real, N, TB, NT, MB>, grid, NT, sm, st, g.pdl,
-                map_phi, map_esA, map_esB, g, sp, kfx, kfy, kfz, flags, ncomp_out, esB ? 1 : 0, ctl, es_mat, ntx, ntiles,
-                status, tw);
-            return cudaSuccess;
-        }
-    }
+    if (launch_zbwd_tma<Real, N>(st, g, sp, kfx, kfy, kfz, flags, ncomp_out, 0, ctl, phi, esA, esB, es_mat, tw))
+        return cudaSuccess;
     if constexpr (N > 0) {
         const size_t sm = dftk::zg_smem_bytes<TZ, N>(sizeof(C));
         dim3 grid((unsigned)ceil_div(g.nxh, TZ), (unsigned)g.ny);
@@ -392,4 +404,27 @@ cudaError_t LaunchZ<Real, N>::zconv_bwd(cudaStream_t st, const GridDesc& g, cons
             g, pz, sp, T, kfx, kfy, kfz, flags, ncomp_out, ctl, phi, esA, esB, es_mat, tw);
     }
     return cudaSuccess;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchZ<Real, N>::zconv_bwd_pair(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx,
+                                             Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
+                                             const C* esB, const C* tw) {
+    if (launch_zbwd_tma<Real, N>(st, g, sp, kfx, kfy, kfz, 3, ncomp_out, 1, ctl, phi, esA, esB,
+                                 static_cast<C*>(nullptr), tw))
+        return cudaSuccess;
+    return cudaErrorNotSupported;
+}
+
+template <typename Real, int N>
+bool LaunchZ<Real, N>::has_zbwd_pair(const GridDesc& g, int ncomp_out) {
+    constexpr int TB = N > 0 ? dft_tile_zb<Real>(N) : 1;
+    if constexpr (N > 0 && (TB * sizeof(C)) % 16 == 0) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return !g.zgrp && dftk::zbwd_tma_smem<Real, N, TB>(2 * ncomp_out) <= size_t(optin);
+    } else {
+        return false;
+    }
 }

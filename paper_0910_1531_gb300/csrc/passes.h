@@ -139,6 +139,10 @@ struct LaunchZ {
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
+    static cudaError_t zconv_bwd_pair(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx,
+                                      Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
+                                      const C* esB, const C* tw);
+    static bool has_zbwd_pair(const GridDesc& g, int ncomp_out);
 };
 
 template <typename Real>
@@ -166,6 +170,14 @@ struct Passes {
     static cudaError_t zconv_bwd(cudaStream_t st, const GridDesc& g, const AxisPlan& pz, const SpeciesDesc<Real>& sp, int T,
                           Real kfx, Real kfy, Real kfz, int flags, int ncomp_out, const Ctl* ctl, C* phi,
                           const C* esA, const C* esB, C* es_mat, const C* tw);
+    // The two line-search samples' second-half z passes in one launch (both hard-sphere and ES
+    // parts): phi holds sample 1's nine Phi' spectra then sample 2's, ctl[0] / ctl[1] their
+    // weights; sample m's ncomp_out results go to phi components m ncomp_out ...  Only where
+    // has_zbwd_pair (the persistent TMA pass); cudaErrorNotSupported otherwise.
+    static cudaError_t zconv_bwd_pair(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx,
+                                      Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
+                                      const C* esB, const C* tw);
+    static bool has_zbwd_pair(const GridDesc& g, int ncomp_out);
     // rho_lo (or nullptr): low part of an extended iterate rho0 + rho_lo, read
     // with rho0 and, when rho_out is written, replaced by the low part of the new iterate
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
