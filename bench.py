@@ -37,18 +37,19 @@ FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
 
 # DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of one
-# profiled iteration, from one capture per kernel kind (1-pass metrics):
+# profiled iteration, from captures of one kernel kind at a time, at most three launches each
+# (1-pass metrics; the six y passes in two captures, -s 0 and -s 3):
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-#       --nvtx --nvtx-include 'profiled_steps/' -k regex:^<kernel>$ -c <launches per iteration> --csv
+#       --nvtx --nvtx-include 'profiled_steps/' -k regex:^<kernel>$ -s <skip> -c <launches> --csv
 #       python bench.py [--workload pore256 --converge-tol 0] --no-extra --no-cpu-baseline --no-cufft
 #       --steps 2 --warmup 3 --e2e-steps 1
-# per workload and precision (the pore's "xupdate" kind includes its fixed-number normalisation
-# pass); valid while the kernel sources and build flags hash to `digest`.
+# per workload and precision (the pore: its three largest passes); valid while the kernel
+# sources and build flags hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "0c633dfdcf07a740",
+    "digest": "2f9d5464f362bceb",
     "captures": {
-        "3species_16obstacles_128^3/fp32": {"xfwd": 25350400, "yfft": 78602934, "zconv_fwd": 79972608, "xphi": 261247488, "zconv_bwd": 137554346, "xupdate": 150797952, "xinv": 8713984, "finalize": 75093},
-        "pore_slab_4species_256^3/fp32": {"xfwd": 499722240, "yfft": 875819520, "zconv_fwd": 1155539200, "xphi": 2413544192, "zconv_bwd": 1682457088, "xupdate": 1152287616, "xinv": 68663552, "finalize": 101205},
+        "3species_16obstacles_128^3/fp32": {"xfwd": 25331456, "yfft": 91751467, "zconv_fwd": 78500096, "xphi": 261333504, "zconv_bwd": 187939584, "xupdate": 151247744, "xinv": 8711936, "finalize": 66560},
+        "pore_slab_4species_256^3/fp32": {"zconv_fwd": 1151653120, "xphi": 2413470464, "zconv_bwd": 1698084352},
     },
 }
 

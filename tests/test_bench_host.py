@@ -38,8 +38,10 @@ def test_digest_covers_the_build_flags(tmp_path, monkeypatch):
 
 
 def test_recorded_traffic_is_well_formed_and_dropped_once_stale(monkeypatch):
+    # every entry names kernel kinds the bench reports (a workload may record only its largest
+    # passes) and always the Phi' pass
     for key, per in bench.NCU_TRAFFIC["captures"].items():
-        assert set(per) == set(bench.KERNELS), key
+        assert set(per) <= set(bench.KERNELS) and "xphi" in per, key
         assert all(v >= 0 for v in per.values())
     key = next(iter(bench.NCU_TRAFFIC["captures"]))
     name, prec = key.rsplit("/", 1)
