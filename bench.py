@@ -34,7 +34,7 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 arithmetic peak: 152 SMs x 4 FP64 flop per clock (two FMAs) x 2.07 GHz (the part's
 # nominal 1.25 TFLOP/s dense FP64)
 FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize")
+KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize", "zfft", "zmul")
 
 # DRAM bytes (read + write) per launch of each kernel kind, averaged over the launches of one
 # profiled iteration, from captures of one kernel kind at a time, at most three launches each

@@ -231,7 +231,9 @@ dft_status dft_iter_run(dft_plan* plan, void* rho_inout, const void* V, int iter
  *    run-time ones under each candidate radix order (the default plan -- 3s, other odd primes,
  *    16s, then 2/4/8 --, its reverse, and for powers of two a plan of 8s and one of 4s);
  *  - the y transform: the persistent TMA pass against the run-time column kernel;
- *  - the z passes: the persistent TMA passes against the grouped one-tile-per-CTA kernels.
+ *  - the z passes: the persistent TMA passes against the grouped one-tile-per-CTA kernels;
+ *    then the first half's z stage as one pass against three (z transform, products, z
+ *    transform).
  * Results are cached per (grid, species count, precision) for the life of the process, so
  * later plans of the same shape reuse them without timing.  Invalidates a preceding
  * dft_iter_begin (call it again).  lines_out (may be NULL) receives the first three row
@@ -250,7 +252,9 @@ const char* dft_plan_tuning(const dft_plan* plan);
  * kernel whose row blocks arrive by bulk copies two blocks ahead, 2 = by per-thread cp.async
  * copies one block ahead (0 = one CTA per row block);
  * y_variant 0 = persistent TMA pass (run-time kernel for lengths without one), 1 = run-time
- * column kernel; z_variant 0 = persistent TMA passes, 1 = grouped one-tile-per-CTA kernels
+ * column kernel; z_variant bit 0: 0 = persistent TMA passes, 1 = grouped one-tile-per-CTA
+ * kernels; bit 1: the first half's z stage as three passes (persistent TMA z transform of the
+ * species, a k-space products pass, z transform of the nine weighted densities) instead of one
  * (lengths without compile-time kernels run the run-time ones either way).  Invalidates a
  * preceding dft_iter_begin. */
 dft_status dft_set_variants(dft_plan* plan, int x_variant, int x_persistent, int y_variant, int z_variant);

@@ -22,8 +22,9 @@
 
 namespace {
 
-enum Kind { K_XFWD, K_YFFT, K_ZFWD, K_XPHI, K_ZBWD, K_XUPD, K_XINV, K_FIN, K_COUNT };
-const char* kKindNames[K_COUNT] = {"xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize"};
+enum Kind { K_XFWD, K_YFFT, K_ZFWD, K_XPHI, K_ZBWD, K_XUPD, K_XINV, K_FIN, K_ZFFT, K_ZMUL, K_COUNT };
+const char* kKindNames[K_COUNT] = {"xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", "finalize",
+                                   "zfft", "zmul"};
 
 constexpr double kN3Bound = 0.9;       // Sec. "Nonlinear solver"
 constexpr double kAlphaFloor = 1e-3;   // lower clamp of the parabola minimiser, in units of alpha_max
@@ -281,8 +282,19 @@ template <typename Real> struct Ops {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
         LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1), p->wait_polls));
-        LAUNCH(p, K_ZFWD, (p->S + DFT_NSPEC + p->S + want_psi) * CB(p), P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi,
-                                       T1(p), slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
+        if (p->g.zsplit && dft_is_ct_size(p->g.nz) && !want_psi && !red_energy) {
+            // z forward transform of the species, the k-space products, z inverse of the nine
+            LAUNCH(p, K_ZFFT, 2.0 * p->S * CB(p),
+                   P::zfft(p->stream, false, p->g, p->S, T1(p), &p->ctl->status, tw(p, 2), p->wait_polls));
+            LAUNCH(p, K_ZMUL, (p->S + DFT_NSPEC + p->S) * CB(p),
+                   P::zmul(p->stream, p->g, sp, kf(p, 0), kf(p, 1), kf(p, 2), T1(p), slot_n(slot), slot_es(p, slot)));
+            LAUNCH(p, K_ZFFT, 2.0 * DFT_NSPEC * CB(p),
+                   P::zfft(p->stream, true, p->g, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 2), p->wait_polls));
+        } else {
+            LAUNCH(p, K_ZFWD, (p->S + DFT_NSPEC + p->S + want_psi) * CB(p),
+                   P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi, T1(p),
+                                slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
+        }
         LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 1), p->wait_polls));
         return DFT_OK;
     }
@@ -829,7 +841,7 @@ struct TuneKey {
 std::mutex g_tune_mu;
 struct TuneResult {
     std::array<int, 6> lines;       // LX, LRphi, LRupd, LRn3, LRphi2, LRupd2
-    int xrt, xpers, yrt, zgrp;      // transform variants (GridDesc)
+    int xrt, xpers, yrt, zgrp, zsplit;   // transform variants (GridDesc)
     AxisPlan ax;                    // radix order of the x passes
 };
 std::map<TuneKey, TuneResult> g_tune_cache;
@@ -899,6 +911,7 @@ void describe_tuning(dft_plan* p) {
     t += "; z: ";
     t += dft_is_ct_size(g.nz) ? (g.zgrp ? std::string("grouped, one tile per CTA") : std::string("TMA persistent"))
                               : "run-time column kernel, " + std::to_string(p->Tz) + "-column tiles";
+    if (dft_is_ct_size(g.nz) && g.zsplit) t += ", first half as z transforms and a k-space products pass";
     t += p->pdl_on ? "; launches: programmatic dependent" : "; launches: stream order";
     p->tuning = t;
 }
@@ -1082,6 +1095,24 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
             });
         }
         p->g.zgrp = ms[1] < ms[0] ? 1 : 0;
+        // the first-half z stage as one pass (the choice above) or split into z transforms and a
+        // k-space products pass
+        for (int v = 0; v < 2; ++v) {
+            p->g.zsplit = v;
+            ms[v] = time_it([&] {
+                if (v) {
+                    P::zfft(p->stream, false, p->g, p->S, O::T1(p), &p->ctl->status, O::tw(p, 2), p->wait_polls);
+                    P::zmul(p->stream, p->g, sp, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), O::T1(p),
+                            O::slot_n(p->slotB), O::slot_es(p, p->slotB));
+                    P::zfft(p->stream, true, p->g, DFT_NSPEC, O::slot_n(p->slotB), &p->ctl->status, O::tw(p, 2),
+                            p->wait_polls);
+                } else {
+                    P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, O::kf(p, 0), O::kf(p, 1), O::kf(p, 2), 0, O::T1(p),
+                                 O::slot_n(p->slotB), O::slot_es(p, p->slotB), nullptr, O::tw(p, 2), &p->ctl->status);
+                }
+            });
+        }
+        p->g.zsplit = ms[1] < ms[0] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1616,6 +1647,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
             p->g.xpers = t.xpers;
             p->g.yrt = t.yrt;
             p->g.zgrp = t.zgrp;
+            p->g.zsplit = t.zsplit;
             p->ax = t.ax;
             cached = true;
         }
@@ -1625,7 +1657,7 @@ dft_status dft_autotune(dft_plan* p, const void* rho, const void* V, int reps, i
         else TRY(autotune_t<float>(p, static_cast<const float*>(rho), static_cast<const float*>(V), reps));
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = TuneResult{{p->LX, p->LRphi, p->LRupd, p->LRn3, p->LRphi2, p->LRupd2},
-                                       p->g.xrt, p->g.xpers, p->g.yrt, p->g.zgrp, p->ax};
+                                       p->g.xrt, p->g.xpers, p->g.yrt, p->g.zgrp, p->g.zsplit, p->ax};
     }
     // the iteration state and its graph depend on the block counts and variants
     p->iter_ready = false;
@@ -1949,14 +1981,15 @@ dft_status dft_set_variants(dft_plan* p, int x_variant, int x_persistent, int y_
     const std::vector<AxisPlan> orders = radix_orders(p->g.nx);
     if (x_variant < 0 || x_variant > (int)orders.size() || (x_variant == 0 && !dft_is_ct_size(p->g.nx)))
         return fail(p, DFT_EINVAL, "x variant out of range for this length");
-    if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 1)
-        return fail(p, DFT_EINVAL, "y and z variants are 0 or 1");
+    if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 3)
+        return fail(p, DFT_EINVAL, "the y variant is 0 or 1, the z variant 0 to 3");
     p->g.xrt = x_variant > 0 ? 1 : 0;
     p->g.xpers = x_persistent;
     if (x_variant > 0) p->ax = orders[x_variant - 1];
     else dft_radix_plan(p->g.nx, &p->ax);
     p->g.yrt = y_variant;
-    p->g.zgrp = z_variant;
+    p->g.zgrp = z_variant & 1;
+    p->g.zsplit = (z_variant >> 1) & 1;
     p->iter_ready = false;
     release_iter_graph(p);
     describe_tuning(p);

@@ -92,6 +92,7 @@ struct GridDesc {
     // the persistent TMA ones
     int xrt, yrt, zgrp;
     int xpers;       // the Phi' x passes as a persistent kernel: 1 bulk-copy prefetch, 2 cp.async prefetch
+    int zsplit;      // the first-half z stage as three passes: z transform, k-space products, z transform
     int pdl;         // launch the passes with programmatic dependent launch (launch_k)
 };
 

@@ -133,6 +133,27 @@ bool Passes<Real>::has_zbwd_pair(const GridDesc& g, int ncomp_out) {
 }
 
 template <typename Real>
+cudaError_t Passes<Real>::zfft(cudaStream_t st, bool inv, const GridDesc& g, int ncomp, C* data, int* status,
+                               const C* tw, long long polls) {
+    DFT_SWITCH_Z(g.nz, zfft(st, inv, g, ncomp, data, status, tw, polls))
+}
+
+template <typename Real>
+cudaError_t Passes<Real>::zmul(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx, Real kfy,
+                               Real kfz, const C* in, C* slot_n, C* slot_es) {
+    const long long npt = (long long)g.nz * g.ny * g.nxh;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long long want = ceil_div(npt, dftk::kThreads), cap = (long long)sms * 16;
+    return launch_k(dftk::k_zmul<Real>, (unsigned)(want < cap ? want : cap), dftk::kThreads, 0, st, g.pdl, g, sp, kfx,
+                    kfy, kfz, in, slot_n, slot_es);
+}
+
+template <typename Real>
 cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                            const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
                            Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,

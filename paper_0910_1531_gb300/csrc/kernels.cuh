@@ -340,11 +340,15 @@ template <typename Real, int NY, int TY> __host__ __device__ constexpr size_t yf
            2 * sizeof(uint64_t) + 128;
 }
 
-template <typename Real, bool INV, int NY, int TY>
+// ZAX: the same pass along z.  The map is then the z passes' view (x: nxh * E, y: ny, plane:
+// nz * ncomp) with box (TY * E, 1, NY): a tile is TY kx columns of all NY z points at one ky
+// of one component, tile t = (kx tile, ky + ny c) -> coordinates (x, ky, c NY); the box lands in
+// shared memory with the same layout (element (z, t) at z TY + t) as a y tile's.
+template <typename Real, bool INV, int NY, int TY, bool ZAX = false>
 __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ CUtensorMap map, int ntiles_x,
                                                        int ntiles, int* __restrict__ status,
                                                        const typename Cplx<Real>::type* __restrict__ twy,
-                                                       long long polls) {
+                                                       long long polls, int ny_planes = 1) {
     dep_launch();
     dep_wait();
     static_assert(NY > 0 && NY <= 256 && TY > 0, "compile-time TMA y pass");
@@ -369,13 +373,16 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
     }
     for (int i = threadIdx.x; i < NY; i += kThreads) tw[i] = twy[i];
     __syncthreads();
+    // tensor-map coordinates of a tile
+    auto cy = [&](int tile) { return ZAX ? (tile / ntiles_x) % ny_planes : 0; };
+    auto cz = [&](int tile) { return ZAX ? (tile / ntiles_x) / ny_planes * NY : tile / ntiles_x; };
     int issued = 0, consumed = 0;   // per stage, packed (stage 1 << 16) | stage 0; thread 0
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
             const int tile = blockIdx.x + s * gridDim.x;
             if (tile < ntiles) {
                 tma::mbar_expect_tx(&bar[s], BYTES);
-                tma::load_3d(stage0 + s * TILE, &map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, &bar[s]);
+                tma::load_3d(stage0 + s * TILE, &map, (tile % ntiles_x) * TY * E, cy(tile), cz(tile), &bar[s]);
                 issued += 1 << (16 * s);
             }
         }
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
             const int next = tile + 2 * gridDim.x;
             if (next < ntiles) {
                 tma::mbar_expect_tx(&bar[cur], BYTES);
-                tma::load_3d(st, &map, (next % ntiles_x) * TY * E, 0, next / ntiles_x, &bar[cur]);
+                tma::load_3d(st, &map, (next % ntiles_x) * TY * E, cy(next), cz(next), &bar[cur]);
                 issued += 1 << (16 * cur);
             }
         }
@@ -417,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_yfft_tma(const __grid_constant__ C
         tma::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma::store_3d(&map, (tile % ntiles_x) * TY * E, 0, tile / ntiles_x, a);
+            tma::store_3d(&map, (tile % ntiles_x) * TY * E, cy(tile), cz(tile), a);
             tma::commit();
         }
     }
@@ -1242,6 +1249,92 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
         }
     }
     if (threadIdx.x == 0) tma::wait_all();
+}
+
+// ------------------------------------------------------------------------------------
+// The k-space products of the first half as a pass of their own (the split first-half z stage:
+// z forward transform of the S species, this pass, z inverse transform of the nine weighted
+// densities).  At each k point of the S species spectra (after the x, y and z forward
+// transforms) the nine weighted-density spectra, 1/N applied, into slot_n and the S
+// bulk-fluid/Poisson spectra into slot_es, both in (kx, ky, kz); the same arithmetic per point as
+// k_zconv_fwd_tma.  One thread per k point, kx fastest.
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_zmul(GridDesc g, SpeciesDesc<Real> sp, Real kfx, Real kfy, Real kfz,
+                                                   const typename Cplx<Real>::type* __restrict__ in,
+                                                   typename Cplx<Real>::type* __restrict__ slot_n,
+                                                   typename Cplx<Real>::type* __restrict__ slot_es) {
+    dep_launch();
+    dep_wait();
+    using C = typename Cplx<Real>::type;
+    const int S = sp.S, nxh = g.nxh;
+    const int Pn = S * (S + 1) / 2;
+    const long long npt = (long long)g.nz * g.ny * nxh;
+    const Real hx = Real(g.hx), hy = Real(g.hy), hz = Real(g.hz);
+    const Real fourpi = Real(4.0 * CUDART_PI);
+    const bool tab = sp.tab_w != nullptr;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < npt; q += (long long)gridDim.x * kThreads) {
+        const int kxi = int(q % nxh);
+        const long long rz = q / nxh;
+        const int kyi = int(rz % g.ny), kzi = int(rz / g.ny);
+        const long long o = rz * g.pxh + kxi;
+        const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
+        const int m2 = tab ? kmode2(kxi, signed_index(kyi, g.ny), kzi, g.nz) : 0;
+        C v[DFT_MAXS];
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s)
+            if (s < S) v[s] = in[(long long)s * g.nc + o];
+        {   // the nine weighted-density spectra, 1/N applied (DFT_NSPEC order), as store_wd_spectra
+            Real wr[DFT_TAB_W];
+            if (tab) load_record(wr, sp.tab_w + (long long)m2 * sp.tab_ws, 2 * S);
+            C acc[5];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
+#pragma unroll
+            for (int s = 0; s < DFT_MAXS; ++s) {
+                if (s >= S) break;
+                Real w0, j3;
+                if (tab) { w0 = wr[2 * s]; j3 = wr[2 * s + 1]; }
+                else fmt_weights<Real>(p.kmag, sp.R[s], &w0, &j3);
+                const Real Rs = sp.R[s];
+                acc[0] = cadd(acc[0], cscale(v[s], w0));
+                acc[1] = cadd(acc[1], cscale(v[s], Rs * w0));
+                acc[2] = cadd(acc[2], cscale(v[s], fourpi * Rs * Rs * w0));
+                acc[3] = cadd(acc[3], cscale(v[s], fourpi * Rs * Rs * Rs * j3));
+                acc[4] = cadd(acc[4], cscale(v[s], Rs * Rs * j3));       // w3 / (4 pi R)
+            }
+            store_wd_spectra<Real>(slot_n, int(g.nc), int(o), acc, sp.inv_n, p);
+        }
+        // the bulk-fluid/Poisson spectra
+        Real kr[DFT_TAB_K];
+        if (tab) load_record(kr, sp.tab_k + (long long)m2 * sp.tab_ks, Pn);
+        const Real inv_lap = inverse_laplacian<Real>(sp, g, p, kxi, kyi, kzi, hx, hy, hz);
+        C es[DFT_MAXS];
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s) {
+            if (s < S && p.zero) v[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
+            es[s] = cmake<C>(Real(0), Real(0));
+        }
+#pragma unroll
+        for (int j = 0; j < DFT_MAXS; ++j) {
+#pragma unroll
+            for (int i2 = 0; i2 <= j; ++i2) {
+                if (j >= S) continue;
+                Real K;
+                if (tab) {
+                    K = kr[dft_pair(i2, j)];
+                    if (!p.zero) K -= sp.pois[i2][j] * inv_lap;
+                } else {
+                    K = es_kernel<Real>(sp, i2, j, p, inv_lap, nullptr);
+                }
+                es[i2] = cadd(es[i2], cscale(v[j], K));
+                if (j != i2) es[j] = cadd(es[j], cscale(v[i2], K));
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < DFT_MAXS; ++s)
+            if (s < S) slot_es[(long long)s * g.nc + o] = es[s];
+    }
 }
 
 // ------------------------------------------------------------------------------------

@@ -229,8 +229,8 @@ cudaError_t LaunchY<Real, N>::yfft(cudaStream_t st, bool inv, const GridDesc& g,
             if (occ < 1) occ = 1;
         }
         const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-        if (inv) launch_k(dftk::k_yfft_tma<Real, true, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls);
-        else launch_k(dftk::k_yfft_tma<Real, false, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls);
+        if (inv) launch_k(dftk::k_yfft_tma<Real, true, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls, 1);
+        else launch_k(dftk::k_yfft_tma<Real, false, N, TY>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx, ntiles, status, tw, polls, 1);
         return cudaSuccess;
     } else {
         dim3 grid((unsigned)ceil_div(g.nxh, T), (unsigned)g.nz, (unsigned)ncomp);
@@ -260,12 +260,53 @@ cudaError_t LaunchZ<Real, N>::init() {
             if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, NB, MBB>)) != cudaSuccess) e = r;
         if constexpr ((TF * sizeof(typename Cplx<Real>::type)) % 16 == 0)
             if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, NF, MBF>)) != cudaSuccess) e = r;
+        constexpr int TY = dft_tile_y<Real>(N);
+        if ((r = set_max_smem(dftk::k_yfft_tma<Real, false, N, TY, true>)) != cudaSuccess) e = r;
+        if ((r = set_max_smem(dftk::k_yfft_tma<Real, true, N, TY, true>)) != cudaSuccess) e = r;
     } else {
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, false>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_fwd<Real, 0, 0, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_zconv_bwd<Real, 0, 0>)) != cudaSuccess) e = r;
     }
     return e;
+}
+
+template <typename Real, int N>
+cudaError_t LaunchZ<Real, N>::zfft(cudaStream_t st, bool inv, const GridDesc& g, int ncomp, C* data, int* status,
+                                   const C* tw, long long polls) {
+    if constexpr (N > 0) {
+        // the y pass's persistent TMA kernel along z: tiles of TY kx columns x nz at one ky
+        constexpr int TY = dft_tile_y<Real>(N);
+        constexpr int E = int(sizeof(C) / 8);
+        CUtensorMap map;
+        cudaError_t e = tma_encode_3d(&map, data, (unsigned long long)g.nxh * E, (unsigned long long)g.ny,
+                                      (unsigned long long)g.nz * ncomp, (unsigned long long)g.pxh * sizeof(C),
+                                      (unsigned long long)g.ny * g.pxh * sizeof(C), TY * E, 1, N);
+        if (e != cudaSuccess) return e;
+        const int ntx = (int)ceil_div(g.nxh, TY);
+        const int ntiles = ntx * g.ny * ncomp;
+        const size_t sm = dftk::yfft_tma_smem<Real, N, TY>();
+        static int per_sm[2] = {0, 0};
+        static int sms = 0;
+        int& occ = per_sm[inv ? 1 : 0];
+        if (occ == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (inv) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_yfft_tma<Real, true, N, TY, true>, dftk::kThreads, sm);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_yfft_tma<Real, false, N, TY, true>, dftk::kThreads, sm);
+            if (occ < 1) occ = 1;
+        }
+        const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
+        if (inv)
+            return launch_k(dftk::k_yfft_tma<Real, true, N, TY, true>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx,
+                            ntiles, status, tw, polls, g.ny);
+        return launch_k(dftk::k_yfft_tma<Real, false, N, TY, true>, grid, dftk::kThreads, sm, st, g.pdl, map, ntx,
+                        ntiles, status, tw, polls, g.ny);
+    } else {
+        (void)st; (void)inv; (void)g; (void)ncomp; (void)data; (void)status; (void)tw; (void)polls;
+        return cudaErrorNotSupported;
+    }
 }
 
 template <typename Real, int N>

@@ -143,6 +143,8 @@ struct LaunchZ {
                                       Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
                                       const C* esB, const C* tw);
     static bool has_zbwd_pair(const GridDesc& g, int ncomp_out);
+    static cudaError_t zfft(cudaStream_t st, bool inv, const GridDesc& g, int ncomp, C* data, int* status,
+                            const C* tw, long long polls);
 };
 
 template <typename Real>
@@ -178,6 +180,14 @@ struct Passes {
                                       Real kfy, Real kfz, int ncomp_out, const Ctl* ctl, C* phi, const C* esA,
                                       const C* esB, const C* tw);
     static bool has_zbwd_pair(const GridDesc& g, int ncomp_out);
+    // The split first-half z stage (compile-time lengths): zfft = the persistent TMA z transform
+    // of ncomp components in place (tiles of the y pass's width; cudaErrorNotSupported for other
+    // lengths), zmul = the k-space products from the S species spectra into the nine
+    // weighted-density spectra (slot_n, 1/N applied) and the S ES spectra (slot_es).
+    static cudaError_t zfft(cudaStream_t st, bool inv, const GridDesc& g, int ncomp, C* data, int* status,
+                            const C* tw, long long polls);
+    static cudaError_t zmul(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx, Real kfy,
+                            Real kfz, const C* in, C* slot_n, C* slot_es);
     // rho_lo (or nullptr): low part of an extended iterate rho0 + rho_lo, read
     // with rho0 and, when rho_out is written, replaced by the low part of the new iterate
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,

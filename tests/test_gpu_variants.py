@@ -4,7 +4,8 @@ The x passes run either as the compile-time kernels (the Phi' passes one CTA per
 persistent with bulk-copy or cp.async prefetch) or as the run-time ones under each candidate radix order
 (default, reversed, all-8 and all-4 plans); the y pass as the persistent TMA kernel or
 the run-time column kernel; the z passes as the persistent TMA kernels or the grouped
-one-tile-per-CTA ones.  Each combination is pinned with dft_set_variants and checked against the
+one-tile-per-CTA ones, the first half's z stage as one pass or three (z transforms around a
+k-space products pass).  Each combination is pinned with dft_set_variants and checked against the
 oracle's G (FP32 1e-5, FP64 1e-10), and one line-search step under a run-time x variant against
 the oracle's step; finally dft_autotune's own choice is checked the same way.
 """
@@ -74,7 +75,7 @@ def test_every_variant_matches_oracle(precision, shape):
     for x in xs:
         for xp in ((0, 1) if x == 0 else (0,)):
             for y in (0, 1):
-                for z in (0, 1):
+                for z in (0, 1, 2, 3):
                     plan.set_variants(x, y, z, x_persistent=xp)
                     g, _ = plan.picard_map(_dev(rho, plan), _dev(V, plan))
                     assert relerr(g.double().cpu().numpy(), g_ref) < TOL[precision], (x, xp, y, z, plan.tuning())
@@ -97,7 +98,7 @@ def test_line_search_steps_under_variants_fp64(which):
         g = F.picard_map(prob, ref, V)
     plan = binding.Plan(shape, prob.h, *SPECIES, precision="fp64")
     if which == "run-time":
-        plan.set_variants(_x_variants(plan)[-1], 1, 1)
+        plan.set_variants(_x_variants(plan)[-1], 1, 3)
     else:
         plan.set_variants(0, 0, 0, x_persistent=1 if which == "persistent-bulk" else 2)
     r, Vd = _dev(rho, plan), _dev(V, plan)
@@ -120,4 +121,28 @@ def test_autotuned_choice_matches_oracle(precision):
     assert desc.startswith("x: ") and "; y: " in desc and "; z: " in desc
     g, _ = plan.picard_map(rd, Vd)
     assert relerr(g.double().cpu().numpy(), F.picard_map(prob, rho, V)) < TOL[precision], desc
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape", [(64, 32, 48), (128, 16, 32)])
+def test_split_first_half_equals_the_single_pass(precision, shape):
+    # the three-pass first-half z stage (z transform, k-space products, z transform) runs the
+    # same butterflies and the same products per point as the single pass; the compiler may
+    # contract the products differently in the two kernels, so the weighted densities and G
+    # agree to rounding (a few ulp of the largest value), and with the oracle
+    from paper_0910_1531_gb300 import binding
+    prob, rho, V = _case(shape, (0.05, 0.06, 0.07), seed=53)
+    plan = binding.Plan(shape, prob.h, *SPECIES, precision=precision)
+    rd, Vd = _dev(rho, plan), _dev(V, plan)
+    out = []
+    for z in (0, 2):
+        plan.set_variants(0, 0, z)
+        n = plan.weighted_densities(rd)
+        g, _ = plan.picard_map(rd, Vd)
+        out.append((n, g))
+    close = {"fp32": 2e-6, "fp64": 1e-13}[precision]
+    for a in range(2):
+        assert relerr(out[1][a].double().cpu().numpy(), out[0][a].double().cpu().numpy()) < close, a
+    assert relerr(out[1][1].double().cpu().numpy(), F.picard_map(prob, rho, V)) < TOL[precision]
     plan.close()
