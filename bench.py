@@ -326,12 +326,16 @@ def batch_measure(args, world, steps, warmup):
     ws = workloads.batch_state_points(count=args.batch_count, seed=4)
     dt = torch.float64 if args.precision == "fp64" else torch.float32
     specs = [dict(shape=w.shape, h=w.h, radius=w.radius, valence=w.z, bulk_molar=w.bulk_molar) for w in ws]
-    rhos, Vs, byte_per_it = [], [], 0.0
+    rhos, Vs, byte_per_it, tunings = [], [], 0.0, {}
     for w in ws:
         plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision=args.precision)
         r = torch.tensor(w.initial_rho_nm3(plan.bulk()["rho"]), dtype=dt, device="cuda")
         V = torch.tensor(w.V, dtype=dt, device="cuda")
-        # algorithmic bytes of one line-search iteration of this state (profiled outside the graph)
+        # the state's autotuned variants (timed once per grid, then cached: the batch's plans below
+        # take the same), and the algorithmic bytes of one line-search iteration under them
+        # (profiled outside the graph)
+        plan.autotune(r, V, reps=3)
+        tunings[str(w.shape[0])] = plan.tuning()
         probe = r.clone()
         plan.iter_begin(probe, V)
         plan.profile_enable(True)
@@ -345,6 +349,7 @@ def batch_measure(args, world, steps, warmup):
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
     batch = binding.Batch(specs, precision=args.precision, stream=stream)
+    batch.autotune(rhos, Vs, reps=3)
     batch.begin(rhos, Vs)
     batch.iterate(warmup, -1.0, resid=False)
     torch.cuda.synchronize()
@@ -370,7 +375,7 @@ def batch_measure(args, world, steps, warmup):
                       "h_nm": 0.1, "c_molar": "log-uniform 0.01-1", "sphere_R_nm": "uniform 0.3-1.0", "seed": 4,
                       "step": "one line-search Picard iteration of every state (the K timed iterations of all "
                               "states: one launch of an on-device-loop CUDA graph)",
-                      "max_resid_after": float(np.max(resid))},
+                      "max_resid_after": float(np.max(resid)), "autotuned": tunings},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None, "kernel": "whole batched iteration", "peak_source": f"{peak_kind} hbm_gbs",
                         "algorithmic_bytes_per_step": byte_per_it}}

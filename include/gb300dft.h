@@ -314,6 +314,10 @@ dft_status dft_batch_create(const dft_params* params, int count, void* cuda_stre
 dft_status dft_batch_destroy(dft_batch* batch);
 const char* dft_batch_last_error(const dft_batch* batch);
 dft_status dft_batch_begin(dft_batch* batch, void* const* rho, const void* const* V);
+/* Autotune every state's plan (dft_autotune on rho[i], V[i], reps repetitions), one state at a
+ * time; states with the same grid, species count and precision share the cached choice.
+ * Synchronises the states' streams; a following dft_batch_begin is needed before iterating. */
+dft_status dft_batch_autotune(dft_batch* batch, void* const* rho, const void* const* V, int reps);
 dft_status dft_batch_iterate(dft_batch* batch, int iters, double alpha_or_neg, double* resid_out);
 
 /*

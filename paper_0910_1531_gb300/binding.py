@@ -79,6 +79,7 @@ SIGNATURES = {
     "dft_batch_destroy": (_I, [_P]),
     "dft_batch_last_error": (ctypes.c_char_p, [_P]),
     "dft_batch_begin": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "dft_batch_autotune": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I]),
     "dft_batch_iterate": (_I, [_P, _I, _D, _PD]),
     "dft_set_wait_polls": (_I, [_P, ctypes.c_longlong]),
     "dft_set_dependent_launch": (_I, [_P, _I]),
@@ -372,12 +373,23 @@ class Batch:
         if st != 0:
             raise DftError(st, self.lib.dft_batch_last_error(self.handle).decode())
 
-    def begin(self, rhos, Vs):
-        torch = self._torch
+    def _check_fields(self, rhos, Vs):
         for (nz, ny, nx, S), r, v in zip(self.states, rhos, Vs):
             for t in (r, v):
                 if t.device.type != "cuda" or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != S * nz * ny * nx:
                     raise ValueError("batch field has the wrong shape, dtype or device")
+
+    def autotune(self, rhos, Vs, reps=3):
+        """Autotune every state's plan on its fields (dft_batch_autotune); call begin afterwards."""
+        self._check_fields(rhos, Vs)
+        n = len(self.states)
+        rp = (_P * n)(*[r.data_ptr() for r in rhos])
+        vp = (_P * n)(*[v.data_ptr() for v in Vs])
+        self._check(self.lib.dft_batch_autotune(self.handle, rp, vp, int(reps)))
+
+    def begin(self, rhos, Vs):
+        torch = self._torch
+        self._check_fields(rhos, Vs)
         n = len(self.states)
         rp = (_P * n)(*[r.data_ptr() for r in rhos])
         vp = (_P * n)(*[v.data_ptr() for v in Vs])

@@ -1873,6 +1873,19 @@ dft_status dft_batch_begin(dft_batch* b, void* const* rho, const void* const* V)
     return DFT_OK;
 }
 
+dft_status dft_batch_autotune(dft_batch* b, void* const* rho, const void* const* V, int reps) {
+    if (!b || !rho || !V) return bfail(b, DFT_EINVAL, "NULL argument");
+    // each state's plan on its own fields, one state at a time (states of one grid share the
+    // cached choice); the begun iteration and its graph no longer apply
+    batch_release_graph(b);
+    b->begun = false;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        dft_status s = dft_autotune(b->plans[i], rho[i], V[i], reps, nullptr);
+        if (s != DFT_OK) return bfail(b, s, "state " + std::to_string(i) + ": " + b->plans[i]->err);
+    }
+    return DFT_OK;
+}
+
 dft_status dft_batch_iterate(dft_batch* b, int iters, double alpha_or_neg, double* resid_out) {
     if (!b || !b->begun) return bfail(b, DFT_EINVAL, "dft_batch_iterate needs a preceding dft_batch_begin");
     if (iters < 0) return bfail(b, DFT_EINVAL, "negative iteration count");

@@ -123,3 +123,40 @@ def test_dependent_launch_is_bitwise_neutral(precision):
         plan.close()
     assert torch.equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1] and np.isfinite(outs[1][1])
+
+
+def test_autotuned_batch_matches_autotuned_plans():
+    # dft_batch_autotune gives each state the autotuner's choice for its grid (cached per grid,
+    # species count and precision); the batch then advances every state exactly as an
+    # independently autotuned plan does
+    from paper_0910_1531_gb300 import binding
+    ws = _states()[:3]
+    dt = torch.float32
+    specs = [dict(shape=w.shape, h=w.h, radius=w.radius, valence=w.z, bulk_molar=w.bulk_molar) for w in ws]
+    fields = []
+    for w in ws:
+        probe = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32")
+        fields.append((torch.tensor(w.initial_rho_nm3(probe.bulk()["rho"]), dtype=dt, device="cuda"),
+                       torch.tensor(w.V, dtype=dt, device="cuda")))
+        probe.close()
+    refs = []
+    for w, (r0, V) in zip(ws, fields):
+        plan = binding.Plan(w.shape, w.h, w.radius, w.z, w.bulk_molar, precision="fp32")
+        plan.autotune(r0, V, reps=2)
+        r = r0.clone()
+        plan.iter_begin(r, V)
+        for _ in range(3):
+            plan.iter_step(r, V, -1.0, sync=False)
+        torch.cuda.synchronize()
+        refs.append(r)
+        plan.close()
+    batch = binding.Batch(specs, precision="fp32")
+    rhos = [r0.clone() for r0, _ in fields]
+    Vs = [V for _, V in fields]
+    batch.autotune(rhos, Vs, reps=2)
+    batch.begin(rhos, Vs)
+    batch.iterate(3, -1.0, resid=False)
+    torch.cuda.synchronize()
+    for a, b in zip(rhos, refs):
+        assert torch.equal(a, b)
+    batch.close()
