@@ -59,6 +59,9 @@ struct dft_plan {
     void* slotA = nullptr;
     void* slotB = nullptr;
     void* gbuf = nullptr;
+    // x half spectra of gbuf's G, written by the update pass that forms G in dft_iter_begin /
+    // dft_iter_step (nothing else writes it): the next iteration's first half starts from them
+    void* gspec = nullptr;
     void* rho_lo = nullptr;         // FP32 plans: low part of the extended iterate of dft_iter_*
     void* stage_rho = nullptr;
     void* stage_V = nullptr;
@@ -277,22 +280,26 @@ template <typename Real> struct Ops {
 
     // rho (S real fields) -> slot: ten weighted densities (kx, ky, z) and the S (+psi)
     // bulk-fluid / Poisson spectra (kx, ky, kz)
+    // pre (or nullptr): rho's x half spectra, already formed (the update pass that computed rho
+    // as G wrote them); the y and z passes then transform them in place
     static dft_status first_half(dft_plan* p, const Real* rho, void* slot, int want_psi,
-                                 double* red_energy = nullptr) {
+                                 double* red_energy = nullptr, C* pre = nullptr) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
-        LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, T1(p), tw(p, 0)));
-        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, T1(p), &p->ctl->status, tw(p, 1), p->wait_polls));
+        C* W = pre ? pre : T1(p);
+        if (!pre)
+            LAUNCH(p, K_XFWD, p->S * (RB(p) + CB(p)), P::xfwd(p->stream, p->g, p->ax, p->S, p->LX, rho, W, tw(p, 0)));
+        LAUNCH(p, K_YFFT, 2.0 * (p->S) * CB(p), P::yfft(p->stream, false, p->g, p->ay, p->Ty, p->S, W, &p->ctl->status, tw(p, 1), p->wait_polls));
         if (p->g.zsplit && dft_is_ct_size(p->g.nz) && !want_psi && !red_energy) {
             // z forward transform of the species, the k-space products, z inverse of the nine
             LAUNCH(p, K_ZFFT, 2.0 * p->S * CB(p),
-                   P::zfft(p->stream, false, p->g, p->S, T1(p), &p->ctl->status, tw(p, 2), p->wait_polls));
+                   P::zfft(p->stream, false, p->g, p->S, W, &p->ctl->status, tw(p, 2), p->wait_polls));
             LAUNCH(p, K_ZMUL, (p->S + DFT_NSPEC + p->S) * CB(p),
-                   P::zmul(p->stream, p->g, sp, kf(p, 0), kf(p, 1), kf(p, 2), T1(p), slot_n(slot), slot_es(p, slot)));
+                   P::zmul(p->stream, p->g, sp, kf(p, 0), kf(p, 1), kf(p, 2), W, slot_n(slot), slot_es(p, slot)));
             LAUNCH(p, K_ZFFT, 2.0 * DFT_NSPEC * CB(p),
                    P::zfft(p->stream, true, p->g, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 2), p->wait_polls));
         } else {
             LAUNCH(p, K_ZFWD, (p->S + DFT_NSPEC + p->S + want_psi) * CB(p),
-                   P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi, T1(p),
+                   P::zconv_fwd(p->stream, p->g, p->az, sp, p->Tz, kf(p, 0), kf(p, 1), kf(p, 2), want_psi, W,
                                 slot_n(slot), slot_es(p, slot), red_energy, tw(p, 2), &p->ctl->status));
         }
         LAUNCH(p, K_YFFT, 2.0 * (DFT_NSPEC) * CB(p), P::yfft(p->stream, true, p->g, p->ay, p->Ty, DFT_NSPEC, slot_n(slot), &p->ctl->status, tw(p, 1), p->wait_polls));
@@ -301,8 +308,10 @@ template <typename Real> struct Ops {
 
     // weighted densities mixed from slot A (and slot B) -> G at rho = w0 rho0 + w1 rho1
     // rho_lo (FP32 iterations, else nullptr): low part of the extended iterate rho0 + rho_lo
+    // gspec_out (or nullptr): G's x half spectra too (the next first half's input)
     static dft_status second_half(dft_plan* p, bool use_B, bool materialise, const Real* rho0, const Real* rho1,
-                                  const Real* V, Real* rho_out, Real* g_out, Real* rho_lo = nullptr) {
+                                  const Real* V, Real* rho_out, Real* g_out, Real* rho_lo = nullptr,
+                                  C* gspec_out = nullptr) {
         const SpeciesDesc<Real>& sp = species<Real>(p);
         C* A = slot_n(p->slotA);
         C* B = use_B ? slot_n(p->slotB) : nullptr;
@@ -324,10 +333,11 @@ template <typename Real> struct Ops {
             LAUNCH(p, K_FIN, p->blocks_x(p->LRupd) * DFT_MAXS * 8.0,
                    P::canon_scale(p->stream, p->ctl, sp, p->red_canon, (int)p->blocks_x(p->LRupd), p->g.pdl));
         }
-        LAUNCH(p, K_XUPD, p->S * (CB(p) + RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0) +
-                                            (rho_lo ? (rho_out ? 2 : 1) : 0))),
+        LAUNCH(p, K_XUPD, p->S * (CB(p) * (gspec_out ? 2 : 1) +
+                                  RB(p) * ((rho1 ? 2 : 1) + 1 + (rho_out ? 1 : 0) + (g_out ? 1 : 0) +
+                                           (rho_lo ? (rho_out ? 2 : 1) : 0))),
                P::xupdate(p->stream, p->g, p->ax, sp, p->LRupd, p->ctl, T1(p), rho0, rho1, V, rho_out,
-                                     g_out, rho_lo, p->red_sum, &p->ctl->status, tw(p, 0)));
+                          g_out, gspec_out, rho_lo, p->red_sum, &p->ctl->status, tw(p, 0)));
         return DFT_OK;
     }
 
@@ -431,6 +441,7 @@ dft_status reset_status(dft_plan* p) {
 // v_ready (optional): an event the second half (the first use of V) waits for
 template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const Real* V, cudaEvent_t v_ready = nullptr) {
     using O = Ops<Real>;
+    using C = typename Cplx<Real>::type;
     TRY(reset_status(p));
     // the extended iterate starts as the caller's rho with a zero low part
     if (p->rho_lo && cudaMemsetAsync(p->rho_lo, 0, size_t(p->S) * p->g.n * sizeof(Real), p->stream) != cudaSuccess)
@@ -439,7 +450,8 @@ template <typename Real> dft_status iter_begin_t(dft_plan* p, Real* rho, const R
     TRY(finalize(p, FIN_IDENTITY, 0, 0, -1.0));
     if (v_ready && cudaStreamWaitEvent(p->stream, v_ready, 0) != cudaSuccess)
         return fail(p, DFT_ECUDA, "stream wait");
-    TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, static_cast<Real*>(p->gbuf)));
+    TRY(O::second_half(p, false, false, rho, nullptr, V, nullptr, static_cast<Real*>(p->gbuf), nullptr,
+                       static_cast<C*>(p->gspec)));
     TRY(finalize(p, FIN_F0 | FIN_N3CUR, (int)p->blocks_x(p->LRupd), (int)p->blocks_x(p->LRphi), -1.0));
     p->iter_ready = true;
     p->iter_rho = rho;
@@ -451,7 +463,10 @@ template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Re
     using O = Ops<Real>;
     using C = typename Cplx<Real>::type;
     Real* g = static_cast<Real*>(p->gbuf);
-    TRY(O::first_half(p, g, p->slotB, 0));
+    C* gspec = static_cast<C*>(p->gspec);
+    // the first half of G's weighted densities starts from G's x spectra (written by the update
+    // pass that formed G: the previous step's accepted point, or dft_iter_begin)
+    TRY(O::first_half(p, g, p->slotB, 0, nullptr, gspec));
     int nb = 0;
     TRY(O::xinv(p, 1, O::slot_n(p->slotB) + 3 * p->g.nc, nullptr, nullptr, nullptr, 0, p->red_max, &nb));
     TRY(finalize(p, FIN_AMAX, 0, nb, alpha));
@@ -469,7 +484,7 @@ template <typename Real> dft_status iter_step_t(dft_plan* p, Real* rho, const Re
         TRY(O::second_half(p, true, false, rho, g, V, nullptr, nullptr, lo));
         TRY(finalize(p, FIN_F2_CHOOSE, nsum, 0, alpha));
     }
-    TRY(O::second_half(p, true, true, rho, g, V, rho, g, lo));
+    TRY(O::second_half(p, true, true, rho, g, V, rho, g, lo, gspec));
     TRY(finalize(p, FIN_ACCEPT, nsum, (int)p->blocks_x(p->LRphi), alpha));
     (void)sizeof(C);
     return DFT_OK;
@@ -978,7 +993,7 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
         }
         if (P::smem_x(p->g.nx, lpr_upd * L) <= size_t(optin)) {
             const float ms = time_it([&] {
-                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, nullptr, p->red_sum,
+                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, nullptr, nullptr, p->red_sum,
                            &p->ctl->status, O::tw(p, 0));
             });
             if (ms < best_ms[2]) { best_ms[2] = ms; best[2] = L; }
@@ -1316,6 +1331,7 @@ dft_status dft_plan_create(const dft_params* prm, void* cuda_stream, dft_plan** 
         {&p->slotA, slot_comps * g.nc * p->csize, "slot A"},
         {&p->slotB, slot_comps * g.nc * p->csize, "slot B"},
         {&p->gbuf, size_t(S) * g.n * p->rsize, "G buffer"},
+        {&p->gspec, size_t(S) * g.nc * p->csize, "G spectra"},
         // FP32 iterations carry the iterate as the caller's field plus this low part
         {f64 ? nullptr : &p->rho_lo, size_t(S) * g.n * p->rsize, "iterate low part"},
         {(void**)&p->red_sum, nred * sizeof(double), "reduction sums"},
@@ -1424,6 +1440,7 @@ dft_status dft_plan_destroy(dft_plan* p) {
     cudaFree(p->slotA);
     cudaFree(p->slotB);
     cudaFree(p->gbuf);
+    cudaFree(p->gspec);
     cudaFree(p->rho_lo);
     cudaFree(p->stage_rho);
     cudaFree(p->stage_V);

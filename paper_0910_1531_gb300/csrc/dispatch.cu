@@ -156,10 +156,10 @@ cudaError_t Passes<Real>::zmul(cudaStream_t st, const GridDesc& g, const Species
 template <typename Real>
 cudaError_t Passes<Real>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                            const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                           Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                           Real* rho_out, Real* g_out, C* gspec_out, Real* rho_lo, double* red_sum, int* status,
                            const C* tw) {
-    DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, status,
-                               tw))
+    DFT_SWITCH_X(g.nx, xupdate(st, g, px, sp, LR, ctl, cspec, rho0, rho1, V, rho_out, g_out, gspec_out, rho_lo,
+                               red_sum, status, tw))
 }
 
 template <typename Real>

@@ -2480,6 +2480,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                                                       const typename Cplx<Real>::type* __restrict__ cspec2,
                                                       const Real* rho0, const Real* rho1,
                                                       const Real* __restrict__ V, Real* rho_out, Real* g_out,
+                                                      typename Cplx<Real>::type* __restrict__ gspec_out,
                                                       Real* rho_lo, double* __restrict__ red_sum,
                                                       double* __restrict__ red_sum2, int* __restrict__ status,
                                                       const typename Cplx<Real>::type* __restrict__ twx) {
@@ -2587,13 +2588,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                 const long long o = (long long)s * g.n + row0 * NX + idx;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
-                    const C* Rl = R + (m * lpr * LR + r * lpr + s / 2) * pitch;
+                    C* Rl = R + (m * lpr * LR + r * lpr + s / 2) * pitch;
                     V16 orho, og, olo;
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
-                        const C pc = Rl[xo<NX>(x + e)];
-                        point(m, s, (s & 1) ? pc.y : pc.x, vel(a0[j], e), vel(a1[j], e), vel(av[j], e),
-                              vel(al[j], e), vel(orho, e), vel(olo, e), vel(og, e));
+                        // this species' half of the line (the other species of the line is another
+                        // item's); with gspec_out, G goes back into the same half
+                        Real* hp = reinterpret_cast<Real*>(Rl + xo<NX>(x + e)) + (s & 1);
+                        point(m, s, *hp, vel(a0[j], e), vel(a1[j], e), vel(av[j], e), vel(al[j], e), vel(orho, e),
+                              vel(olo, e), vel(og, e));
+                        if (NM == 1 && gspec_out) *hp = vel(og, e);
                     }
                     if (NM == 1 && rho_out) {
                         st16(rho_out + o, orho);
@@ -2636,9 +2640,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                     const long long o = (long long)s * g.n + pt;
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
-                        const C pr = R[(m * lpr * LR + r * lpr + s / 2) * pitch + xo<NX>(x)];
+                        Real* hp = reinterpret_cast<Real*>(R + (m * lpr * LR + r * lpr + s / 2) * pitch + xo<NX>(x)) +
+                                   (s & 1);
                         Real rho, lo, gval;
-                        point(m, s, (s & 1) ? pr.y : pr.x, r0[s], r1[s], vv[s], rl[s], rho, lo, gval);
+                        point(m, s, *hp, r0[s], r1[s], vv[s], rl[s], rho, lo, gval);
+                        if (NM == 1 && gspec_out) *hp = gval;
                         if (NM == 1 && rho_out) {
                             rho_out[o] = rho;
                             if (rho_lo) rho_lo[o] = lo;
@@ -2657,6 +2663,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
         }
     }
     if (bad) atomicOr(status, DEV_NONFINITE);
+    if (NM == 1 && gspec_out) {
+        // the x half spectra of the G rows just formed (the next first half's input): the lines
+        // now hold G in place of c1, two species per complex line
+        __syncthreads();
+        C* other = (R == A) ? B : A;
+        C* F = any_fft<NX, false, false, 0>(R, other, px, lines, 1, pitch, tw);
+        store_pair_rows<Real, NX>(g, lines, lpr, row0, nrows, S, F, gspec_out);
+    }
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         double bs;

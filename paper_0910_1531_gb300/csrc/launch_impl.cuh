@@ -121,12 +121,13 @@ cudaError_t LaunchX<Real, N>::xphi2(cudaStream_t st, const GridDesc& g, const Ax
 template <typename Real, int N>
 cudaError_t LaunchX<Real, N>::xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp,
                                int LR, const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1,
-                               const Real* V, Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum,
-                               int* status, const C* tw) {
+                               const Real* V, Real* rho_out, Real* g_out, C* gspec_out, Real* rho_lo,
+                               double* red_sum, int* status, const C* tw) {
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
     launch_k(dftk::k_xupdate<Real, N, 1>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, lpr * LR), st, g.pdl,
-        g, px, sp, LR, ctl, cspec, nullptr, rho0, rho1, V, rho_out, g_out, rho_lo, red_sum, nullptr, status, tw);
+        g, px, sp, LR, ctl, cspec, nullptr, rho0, rho1, V, rho_out, g_out, gspec_out, rho_lo, red_sum, nullptr,
+        status, tw);
     return cudaSuccess;
 }
 
@@ -138,7 +139,8 @@ cudaError_t LaunchX<Real, N>::xupdate2(cudaStream_t st, const GridDesc& g, const
     const unsigned blocks = (unsigned)ceil_div((long long)g.ny * g.nz, LR);
     const int lpr = (sp.S + 1) / 2;
     launch_k(dftk::k_xupdate<Real, N, 2>, blocks, dftk::kThreads, smem_x_of<C, N>(g.nx, 2 * lpr * LR), st, g.pdl,
-        g, px, sp, LR, ctl, cspec, cspec2, rho0, rho1, V, nullptr, nullptr, rho_lo, red_sum, red_sum2, status, tw);
+        g, px, sp, LR, ctl, cspec, cspec2, rho0, rho1, V, nullptr, nullptr, static_cast<C*>(nullptr), rho_lo,
+        red_sum, red_sum2, status, tw);
     return cudaSuccess;
 }
 

@@ -99,7 +99,7 @@ struct LaunchX {
                      const C* tw);
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                        Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                        Real* rho_out, Real* g_out, C* gspec_out, Real* rho_lo, double* red_sum, int* status,
                         const C* tw);
     // the two line-search samples in one pass each (weights from ctl[1] and ctl[2]): Phi' of
     // both mixtures of the slots (sample m's nine spectra at phi + m DFT_NSPEC nc), and the
@@ -189,10 +189,12 @@ struct Passes {
     static cudaError_t zmul(cudaStream_t st, const GridDesc& g, const SpeciesDesc<Real>& sp, Real kfx, Real kfy,
                             Real kfz, const C* in, C* slot_n, C* slot_es);
     // rho_lo (or nullptr): low part of an extended iterate rho0 + rho_lo, read
-    // with rho0 and, when rho_out is written, replaced by the low part of the new iterate
+    // with rho0 and, when rho_out is written, replaced by the low part of the new iterate;
+    // gspec_out (or nullptr): also the x half spectra of G (S components, the layout of xfwd's
+    // output), the next first half's input
     static cudaError_t xupdate(cudaStream_t st, const GridDesc& g, const AxisPlan& px, const SpeciesDesc<Real>& sp, int LR,
                         const Ctl* ctl, const C* cspec, const Real* rho0, const Real* rho1, const Real* V,
-                        Real* rho_out, Real* g_out, Real* rho_lo, double* red_sum, int* status,
+                        Real* rho_out, Real* g_out, C* gspec_out, Real* rho_lo, double* red_sum, int* status,
                         const C* tw);
     // the two line-search samples in one pass each (weights from ctl[1] and ctl[2]): Phi' of
     // both mixtures of the slots (sample m's nine spectra at phi + m DFT_NSPEC nc), and the
