@@ -43,13 +43,13 @@ KERNELS = ("xfwd", "yfft", "zconv_fwd", "xphi", "zconv_bwd", "xupdate", "xinv", 
 #       --nvtx --nvtx-include 'profiled_steps/' -k regex:^<kernel>$ -s <skip> -c <launches> --csv
 #       python bench.py [--workload pore256 --converge-tol 0] --no-extra --no-cpu-baseline --no-cufft
 #       --steps 2 --warmup 3 --e2e-steps 1
-# per workload and precision (the pore: its three largest passes); valid while the kernel
-# sources and build flags hash to `digest`.
+# per workload and precision (the kinds the autotuned iteration ran when captured); valid
+# while the kernel sources and build flags hash to `digest`.
 NCU_TRAFFIC = {
-    "digest": "2f9d5464f362bceb",
+    "digest": "f79850a227c6bdac",
     "captures": {
-        "3species_16obstacles_128^3/fp32": {"xfwd": 25331456, "yfft": 91751467, "zconv_fwd": 78500096, "xphi": 261333504, "zconv_bwd": 187939584, "xupdate": 151247744, "xinv": 8711936, "finalize": 66560},
-        "pore_slab_4species_256^3/fp32": {"zconv_fwd": 1151653120, "xphi": 2413470464, "zconv_bwd": 1698084352},
+        "3species_16obstacles_128^3/fp32": {"yfft": 91782613, "zconv_fwd": 78983424, "xphi": 261382784, "zconv_bwd": 187985408, "xupdate": 164625152, "xinv": 8711936, "finalize": 68437},
+        "pore_slab_4species_256^3/fp32": {"xphi": 2413688576, "zconv_bwd": 1723225344, "zmul": 1138373632, "yfft": 828222272, "zfft": 826826880},
     },
 }
 
