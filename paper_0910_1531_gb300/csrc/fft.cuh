@@ -229,12 +229,49 @@ __host__ __device__ constexpr int ct_row_pitch(int n) {
 
 // One stage.  COLS: lines are tile columns (element e of line l at e*T + l, line index fastest
 // across threads); otherwise lines are rows (element e of line l at e + l*ls, e fastest).
+// Rows: the padded position ct_xpad(a + r s) of the r-th element a butterfly touches splits
+// into a per-thread part and a compile-time part when s is a multiple of 16 (then (a + r s) >> 4
+// = (a >> 4) + r s / 16), or when every a + r s stays inside one block of 16 positions past a
+// multiple of 16 (loads: a < M, 16 % M == 0; stores: NS R == 16).  The butterfly then addresses
+// its elements at one base pointer plus constants.
+template <int M, int R> __host__ __device__ constexpr bool ct_split_loads() { return M % 16 == 0 || 16 % M == 0; }
+template <int NS, int R> __host__ __device__ constexpr bool ct_split_stores() { return NS % 16 == 0 || NS * R == 16; }
+
 template <int N, int R, int NS, bool INV, bool COLS, int T, typename C>
 __device__ __forceinline__ void ct_stage(const C* __restrict__ src, C* __restrict__ dst, int lines, int ls,
                                          const C* __restrict__ tw) {
     constexpr int M = N / R;
     constexpr int TWSTEP = N / (NS * R);
     const int total = COLS ? M * T : M * lines;
+    if constexpr (!COLS && ct_split_loads<M, R>() && ct_split_stores<NS, R>()) {
+#pragma unroll 2
+        for (int task = threadIdx.x; task < total; task += kFftThreads) {
+            const int j = task % M, line = task / M;
+            const int k = j % NS;
+            // loads: element j + r M at pad(j) + r (M + M / 16) (M a multiple of 16), or at
+            // j + pad(r M) (j < M <= 16, 16 % M == 0)
+            const C* s0 = src + line * ls + (M % 16 == 0 ? ct_xpad(j) : j);
+            C v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s0[M % 16 == 0 ? r * (M + M / 16) : ct_xpad(r * M)];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[k * r * TWSTEP];
+                    if (INV) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            dft_small<R, INV>(v);
+            // stores: element b + r NS, b = (j / NS) NS R + k, at pad(b) + r (NS + NS / 16) (NS a
+            // multiple of 16), or at b + b / 16 + r NS (NS R = 16: b a multiple of 16 plus k < NS)
+            const int b = (j / NS) * (NS * R) + k;
+            C* d0 = dst + line * ls + ct_xpad(b);
+#pragma unroll
+            for (int r = 0; r < R; ++r) d0[NS % 16 == 0 ? r * (NS + NS / 16) : r * NS] = v[r];
+        }
+        return;
+    }
 #pragma unroll 2
     for (int task = threadIdx.x; task < total; task += kFftThreads) {
         int line, j;
