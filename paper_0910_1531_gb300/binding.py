@@ -388,7 +388,6 @@ class Batch:
         self._check(self.lib.dft_batch_autotune(self.handle, rp, vp, int(reps)))
 
     def begin(self, rhos, Vs):
-        torch = self._torch
         self._check_fields(rhos, Vs)
         n = len(self.states)
         rp = (_P * n)(*[r.data_ptr() for r in rhos])

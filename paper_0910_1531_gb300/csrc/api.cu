@@ -993,8 +993,9 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
         }
         if (P::smem_x(p->g.nx, lpr_upd * L) <= size_t(optin)) {
             const float ms = time_it([&] {
-                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr, nullptr, nullptr, p->red_sum,
-                           &p->ctl->status, O::tw(p, 0));
+                // as in the iteration: the accepted point's pass also writes G's x spectra
+                P::xupdate(p->stream, p->g, p->ax, sp, L, p->ctl, O::T1(p), rho, rho, V, nullptr, nullptr,
+                           static_cast<C*>(p->gspec), nullptr, p->red_sum, &p->ctl->status, O::tw(p, 0));
             });
             if (ms < best_ms[2]) { best_ms[2] = ms; best[2] = L; }
         }
