@@ -346,12 +346,29 @@ __host__ __device__ constexpr int ct_gstride(int n, int T, int csize) {
     return (ct_gtile(n, T) + 128 / csize - 1) / (128 / csize) * (128 / csize);
 }
 
-template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, typename C>
+// FOLD (a first stage only): the inputs of groups 3 and 4 are taken as group g - i kf.x group
+// fold_partner(g) -- the y derivatives of the back convolution added before a z transform, where
+// the wave number k_y is one constant per tile (kf.x = 0 leaves the groups as they are).
+__host__ __device__ constexpr int fold_partner(int g) { return g == 4 ? 7 : 8; }
+
+template <bool FOLD, int T, bool SD, int GSTR, typename C>
+__device__ __forceinline__ void fold_input(C& v, const C* __restrict__ src, int e, int g, int off, C kf) {
+    if constexpr (FOLD) {
+        if ((g == 3 || g == 4) && kf.x != decltype(kf.x)(0)) {
+            const C u = src[(SD ? e * T : ct_gpos(e, T)) + off + (fold_partner(g) - g) * GSTR];
+            v.x += kf.x * u.y;
+            v.y -= kf.x * u.x;
+        }
+    }
+}
+
+template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, bool FOLD = false, typename C>
 __device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* __restrict__ dst, int groups,
-                                                 const C* __restrict__ tw) {
+                                                 const C* __restrict__ tw, C kf = C{}) {
     constexpr int M = N / R;
     constexpr int TWSTEP = N / (NS * R);
     constexpr int PERG = M * T;
+    static_assert(!FOLD || NS == 1, "the fold belongs to a first stage");
     const int total = PERG * groups;
     for (int task = threadIdx.x; task < total; task += NT) {
         const int g = task / PERG;
@@ -364,6 +381,7 @@ __device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* _
         for (int r = 0; r < R; ++r) {
             const int e = j + r * M;
             v[r] = src[(SD ? e * T : ct_gpos(e, T)) + off];
+            fold_input<FOLD, T, SD, GSTR>(v[r], src, e, g, off, kf);
         }
         if constexpr (NS > 1) {
 #pragma unroll
@@ -383,13 +401,13 @@ __device__ __forceinline__ void ct_stage_grouped(const C* __restrict__ src, C* _
     }
 }
 
-template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, typename C>
-__device__ __forceinline__ void ct_stages_grouped(C*& a, C*& b, int groups, const C* tw) {
+template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, bool FOLD = false, typename C>
+__device__ __forceinline__ void ct_stages_grouped(C*& a, C*& b, int groups, const C* tw, C kf = C{}) {
     if constexpr (S < ct_nstages(N)) {
         constexpr int R = ct_radix_at(N, S);
         constexpr int NS = ct_ns_at(N, S);
         constexpr bool last = (S + 1 == ct_nstages(N));
-        ct_stage_grouped<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT>(a, b, groups, tw);
+        ct_stage_grouped<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT, FOLD && S == 0>(a, b, groups, tw, kf);
         __syncthreads();
         C* t = a; a = b; b = t;
         ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, S + 1>(a, b, groups, tw);
@@ -397,10 +415,11 @@ __device__ __forceinline__ void ct_stages_grouped(C*& a, C*& b, int groups, cons
 }
 
 // Transform `groups` tiles held in a (b: scratch of the same size); the caller syncs before;
-// returns the buffer holding the result (synced).
-template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads, typename C>
-__device__ __forceinline__ C* ct_fft_grouped(C* a, C* b, int groups, const C* tw) {
-    ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, 0>(a, b, groups, tw);
+// returns the buffer holding the result (synced).  FOLD: see ct_stage_grouped (kf.x = k_y).
+template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads,
+          bool FOLD = false, typename C>
+__device__ __forceinline__ C* ct_fft_grouped(C* a, C* b, int groups, const C* tw, C kf = C{}) {
+    ct_stages_grouped<N, INV, T, GSTR, SD, DD, NT, 0, FOLD>(a, b, groups, tw, kf);
     return a;
 }
 
@@ -418,8 +437,9 @@ __device__ __forceinline__ void bar_sync_first(int count) {
     asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
 }
 
-template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, bool END_SYNC, typename C>
-__device__ __forceinline__ void ct_stage_grouped_ip(C* buf, int groups, const C* __restrict__ tw) {
+template <int N, int R, int NS, bool INV, int T, int GSTR, bool SD, bool DD, int NT, bool END_SYNC, bool FOLD = false,
+          typename C>
+__device__ __forceinline__ void ct_stage_grouped_ip(C* buf, int groups, const C* __restrict__ tw, C kf = C{}) {
     constexpr int M = N / R;
     constexpr int TWSTEP = N / (NS * R);
     constexpr int PERG = M * T;
@@ -442,12 +462,15 @@ __device__ __forceinline__ void ct_stage_grouped_ip(C* buf, int groups, const C*
         const int nthr = (ng * PERG + 31) & ~31;
         if (tid < nthr) {
             const bool act = gl < ng;
-            const int off = (g0 + (act ? gl : 0)) * GSTR + t;
+            const int g = g0 + (act ? gl : 0);
+            const int off = g * GSTR + t;
             C v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int e = j + r * M;
                 v[r] = buf[(SD ? e * T : ct_gpos(e, T)) + off];
+                // the fold's partner groups lie past the transformed ones: never written here
+                fold_input<FOLD, T, SD, GSTR>(v[r], buf, e, g, off, kf);
             }
             if constexpr (NS > 1) {
 #pragma unroll
@@ -471,19 +494,22 @@ __device__ __forceinline__ void ct_stage_grouped_ip(C* buf, int groups, const C*
     if constexpr (END_SYNC) __syncthreads();
 }
 
-template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, typename C>
-__device__ __forceinline__ void ct_stages_grouped_ip(C* a, int groups, const C* tw) {
+template <int N, bool INV, int T, int GSTR, bool SD, bool DD, int NT, int S, bool FOLD = false, typename C>
+__device__ __forceinline__ void ct_stages_grouped_ip(C* a, int groups, const C* tw, C kf = C{}) {
     if constexpr (S < ct_nstages(N)) {
         constexpr int R = ct_radix_at(N, S);
         constexpr int NS = ct_ns_at(N, S);
         constexpr bool last = (S + 1 == ct_nstages(N));
-        ct_stage_grouped_ip<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT, !last>(a, groups, tw);
+        ct_stage_grouped_ip<N, R, NS, INV, T, GSTR, SD && S == 0, DD && last, NT, !last, FOLD && S == 0>(a, groups,
+                                                                                                       tw, kf);
         ct_stages_grouped_ip<N, INV, T, GSTR, SD, DD, NT, S + 1>(a, groups, tw);
     }
 }
 
-// Transform `groups` tiles held in a, in place; the caller syncs before and after.
-template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads, typename C>
-__device__ __forceinline__ void ct_fft_grouped_ip(C* a, int groups, const C* tw) {
-    ct_stages_grouped_ip<N, INV, T, GSTR, SD, DD, NT, 0>(a, groups, tw);
+// Transform `groups` tiles held in a, in place; the caller syncs before and after.  FOLD: see
+// ct_stage_grouped (the partner groups must lie at or past `groups`).
+template <int N, bool INV, int T, int GSTR, bool SD = false, bool DD = false, int NT = kFftThreads,
+          bool FOLD = false, typename C>
+__device__ __forceinline__ void ct_fft_grouped_ip(C* a, int groups, const C* tw, C kf = C{}) {
+    ct_stages_grouped_ip<N, INV, T, GSTR, SD, DD, NT, 0, FOLD>(a, groups, tw, kf);
 }

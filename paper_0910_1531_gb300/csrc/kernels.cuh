@@ -695,6 +695,58 @@ __device__ __forceinline__ void bwd_sums(const typename Cplx<Real>::type* X, int
     }
 }
 
+// The persistent TMA z passes transform seven of the nine spectra: the y-derivative spectra
+// (components 5 and 7: i k_y m and i k_y n3, or their Phi' counterparts) differ from the m and n3
+// spectra by the factor i k_y, which is one constant per z tile, so it is applied on the tile
+// (after the first half's z inverse, before the second half's z forward) instead of transforming
+// them.  In a tile's shared memory, component c sits at group zgroup(c): the seven transformed
+// spectra first (0..4, then i k_z m, i k_z n3), the two y-derivative spectra at 7 and 8 (the
+// fold partners of groups 4 and 3).
+constexpr int kZGroups = 7;
+__host__ __device__ constexpr int zgroup(int c) { return c < 5 ? c : (c == 5 ? 7 : c == 6 ? 5 : c == 7 ? 8 : 6); }
+
+// bwd_sums on the seven transformed groups, the y derivatives already folded into groups 3 and 4
+// (a3 = B3 - i k_y Phi_V2y, a4 = B4 - i k_y Phi_V1y): the z derivatives remain.
+template <typename Real>
+__device__ __forceinline__ void bwd_sums_folded(const typename Cplx<Real>::type* X, int GS, int pos,
+                                                const KPoint<Real>& p, typename Cplx<Real>::type* a) {
+    using C = typename Cplx<Real>::type;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) a[q] = X[q * GS + pos];
+    if (!p.nyq_z) {
+        const C u1 = X[zgroup(6) * GS + pos], u2 = X[zgroup(8) * GS + pos];
+        a[4] = cadd(a[4], cmake<C>(p.kz * u1.y, -p.kz * u1.x));
+        a[3] = cadd(a[3], cmake<C>(p.kz * u2.y, -p.kz * u2.x));
+    }
+}
+
+// store_wd_spectra without the y derivatives: groups 0..4 and i k_z m, i k_z n3 at zgroup(6),
+// zgroup(8); the z inverse transforms these seven and zfwd_add_y_derivatives forms the other two.
+template <typename Real>
+__device__ __forceinline__ void store_wd_spectra_z(typename Cplx<Real>::type* O, int GS, int pos,
+                                                   const typename Cplx<Real>::type* acc, Real inv_n,
+                                                   const KPoint<Real>& p) {
+    using C = typename Cplx<Real>::type;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) O[a * GS + pos] = cscale(acc[a], inv_n);
+    const C m = cscale(acc[4], inv_n), n3 = cscale(acc[3], inv_n);
+    const C zero = cmake<C>(Real(0), Real(0));
+    O[zgroup(6) * GS + pos] = p.nyq_z ? zero : cmake<C>(-p.kz * m.y, p.kz * m.x);
+    O[zgroup(8) * GS + pos] = p.nyq_z ? zero : cmake<C>(-p.kz * n3.y, p.kz * n3.x);
+}
+
+// After the first half's z inverse (dense tiles, TILE elements per group): the y-derivative
+// spectra i k_y m -> zgroup(5), i k_y n3 -> zgroup(7), zero on the Nyquist index of y.
+template <typename Real, int TILE, int NT>
+__device__ __forceinline__ void zfwd_add_y_derivatives(typename Cplx<Real>::type* Q, int GS, Real ky) {
+    using C = typename Cplx<Real>::type;
+    for (int idx = threadIdx.x; idx < 2 * TILE; idx += NT) {
+        const int h = idx / TILE, e = idx - h * TILE;
+        const C u = Q[(h ? 3 : 4) * GS + e];
+        Q[(h ? zgroup(7) : zgroup(5)) * GS + e] = cmake<C>(-ky * u.y, ky * u.x);
+    }
+}
+
 template <int TT, int NN> __host__ __device__ constexpr size_t zg_smem_bytes(size_t csize) {
     return (size_t(NN) + 2 * size_t(DFT_NSPEC) * ct_gstride(NN, TT, int(csize))) * csize + 16;
 }
@@ -1231,8 +1283,8 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                     slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
                 }
             }
-            // the nine weighted-density spectra, 1/N applied (DFT_NSPEC order)
-            store_wd_spectra<Real>(W, GS, pos, acc, sp.inv_n, p);
+            // the weighted-density spectra but the y derivatives, 1/N applied
+            store_wd_spectra_z<Real>(W, GS, pos, acc, sp.inv_n, p);
         }
         __syncthreads();
         // the stage is free now: refill it with the tile after next while the inverse runs
@@ -1240,11 +1292,13 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
             const int next = tile + 2 * gridDim.x;
             if (next < ntiles) { issue(next, cur); issued += 1 << (16 * cur); }
         }
-        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(W, Vb, DFT_NSPEC, tw);
+        C* Q = ct_fft_grouped<NZ, true, TZ, GS, false, true, NT>(W, Vb, kZGroups, tw);
+        const bool nyq_y = (ny % 2 == 0) && (2 * kyi == ny);
+        zfwd_add_y_derivatives<Real, TILE, NT>(Q, GS, nyq_y ? Real(0) : kval<Real>(kyi, ny, kfy));
         tma::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int a = 0; a < DFT_NSPEC; ++a) tma::store_3d(&map_n, kx0 * E, kyi, a * NZ, Q + a * GS);
+            for (int a = 0; a < DFT_NSPEC; ++a) tma::store_3d(&map_n, kx0 * E, kyi, a * NZ, Q + zgroup(a) * GS);
             tma::commit();
         }
     }
@@ -1416,7 +1470,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
         tma::mbar_expect_tx(&bar[s], uint32_t(DFT_NSPEC) * BOX);
         for (int c = 0; c < DFT_NSPEC; ++c)
-            tma::load_3d(st + c * GS, &map_phi, x, y, (m * DFT_NSPEC + c) * NZ, &bar[s]);
+            tma::load_3d(st + zgroup(c) * GS, &map_phi, x, y, (m * DFT_NSPEC + c) * NZ, &bar[s]);
     };
     auto issue_es = [&](int tile) {
         const int x = (tile % ntiles_x) * TZ * E, y = tile / ntiles_x;
@@ -1479,8 +1533,12 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
             const bool ok = tma::mbar_wait(&bar[cur], (it >> 1) & 1);
             if (__syncthreads_or(!ok)) { drain(); break; }
             if (threadIdx.x == 0) consumed += 1 << (16 * cur);
-            if constexpr (IP) ct_fft_grouped_ip<NZ, false, TZ, GS, true, false, NT>(X, DFT_NSPEC, tw);
-            else X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT>(st, W, DFT_NSPEC, tw);
+            // the y derivatives folded into groups 3 and 4 on the way into the first stage: seven
+            // groups transformed
+            const bool nyq_y = (ny % 2 == 0) && (2 * kyi == ny);
+            const C kf = cmake<C>(nyq_y ? Real(0) : kval<Real>(kyi, ny, kfy), Real(0));
+            if constexpr (IP) ct_fft_grouped_ip<NZ, false, TZ, GS, true, false, NT, true>(X, kZGroups, tw, kf);
+            else X = ct_fft_grouped<NZ, false, TZ, GS, true, false, NT, true>(st, W, kZGroups, tw, kf);
         }
         // the ES tiles of this tile (loaded since the previous tile's pointwise phase; a pair's
         // second item reuses them); the barrier also ends the forward transform
@@ -1516,7 +1574,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
                                 2 * S);
                 const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
                 C asum[5];
-                bwd_sums<Real>(X, GS, pos, p, asum);
+                bwd_sums_folded<Real>(X, GS, pos, p, asum);
                 const C a0 = asum[0], a1 = asum[1], a2 = asum[2], a3 = asum[3], a4 = asum[4];
 #pragma unroll
                 for (int s = 0; s < DFT_MAXS; ++s) {
