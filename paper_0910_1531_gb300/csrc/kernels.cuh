@@ -1694,7 +1694,10 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
     const Real fiD2 = fiD * fiD, fiD3 = fiD2 * fiD;
     const Real q = v2x * v2x + v2y * v2y + v2z * v2z;
     const Real dot = v1x * v2x + v1y * v2y + v1z * v2z;
-    const Real pi = Real(CUDART_PI);
+    // the constant denominators as products with their reciprocals (rounded once, from double)
+    const Real i4pi = Real(1.0 / (4.0 * CUDART_PI)), i8pi = Real(1.0 / (8.0 * CUDART_PI));
+    const Real i12pi = Real(1.0 / (12.0 * CUDART_PI)), i24pi = Real(1.0 / (24.0 * CUDART_PI));
+    const Real i36pi = Real(1.0 / (36.0 * CUDART_PI));
     n[0] = -lnD;
     n[1] = n2 * fiD;
     n[4] = -v2x * fiD;
@@ -1703,13 +1706,13 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
     if (kind != DFT_PHI_RSLT) {
         Real f, df;
         if (kind == DFT_PHI_ROSENFELD) {
-            f = fiD2 / (Real(24) * pi);
-            df = fiD3 / (Real(12) * pi);
+            f = fiD2 * i24pi;
+            df = fiD3 * i12pi;
         } else {
             Real g, dg;
             wb_g<Real>(n3, lnD_hi, &g, &dg);
-            f = g * fiD2 / (Real(36) * pi);
-            df = (dg * fiD2 + Real(2) * g * fiD3) / (Real(36) * pi);
+            f = g * fiD2 * i36pi;
+            df = (dg * fiD2 + Real(2) * g * fiD3) * i36pi;
         }
         const Real T = n2 * n2 * n2 - Real(3) * n2 * q;
         const Real c6 = Real(6) * n2 * f;
@@ -1723,9 +1726,9 @@ template <typename Real> __device__ __forceinline__ bool phi_derivatives(Real* n
     Real xi = (n2 > Real(1e-30)) ? q / (n2 * n2) : Real(1);
     xi = xi < Real(0) ? Real(0) : (xi > Real(1) ? Real(1) : xi);
     const Real om = Real(1) - xi;
-    n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 / (Real(8) * pi);
-    n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 / (Real(12) * pi);
-    const Real cv = n2 * om * om * fiD2 / (Real(4) * pi);
+    n[2] = n1 * fiD + n2 * n2 * om * om * (Real(1) + xi) * fiD2 * i8pi;
+    n[3] = n0 * fiD + (n1 * n2 - dot) * fiD2 + n2 * n2 * n2 * om * om * om * fiD3 * i12pi;
+    const Real cv = n2 * om * om * fiD2 * i4pi;
     n[7] = -v1x * fiD - cv * v2x;
     n[8] = -v1y * fiD - cv * v2y;
     n[9] = -v1z * fiD - cv * v2z;
@@ -1820,34 +1823,48 @@ __device__ __forceinline__ void load_pair_rows(const GridDesc& g, int lines, int
 }
 
 // The S species' half rows of `rows` grid rows as ceil(S/2) complex lines each (species 2l and
-// 2l + 1 in line l), one thread per (row, k) with all its loads issued first.
-template <typename Real, int NX>
+// 2l + 1 in line l of a row's lines), for NM sets of spectra (spec, then spec2 into the lines
+// after the first set's).  Items are (set, line, k), k fastest; each thread issues the loads of
+// kBatch items before any store, so that they are in flight together.
+template <typename Real, int NX, int NM = 1>
 __device__ __forceinline__ void load_species_rows(const GridDesc& g, int rows, long long row0, long long nrows, int S,
                                                   const typename Cplx<Real>::type* __restrict__ spec,
+                                                  const typename Cplx<Real>::type* __restrict__ spec2,
                                                   typename Cplx<Real>::type* dst) {
     using C = typename Cplx<Real>::type;
+    constexpr int kBatch = 4;
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
     const int lpr = (S + 1) / 2;
-    for (int idx = threadIdx.x; idx < rows * nxh; idx += blockDim.x) {
-        const int r = idx / nxh, k = idx - (idx / nxh) * nxh;
-        const long long row = row0 + r;
-        const bool live = row < nrows;
-        const long long o = row * g.pxh + k;
-        C v[DFT_MAXS + 1];
+    const int lines = rows * lpr;                 // lines of one set
+    const int total = NM * lines * nxh;
+    for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
+        C av[kBatch], bv[kBatch];
 #pragma unroll
-        for (int c = 0; c < DFT_MAXS + 1; ++c) {
-            v[c] = cmake<C>(Real(0), Real(0));
-            if (live && c < S) v[c] = spec[(long long)c * g.nc + o];
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            const int ml = idx / nxh, k = idx - (idx / nxh) * nxh;
+            const int m = NM == 1 ? 0 : ml / lines, l = ml - m * lines;
+            const long long row = row0 + l / lpr;
+            const int ca = 2 * (l % lpr), cb = ca + 1;
+            const C* src = (NM == 2 && m == 1) ? spec2 : spec;
+            const long long o = row * g.pxh + k;
+            av[j] = bv[j] = cmake<C>(Real(0), Real(0));
+            if (idx < total && row < nrows) {
+                av[j] = src[(long long)ca * g.nc + o];
+                if (cb < S) bv[j] = src[(long long)cb * g.nc + o];
+            }
         }
-        const bool edge = k == 0 || (even && 2 * k == nx);
 #pragma unroll
-        for (int l = 0; l < (DFT_MAXS + 1) / 2; ++l) {
-            if (l >= lpr) break;
-            C a = v[2 * l], b = v[2 * l + 1];
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            if (idx >= total) continue;
+            const int ml = idx / nxh, k = idx - (idx / nxh) * nxh;
+            C a = av[j], b = bv[j];
+            const bool edge = k == 0 || (even && 2 * k == nx);
             if (edge) { a.y = Real(0); b.y = Real(0); }
-            dst[(r * lpr + l) * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
-            if (!edge) dst[(r * lpr + l) * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+            dst[ml * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (!edge) dst[ml * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
         }
     }
 }
@@ -1862,16 +1879,33 @@ __device__ __forceinline__ void load_row_pairs(const GridDesc& g, int rows, long
     const int nx = NX > 0 ? NX : g.nx, nxh = nx / 2 + 1, pitch = NX > 0 ? ct_row_pitch(NX) : nx + 1;
     const bool even = (nx % 2) == 0;
     const int lines = (rows + 1) / 2;
-    for (int idx = threadIdx.x; idx < lines * nxh; idx += blockDim.x) {
-        const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
-        const int ra = 2 * l, rb = 2 * l + 1;
-        C a = cmake<C>(Real(0), Real(0)), b = a;
-        if (row0 + ra < nrows) a = spec[(row0 + ra) * g.pxh + k];
-        if (rb < rows && row0 + rb < nrows) b = spec[(row0 + rb) * g.pxh + k];
-        const bool edge = k == 0 || (even && 2 * k == nx);
-        if (edge) { a.y = Real(0); b.y = Real(0); }
-        dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
-        if (!edge) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+    const int total = lines * nxh;
+    // the loads of kBatch items per thread in flight together
+    constexpr int kBatch = 4;
+    for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
+        C av[kBatch], bv[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+            const int ra = 2 * l, rb = 2 * l + 1;
+            av[j] = bv[j] = cmake<C>(Real(0), Real(0));
+            if (idx < total) {
+                if (row0 + ra < nrows) av[j] = spec[(row0 + ra) * g.pxh + k];
+                if (rb < rows && row0 + rb < nrows) bv[j] = spec[(row0 + rb) * g.pxh + k];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const int idx = base + j * kThreads;
+            if (idx >= total) continue;
+            const int l = idx / nxh, k = idx - (idx / nxh) * nxh;
+            C a = av[j], b = bv[j];
+            const bool edge = k == 0 || (even && 2 * k == nx);
+            if (edge) { a.y = Real(0); b.y = Real(0); }
+            dst[l * pitch + xo<NX>(k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (!edge) dst[l * pitch + xo<NX>(nx - k)] = cmake<C>(a.x + b.y, b.x - a.y);
+        }
     }
 }
 
@@ -2556,8 +2590,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
     for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twx[i];
     const long long nrows = (long long)g.ny * g.nz;
     const long long row0 = (long long)blockIdx.x * LR;
-    load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec, A);
-    if constexpr (NM == 2) load_species_rows<Real, NX>(g, LR, row0, nrows, S, cspec2, A + lpr * LR * pitch);
+    load_species_rows<Real, NX, NM>(g, LR, row0, nrows, S, cspec, cspec2, A);
     const int total = LR * nx;
     // G_i = pref_i exp(mu0_i - V_i + c_i): the bath (rho_b, beta mu_HS,b), or for a
     // fixed-number species the normalisation of this evaluation and no bath constant
