@@ -2654,12 +2654,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
         static_assert(NX % VW == 0, "row length a multiple of the vector width");
         const int groups = total / VW;
         const int items = S * groups;
+        // item it = s groups + gi, kept as (s, gi) and advanced without dividing
+        int s_b = threadIdx.x / groups, gi_b = threadIdx.x - s_b * groups;
         for (int base = threadIdx.x; base < items; base += KB * kThreads) {
             V16 a0[KB], a1[KB], av[KB], al[KB];
+            int sj[KB], gj[KB];
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
+                if (j == 0) { sj[0] = s_b; gj[0] = gi_b; }
+                else {
+                    sj[j] = sj[j - 1];
+                    gj[j] = gj[j - 1] + kThreads;
+                    while (gj[j] >= groups) { gj[j] -= groups; ++sj[j]; }
+                }
                 const int it = base + j * kThreads;
-                const int s = it / groups, gi = it - (it / groups) * groups;
+                const int s = sj[j], gi = gj[j];
                 const bool live = it < items && row0 + (gi * VW) / NX < nrows;
                 const long long o = (long long)s * g.n + row0 * NX + (long long)gi * VW;
                 a0[j] = a1[j] = av[j] = al[j] = vzero<V16>();
@@ -2670,10 +2679,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
                     if (rho_lo) al[j] = ld16(rho_lo + o);
                 }
             }
+            gi_b += KB * kThreads;
+            while (gi_b >= groups) { gi_b -= groups; ++s_b; }
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
                 const int it = base + j * kThreads;
-                const int s = it / groups, gi = it - (it / groups) * groups;
+                const int s = sj[j], gi = gj[j];
                 const int idx = gi * VW, r = idx / NX, x = idx - (idx / NX) * NX;
                 if (!(it < items && row0 + r < nrows)) continue;
                 const long long o = (long long)s * g.n + row0 * NX + idx;
