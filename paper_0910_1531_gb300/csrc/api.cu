@@ -201,6 +201,9 @@ template <typename C> void fill_twiddles(int n, std::vector<C>* out) {
 // --------------------------------------------------------------------------------------
 // profiling helpers
 // --------------------------------------------------------------------------------------
+// profiled launches whose event pairs are kept before their times are collected
+constexpr size_t kProfBatch = 4096;
+
 cudaEvent_t take_event(dft_plan* p) {
     if (p->ev_used == p->evpool.size()) {
         cudaEvent_t e;
@@ -262,7 +265,7 @@ void collect_profile(dft_plan* p) {
         if (_e == cudaSuccess) _e = cudaGetLastError();                                       \
         if (_e != cudaSuccess)                                                                \
             return fail((p), DFT_ECUDA, std::string(kKindNames[kind]) + ": " + cudaGetErrorString(_e)); \
-        if ((p)->prof && (p)->recs.size() > 4096) collect_profile(p);                         \
+        if ((p)->prof && (p)->recs.size() > kProfBatch) collect_profile(p);                   \
     } while (0)
 
 // --------------------------------------------------------------------------------------
@@ -947,7 +950,7 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cand[] = {1, 2, 3, 4, 6, 8, 11, 16};
+    const int cand[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 16};
     // a candidate whose launch is refused (shared memory) is skipped
     auto time_it = [&](auto&& launch) -> float {
         cudaGetLastError();
@@ -968,7 +971,7 @@ template <typename Real> dft_status autotune_t(dft_plan* p, const Real* rho, con
     const C* A = O::slot_n(p->slotA);
     Offsets<Real> off0;
     for (int c = 0; c < DFT_NCOMP + 2; ++c) off0.v[c] = Real(0);
-    const int cand_n3[] = {8, 16, 24, 32, 48, 64};
+    const int cand_n3[] = {8, 16, 24, 30, 32, 48, 62, 64};
     for (int L : cand_n3) {
         if (P::smem_x(p->g.nx, L) > size_t(optin)) continue;
         const float ms = time_it([&] {
@@ -2044,6 +2047,17 @@ dft_status dft_profile_enable(dft_plan* p, int enable) {
     p->prof = enable != 0;
     // per-pass event timing: each pass starts after the previous one has completed
     p->g.pdl = (p->pdl_on && !p->prof) ? 1 : 0;
+    // the events of a full record batch created now, so that queuing profiled passes does not
+    // wait on event creation (a slow host would otherwise leave gaps between the passes, which
+    // the events around the next pass would count)
+    if (p->prof) {
+        const size_t need = 2 * (kProfBatch + 1);
+        while (p->evpool.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(p, DFT_ECUDA, "cudaEventCreate");
+            p->evpool.push_back(e);
+        }
+    }
     return DFT_OK;
 }
 

@@ -2935,10 +2935,10 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
                                                           double alpha_floor) {
     dep_launch();
     dep_wait();
-    __shared__ double scratch_d[32];
+    __shared__ double scratch_d[64];
     __shared__ float scratch_f[32];
-    const double s = partial_sum<B>(red_sum, nsum);
-    const double s_2 = red_sum2 ? partial_sum<B>(red_sum2, nsum) : 0.0;
+    double s = partial_sum<B>(red_sum, nsum);
+    double s_2 = red_sum2 ? partial_sum<B>(red_sum2, nsum) : 0.0;
     float m0 = -CUDART_INF_F, m1 = -CUDART_INF_F, m2 = -CUDART_INF_F, m3 = -CUDART_INF_F;
     int i = threadIdx.x;
     for (; i + 3 * B < nmax; i += 4 * B) {
@@ -2948,10 +2948,31 @@ __global__ void __launch_bounds__(B) k_finalize(Ctl* ctl, const double* __restri
         m3 = fmaxf(m3, red_max[i + 3 * B]);
     }
     for (; i < nmax; i += B) m0 = fmaxf(m0, red_max[i]);
-    const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-    const double tot = block_sum(s, scratch_d);
-    const double tot2 = red_sum2 ? block_sum(s_2, scratch_d) : 0.0;
-    const float mx = block_max(m, scratch_f);
+    float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+    // the two sums and the maximum through one pair of barriers (the same order of operations
+    // per quantity as block_sum / block_max)
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s_2 += __shfl_xor_sync(0xffffffffu, s_2, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    {
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) { scratch_d[w] = s; scratch_d[32 + w] = s_2; scratch_f[w] = m; }
+        __syncthreads();
+        if (threadIdx.x >= 32) return;
+        const bool in = l < B / 32;
+        s = in ? scratch_d[l] : 0.0;
+        s_2 = in ? scratch_d[32 + l] : 0.0;
+        m = in ? scratch_f[l] : -CUDART_INF_F;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            s_2 += __shfl_xor_sync(0xffffffffu, s_2, o);
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        }
+    }
+    const double tot = s, tot2 = s_2;
+    const float mx = m;
     if (threadIdx.x != 0) return;
     Ctl* c = ctl;
     const double f = tot * inv_count;
