@@ -205,6 +205,24 @@ struct Ctl {
     int loop_left;          // iterations left in an on-device loop of dft_iter_run / dft_batch_iterate
     // fixed-number species: G_i = canon_scale[i] exp(-V_i + c_i), canon_scale = N_i / (h^3 sum e)
     double canon_scale[DFT_MAXS];
+    // the four weights rounded to float when they are set: the FP32 passes read these, since a
+    // double-to-float conversion in every thread queues on the narrow FP64 pipe
+    float wAf, wBf, w0f, w1f;
+};
+
+// The weights of a control block in the working precision.
+template <typename Real> struct CtlW;
+template <> struct CtlW<float> {
+    static __device__ __forceinline__ float wA(const Ctl* c) { return c->wAf; }
+    static __device__ __forceinline__ float wB(const Ctl* c) { return c->wBf; }
+    static __device__ __forceinline__ float w0(const Ctl* c) { return c->w0f; }
+    static __device__ __forceinline__ float w1(const Ctl* c) { return c->w1f; }
+};
+template <> struct CtlW<double> {
+    static __device__ __forceinline__ double wA(const Ctl* c) { return c->wA; }
+    static __device__ __forceinline__ double wB(const Ctl* c) { return c->wB; }
+    static __device__ __forceinline__ double w0(const Ctl* c) { return c->w0; }
+    static __device__ __forceinline__ double w1(const Ctl* c) { return c->w1; }
 };
 
 enum {

@@ -1025,7 +1025,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
     const long long zstride = (long long)ny * g.pxh;
     const long long col0 = (long long)kyi * g.pxh + kx0;
     const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
-    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+    const Real wA = CtlW<Real>::wA(ctl), wB = CtlW<Real>::wB(ctl);
     C* R = A;
     if (hs) {
         tiles_load_grouped<TZ, NZ, DFT_NSPEC>(A, phi + col0, g.nc, DFT_NSPEC, zstride, nxh - kx0);
@@ -1514,7 +1514,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_bwd_tma(const __grid_constan
         const int m = pair ? (it & 1) : 0;
         const int ti = it >> shift;                 // this CTA's tile count so far
         const bool last_of_tile = !pair || m == 1;
-        const Real wA = Real(ctl[m].wA), wB = Real(ctl[m].wB);
+        const Real wA = CtlW<Real>::wA(ctl + m), wB = CtlW<Real>::wB(ctl + m);
         const int cur = it & 1;
         const int kx0 = (tile % ntiles_x) * TZ, kyi = tile / ntiles_x;
         const int my = signed_index(kyi, ny);
@@ -2073,8 +2073,8 @@ __global__ void __launch_bounds__(kThreads) k_xphi(GridDesc g, AxisPlan px, int 
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
-        wA[m] = Real(cw->wA);
-        wB[m] = Real(cw->wB);
+        wA[m] = CtlW<Real>::wA(cw);
+        wB[m] = CtlW<Real>::wB(cw);
     }
     load_wd_rows<Real, NX, NM>(g, LR, row0, nrows, slotA, slotB, wA, wB, mat_out, kfx, A);
     __syncthreads();
@@ -2203,8 +2203,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 1) k_xphi_tm
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
-        wA[m] = Real(cw->wA);
-        wB[m] = Real(cw->wB);
+        wA[m] = CtlW<Real>::wA(cw);
+        wB[m] = CtlW<Real>::wB(cw);
     }
     auto issue = [&](int blk, int s) {
         const long long r0 = (long long)blk * LR;
@@ -2309,8 +2309,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 1) k_xphi_cp
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
-        wA[m] = Real(cw->wA);
-        wB[m] = Real(cw->wB);
+        wA[m] = CtlW<Real>::wA(cw);
+        wB[m] = CtlW<Real>::wB(cw);
     }
     // the nsrc components of row block blk, in 16-byte chunks spread over the threads
     auto issue = [&](int blk) {
@@ -2379,7 +2379,7 @@ __global__ void __launch_bounds__(kThreads) k_zconv_bwd(GridDesc g, AxisPlan pz,
     const long long zstride = (long long)ny * g.pxh;
     const long long col0 = (long long)kyi * g.pxh + kx0;
     const bool hs = (flags & 1) != 0, es_on = (flags & 2) != 0;
-    const Real wA = Real(ctl->wA), wB = Real(ctl->wB);
+    const Real wA = CtlW<Real>::wA(ctl), wB = CtlW<Real>::wB(ctl);
 
     if (hs) {
         // nine Phi' spectra (DFT_NSPEC order): 0..3 transform into accumulators 0..3, B4 into
@@ -2608,8 +2608,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_xupdate
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const Ctl* cw = NM == 1 ? ctl : ctl + 1 + m;
-        w0[m] = Real(cw->w0);
-        w1[m] = Real(cw->w1);
+        w0[m] = CtlW<Real>::w0(cw);
+        w1[m] = CtlW<Real>::w1(cw);
     }
     // per-thread partial sums in the working precision with Kahan compensation, then
     // double-single (FP32) or FP64 across threads, FP64 across blocks
@@ -2907,6 +2907,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(GridDesc g, AxisPlan px, int 
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ void set_weights(Ctl* c, double a) {
     c->wA = 1.0 - a; c->wB = a; c->w0 = 1.0 - a; c->w1 = a;
+    c->wAf = float(c->wA); c->wBf = float(c->wB); c->w0f = float(c->w0); c->w1f = float(c->w1);
 }
 
 // ctl points at three control blocks: the iteration's, then the weights of the two line-search
