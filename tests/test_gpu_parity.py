@@ -86,6 +86,10 @@ CASES = [
     ((256, 6, 8), (0.1, 0.1, 0.03), 5),   # z 256 with five species (the largest ES tile set)
     ((64, 32, 48), 0.08, 2),       # compile-time z 64, y 32 (TMA), x 48
     ((12, 8, 256), 0.05, 2),       # compile-time x 256
+    # odd y axes under the persistent z passes (no Nyquist row: every tile's y derivatives are
+    # formed or folded with its own k_y)
+    ((64, 15, 32), (0.1, 0.09, 0.1), 2),   # compile-time z 64, y 15 = 3 * 5, x 32
+    ((128, 9, 16), 0.07, 3),               # compile-time z 128, y 9 = 3 * 3, x 16
 ]
 
 
