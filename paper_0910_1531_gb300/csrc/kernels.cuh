@@ -1111,12 +1111,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_zconv_bwd_g(GridDesc g, Species
 // ------------------------------------------------------------------------------------
 // First-half z pass with TMA tiles (same contract as k_zconv_fwd without the grand-potential
 // sums), persistent like k_zconv_bwd_tma: two stages of S species tiles are filled by TMA loads
-// while the previous tile is transformed; the ten weighted densities leave through TMA stores,
-// the bulk-fluid/Poisson spectra through plain stores.  A tensor map views a half-spectrum
+// while the previous tile is transformed; seven weighted-density spectra are transformed back
+// (zgroup order), the two y derivatives formed from m and n3 after that, and the nine leave
+// through TMA stores, the bulk-fluid/Poisson spectra through plain stores.  A tensor map views a half-spectrum
 // array as (x: nxh * E, y: ny, plane: nz * ncomp) 8-byte elements; a tile is the box
 // (TZ * E, 1, NZ) at plane c * nz.  A wait that runs out sets DEV_TIMEOUT and the CTA stops
 // after draining the loads it has in flight.
-// Shared memory: stage 0 | stage 1 (S padded groups each) | W | V (ten padded groups each) |
+// Shared memory: stage 0 | stage 1 (S padded groups each) | W | V (nine padded groups each) |
 // twiddles | two mbarriers.
 // ------------------------------------------------------------------------------------
 template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zfwd_tma_smem(int S) {
@@ -1394,8 +1395,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2) k_zmul(Gr
 // ------------------------------------------------------------------------------------
 // Second-half z pass with TMA tiles (same contract as k_zconv_bwd), persistent: CTA b handles
 // tiles b, b + gridDim.x, ...  Two shared-memory stages, each holding one tile's nine Phi'
-// spectra, are filled by TMA loads (one cp.async.bulk.tensor per component, completing on the
-// stage's mbarrier) while the previous tile is transformed; the tile's bulk-fluid/Poisson
+// spectra (in zgroup order), are filled by TMA loads (one cp.async.bulk.tensor per component,
+// completing on the stage's mbarrier) while the previous tile is transformed (seven groups: the
+// y-derivative spectra folded into groups 3 and 4 by the first stage); the tile's bulk-fluid/Poisson
 // spectra arrive in one single-buffered area (third mbarrier), loaded while the previous tile's
 // inverse and this tile's forward transform run.  The ncomp_out results are written over the
 // first groups of the transformed tile and leave through TMA stores.  At length 256 both
