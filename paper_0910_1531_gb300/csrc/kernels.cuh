@@ -1126,7 +1126,7 @@ template <typename Real, int NZ, int TZ> __host__ __device__ constexpr size_t zf
     return ((2 * size_t(S) + 2 * DFT_NSPEC) * GS + NZ) * sizeof(C) + 2 * sizeof(uint64_t) + 128;
 }
 
-template <typename Real, int NZ, int TZ, int NT, int MINB>
+template <typename Real, int NZ, int TZ, int NT, int MINB, int SM = DFT_MAXS>
 __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constant__ CUtensorMap map_in,
                                                                          const __grid_constant__ CUtensorMap map_n,
                                                                          GridDesc g, SpeciesDesc<Real> sp, Real kfx,
@@ -1190,8 +1190,8 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
         const int my = signed_index(kyi, ny);
         // table records of this thread's points, in flight while the tile arrives
         // (the first point's; a thread's later points load theirs at the top of their iteration)
-        Real wr[DFT_TAB_W];
-        Real kr[DFT_TAB_K];
+        Real wr[SM <= 3 ? 8 : DFT_TAB_W];
+        Real kr[SM <= 3 ? 8 : DFT_TAB_K];
         auto load_tab = [&](int idx) {
             const int kxi = kx0 + idx % TZ;
             const int m2 = (((TILE % NT == 0) || idx < TILE) && kxi < nxh) ? kmode2(kxi, my, idx / TZ, g.nz) : 0;
@@ -1225,15 +1225,15 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
             const int kxi = kx0 + t;
             const bool live = kxi < nxh;
             const KPoint<Real> p = kpoint<Real>(g, kxi, kyi, kzi, kfx, kfy, kfz);
-            C v[DFT_MAXS];
+            C v[SM];
 #pragma unroll
-            for (int s = 0; s < DFT_MAXS; ++s)
+            for (int s = 0; s < SM; ++s)
                 if (s < S) v[s] = X[s * GS + pos];
             C acc[5];
 #pragma unroll
             for (int a = 0; a < 5; ++a) acc[a] = cmake<C>(Real(0), Real(0));
 #pragma unroll
-            for (int s = 0; s < DFT_MAXS; ++s) {
+            for (int s = 0; s < SM; ++s) {
                 if (s >= S) break;
                 Real w0, j3;
                 if (tab) { w0 = wr[2 * s]; j3 = wr[2 * s + 1]; }
@@ -1247,9 +1247,9 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
             }
             if (live) {
                 const Real inv_lap = inverse_laplacian<Real>(sp, g, p, kxi, kyi, kzi, hx, hy, hz);
-                C dv[DFT_MAXS], es[DFT_MAXS];
+                C dv[SM], es[SM];
 #pragma unroll
-                for (int s = 0; s < DFT_MAXS; ++s) {
+                for (int s = 0; s < SM; ++s) {
                     if (s < S) {
                         dv[s] = v[s];
                         if (p.zero) dv[s].x -= sp.n_rho_b[s];       // DFT(rho - rho_bath) at k = 0
@@ -1257,7 +1257,7 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                     es[s] = cmake<C>(Real(0), Real(0));
                 }
 #pragma unroll
-                for (int j = 0; j < DFT_MAXS; ++j) {
+                for (int j = 0; j < SM; ++j) {
 #pragma unroll
                     for (int i2 = 0; i2 <= j; ++i2) {
                         if (j >= S) continue;
@@ -1274,12 +1274,12 @@ __global__ void __launch_bounds__(NT, MINB) k_zconv_fwd_tma(const __grid_constan
                 }
                 const long long o = (long long)kzi * zstride + (long long)kyi * g.pxh + kxi;
 #pragma unroll
-                for (int s = 0; s < DFT_MAXS; ++s)
+                for (int s = 0; s < SM; ++s)
                     if (s < S) slot_es[(long long)s * g.nc + o] = es[s];
                 if (want_psi) {
                     C q = cmake<C>(Real(0), Real(0));
 #pragma unroll
-                    for (int s = 0; s < DFT_MAXS; ++s)
+                    for (int s = 0; s < SM; ++s)
                         if (s < S) q = cadd(q, cscale(v[s], sp.z[s]));
                     slot_es[(long long)S * g.nc + o] = cscale(q, flb * inv_lap);
                 }

@@ -260,8 +260,11 @@ cudaError_t LaunchZ<Real, N>::init() {
         constexpr int NF = dft_zfwd_threads<Real>(N), MBF = dft_zfwd_minb<Real>(N);
         if constexpr ((TB * sizeof(typename Cplx<Real>::type)) % 16 == 0)
             if ((r = set_max_smem(dftk::k_zconv_bwd_tma<Real, N, TB, NB, MBB>)) != cudaSuccess) e = r;
-        if constexpr ((TF * sizeof(typename Cplx<Real>::type)) % 16 == 0)
-            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, NF, MBF>)) != cudaSuccess) e = r;
+        if constexpr ((TF * sizeof(typename Cplx<Real>::type)) % 16 == 0) {
+            constexpr int MBF3 = dft_zfwd_minb_s3<Real>(N);
+            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, NF, MBF, DFT_MAXS>)) != cudaSuccess) e = r;
+            if ((r = set_max_smem(dftk::k_zconv_fwd_tma<Real, N, TF, NF, MBF3, 3>)) != cudaSuccess) e = r;
+        }
         constexpr int TY = dft_tile_y<Real>(N);
         if ((r = set_max_smem(dftk::k_yfft_tma<Real, false, N, TY, true>)) != cudaSuccess) e = r;
         if ((r = set_max_smem(dftk::k_yfft_tma<Real, true, N, TY, true>)) != cudaSuccess) e = r;
@@ -342,12 +345,16 @@ cudaError_t LaunchZ<Real, N>::zconv_fwd(cudaStream_t st, const GridDesc& g, cons
             if (e != cudaSuccess) return e;
             const int ntx = (int)ceil_div(g.nxh, TB);
             const int ntiles = ntx * g.ny;
+            // at most three species: the instance whose records and species loops are sized for three
+            constexpr int MB3 = dft_zfwd_minb_s3<Real>(N);
+            auto kern = sp.S <= 3 ? dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB3, 3>
+                                  : dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB, DFT_MAXS>;
             int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB>, NT, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, sm);
             if (occ < 1) occ = 1;
             const int grid = (int)(ntiles < (long long)sms * occ ? ntiles : sms * occ);
-            launch_k(dftk::k_zconv_fwd_tma<Real, N, TB, NT, MB>, grid, NT, sm, st, g.pdl, map_in, map_n, g, sp, kfx, kfy, kfz, want_psi,
-                                                                         slot_es, ntx, ntiles, status, tw);
+            launch_k(kern, grid, NT, sm, st, g.pdl, map_in, map_n, g, sp, kfx, kfy, kfz, want_psi, slot_es, ntx, ntiles,
+                     status, tw);
             return cudaSuccess;
         }
     }

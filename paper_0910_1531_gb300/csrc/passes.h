@@ -73,6 +73,15 @@ template <typename Real> __host__ __device__ constexpr int dft_zfwd_minb(int n) 
     return dft_zfwd_threads<Real>(n) <= 256 ? 2 : 1;
 #endif
 }
+// The first-half pass for at most three species (its table records and species loops sized for
+// three): resident CTAs per SM its register budget is sized for (DFT_ZFWD_MINB_S3 overrides).
+template <typename Real> __host__ __device__ constexpr int dft_zfwd_minb_s3(int n) {
+#ifdef DFT_ZFWD_MINB_S3
+    return DFT_ZFWD_MINB_S3;
+#else
+    return dft_zfwd_minb<Real>(n);
+#endif
+}
 template <typename Real> __host__ __device__ constexpr int dft_zbwd_threads(int n) {
 #ifdef DFT_ZBWD_THREADS
     return DFT_ZBWD_THREADS;
